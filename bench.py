@@ -1,0 +1,323 @@
+"""Benchmark: amplitude updates/s of the fused state-vector path on GB300.
+
+Workload (default): QFT on n=28 qubits with the textbook H + controlled-phase
+ladder and final swaps (420 gates) applied to a seeded random basis state,
+complex64, then 100 shots and <Z_i> for all qubits.  One step = state init,
+plan + fused apply, probability block sums, block CDF scan, sampling and
+<Z>: every stage of the hot path.  The state (2 GiB) is larger than L2
+(129 MB), so no flush is needed between steps.
+
+value      = whole-job amplitude updates/s (420 * 2^28 per step per GPU),
+             device-timed with CUDA events on the library's stream.
+e2e        = the same metric through the C ABI with host buffers: gate list
+             from host memory in, samples and <Z> copied back every step.
+roofline   = the tile-pass kernel: algorithmic bytes per launch (one read and
+             one write of the state, 16 B per amplitude) / mean launch time
+             from CUDA events recorded by the library around each pass.
+plain      = the same step with one kernel per gate (no fusion).
+cpu_baseline = the FP64 oracle on the host cores over a bounded prefix of
+             the same gate list (rank 0, N=1 only).
+
+--impl reference runs the oracle as the reference arm (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "amplitude updates/s and % HBM roofline, learned-fused vs plain, F≥1-1e-6"
+UNIT = "amp_updates/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name):
+    if name == "qft28":
+        n = 28
+        g = W.qft(n)
+        x = W.random_basis_index(n, W.SEED[2])
+        return n, g, x, "QFT n=28 (420 gates) on a seeded random basis state"
+    if name.startswith("qft"):
+        n = int(name[3:])
+        return n, W.qft(n), W.random_basis_index(n, W.SEED[2]), "QFT n=%d" % n
+    if name.startswith("random"):
+        n = int(name[6:])
+        g = W.random_u3_cx(n, 60, W.SEED[4])
+        return n, g, 0, "random U3+CX n=%d, 60 layers (%d gates) from |0>" % (n, len(g))
+    raise SystemExit("unknown workload " + name)
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(n, gates, x, budget_s=12.0):
+    """FP64 oracle on all host cores over a bounded prefix of the gate list."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    psi = oracle.basis_state(n, x)
+    t0 = time.perf_counter()
+    psi = oracle.apply_circuit(n, gates[:1], psi)
+    t1 = time.perf_counter() - t0
+    G = int(max(1, min(len(gates) - 1, budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.apply_circuit(n, gates[1:1 + G], psi)
+    dt = time.perf_counter() - t0
+    return {"value": G * float(1 << n) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "gates 2..%d of the %d-gate list at n=%d, FP64 complex128, %.1f s" % (G + 1, len(gates), n, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    n, g, x, desc = workload(args.workload)
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    psi = oracle.basis_state(n, x)
+    per = max(1, args.ref_gates)
+    for s in range(args.warmup):
+        oracle.apply_circuit(n, g[:per], psi)
+    times = []
+    for s in range(args.steps):
+        lo = (s * per) % len(g)
+        t0 = time.perf_counter()
+        psi = oracle.apply_circuit(n, g[lo:lo + per], psi)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    val = per * float(1 << n) / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "gates_per_step": per, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d gates of the list per step at n=%d, FP64" % (per, n)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qft28")
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--planner", default="greedy", choices=["greedy", "mlp", "plain"])
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--tile-m", type=int, default=0)
+    ap.add_argument("--shots", type=int, default=100)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-gates", type=int, default=4)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2504_03967_gb300 as S
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    S.lib()
+
+    n, g, x, desc = workload(args.workload)
+    dt = S.C64 if args.dtype == "c64" else S.C128
+    amp_b = 8 if dt == S.C64 else 16
+    planner = {"greedy": S.PLAN_GREEDY, "mlp": S.PLAN_MLP, "plain": S.PLAN_PLAIN}[args.planner]
+    stream = torch.cuda.current_stream()
+    state = torch.empty((amp_b // 4) << n, dtype=torch.float32, device="cuda")
+    shots_out = torch.empty(max(1, args.shots), dtype=torch.int64, device="cuda")
+    ez_out = torch.empty(n, dtype=torch.float64, device="cuda")
+    h = S.sv_attach(n, dt, state.data_ptr(), stream.cuda_stream)
+    updates = float(len(g)) * float(1 << n)
+
+    def step(i, pl, record):
+        S.sv_init_basis(h, x)
+        S.sv_apply_circuit(h, g, planner=pl, k_max=args.k, tile_m=args.tile_m, record=record)
+        S.sv_sample_device(h, args.shots, 1000 + i, shots_out.data_ptr())
+        S.sv_expect_z_device(h, ez_out.data_ptr())
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def timed(pl, steps, warmup, record):
+        for i in range(warmup):
+            step(i, pl, 0)
+        torch.cuda.synchronize()
+        if record:
+            S.sv_pass_times(h)  # clear
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = S.sv_launch_count()
+        e0.record(stream)
+        for i in range(steps):
+            step(i, pl, record)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = S.sv_launch_count() - l0
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    with Clocks(local) as clk:
+        ms, launches = timed(planner, args.steps, args.warmup, 1)
+    pass_ms = S.sv_pass_times(h)
+    plan = S.sv_plan_circuit(n, dt, g, k_max=args.k, tile_m=args.tile_m,
+                             planner=S.PLAN_PLAIN if planner == S.PLAN_PLAIN else S.PLAN_GREEDY)
+    value = world * updates / (ms / 1e3)
+    hbm, src = peaks()
+    # dominant kernel: the tile pass (one read + one write of 2^n amplitudes)
+    roof = None
+    if len(pass_ms):
+        per_launch_bytes = 2.0 * amp_b * float(1 << n)
+        achieved = per_launch_bytes / (float(np.mean(pass_ms)) / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_pass (tile pass)", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": src,
+                "frac_of_8tbs_nominal": achieved / 8000.0, "traffic": None,
+                "launches_timed": int(len(pass_ms)), "mean_launch_ms": float(np.mean(pass_ms)),
+                "step_frac": float(np.sum(pass_ms)) / args.steps / ms}
+
+    plain = None
+    if not args.no_plain and planner != S.PLAN_PLAIN:
+        pms, _ = timed(S.PLAN_PLAIN, max(2, args.steps // 3), 1, 0)
+        plain = {"value": world * updates / (pms / 1e3), "ms_per_step": pms,
+                 "fused_over_plain": pms / ms}
+
+    e2e = None
+    if not args.no_e2e:
+        h2 = S.sv_alloc(n, dt)
+        gh = np.ascontiguousarray(g)
+        for i in range(2):
+            S.sv_init_basis(h2, x)
+            S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m)
+            S.sv_sample(h2, args.shots, i)
+            S.sv_expect_z(h2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        K = max(3, args.steps // 2)
+        for i in range(K):
+            S.sv_init_basis(h2, x)
+            S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m)
+            S.sv_sample(h2, args.shots, 1000 + i)
+            S.sv_expect_z(h2)
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / K
+        S.sv_free(h2)
+        e2e = {"value": world * updates / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(gh.nbytes + 8), "d2h_bytes_per_step": int(8 * args.shots + 8 * n)}
+
+    # fidelity check on sampled amplitudes (QFT of a basis state has a closed form)
+    fid = None
+    if args.workload.startswith("qft"):
+        st = state.view(torch.complex64 if dt == S.C64 else torch.complex128)
+        S.sv_init_basis(h, x)
+        S.sv_apply_circuit(h, g, planner=planner, k_max=args.k, tile_m=args.tile_m)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(0)
+        ys = rng.integers(0, 1 << n, size=1 << 16)
+        got = st[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+        N = 1 << n
+        ref = np.exp(2j * np.pi * ((x * ys) % N) / N) / np.sqrt(N)
+        fid = {"sampled_amplitudes": int(len(ys)), "max_abs_err": float(np.abs(got - ref).max()),
+               "max_rel_err": float(np.abs(got - ref).max() * np.sqrt(N))}
+    S.sv_free(h)
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, g, x)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": desc, "n": n, "gates": len(g), "shots": args.shots, "planner": args.planner,
+                       "passes": plan["passes"], "k_max": args.k or 5, "tile_m": args.tile_m or None,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (state %d MiB)" % ((amp_b << n) >> 20)},
+            "roofline": roof, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "check": fid}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * libsv: GB300-native (sm_103a) state-vector simulator, C ABI.
+ *
+ * The computation is the one the paper (Q-GEAR, arXiv 2504.03967) accelerates
+ * by turning a circuit's gate list into GPU kernels: apply a gate list to a
+ * 2^n-amplitude complex state (App. A, Eq. "hilbert": |psi> = sum_i a_i |i>,
+ * sum |a_i|^2 = 1) and then read probabilities, <Z_i> or measurement shots
+ * (Sec. 3, shots per circuit).  One process drives one GPU; every call is
+ * asynchronous on the handle's CUDA stream unless it writes host memory, in
+ * which case it returns after the result has been copied.
+ *
+ * Conventions
+ *   - Qubit q is bit q of the amplitude index (LSB = qubit 0).  An outcome x
+ *     returned by the samplers is that index, so bit q of x is qubit q.
+ *   - Amplitudes are interleaved (re, im): SV_C64 = 2 x float (8 bytes),
+ *     SV_C128 = 2 x double (16 bytes), 2^n of them, index order.
+ *   - Every call returns SV_OK (0) or a negative sv_status.  sv_last_error()
+ *     gives a message for the calling thread's last failure.  Validation
+ *     failures (SV_EINVAL, SV_EUNSUPPORTED, SV_ENOMEM before any launch) leave
+ *     the state unchanged.  After SV_ECUDA or SV_ETIMEOUT the state content is
+ *     undefined and the handle is flagged: later calls other than sv_free and
+ *     sv_init_* return SV_ESTATE until the state is re-initialised.
+ *   - Pointers named dev_* are device pointers, host_* are host pointers.
+ *     Nothing returned is owned by the caller unless stated; the caller owns
+ *     every buffer it passes in and must keep it alive for the call.
+ */
+#ifndef SV_H_
+#define SV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_state *sv_handle;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+typedef enum {
+    SV_OK = 0,
+    SV_EINVAL = -1,       /* bad argument: n out of range, qubit >= n,
+                             duplicate qubits, unknown gate type, wrong arity,
+                             NULL pointer */
+    SV_ENOMEM = -2,       /* device or pinned allocation failed */
+    SV_EUNSUPPORTED = -3, /* valid request this build does not provide */
+    SV_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+    SV_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
+    SV_ESTATE = -6        /* handle flagged by an earlier SV_ECUDA/SV_ETIMEOUT */
+} sv_status;
+
+/* Gate alphabet.  The paper's one-hot gate set h, ry, rz, cx, measure
+ * (App. D.1, Eq. "onehot"), cr1 = SV_CP (App. D.2, Eq. "cr1"), and the
+ * single-qubit rotations Rx (App. A) and U3 used by the random circuits.
+ * Matrices (c = cos(t/2), s = sin(t/2)):
+ *   H = [[1,1],[1,-1]]/sqrt2, X, Y = [[0,-i],[i,0]], Z = diag(1,-1),
+ *   RX(t) = [[c,-is],[-is,c]], RY(t) = [[c,-s],[s,c]],
+ *   RZ(f) = diag(e^{-if/2}, e^{if/2}), P(l) = diag(1, e^{il}),
+ *   U3(t,f,l) = [[c, -e^{il}s], [e^{if}s, e^{i(f+l)}c]],
+ *   CX(control q[0], target q[1]) flips the target where the control is 1
+ *   (App. A, Eq. "cx" and its 3-qubit example), CZ = diag(1,1,1,-1),
+ *   CP(l) = CR1(l) = diag(1,1,1,e^{il}), SWAP exchanges the two qubits.
+ * SV_MEASURE is terminal: accepted, validated and ignored by the apply calls
+ * (sampling always measures every qubit). */
+typedef enum {
+    SV_H = 0, SV_X = 1, SV_Y = 2, SV_Z = 3, SV_RX = 4, SV_RY = 5, SV_RZ = 6,
+    SV_P = 7, SV_U3 = 8, SV_CX = 9, SV_CZ = 10, SV_CP = 11, SV_SWAP = 12,
+    SV_MEASURE = 13
+} sv_gate_type;
+
+/* One gate: the (type, control, target, params) record of the paper's circuit
+ * tensor (Sec. 2.1 "Circuit encoding"; App. D.1 gate_type / gate_param).
+ * nq must equal the type's arity (1 or 2); q[0] is the control of CX/CP.
+ * Unused q[] and p[] entries are ignored.  48 bytes. */
+typedef struct {
+    uint32_t type;
+    uint32_t nq;
+    uint32_t q[3];
+    double p[3];
+} sv_gate;
+
+/* Planner choice for sv_apply_circuit. */
+typedef enum {
+    SV_PLAN_GREEDY = 0, /* greedy tile passes with fixed fusion width k_max */
+    SV_PLAN_MLP = 1,    /* cost-model-guided plan; greedy when no model */
+    SV_PLAN_PLAIN = 2   /* one kernel per gate over the whole state */
+} sv_planner;
+
+/* Options for sv_apply_circuit; pass NULL for defaults.  A zero field means
+ * "default".  k_max: widest fused dense block, 1..5 (App. D.2: gate fusion =
+ * 5); tile_m: qubits per shared-memory tile pass (c64 10..14, c128 9..13);
+ * planner: sv_planner; record: store per-pass CUDA-event times for the cost
+ * model (sv_record_*). */
+typedef struct {
+    int k_max;
+    int tile_m;
+    int planner;
+    int record;
+    int reserved[4];
+} sv_options;
+
+/* Plan summary returned by sv_plan_circuit (host only, no device work). */
+typedef struct {
+    int64_t gates;        /* gate records given (MEASURE included) */
+    int64_t passes;       /* HBM passes the plan makes over the state */
+    int64_t dense_ops;    /* fused dense blocks over all passes */
+    int64_t diag_ops;     /* diagonal-phase runs over all passes */
+    int64_t max_k;        /* widest dense block */
+    int64_t bytes_moved;  /* algorithmic HBM bytes: sum over passes of the
+                             amplitudes each pass reads and writes */
+} sv_plan_info;
+
+/* ---- state lifetime (App. A, Eq. "hilbert") ---------------------------- */
+
+/* Allocate a library-owned 2^n state of dtype dt on the current device.
+ * n: 1..34 (c64) or 1..33 (c128).  cuda_stream: a cudaStream_t to run on
+ * (NULL = the legacy default stream).  The state content is undefined until
+ * an sv_init_* or sv_load_state call.  SV_ENOMEM if the device cannot hold
+ * it (checked before any allocation touches the device). */
+int sv_alloc(int n, sv_dtype dt, void *cuda_stream, sv_handle *out);
+
+/* Wrap caller-owned device memory (e.g. a torch tensor) of 2^n amplitudes of
+ * dtype dt, 16-byte aligned.  The library never frees dev_amps; the caller
+ * keeps it alive until sv_free. */
+int sv_attach(int n, sv_dtype dt, void *dev_amps, void *cuda_stream, sv_handle *out);
+
+/* Release the handle and any memory the library allocated for it. */
+int sv_free(sv_handle h);
+
+/* Change the stream later calls on h run on. */
+int sv_set_stream(sv_handle h, void *cuda_stream);
+
+/* Number of qubits / dtype / device pointer of the state (for interop). */
+int sv_info(sv_handle h, int *n, int *dtype, void **dev_amps);
+
+/* |x>: all amplitudes 0 except a_x = 1.  SV_EINVAL if x >= 2^n. */
+int sv_init_basis(sv_handle h, uint64_t x);
+
+/* Copy 2^n amplitudes (interleaved, the handle's dtype) from host memory to
+ * the state / from the state to host memory. */
+int sv_load_state(sv_handle h, const void *host_amps);
+int sv_store_state(sv_handle h, void *host_amps);
+
+/* ---- gate application (App. A Eqs. "tp", "cx"; App. D.2 Eq. "cr1") ---- */
+
+/* Apply count gate records in list order to the state.  The result equals
+ * applying each gate's matrix to every group of amplitudes that differ only
+ * in the gate's qubit bits, one gate after the other; the planner may fuse
+ * consecutive gates into dense blocks of <= k_max qubits (App. D.2, "gate
+ * fusion = 5") and diagonal-phase runs, which is exact up to rounding.  All
+ * records are validated before any device work. */
+int sv_apply_circuit(sv_handle h, const sv_gate *gates, size_t count, const sv_options *opt);
+
+/* Plan without running: fills *info for a circuit on n qubits of dtype dt.
+ * Host only; usable without a GPU. */
+int sv_plan_circuit(int n, sv_dtype dt, const sv_gate *gates, size_t count,
+                    const sv_options *opt, sv_plan_info *info);
+
+/* ---- read-out (Sec. 3 shots; App. A Eq. "hilbert") --------------------- */
+
+/* p_x = |a_x|^2 in FP64 for all 2^n x, to host or device memory. */
+int sv_probs(sv_handle h, double *host_out);
+int sv_probs_device(sv_handle h, double *dev_out);
+
+/* sum_x |a_x|^2 in FP64. */
+int sv_norm(sv_handle h, double *host_out);
+
+/* <Z_i> = sum_x p_x (1 - 2 x_i) for i = 0..n-1, FP64, to host or device. */
+int sv_expect_z(sv_handle h, double *host_out);
+int sv_expect_z_device(sv_handle h, double *dev_out);
+
+/* Draw shots outcomes x with probability p_x / sum p: outcome = min{x :
+ * C_x > u * C_{N-1}} with C the inclusive FP64 CDF.  sv_sample draws u from
+ * Philox4x64-10 (Salmon et al. SC'11): shot s uses word s mod 4 of block
+ * Philox(counter = (s div 4, 0, 0, 0), key = (seed, 0)), u = (w >> 11) 2^-53.
+ * sv_sample_uniforms takes the uniforms u[0..shots) from the caller (host).
+ * Outcomes are uint64 indices, to host or device memory. */
+int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_out);
+int sv_sample_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_out);
+int sv_sample_uniforms(sv_handle h, const double *host_u, uint64_t shots, uint64_t *host_out);
+
+/* ---- recorder (per-pass timings; the cost model's training data) ------- */
+
+/* Timings of the tile passes run by sv_apply_circuit calls made with
+ * opt->record = 1 since the last sv_pass_times call on h.  Waits for the
+ * stream, then writes min(count, cap) CUDA-event durations in milliseconds
+ * (host_ms, may be NULL) and their feature vectors (host_feat, cap x
+ * sv_feature_count() floats, may be NULL) in launch order, sets *count to
+ * the number recorded and clears the record. */
+int sv_pass_times(sv_handle h, double *host_ms, float *host_feat, int cap, int *count);
+
+/* Length of one pass feature vector. */
+int sv_feature_count(void);
+
+/* ---- misc -------------------------------------------------------------- */
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char *sv_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int sv_version(void);
+
+/* Number of kernel launches this library made on the calling process since
+ * load (all handles).  For launch accounting in benchmarks. */
+uint64_t sv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_H_ */

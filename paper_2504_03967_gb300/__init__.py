@@ -1,0 +1,259 @@
+"""GB300-native (sm_103a) state-vector simulator: Python binding of libsv.
+
+Argument marshalling only: every step runs in the CUDA library ``libsv.so``
+(built in-tree by ``paper_2504_03967_gb300.build``).  There is no CPU fallback:
+importing a function whose library is missing raises.  PyTorch is used by
+callers for device memory and streams; pass ``tensor.data_ptr()`` and
+``torch.cuda.current_stream().cuda_stream`` where a device pointer or stream is
+expected.
+
+The functions carry the names of the C ABI (include/sv.h); each returns the
+C status converted to an exception (``SVError``) on failure.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsv.so")
+
+C64, C128 = 0, 1
+PLAN_GREEDY, PLAN_MLP, PLAN_PLAIN = 0, 1, 2
+
+STATUS = {0: "SV_OK", -1: "SV_EINVAL", -2: "SV_ENOMEM", -3: "SV_EUNSUPPORTED", -4: "SV_ECUDA",
+          -5: "SV_ETIMEOUT", -6: "SV_ESTATE"}
+
+GATE_DTYPE = np.dtype([("type", "<u4"), ("nq", "<u4"), ("q", "<u4", (3,)),
+                       ("pad", "<u4"), ("p", "<f8", (3,))])
+
+
+class SVError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class sv_options(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
+                ("record", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class sv_plan_info(ctypes.Structure):
+    _fields_ = [("gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_ops", ctypes.c_int64),
+                ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsv.so not built: run paper_2504_03967_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, u64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+        P = ctypes.POINTER
+        sig = {
+            "sv_alloc": [i, i, vp, P(vp)],
+            "sv_attach": [i, i, vp, vp, P(vp)],
+            "sv_free": [vp],
+            "sv_set_stream": [vp, vp],
+            "sv_info": [vp, P(i), P(i), P(vp)],
+            "sv_init_basis": [vp, u64],
+            "sv_load_state": [vp, vp],
+            "sv_store_state": [vp, vp],
+            "sv_apply_circuit": [vp, vp, sz, P(sv_options)],
+            "sv_plan_circuit": [i, i, vp, sz, P(sv_options), P(sv_plan_info)],
+            "sv_probs": [vp, vp],
+            "sv_probs_device": [vp, vp],
+            "sv_norm": [vp, P(ctypes.c_double)],
+            "sv_expect_z": [vp, vp],
+            "sv_expect_z_device": [vp, vp],
+            "sv_sample": [vp, u64, u64, vp],
+            "sv_sample_device": [vp, u64, u64, vp],
+            "sv_sample_uniforms": [vp, vp, u64, vp],
+            "sv_pass_times": [vp, vp, vp, i, P(i)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.sv_last_error.restype = ctypes.c_char_p
+        L.sv_version.restype = ctypes.c_int
+        L.sv_launch_count.restype = ctypes.c_uint64
+        L.sv_feature_count.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names declared in include/sv.h that the loaded library exports."""
+    L = lib()
+    return [n for n in declared_symbols() if hasattr(L, n)]
+
+
+def declared_symbols():
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "sv.h")
+    with open(hdr) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*|uint64_t)\s*\*?\s*(sv_\w+)\s*\(", txt, re.M)))
+
+
+def _check(rc):
+    if rc != 0:
+        raise SVError(rc, lib().sv_last_error().decode())
+    return rc
+
+
+def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0):
+    o = sv_options()
+    o.k_max, o.tile_m, o.planner, o.record = k_max, tile_m, planner, record
+    return o
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def as_gates(g):
+    g = np.ascontiguousarray(g)
+    if g.dtype.itemsize != GATE_DTYPE.itemsize:
+        raise ValueError("gate records must be 48-byte sv_gate structs")
+    return g
+
+
+# ---- C ABI names ----------------------------------------------------------
+def sv_version():
+    return lib().sv_version()
+
+
+def sv_launch_count():
+    return lib().sv_launch_count()
+
+
+def sv_last_error():
+    return lib().sv_last_error().decode()
+
+
+def sv_alloc(n, dtype=C64, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().sv_alloc(n, dtype, stream, ctypes.byref(h)))
+    return h
+
+
+def sv_attach(n, dtype, dev_ptr, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().sv_attach(n, dtype, ctypes.c_void_p(dev_ptr), stream, ctypes.byref(h)))
+    return h
+
+
+def sv_free(h):
+    _check(lib().sv_free(h))
+
+
+def sv_set_stream(h, stream):
+    _check(lib().sv_set_stream(h, stream))
+
+
+def sv_info(h):
+    n, dt, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
+    _check(lib().sv_info(h, ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p)))
+    return n.value, dt.value, p.value
+
+
+def sv_init_basis(h, x=0):
+    _check(lib().sv_init_basis(h, int(x)))
+
+
+def sv_load_state(h, amps):
+    n, dt, _ = sv_info(h)
+    a = np.ascontiguousarray(amps, dtype=np.complex64 if dt == C64 else np.complex128)
+    assert a.shape == (1 << n,)
+    _check(lib().sv_load_state(h, _ptr(a)))
+
+
+def sv_store_state(h):
+    n, dt, _ = sv_info(h)
+    a = np.empty(1 << n, dtype=np.complex64 if dt == C64 else np.complex128)
+    _check(lib().sv_store_state(h, _ptr(a)))
+    return a
+
+
+def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0):
+    g = as_gates(gates)
+    o = _opts(k_max, tile_m, planner, record)
+    _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
+
+
+def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY):
+    g = as_gates(gates)
+    o = _opts(k_max, tile_m, planner)
+    info = sv_plan_info()
+    _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}
+
+
+def sv_probs(h):
+    n, _, _ = sv_info(h)
+    out = np.empty(1 << n, dtype=np.float64)
+    _check(lib().sv_probs(h, _ptr(out)))
+    return out
+
+
+def sv_probs_device(h, dev_out_ptr):
+    _check(lib().sv_probs_device(h, ctypes.c_void_p(dev_out_ptr)))
+
+
+def sv_norm(h):
+    v = ctypes.c_double()
+    _check(lib().sv_norm(h, ctypes.byref(v)))
+    return v.value
+
+
+def sv_expect_z(h):
+    n, _, _ = sv_info(h)
+    out = np.empty(n, dtype=np.float64)
+    _check(lib().sv_expect_z(h, _ptr(out)))
+    return out
+
+
+def sv_expect_z_device(h, dev_out_ptr):
+    _check(lib().sv_expect_z_device(h, ctypes.c_void_p(dev_out_ptr)))
+
+
+def sv_sample(h, shots, seed):
+    out = np.empty(int(shots), dtype=np.uint64)
+    _check(lib().sv_sample(h, int(shots), int(seed), _ptr(out)))
+    return out
+
+
+def sv_sample_device(h, shots, seed, dev_out_ptr):
+    _check(lib().sv_sample_device(h, int(shots), int(seed), ctypes.c_void_p(dev_out_ptr)))
+
+
+def sv_feature_count():
+    return lib().sv_feature_count()
+
+
+def sv_pass_times(h, cap=1 << 16, features=False):
+    """Recorded pass times (ms) [and features] since the last call."""
+    ms = np.empty(cap, dtype=np.float64)
+    F = sv_feature_count()
+    feat = np.empty((cap, F), dtype=np.float32) if features else None
+    cnt = ctypes.c_int()
+    _check(lib().sv_pass_times(h, _ptr(ms), _ptr(feat) if features else None, cap, ctypes.byref(cnt)))
+    k = min(cnt.value, cap)
+    return (ms[:k].copy(), feat[:k].copy()) if features else ms[:k].copy()
+
+
+def sv_sample_uniforms(h, u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(len(u), dtype=np.uint64)
+    _check(lib().sv_sample_uniforms(h, _ptr(u), len(u), _ptr(out)))
+    return out

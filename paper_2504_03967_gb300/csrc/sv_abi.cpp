@@ -1,0 +1,406 @@
+// C ABI entry points of libsv (declared in include/sv.h).
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <string>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+namespace {
+thread_local std::string t_err;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+    t_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return set_error(SV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int ensure_scratch(Scratch* s, size_t bytes, cudaStream_t st) {
+    if (s->cap >= bytes) return SV_OK;
+    if (s->ptr) {
+        cudaError_t e = cudaFreeAsync(s->ptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(scratch)");
+        s->ptr = nullptr;
+        s->cap = 0;
+    }
+    size_t cap = bytes < 4096 ? 4096 : bytes;
+    cudaError_t e = cudaMallocAsync(&s->ptr, cap, st);
+    if (e != cudaSuccess) {
+        s->ptr = nullptr;
+        cudaGetLastError();
+        return set_error(SV_ENOMEM, "scratch allocation of " + std::to_string(cap) + " bytes failed");
+    }
+    s->cap = cap;
+    return SV_OK;
+}
+
+int ensure_pinned(Scratch* s, size_t bytes) {
+    if (s->cap >= bytes) return SV_OK;
+    if (s->ptr) cudaFreeHost(s->ptr);
+    s->ptr = nullptr;
+    s->cap = 0;
+    size_t cap = bytes < 65536 ? 65536 : bytes * 2;
+    cudaError_t e = cudaMallocHost(&s->ptr, cap);
+    if (e != cudaSuccess) {
+        s->ptr = nullptr;
+        cudaGetLastError();
+        return set_error(SV_ENOMEM, "pinned staging allocation failed");
+    }
+    s->cap = cap;
+    return SV_OK;
+}
+
+}  // namespace sv
+
+using namespace sv;
+
+namespace {
+
+int check_handle(sv_handle h) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (h->bad) return set_error(SV_ESTATE, "state flagged by an earlier CUDA failure; re-initialise it");
+    return SV_OK;
+}
+
+int max_qubits(int dt) { return dt == SV_C64 ? kMaxQubitsC64 : kMaxQubitsC128; }
+
+size_t amp_bytes(int dt) { return dt == SV_C64 ? 8 : 16; }
+
+int make_handle(int n, sv_dtype dt, void* amps, bool owned, void* stream, sv_handle* out) {
+    sv_state* h = new (std::nothrow) sv_state();
+    if (!h) return set_error(SV_ENOMEM, "host allocation failed");
+    h->n = n;
+    h->dtype = dt;
+    h->amps = amps;
+    h->owned = owned;
+    h->stream = (cudaStream_t)stream;
+    h->bad = false;
+    h->ev_used = 0;
+    h->upload_ev = nullptr;
+    h->upload_pending = false;
+    *out = h;
+    return SV_OK;
+}
+
+// Next free event of the recorder pool (created on demand).
+cudaEvent_t next_event(sv_handle h) {
+    if (h->ev_used == (int)h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+int fail_state(sv_handle h, int rc) {
+    if (rc == SV_ECUDA || rc == SV_ETIMEOUT) h->bad = true;
+    return rc;
+}
+
+int sync_d2h(sv_handle h, void* host, const void* dev, size_t bytes, const char* what) {
+    cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, what));
+    return SV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sv_version(void) { return 100; }
+
+const char* sv_last_error(void) { return t_err.c_str(); }
+
+uint64_t sv_launch_count(void) { return g_launches.load(); }
+
+int sv_alloc(int n, sv_dtype dt, void* cuda_stream, sv_handle* out) {
+    if (!out) return set_error(SV_EINVAL, "NULL output handle pointer");
+    *out = nullptr;
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (n < 1 || n > max_qubits(dt))
+        return set_error(SV_EINVAL, "n = " + std::to_string(n) + " out of range 1.." + std::to_string(max_qubits(dt)));
+    const size_t bytes = amp_bytes(dt) << n;
+    size_t freeb = 0, totalb = 0;
+    cudaError_t e = cudaMemGetInfo(&freeb, &totalb);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    if (bytes > freeb)
+        return set_error(SV_ENOMEM, "state of " + std::to_string(bytes) + " bytes exceeds free device memory " +
+                                        std::to_string(freeb));
+    void* p = nullptr;
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SV_ENOMEM, std::string("cudaMalloc(state): ") + cudaGetErrorString(e));
+    }
+    int rc = make_handle(n, dt, p, true, cuda_stream, out);
+    if (rc) cudaFree(p);
+    return rc;
+}
+
+int sv_attach(int n, sv_dtype dt, void* dev_amps, void* cuda_stream, sv_handle* out) {
+    if (!out) return set_error(SV_EINVAL, "NULL output handle pointer");
+    *out = nullptr;
+    if (!dev_amps) return set_error(SV_EINVAL, "NULL device pointer");
+    if (((uintptr_t)dev_amps & 15) != 0) return set_error(SV_EINVAL, "device pointer not 16-byte aligned");
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (n < 1 || n > max_qubits(dt)) return set_error(SV_EINVAL, "n out of range");
+    return make_handle(n, dt, dev_amps, false, cuda_stream, out);
+}
+
+int sv_free(sv_handle h) {
+    if (!h) return SV_OK;
+    cudaStreamSynchronize(h->stream);
+    if (h->owned && h->amps) cudaFree(h->amps);
+    if (h->plan_dev.ptr) cudaFree(h->plan_dev.ptr);
+    if (h->red.ptr) cudaFree(h->red.ptr);
+    if (h->out_dev.ptr) cudaFree(h->out_dev.ptr);
+    if (h->host_pin.ptr) cudaFreeHost(h->host_pin.ptr);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->upload_ev) cudaEventDestroy(h->upload_ev);
+    cudaGetLastError();
+    delete h;
+    return SV_OK;
+}
+
+int sv_set_stream(sv_handle h, void* cuda_stream) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    cudaStreamSynchronize(h->stream);
+    h->stream = (cudaStream_t)cuda_stream;
+    return SV_OK;
+}
+
+int sv_info(sv_handle h, int* n, int* dtype, void** dev_amps) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (n) *n = h->n;
+    if (dtype) *dtype = h->dtype;
+    if (dev_amps) *dev_amps = h->amps;
+    return SV_OK;
+}
+
+int sv_init_basis(sv_handle h, uint64_t x) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (x >> h->n) return set_error(SV_EINVAL, "basis index out of range");
+    cudaError_t e = launch_init_basis(h, x);
+    if (e != cudaSuccess) {
+        h->bad = true;
+        return cuda_fail(e, "init_basis");
+    }
+    h->bad = false;
+    return SV_OK;
+}
+
+int sv_load_state(sv_handle h, const void* host_amps) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (!host_amps) return set_error(SV_EINVAL, "NULL host buffer");
+    cudaError_t e = cudaMemcpyAsync(h->amps, host_amps, amp_bytes(h->dtype) << h->n, cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        h->bad = true;
+        return cuda_fail(e, "load_state");
+    }
+    h->bad = false;
+    return SV_OK;
+}
+
+int sv_store_state(sv_handle h, void* host_amps) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!host_amps) return set_error(SV_EINVAL, "NULL host buffer");
+    return sync_d2h(h, host_amps, h->amps, amp_bytes(h->dtype) << h->n, "store_state");
+}
+
+int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, const sv_options* opt,
+                    sv_plan_info* info) {
+    if (!info) return set_error(SV_EINVAL, "NULL info");
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (n < 1 || n > max_qubits(dt)) return set_error(SV_EINVAL, "n out of range");
+    if (count && !gates) return set_error(SV_EINVAL, "NULL gate list");
+    std::vector<CGate> cg;
+    size_t bad = 0;
+    if (canonicalise(n, gates, count, &cg, &bad) != SV_OK)
+        return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
+    const PlanOptions po = resolve_options(n, dt, opt);
+    Plan plan;
+    if (po.planner == SV_PLAN_PLAIN) plan_plain(n, dt, cg, &plan);
+    else plan_greedy(n, dt, cg, po, &plan);
+    plan.gates = (int64_t)count;
+    plan_summary(plan, info);
+    return SV_OK;
+}
+
+int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_options* opt) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (count && !gates) return set_error(SV_EINVAL, "NULL gate list");
+    std::vector<CGate> cg;
+    size_t bad = 0;
+    if (canonicalise(h->n, gates, count, &cg, &bad) != SV_OK)
+        return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
+    if (cg.empty()) return SV_OK;
+    const PlanOptions po = resolve_options(h->n, h->dtype, opt);
+    Plan plan;
+    if (po.planner == SV_PLAN_PLAIN) {
+        plan_plain(h->n, h->dtype, cg, &plan);
+        for (const PlainOp& op : plan.plain_ops) {
+            cudaError_t e = launch_plain_op(h, op);
+            if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "plain gate kernel"));
+        }
+        return SV_OK;
+    }
+    plan_greedy(h->n, h->dtype, cg, po, &plan);
+    PlanBlob blob;
+    serialise_plan(plan, &blob);
+    // Stage through pinned memory; only the previous upload from it has to
+    // be finished (the passes of earlier calls may still be running).
+    cudaError_t e = cudaSuccess;
+    if (h->upload_pending) {
+        e = cudaEventSynchronize(h->upload_ev);
+        if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
+        h->upload_pending = false;
+    }
+    if (!h->upload_ev) {
+        e = cudaEventCreateWithFlags(&h->upload_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    rc = ensure_pinned(&h->host_pin, blob.bytes.size());
+    if (rc) return rc;
+    rc = ensure_scratch(&h->plan_dev, blob.bytes.size(), h->stream);
+    if (rc) return rc;
+    memcpy(h->host_pin.ptr, blob.bytes.data(), blob.bytes.size());
+    e = cudaMemcpyAsync(h->plan_dev.ptr, h->host_pin.ptr, blob.bytes.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "plan upload"));
+    e = cudaEventRecord(h->upload_ev, h->stream);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
+    h->upload_pending = true;
+    const bool rec = opt && opt->record;
+    for (int p = 0; p < blob.npasses; ++p) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (rec && (e0 = next_event(h)) && (e1 = next_event(h))) cudaEventRecord(e0, h->stream);
+        e = launch_pass(h, h->plan_dev.ptr, blob, p, plan.passes[p]);
+        if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "tile pass kernel"));
+        if (rec && e1) {
+            cudaEventRecord(e1, h->stream);
+            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p]));
+        }
+    }
+    return SV_OK;
+}
+
+int sv_pass_times(sv_handle h, double* host_ms, float* host_feat, int cap, int* count) {
+    if (!h || !count) return set_error(SV_EINVAL, "NULL argument");
+    const int np = h->ev_used / 2;
+    *count = np;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "stream sync"));
+    for (int i = 0; i < np && i < cap; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        if (host_ms) host_ms[i] = ms;
+        if (host_feat)
+            for (int f = 0; f < kFeatures; ++f) host_feat[(size_t)i * kFeatures + f] = h->rec_feat[i][f];
+    }
+    h->ev_used = 0;
+    h->rec_feat.clear();
+    return SV_OK;
+}
+
+int sv_feature_count(void) { return kFeatures; }
+
+int sv_probs_device(sv_handle h, double* dev_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!dev_out) return set_error(SV_EINVAL, "NULL output");
+    cudaError_t e = launch_probs(h, dev_out);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "probs"));
+    return SV_OK;
+}
+
+int sv_probs(sv_handle h, double* host_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!host_out) return set_error(SV_EINVAL, "NULL output");
+    const size_t bytes = sizeof(double) << h->n;
+    rc = ensure_scratch(&h->out_dev, bytes, h->stream);
+    if (rc) return rc;
+    cudaError_t e = launch_probs(h, (double*)h->out_dev.ptr);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "probs"));
+    return sync_d2h(h, host_out, h->out_dev.ptr, bytes, "probs readback");
+}
+
+int sv_norm(sv_handle h, double* host_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!host_out) return set_error(SV_EINVAL, "NULL output");
+    return fail_state(h, measure_norm(h, host_out));
+}
+
+int sv_expect_z_device(sv_handle h, double* dev_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!dev_out) return set_error(SV_EINVAL, "NULL output");
+    return fail_state(h, measure_expect_z(h, dev_out));
+}
+
+int sv_expect_z(sv_handle h, double* host_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!host_out) return set_error(SV_EINVAL, "NULL output");
+    rc = ensure_scratch(&h->out_dev, sizeof(double) * 64, h->stream);
+    if (rc) return rc;
+    rc = measure_expect_z(h, (double*)h->out_dev.ptr);
+    if (rc) return fail_state(h, rc);
+    return sync_d2h(h, host_out, h->out_dev.ptr, sizeof(double) * h->n, "expect_z readback");
+}
+
+int sv_sample_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t* dev_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (shots && !dev_out) return set_error(SV_EINVAL, "NULL output");
+    return fail_state(h, measure_sample(h, shots, seed, nullptr, dev_out));
+}
+
+int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t* host_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (shots == 0) return SV_OK;
+    if (!host_out) return set_error(SV_EINVAL, "NULL output");
+    rc = ensure_scratch(&h->out_dev, sizeof(uint64_t) * shots, h->stream);
+    if (rc) return rc;
+    rc = measure_sample(h, shots, seed, nullptr, (uint64_t*)h->out_dev.ptr);
+    if (rc) return fail_state(h, rc);
+    return sync_d2h(h, host_out, h->out_dev.ptr, sizeof(uint64_t) * shots, "sample readback");
+}
+
+int sv_sample_uniforms(sv_handle h, const double* host_u, uint64_t shots, uint64_t* host_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (shots == 0) return SV_OK;
+    if (!host_u || !host_out) return set_error(SV_EINVAL, "NULL buffer");
+    for (uint64_t s = 0; s < shots; ++s)
+        if (!(host_u[s] >= 0.0 && host_u[s] < 1.0)) return set_error(SV_EINVAL, "uniform outside [0,1)");
+    rc = ensure_scratch(&h->out_dev, 16 * shots, h->stream);
+    if (rc) return rc;
+    double* du = (double*)h->out_dev.ptr;
+    uint64_t* dout = (uint64_t*)(du + shots);
+    cudaError_t e = cudaMemcpyAsync(du, host_u, sizeof(double) * shots, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "uniforms upload"));
+    rc = measure_sample(h, shots, 0, du, dout);
+    if (rc) return fail_state(h, rc);
+    return sync_d2h(h, host_out, dout, sizeof(uint64_t) * shots, "sample readback");
+}
+
+}  // extern "C"

@@ -1,0 +1,532 @@
+// Gate-application kernels for sm_103a.
+//
+//  * Plain path: one kernel per gate over the whole state (App. A: a gate
+//    U_k = I (x) .. (x) U (x) .. (x) I acts on every amplitude pair that
+//    differs only in bit k; CX exchanges the target pair where the control is
+//    1, touching 2^(n-1) amplitudes; CR1 multiplies the |11> quarter).
+//  * Tile pass: one HBM read + one write of the state applies a whole list of
+//    fused dense blocks (<= 5 qubits, App. D.2 "gate fusion = 5") and
+//    diagonal-phase runs to each 2^m-amplitude tile held in shared memory.
+//    Tiles are gathered with 16-byte cp.async copies of contiguous rows of
+//    2^L amplitudes (128 bytes), so every HBM access is a full line.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+template <typename R> struct CT;
+template <> struct CT<float> { using V = float2; };
+template <> struct CT<double> { using V = double2; };
+
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename V> __device__ __forceinline__ V cfma(V a, V b, V c) {  // a*b + c
+    V r;
+    r.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+    r.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+    return r;
+}
+template <typename V> __device__ __forceinline__ V czero() {
+    V r;
+    r.x = 0;
+    r.y = 0;
+    return r;
+}
+
+__device__ __forceinline__ uint64_t insert_zero(uint64_t v, int pos) {
+    const uint64_t lo = v & ((1ull << pos) - 1ull);
+    return ((v >> pos) << (pos + 1)) | lo;
+}
+
+template <typename V> V to_dev(const cd& c) {
+    V r;
+    r.x = (decltype(r.x))c.real();
+    r.y = (decltype(r.y))c.imag();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// |x>
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_init_basis(V* __restrict__ psi, uint64_t N, uint64_t x) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        V v = czero<V>();
+        if (i == x) v.x = 1;
+        psi[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain per-gate kernels.  Each thread handles UNR independent items per
+// loop trip with all loads issued before any store (memory-level
+// parallelism); items never overlap, so this is safe in place.
+// ---------------------------------------------------------------------------
+constexpr int UNR = 4;
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_plain_1q(V* __restrict__ psi, uint64_t npairs, int q, V u00, V u01,
+                                                  V u10, V u11) {
+    const uint64_t lom = (1ull << q) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < npairs; r0 += stride * UNR) {
+        V a[UNR], b[UNR];
+        uint64_t i0[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const uint64_t r = r0 + u * stride;
+            i0[u] = ((r & ~lom) << 1) | (r & lom);
+            if (r < npairs) {
+                a[u] = psi[i0[u]];
+                b[u] = psi[i0[u] | (lom + 1)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (r0 + u * stride < npairs) {
+                psi[i0[u]] = cfma(u00, a[u], cmul(u01, b[u]));
+                psi[i0[u] | (lom + 1)] = cfma(u10, a[u], cmul(u11, b[u]));
+            }
+        }
+    }
+}
+
+// Exchange psi[i | A] and psi[i | B] for every i with bits lo, hi clear
+// (CX: A = 1<<c, B = 1<<c | 1<<t; SWAP: A = 1<<q0, B = 1<<q1).
+template <typename V>
+__global__ void __launch_bounds__(256) k_plain_swap(V* __restrict__ psi, uint64_t nquads, int lo, int hi,
+                                                    uint64_t A, uint64_t B) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < nquads; r0 += stride * UNR) {
+        V a[UNR], b[UNR];
+        uint64_t i[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const uint64_t r = r0 + u * stride;
+            i[u] = insert_zero(insert_zero(r, lo), hi);
+            if (r < nquads) {
+                a[u] = psi[i[u] | A];
+                b[u] = psi[i[u] | B];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (r0 + u * stride < nquads) {
+                psi[i[u] | A] = b[u];
+                psi[i[u] | B] = a[u];
+            }
+        }
+    }
+}
+
+// Multiply psi[i | M] by f for every i with bits lo, hi clear (CP/CZ: M =
+// both bits); with lo == hi a single bit (P, Z: the bit-1 half).
+template <typename V>
+__global__ void __launch_bounds__(256) k_plain_phase(V* __restrict__ psi, uint64_t nitems, int lo, int hi,
+                                                     uint64_t M, V f) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < nitems; r0 += stride * UNR) {
+        V a[UNR];
+        uint64_t i[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const uint64_t r = r0 + u * stride;
+            uint64_t x = insert_zero(r, lo);
+            if (hi != lo) x = insert_zero(x, hi);
+            i[u] = x | M;
+            if (r < nitems) a[u] = psi[i[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (r0 + u * stride < nitems) psi[i[u]] = cmul(f, a[u]);
+    }
+}
+
+// Diagonal single-qubit gate on every amplitude: psi[x] *= d[bit q of x].
+template <typename V>
+__global__ void __launch_bounds__(256) k_plain_diag1(V* __restrict__ psi, uint64_t N, int q, V d0, V d1) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < N; x0 += stride * UNR) {
+        V a[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (x0 + u * stride < N) a[u] = psi[x0 + u * stride];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const uint64_t x = x0 + u * stride;
+            if (x < N) psi[x] = cmul(((x >> q) & 1) ? d1 : d0, a[u]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile pass.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Dense k-qubit block on tile positions lq[0..K-1] (ascending).  A round
+// covers blockDim/G whole slices; thread t takes row group g = t / (blockDim/G)
+// (uniform across each warp, so matrix reads are shared-memory broadcasts)
+// and slice t mod (blockDim/G).  With more than one group per slice all
+// inputs of the round are read before any output is written (block barrier).
+template <typename V, int K>
+__device__ __forceinline__ void tile_dense(V* __restrict__ tile, int m, const OpDev& op, const V* __restrict__ sU) {
+    constexpr int D = 1 << K;
+    constexpr int RG = D < 8 ? D : 8;
+    constexpr int G = D / RG;
+    int bitv[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) bitv[i] = 1 << op.lq[i];
+    const int nslices = 1 << (m - K);
+    const int per_round = blockDim.x / G;
+    const int g = threadIdx.x / per_round;
+    const int sl = threadIdx.x - g * per_round;
+    for (int s0 = 0; s0 < nslices; s0 += per_round) {
+        const int s = s0 + sl;
+        const bool act = s < nslices;
+        int base = s;
+#pragma unroll
+        for (int i = 0; i < K; ++i) base = (int)insert_zero((uint64_t)base, op.lq[i]);
+        V acc[RG];
+#pragma unroll
+        for (int r = 0; r < RG; ++r) acc[r] = czero<V>();
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                int o = 0;
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+                    if ((j >> i) & 1) o += bitv[i];
+                const V x = tile[base + o];
+#pragma unroll
+                for (int r = 0; r < RG; ++r) acc[r] = cfma(sU[(g * RG + r) * D + j], x, acc[r]);
+            }
+        }
+        if (G > 1) __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < RG; ++r) {
+                const int row = g * RG + r;
+                int o = 0;
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+                    if ((row >> i) & 1) o += bitv[i];
+                tile[base + o] = acc[r];
+            }
+        }
+        if (G > 1) __syncthreads();
+    }
+}
+
+template <typename R> __device__ __forceinline__ R frac_r(R v) { return v - rint(v); }
+
+__device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
+    __sincosf(6.28318530717958647692f * t, s, c);  // |t| <= 0.5 after reduction
+}
+__device__ __forceinline__ void sincos_turns(double t, double* s, double* c) { sincospi(2.0 * t, s, c); }
+
+// Diagonal-phase run: psi_x *= exp(2 pi i phase(x)), phase(x) = c + sum_q a_q
+// x_q + sum_{p<q} b_pq x_p x_q (turns).  For the tile with non-tile bits
+// "base" the non-tile part folds into a constant C and per-tile linear
+// coefficients a'_t; the tile-internal quadratic part comes precomputed per
+// pass (Qlo, Qhi over the lo/hi halves of the tile index, Rt coupling them),
+// so each amplitude costs a few table lookups and one sincos.
+template <typename V, typename R>
+__device__ __forceinline__ void tile_diag(V* __restrict__ tile, const PassDev& P, uint64_t base,
+                                          const double* __restrict__ dd, R* tabs, R* s_ap, double* s_c) {
+    const int m = P.m, no = P.nother;
+    const DiagLayout Lo(m, no);
+    const int h = Lo.h, mh = Lo.mh;
+    const int tid = threadIdx.x;
+    // One round trip each: every load of the row is independent (unrolled to
+    // the 32-qubit bound and predicated), then summed in order.
+    if (tid < m) {
+        const double* row = dd + Lo.bo + tid * no;
+        double r[32];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) r[o] = (o < no && ((base >> P.oq[o]) & 1)) ? row[o] : 0.0;
+        double v = dd[Lo.at + tid];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) v += r[o];
+        s_ap[tid] = (R)(v - floor(v + 0.5));
+    }
+    if (tid >= 32 && tid < 64) {
+        const int o = tid - 32;
+        const bool set = o < no && ((base >> P.oq[o < no ? o : 0]) & 1);
+        double v = 0.0;
+        if (set) {
+            const double* row = dd + Lo.boo + o * no;
+            double r[32];
+#pragma unroll
+            for (int o2 = 0; o2 < 32; ++o2) r[o2] = (o2 < o && ((base >> P.oq[o2]) & 1)) ? row[o2] : 0.0;
+            v = dd[Lo.ao + o];
+#pragma unroll
+            for (int o2 = 0; o2 < 32; ++o2) v += r[o2];
+        }
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+        if (o == 0) {
+            v += dd[Lo.c];
+            *s_c = v - floor(v + 0.5);
+        }
+    }
+    __syncthreads();
+    R* Llo = tabs;
+    R* Lhi = Llo + (1 << h);
+    R* Rt = Lhi + (1 << mh);
+    for (int e = tid; e < (1 << h); e += blockDim.x) {
+        R v = (R)dd[Lo.qlo + e];
+        for (int b = 0; b < h; ++b)
+            if ((e >> b) & 1) v += s_ap[b];
+        Llo[e] = frac_r(v);
+    }
+    const R cc = (R)*s_c;
+    for (int e = tid; e < (1 << mh); e += blockDim.x) {
+        R v = (R)dd[Lo.qhi + e] + cc;
+        for (int b = 0; b < mh; ++b)
+            if ((e >> b) & 1) v += s_ap[h + b];
+        Lhi[e] = frac_r(v);
+    }
+    for (int e = tid; e < (mh << h); e += blockDim.x) Rt[e] = (R)dd[Lo.rt + e];
+    __syncthreads();
+    const int lomask = (1 << h) - 1;
+#pragma unroll 4
+    for (int i = tid; i < (1 << m); i += blockDim.x) {
+        const int lo = i & lomask, hi = i >> h;
+        R ph = Llo[lo] + Lhi[hi];
+#pragma unroll
+        for (int t = 0; t < 7; ++t)
+            if (t < mh && ((hi >> t) & 1)) ph += Rt[(t << h) + lo];
+        ph = frac_r(ph);
+        R sn, cs;
+        sincos_turns(ph, &sn, &cs);
+        V f;
+        f.x = cs;
+        f.y = sn;
+        tile[i] = cmul(f, tile[i]);
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ void load_tile(V* tile, const V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
+                                          int m, int L) {
+    constexpr int PER = 16 / sizeof(V);  // amplitudes per 16-byte chunk
+    const int nch = (1 << m) / PER;
+    const int rmask = (1 << L) - 1;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        const int i = c * PER;
+        const uint64_t g = base + ((uint64_t)rowoff[i >> L] << L) + (uint64_t)(i & rmask);
+        cp_async16(tile + i, psi + g);
+    }
+    cp_async_wait_all();
+}
+
+template <typename V>
+__device__ __forceinline__ void store_tile(const V* tile, V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
+                                           int m, int L) {
+    constexpr int PER = 16 / sizeof(V);
+    const int nch = (1 << m) / PER;
+    const int rmask = (1 << L) - 1;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        const int i = c * PER;
+        const uint64_t g = base + ((uint64_t)rowoff[i >> L] << L) + (uint64_t)(i & rmask);
+        *(float4*)(psi + g) = *(const float4*)(tile + i);
+    }
+}
+
+__host__ __device__ inline int diag_table_elems(int m) {
+    const int h = m < 7 ? m : 7;
+    const int mh = m - h;
+    return (1 << h) + (1 << mh) + (mh << h);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kPassThreads) k_pass(typename CT<R>::V* __restrict__ psi, int n,
+                                                      const PassDev* __restrict__ pdp,
+                                                      const OpDev* __restrict__ ops,
+                                                      const typename CT<R>::V* __restrict__ mats,
+                                                      const double* __restrict__ diags) {
+    using V = typename CT<R>::V;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PassDev P;
+    __shared__ R s_ap[kMaxTileM];
+    __shared__ double s_c;
+    {
+        const int* src = (const int*)pdp;
+        int* dst = (int*)&P;
+        for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int m = P.m, L = P.L;
+    V* tile = (V*)smem;
+    uint32_t* rowoff = (uint32_t*)(smem + (sizeof(V) << m));
+    const int nrows = 1 << (m - L);
+    R* work = (R*)(rowoff + ((nrows + 3) & ~3));
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+        uint32_t o = 0;
+        for (int b = 0; b < m - L; ++b)
+            if ((r >> b) & 1) o |= 1u << (P.tq[L + b] - L);
+        rowoff[r] = o;
+    }
+    __syncthreads();
+    const uint64_t ntiles = 1ull << (n - m);
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint64_t base = 0;
+        for (int b = 0; b < P.nother; ++b) base |= ((t >> b) & 1ull) << P.oq[b];
+        load_tile(tile, psi, base, rowoff, m, L);
+        __syncthreads();
+        for (int oi = P.op_begin; oi < P.op_end; ++oi) {
+            const OpDev op = ops[oi];
+            if (op.kind == OP_DENSE) {
+                V* sU = (V*)work;
+                const int DD = 1 << (2 * op.k);
+                for (int e = threadIdx.x; e < DD; e += blockDim.x) sU[e] = mats[op.mat_off + e];
+                __syncthreads();
+                switch (op.k) {
+                case 1: tile_dense<V, 1>(tile, m, op, sU); break;
+                case 2: tile_dense<V, 2>(tile, m, op, sU); break;
+                case 3: tile_dense<V, 3>(tile, m, op, sU); break;
+                case 4: tile_dense<V, 4>(tile, m, op, sU); break;
+                default: tile_dense<V, 5>(tile, m, op, sU); break;
+                }
+            } else {
+                tile_diag<V, R>(tile, P, base, diags + op.diag_off, work, s_ap, &s_c);
+            }
+            __syncthreads();
+        }
+        store_tile(tile, psi, base, rowoff, m, L);
+        __syncthreads();
+    }
+}
+
+size_t pass_smem_bytes(int dtype, int m, int L) {
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    const size_t rsz = dtype == SV_C64 ? 4 : 8;
+    const int nrows = 1 << (m - L);
+    size_t work = csz * (1 << (2 * kMaxK));
+    const size_t dt = rsz * diag_table_elems(m);
+    if (dt > work) work = dt;
+    return (csz << m) + 4 * (size_t)((nrows + 3) & ~3) + work;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+namespace {
+int g_sms = 0;
+int num_sms() {
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 148;
+    }
+    return g_sms;
+}
+unsigned grid_for(uint64_t items, int per_thread = UNR) {
+    const uint64_t want = (items + (uint64_t)256 * per_thread - 1) / ((uint64_t)256 * per_thread);
+    const uint64_t cap = (uint64_t)num_sms() * 16;
+    uint64_t g = want < cap ? want : cap;
+    return (unsigned)(g ? g : 1);
+}
+}  // namespace
+
+cudaError_t launch_init_basis(sv_state* h, uint64_t x) {
+    const uint64_t N = 1ull << h->n;
+    count_launch();
+    if (h->dtype == SV_C64)
+        k_init_basis<float2><<<grid_for(N, 1), 256, 0, h->stream>>>((float2*)h->amps, N, x);
+    else
+        k_init_basis<double2><<<grid_for(N, 1), 256, 0, h->stream>>>((double2*)h->amps, N, x);
+    return cudaGetLastError();
+}
+
+template <typename V>
+static cudaError_t plain_op_t(sv_state* h, const PlainOp& op) {
+    V* psi = (V*)h->amps;
+    const int n = h->n;
+    const uint64_t N = 1ull << n;
+    cudaStream_t st = h->stream;
+    count_launch();
+    switch (op.kind) {
+    case PK_1Q:
+        k_plain_1q<V><<<grid_for(N / 2), 256, 0, st>>>(psi, N / 2, op.q0, to_dev<V>(op.m[0]), to_dev<V>(op.m[1]),
+                                                       to_dev<V>(op.m[2]), to_dev<V>(op.m[3]));
+        break;
+    case PK_CX: {
+        const int lo = op.q0 < op.q1 ? op.q0 : op.q1, hi = op.q0 < op.q1 ? op.q1 : op.q0;
+        const uint64_t A = 1ull << op.q0, B = A | (1ull << op.q1);
+        k_plain_swap<V><<<grid_for(N / 4), 256, 0, st>>>(psi, N / 4, lo, hi, A, B);
+        break;
+    }
+    case PK_SWAP: {
+        const int lo = op.q0 < op.q1 ? op.q0 : op.q1, hi = op.q0 < op.q1 ? op.q1 : op.q0;
+        k_plain_swap<V><<<grid_for(N / 4), 256, 0, st>>>(psi, N / 4, lo, hi, 1ull << op.q0, 1ull << op.q1);
+        break;
+    }
+    case PK_CPHASE: {
+        const int lo = op.q0 < op.q1 ? op.q0 : op.q1, hi = op.q0 < op.q1 ? op.q1 : op.q0;
+        k_plain_phase<V><<<grid_for(N / 4), 256, 0, st>>>(psi, N / 4, lo, hi, (1ull << lo) | (1ull << hi),
+                                                          to_dev<V>(op.m[0]));
+        break;
+    }
+    case PK_PHASE1:
+        k_plain_phase<V><<<grid_for(N / 2), 256, 0, st>>>(psi, N / 2, op.q0, op.q0, 1ull << op.q0,
+                                                          to_dev<V>(op.m[0]));
+        break;
+    case PK_DIAG1:
+        k_plain_diag1<V><<<grid_for(N), 256, 0, st>>>(psi, N, op.q0, to_dev<V>(op.m[0]), to_dev<V>(op.m[1]));
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_op(sv_state* h, const PlainOp& op) {
+    if (h->dtype == SV_C64) return plain_op_t<float2>(h, op);
+    return plain_op_t<double2>(h, op);
+}
+
+template <typename R>
+static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
+    using V = typename CT<R>::V;
+    const int m = (int)hp.tile.size();
+    const size_t smem = pass_smem_bytes(h->dtype, m, hp.L);
+    static bool attr_set[2] = {false, false};
+    const int di = h->dtype == SV_C64 ? 0 : 1;
+    if (!attr_set[di]) {
+        cudaError_t e = cudaFuncSetAttribute(k_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pass_smem_bytes(h->dtype, h->dtype == SV_C64 ? 14 : 13, 1));
+        if (e != cudaSuccess) return e;
+        attr_set[di] = true;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R>, kPassThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t ntiles = 1ull << (h->n - m);
+    uint64_t grid = (uint64_t)num_sms() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const unsigned char* b = (const unsigned char*)blob_dev;
+    count_launch();
+    k_pass<R><<<(unsigned)grid, kPassThreads, smem, h->stream>>>(
+        (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, (const OpDev*)(b + blob.op_off),
+        (const V*)(b + blob.mat_off), (const double*)(b + blob.diag_off));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
+    if (h->dtype == SV_C64) return pass_t<float>(h, blob_dev, blob, pass, hp);
+    return pass_t<double>(h, blob_dev, blob, pass, hp);
+}
+
+}  // namespace sv

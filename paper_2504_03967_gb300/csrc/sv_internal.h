@@ -1,0 +1,227 @@
+// Internal declarations shared by the libsv translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+
+namespace sv {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxQubitsC64 = 34;
+constexpr int kMaxQubitsC128 = 33;
+constexpr int kMaxK = 5;         // widest fused dense block
+constexpr int kMaxTileM = 14;    // qubits per shared-memory tile
+constexpr int kPassThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Canonical gates (host, FP64).  A gate is either dense (a 2^k x 2^k matrix,
+// local bit i <-> qubit q[i]) or diagonal (phase e^{i ph[j]} on local index
+// j, same bit convention).  MEASURE records are dropped.
+// ---------------------------------------------------------------------------
+enum GateKind { GK_DENSE = 0, GK_DIAG = 1 };
+
+struct CGate {
+    int kind;
+    int nq;
+    int q[2];
+    cd m[16];       // dense: row-major 2^nq x 2^nq
+    double ph[4];   // diag: phases (radians) per local index
+    uint32_t type;  // original sv_gate_type
+    double p[3];
+};
+
+// Validate and canonicalise; returns SV_OK or SV_EINVAL with *bad = index.
+int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out, size_t* bad);
+
+// ---------------------------------------------------------------------------
+// Plans.  A pass loads every tile of 2^m amplitudes whose index varies only in
+// the tile qubits T (sorted, always holding bits 0..L-1 so that each row of
+// 2^L amplitudes is contiguous), applies its ops in shared memory and writes
+// the tile back: one HBM read and one write of the state per pass.
+// ---------------------------------------------------------------------------
+enum OpKind { OP_DENSE = 0, OP_DIAG = 1 };
+
+struct DiagForm {
+    // phase(x) = c + sum_q a[q] x_q + sum_{p<q} b[p*n+q] x_p x_q  (radians)
+    double c = 0.0;
+    std::vector<double> a, b;
+    std::vector<char> support;
+    void init(int n) {
+        c = 0.0;
+        a.assign(n, 0.0);
+        b.assign((size_t)n * n, 0.0);
+        support.assign(n, 0);
+    }
+    bool empty() const {
+        for (char s : support)
+            if (s) return false;
+        return c == 0.0;
+    }
+};
+
+struct HostOp {
+    int kind;
+    std::vector<int> qubits;  // dense: sorted ascending, block bit i <-> qubits[i]
+    std::vector<cd> mat;      // dense: 2^k x 2^k row-major
+    DiagForm diag;            // diag
+    int ngates = 0;           // logical gates folded into the op
+};
+
+struct HostPass {
+    std::vector<int> tile;  // sorted ascending
+    int L = 0;              // bits 0..L-1 are in the tile
+    std::vector<HostOp> ops;
+    int ngates = 0;
+    int type_count[14] = {0};  // logical gates of each sv_gate_type in the pass
+};
+
+// Plain (unfused) per-gate kernels over the whole state.
+enum PlainKind { PK_1Q = 0, PK_CX, PK_SWAP, PK_CPHASE, PK_DIAG1, PK_PHASE1 };
+
+struct PlainOp {
+    int kind;
+    int q0, q1;
+    cd m[4];  // PK_1Q: 2x2; PK_DIAG1: m[0], m[1] = d0, d1; PK_PHASE1/PK_CPHASE: m[0]
+};
+
+struct Plan {
+    int n = 0;
+    int dtype = 0;
+    bool plain = false;
+    std::vector<HostPass> passes;
+    std::vector<PlainOp> plain_ops;
+    int64_t gates = 0;
+};
+
+struct PlanOptions {
+    int k_max = 5;
+    int tile_m = 13;
+    int planner = SV_PLAN_GREEDY;
+};
+
+PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
+void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out);
+void plan_plain(int n, int dtype, const std::vector<CGate>& gates, Plan* out);
+void plan_summary(const Plan& p, sv_plan_info* info);
+
+// Cost-model features of one pass (fixed length kFeatures): qubit count,
+// dtype, tile width, dense blocks per width, diagonal runs, logical gates per
+// type (the paper's one-hot gate-type encoding, App. D.1 Eq. "onehot",
+// summed over the pass), arithmetic and byte volume, and a bias input.
+constexpr int kFeatures = 32;
+std::vector<float> pass_features(int n, int dtype, const HostPass& p);
+
+// ---------------------------------------------------------------------------
+// Device-side plan blob.  Layout: [PassDev x P][OpDev x O][mats][diag doubles]
+// ---------------------------------------------------------------------------
+struct OpDev {
+    int kind;
+    int k;
+    int mat_off;   // dense: element offset into the matrix array (complex units)
+    int diag_off;  // diag: offset (doubles) of [c, a[n], b[n*n]] in turns
+    int lq[kMaxK]; // dense: local tile positions, ascending
+    int ngates;
+};
+
+struct PassDev {
+    int m;
+    int L;
+    int op_begin;
+    int op_end;
+    int tq[kMaxTileM];   // tile qubits ascending
+    int nother;
+    int oq[40];          // non-tile qubits ascending
+};
+
+// Layout (in doubles, phases in turns) of one diagonal run inside a pass
+// with m tile qubits and no = n - m other qubits:
+//   c | a_t[m] | a_o[no] | Bo[m][no] | Boo[no][no] | Qlo[2^h] | Qhi[2^(m-h)]
+//   | Rt[(m-h)][2^h]
+// with h = min(m, 7): the tile index splits into lo = bits 0..h-1 and hi.
+struct DiagLayout {
+    int h, mh, c, at, ao, bo, boo, qlo, qhi, rt, total;
+    __host__ __device__ DiagLayout(int m, int no) {
+        h = m < 7 ? m : 7;
+        mh = m - h;
+        c = 0;
+        at = 1;
+        ao = at + m;
+        bo = ao + no;
+        boo = bo + m * no;
+        qlo = boo + no * no;
+        qhi = qlo + (1 << h);
+        rt = qhi + (1 << mh);
+        total = rt + (mh << h);
+    }
+};
+__host__ __device__ inline size_t diag_doubles(int m, int no) { return (size_t)DiagLayout(m, no).total; }
+
+struct PlanBlob {
+    std::vector<unsigned char> bytes;
+    size_t pass_off = 0, op_off = 0, mat_off = 0, diag_off = 0;
+    int npasses = 0;
+};
+
+void serialise_plan(const Plan& p, PlanBlob* blob);
+
+// ---------------------------------------------------------------------------
+// Handle.
+// ---------------------------------------------------------------------------
+struct Scratch {
+    void* ptr = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace sv
+
+struct sv_state {
+    int n;
+    int dtype;
+    void* amps;
+    bool owned;
+    cudaStream_t stream;
+    bool bad;
+    sv::Scratch plan_dev;    // device plan blob
+    sv::Scratch red;         // reduction scratch (block sums, CDF, partials)
+    sv::Scratch out_dev;     // device staging for host outputs
+    sv::Scratch host_pin;    // pinned staging for plan uploads
+    cudaEvent_t upload_ev;   // recorded after the last plan upload from host_pin
+    bool upload_pending;
+    // recorder: CUDA events around each pass of applies made with record=1
+    std::vector<cudaEvent_t> ev_pool;
+    int ev_used;             // events in use (pairs: begin, end)
+    std::vector<std::vector<float>> rec_feat;  // per recorded pass features
+};
+
+namespace sv {
+
+// Error handling (thread-local message).
+int set_error(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+void count_launch(uint64_t k = 1);
+
+int ensure_scratch(Scratch* s, size_t bytes, cudaStream_t st);
+int ensure_pinned(Scratch* s, size_t bytes);
+
+// Kernel launchers (sv_kernels.cu).  All return cudaError_t of the launch.
+cudaError_t launch_init_basis(sv_state* h, uint64_t x);
+cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
+cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
+                        const HostPass& hp);
+size_t pass_smem_bytes(int dtype, int m, int L);
+
+// Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
+int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks);
+cudaError_t launch_probs(sv_state* h, double* dev_out);
+int measure_norm(sv_state* h, double* host_out);
+int measure_expect_z(sv_state* h, double* dev_out);
+int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev_u, uint64_t* dev_out);
+
+}  // namespace sv

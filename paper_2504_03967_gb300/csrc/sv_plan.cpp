@@ -1,0 +1,629 @@
+// Host side of the simulator: gate canonicalisation (FP64) and planning.
+//
+// A plan turns the gate list into passes over the state.  Fusion is exact in
+// exact arithmetic: consecutive gates are multiplied into dense blocks of at
+// most k_max qubits (App. D.2, "gate fusion = 5"; a k-qubit block is a
+// 2^k x 2^k unitary, stored row-major as in App. B Lemma 1), and diagonal
+// gates (RZ, P, Z, CZ, CP = cr1 of App. D.2 Eq. "cr1") are collected into
+// phase runs phase(x) = c + sum a_q x_q + sum b_pq x_p x_q that can be applied
+// to any amplitude from its index alone.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+int arity(uint32_t t) {
+    switch (t) {
+    case SV_H: case SV_X: case SV_Y: case SV_Z: case SV_RX: case SV_RY: case SV_RZ:
+    case SV_P: case SV_U3: case SV_MEASURE:
+        return 1;
+    case SV_CX: case SV_CZ: case SV_CP: case SV_SWAP:
+        return 2;
+    default:
+        return -1;
+    }
+}
+
+// Gate -> canonical form.  Local index j = sum_i bit(q[i]) << i (LSB first).
+void make_canonical(const sv_gate& g, CGate* c) {
+    memset(c, 0, sizeof(*c));
+    c->type = g.type;
+    c->nq = (int)g.nq;
+    c->q[0] = (int)g.q[0];
+    c->q[1] = g.nq > 1 ? (int)g.q[1] : -1;
+    for (int i = 0; i < 3; ++i) c->p[i] = g.p[i];
+    const cd I(0.0, 1.0);
+    const double h = 0.5 * g.p[0];
+    const double cs = cos(h), sn = sin(h);
+    cd* m = c->m;
+    c->kind = GK_DENSE;
+    switch (g.type) {
+    case SV_H: {
+        const double r = 1.0 / sqrt(2.0);
+        m[0] = r; m[1] = r; m[2] = r; m[3] = -r;
+        break;
+    }
+    case SV_X: m[1] = 1.0; m[2] = 1.0; break;
+    case SV_Y: m[1] = -I; m[2] = I; break;
+    case SV_RX: m[0] = cs; m[1] = -I * sn; m[2] = -I * sn; m[3] = cs; break;
+    case SV_RY: m[0] = cs; m[1] = -sn; m[2] = sn; m[3] = cs; break;
+    case SV_U3: {
+        const double ph = g.p[1], la = g.p[2];
+        m[0] = cs;
+        m[1] = -std::polar(1.0, la) * sn;
+        m[2] = std::polar(1.0, ph) * sn;
+        m[3] = std::polar(1.0, ph + la) * cs;
+        break;
+    }
+    case SV_Z: c->kind = GK_DIAG; c->ph[0] = 0.0; c->ph[1] = kPi; break;
+    case SV_RZ: c->kind = GK_DIAG; c->ph[0] = -h; c->ph[1] = h; break;
+    case SV_P: c->kind = GK_DIAG; c->ph[0] = 0.0; c->ph[1] = g.p[0]; break;
+    case SV_CZ: c->kind = GK_DIAG; c->ph[3] = kPi; break;
+    case SV_CP: c->kind = GK_DIAG; c->ph[3] = g.p[0]; break;
+    case SV_CX:
+        // control = local bit 0, target = local bit 1: |1,t> -> |1,1-t>
+        m[0 * 4 + 0] = 1.0; m[2 * 4 + 2] = 1.0; m[3 * 4 + 1] = 1.0; m[1 * 4 + 3] = 1.0;
+        break;
+    case SV_SWAP:
+        m[0 * 4 + 0] = 1.0; m[3 * 4 + 3] = 1.0; m[1 * 4 + 2] = 1.0; m[2 * 4 + 1] = 1.0;
+        break;
+    default:
+        break;
+    }
+}
+
+// Dense block under construction.
+struct Block {
+    std::vector<int> qubits;  // sorted
+    std::vector<cd> mat;
+    int ngates = 0;
+    bool active() const { return !qubits.empty(); }
+    int pos(int q) const {
+        for (size_t i = 0; i < qubits.size(); ++i)
+            if (qubits[i] == q) return (int)i;
+        return -1;
+    }
+};
+
+// Re-express the block on the sorted qubit set nq (a superset), identity on
+// the added qubits.
+void expand_block(Block* b, const std::vector<int>& nq) {
+    const int k = (int)nq.size();
+    const int d = 1 << k;
+    std::vector<cd> out((size_t)d * d, cd(0.0, 0.0));
+    std::vector<int> old_pos;  // position in nq of each old qubit
+    int oldmask = 0;
+    for (int q : b->qubits) {
+        int p = (int)(std::find(nq.begin(), nq.end(), q) - nq.begin());
+        old_pos.push_back(p);
+        oldmask |= 1 << p;
+    }
+    const int ko = (int)b->qubits.size();
+    const int dold = 1 << ko;
+    for (int r = 0; r < d; ++r) {
+        int ro = 0;
+        for (int i = 0; i < ko; ++i) ro |= ((r >> old_pos[i]) & 1) << i;
+        for (int cc = 0; cc < d; ++cc) {
+            if ((r & ~oldmask) != (cc & ~oldmask)) continue;
+            int co = 0;
+            for (int i = 0; i < ko; ++i) co |= ((cc >> old_pos[i]) & 1) << i;
+            out[(size_t)r * d + cc] = ko ? b->mat[(size_t)ro * dold + co] : cd(r == cc ? 1.0 : 0.0);
+        }
+    }
+    b->qubits = nq;
+    b->mat.swap(out);
+}
+
+// Left-multiply the block by a dense gate whose qubits are in the block.
+void block_apply_dense(Block* b, const CGate& g) {
+    const int k = (int)b->qubits.size();
+    const int d = 1 << k;
+    const int gd = 1 << g.nq;
+    int gp[2] = {b->pos(g.q[0]), g.nq > 1 ? b->pos(g.q[1]) : -1};
+    int gmask = 0;
+    for (int i = 0; i < g.nq; ++i) gmask |= 1 << gp[i];
+    std::vector<cd> col(d), nc(d);
+    for (int c = 0; c < d; ++c) {
+        for (int r = 0; r < d; ++r) col[r] = b->mat[(size_t)r * d + c];
+        for (int r = 0; r < d; ++r) {
+            if (r & gmask) continue;  // r = group base (gate bits zero)
+            cd v[4], w[4];
+            int idx[4];
+            for (int j = 0; j < gd; ++j) {
+                int x = r;
+                for (int i = 0; i < g.nq; ++i)
+                    if ((j >> i) & 1) x |= 1 << gp[i];
+                idx[j] = x;
+                v[j] = col[x];
+            }
+            for (int a = 0; a < gd; ++a) {
+                cd acc(0.0, 0.0);
+                for (int bb = 0; bb < gd; ++bb) acc += g.m[a * gd + bb] * v[bb];
+                w[a] = acc;
+            }
+            for (int j = 0; j < gd; ++j) nc[idx[j]] = w[j];
+        }
+        for (int r = 0; r < d; ++r) b->mat[(size_t)r * d + c] = nc[r];
+    }
+}
+
+// Left-multiply the block by a diagonal gate whose qubits are in the block.
+void block_apply_diag(Block* b, const CGate& g) {
+    const int k = (int)b->qubits.size();
+    const int d = 1 << k;
+    int gp[2] = {b->pos(g.q[0]), g.nq > 1 ? b->pos(g.q[1]) : -1};
+    for (int r = 0; r < d; ++r) {
+        int j = 0;
+        for (int i = 0; i < g.nq; ++i) j |= ((r >> gp[i]) & 1) << i;
+        const cd f = std::polar(1.0, g.ph[j]);
+        for (int c = 0; c < d; ++c) b->mat[(size_t)r * d + c] *= f;
+    }
+}
+
+void diag_add(DiagForm* D, int n, const CGate& g) {
+    if (g.nq == 1) {
+        const int q = g.q[0];
+        D->c += g.ph[0];
+        D->a[q] += g.ph[1] - g.ph[0];
+        D->support[q] = 1;
+    } else {
+        const int q0 = g.q[0], q1 = g.q[1];
+        const double* t = g.ph;  // local j = b0 + 2 b1
+        D->c += t[0];
+        D->a[q0] += t[1] - t[0];
+        D->a[q1] += t[2] - t[0];
+        const int lo = std::min(q0, q1), hi = std::max(q0, q1);
+        D->b[(size_t)lo * n + hi] += t[3] - t[2] - t[1] + t[0];
+        D->support[q0] = 1;
+        D->support[q1] = 1;
+    }
+}
+
+bool touches(const DiagForm& D, const CGate& g) {
+    for (int i = 0; i < g.nq; ++i)
+        if (D.support[g.q[i]]) return true;
+    return false;
+}
+
+}  // namespace
+
+int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out, size_t* bad) {
+    out->clear();
+    out->reserve(count);
+    for (size_t i = 0; i < count; ++i) {
+        const int k = arity(g[i].type);
+        bool ok = k > 0 && (int)g[i].nq == k;
+        for (int a = 0; ok && a < k; ++a) {
+            if (g[i].q[a] >= (uint32_t)n) ok = false;
+            for (int b = 0; ok && b < a; ++b)
+                if (g[i].q[a] == g[i].q[b]) ok = false;
+        }
+        const uint32_t t = g[i].type;
+        const int np = t == SV_U3 ? 3 : ((t == SV_RX || t == SV_RY || t == SV_RZ || t == SV_P || t == SV_CP) ? 1 : 0);
+        for (int a = 0; ok && a < np; ++a)
+            if (!std::isfinite(g[i].p[a])) ok = false;
+        if (!ok) {
+            *bad = i;
+            return SV_EINVAL;
+        }
+        if (g[i].type == SV_MEASURE) continue;
+        CGate c;
+        make_canonical(g[i], &c);
+        out->push_back(c);
+    }
+    return SV_OK;
+}
+
+PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
+    PlanOptions po;
+    po.tile_m = dtype == SV_C64 ? 13 : 12;
+    if (opt) {
+        if (opt->k_max > 0) po.k_max = opt->k_max;
+        if (opt->tile_m > 0) po.tile_m = opt->tile_m;
+        po.planner = opt->planner;
+    }
+    po.k_max = std::max(2, std::min(kMaxK, po.k_max));
+    const int mmax = dtype == SV_C64 ? 14 : 13;
+    po.tile_m = std::max(1, std::min(mmax, po.tile_m));
+    po.tile_m = std::min(po.tile_m, n);
+    return po;
+}
+
+void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out) {
+    out->n = n;
+    out->dtype = dtype;
+    out->plain = false;
+    out->passes.clear();
+    out->gates = (int64_t)gates.size();
+    const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
+    // the tile holds the row bits plus room for any two-qubit gate
+    const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
+    const int kmax = std::min(po.k_max, m);
+
+    std::vector<int> remaining(gates.size());
+    for (size_t i = 0; i < gates.size(); ++i) remaining[i] = (int)i;
+    std::vector<char> inT(n), blocked(n);
+    std::vector<int> executed, deferred;
+
+    while (!remaining.empty()) {
+        // Scan 1: grow the tile set T from the front of the remaining list.
+        std::fill(inT.begin(), inT.end(), 0);
+        std::fill(blocked.begin(), blocked.end(), 0);
+        int cnt = 0, nblocked = 0;
+        for (int q = 0; q < L; ++q) inT[q] = 1, ++cnt;
+        auto block = [&](const CGate& g) {
+            for (int i = 0; i < g.nq; ++i)
+                if (!blocked[g.q[i]]) blocked[g.q[i]] = 1, ++nblocked;
+        };
+        for (int gi : remaining) {
+            const CGate& g = gates[gi];
+            bool tb = false;
+            for (int i = 0; i < g.nq; ++i) tb |= blocked[g.q[i]] != 0;
+            if (tb) { block(g); }
+            else if (g.kind == GK_DENSE) {
+                int need = 0;
+                for (int i = 0; i < g.nq; ++i) need += !inT[g.q[i]];
+                if (cnt + need <= m) {
+                    for (int i = 0; i < g.nq; ++i)
+                        if (!inT[g.q[i]]) inT[g.q[i]] = 1, ++cnt;
+                } else {
+                    block(g);
+                }
+            }
+            if (nblocked == n) break;
+        }
+        // Fill the tile up to m qubits (lowest unused qubits first): a wider
+        // tile costs nothing extra and keeps all passes the same shape.
+        for (int q = 0; q < n && cnt < m; ++q)
+            if (!inT[q]) inT[q] = 1, ++cnt;
+
+        // Scan 2: partition with the final T.
+        std::fill(blocked.begin(), blocked.end(), 0);
+        nblocked = 0;
+        executed.clear();
+        deferred.clear();
+        for (int gi : remaining) {
+            const CGate& g = gates[gi];
+            if (nblocked == n) { deferred.push_back(gi); continue; }
+            bool tb = false, fits = true;
+            for (int i = 0; i < g.nq; ++i) {
+                tb |= blocked[g.q[i]] != 0;
+                fits &= inT[g.q[i]] != 0;
+            }
+            if (!tb && (g.kind == GK_DIAG || fits)) executed.push_back(gi);
+            else { deferred.push_back(gi); block(g); }
+        }
+
+        HostPass pass;
+        for (int q = 0; q < n; ++q)
+            if (inT[q]) pass.tile.push_back(q);
+        pass.L = L;
+        pass.ngates = (int)executed.size();
+        for (int gi : executed) pass.type_count[gates[gi].type < 14 ? gates[gi].type : 13]++;
+
+        // Fuse the executed gates into dense blocks and diagonal runs.
+        Block B;
+        DiagForm D;
+        D.init(n);
+        bool dpend = false;
+        auto flushB = [&]() {
+            if (!B.active()) return;
+            HostOp op;
+            op.kind = OP_DENSE;
+            op.qubits = B.qubits;
+            op.mat = B.mat;
+            op.ngates = B.ngates;
+            pass.ops.push_back(std::move(op));
+            B = Block();
+        };
+        int dgates = 0;
+        auto flushD = [&]() {
+            if (!dpend) return;
+            HostOp op;
+            op.kind = OP_DIAG;
+            op.diag = D;
+            op.ngates = dgates;
+            pass.ops.push_back(std::move(op));
+            D.init(n);
+            dpend = false;
+            dgates = 0;
+        };
+        for (int gi : executed) {
+            const CGate& g = gates[gi];
+            if (g.kind == GK_DIAG) {
+                bool inB = B.active();
+                for (int i = 0; inB && i < g.nq; ++i) inB = B.pos(g.q[i]) >= 0;
+                // A diagonal gate on tile qubits may also widen the current
+                // block (diagonals commute with the pending run D, so moving
+                // it into the block is exact).
+                bool widen = false;
+                std::vector<int> u;
+                if (!inB && B.active()) {
+                    bool inT_all = true;
+                    u = B.qubits;
+                    for (int i = 0; i < g.nq; ++i) {
+                        inT_all &= inT[g.q[i]] != 0;
+                        if (B.pos(g.q[i]) < 0) u.push_back(g.q[i]);
+                    }
+                    widen = inT_all && (int)u.size() <= kmax;
+                }
+                if (widen) {
+                    std::sort(u.begin(), u.end());
+                    expand_block(&B, u);
+                }
+                if (inB || widen) {
+                    block_apply_diag(&B, g);
+                    B.ngates++;
+                } else {
+                    diag_add(&D, n, g);
+                    dpend = true;
+                    dgates++;
+                }
+                continue;
+            }
+            if (dpend && touches(D, g)) {
+                flushB();
+                flushD();
+            }
+            std::vector<int> u = B.qubits;
+            for (int i = 0; i < g.nq; ++i)
+                if (std::find(u.begin(), u.end(), g.q[i]) == u.end()) u.push_back(g.q[i]);
+            std::sort(u.begin(), u.end());
+            if (B.active() && (int)u.size() > kmax) {
+                flushB();
+                u.assign(g.q, g.q + g.nq);
+                std::sort(u.begin(), u.end());
+            }
+            expand_block(&B, u);
+            block_apply_dense(&B, g);
+            B.ngates++;
+        }
+        flushB();
+        flushD();
+        out->passes.push_back(std::move(pass));
+        remaining.swap(deferred);
+    }
+}
+
+void plan_plain(int n, int dtype, const std::vector<CGate>& gates, Plan* out) {
+    out->n = n;
+    out->dtype = dtype;
+    out->plain = true;
+    out->passes.clear();
+    out->plain_ops.clear();
+    out->gates = (int64_t)gates.size();
+    for (const CGate& g : gates) {
+        PlainOp op;
+        memset(&op, 0, sizeof(op));
+        op.q0 = g.q[0];
+        op.q1 = g.q[1];
+        if (g.kind == GK_DENSE && g.nq == 1) {
+            op.kind = PK_1Q;
+            for (int i = 0; i < 4; ++i) op.m[i] = g.m[i];
+        } else if (g.kind == GK_DIAG && g.nq == 1) {
+            if (g.ph[0] == 0.0) {
+                op.kind = PK_PHASE1;
+                op.m[0] = std::polar(1.0, g.ph[1]);
+            } else {
+                op.kind = PK_DIAG1;
+                op.m[0] = std::polar(1.0, g.ph[0]);
+                op.m[1] = std::polar(1.0, g.ph[1]);
+            }
+        } else if (g.type == SV_CX) {
+            op.kind = PK_CX;
+        } else if (g.type == SV_SWAP) {
+            op.kind = PK_SWAP;
+        } else {  // CZ, CP: phase on |11>
+            op.kind = PK_CPHASE;
+            op.m[0] = std::polar(1.0, g.ph[3]);
+        }
+        out->plain_ops.push_back(op);
+    }
+}
+
+void plan_summary(const Plan& p, sv_plan_info* info) {
+    memset(info, 0, sizeof(*info));
+    info->gates = p.gates;
+    const double N = ldexp(1.0, p.n);
+    const double s = p.dtype == SV_C64 ? 8.0 : 16.0;
+    double bytes = 0.0;
+    if (p.plain) {
+        info->passes = (int64_t)p.plain_ops.size();
+        for (const PlainOp& o : p.plain_ops) {
+            switch (o.kind) {
+            case PK_1Q: case PK_DIAG1: bytes += 2.0 * N * s; break;
+            case PK_CX: case PK_SWAP: case PK_PHASE1: bytes += N * s; break;
+            case PK_CPHASE: bytes += 0.5 * N * s; break;
+            }
+            info->dense_ops += (o.kind == PK_1Q || o.kind == PK_CX || o.kind == PK_SWAP);
+            info->diag_ops += !(o.kind == PK_1Q || o.kind == PK_CX || o.kind == PK_SWAP);
+        }
+        info->max_k = p.plain_ops.empty() ? 0 : 2;
+    } else {
+        info->passes = (int64_t)p.passes.size();
+        for (const HostPass& hp : p.passes) {
+            bytes += 2.0 * N * s;
+            for (const HostOp& o : hp.ops) {
+                if (o.kind == OP_DENSE) {
+                    info->dense_ops++;
+                    info->max_k = std::max<int64_t>(info->max_k, (int64_t)o.qubits.size());
+                } else {
+                    info->diag_ops++;
+                }
+            }
+        }
+    }
+    info->bytes_moved = (int64_t)bytes;
+}
+
+std::vector<float> pass_features(int n, int dtype, const HostPass& p) {
+    std::vector<float> f(kFeatures, 0.0f);
+    const int m = (int)p.tile.size();
+    f[0] = n / 34.0f;
+    f[1] = (float)dtype;
+    f[2] = m / 14.0f;
+    f[3] = p.L / 4.0f;
+    double flops = 0.0, msize = 0.0;
+    int ndiag = 0;
+    for (const HostOp& o : p.ops) {
+        if (o.kind == OP_DENSE) {
+            const int k = (int)o.qubits.size();
+            f[3 + k] += 1.0f / 8.0f;  // f[4..8]: dense blocks of width 1..5
+            flops += ldexp(1.0, k);
+            msize += ldexp(1.0, 2 * k);
+        } else {
+            ++ndiag;
+        }
+    }
+    f[9] = ndiag / 8.0f;
+    f[10] = p.ngates / 64.0f;
+    f[11] = (float)(flops / 64.0);
+    f[12] = (float)(msize / 1024.0);
+    f[13] = (float)p.ops.size() / 16.0f;
+    for (int t = 0; t < 14; ++t) f[14 + t] = p.type_count[t] / 16.0f;  // f[14..27]
+    f[28] = (float)(ldexp(1.0, n) * (dtype == SV_C64 ? 16.0 : 32.0) / ldexp(1.0, 36));
+    f[29] = (n - m) / 34.0f;
+    f[30] = 0.0f;
+    f[31] = 1.0f;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// Device blob: [PassDev x P][OpDev x O][mats (float2 or double2)][diag doubles]
+// ---------------------------------------------------------------------------
+namespace {
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Phase in turns reduced to [-0.5, 0.5).
+double red_turns(double rad) {
+    const double t = rad / (2.0 * kPi);
+    return t - floor(t + 0.5);
+}
+
+// A diagonal run, split for pass P (layout in DiagLayout).  Everything that
+// does not depend on the tile's non-tile bits is precomputed here in FP64:
+// the tile-internal quadratic tables over the lo (h bits) and hi (m-h bits)
+// halves of the tile index and the lo-hi coupling table.
+void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, double* d) {
+    const int m = P.m, no = P.nother;
+    const DiagLayout Lo(m, no);
+    auto B = [&](int qa, int qb) {
+        if (qa == qb) return 0.0;
+        const int lo = qa < qb ? qa : qb, hi = qa < qb ? qb : qa;
+        return D.b[(size_t)lo * n + hi];
+    };
+    d[Lo.c] = red_turns(D.c);
+    for (int t = 0; t < m; ++t) d[Lo.at + t] = red_turns(D.a[P.tq[t]]);
+    for (int o = 0; o < no; ++o) d[Lo.ao + o] = red_turns(D.a[P.oq[o]]);
+    for (int t = 0; t < m; ++t)
+        for (int o = 0; o < no; ++o) d[Lo.bo + t * no + o] = red_turns(B(P.tq[t], P.oq[o]));
+    for (int o = 0; o < no; ++o)
+        for (int o2 = 0; o2 < no; ++o2) d[Lo.boo + o * no + o2] = red_turns(B(P.oq[o], P.oq[o2]));
+    const int h = Lo.h, mh = Lo.mh;
+    for (int e = 0; e < (1 << h); ++e) {
+        double v = 0.0;
+        for (int b = 0; b < h; ++b)
+            for (int b2 = 0; b2 < b; ++b2)
+                if (((e >> b) & 1) && ((e >> b2) & 1)) v += B(P.tq[b], P.tq[b2]);
+        d[Lo.qlo + e] = red_turns(v);
+    }
+    for (int e = 0; e < (1 << mh); ++e) {
+        double v = 0.0;
+        for (int b = 0; b < mh; ++b)
+            for (int b2 = 0; b2 < b; ++b2)
+                if (((e >> b) & 1) && ((e >> b2) & 1)) v += B(P.tq[h + b], P.tq[h + b2]);
+        d[Lo.qhi + e] = red_turns(v);
+    }
+    for (int t = 0; t < mh; ++t)
+        for (int e = 0; e < (1 << h); ++e) {
+            double v = 0.0;
+            for (int b = 0; b < h; ++b)
+                if ((e >> b) & 1) v += B(P.tq[b], P.tq[h + t]);
+            d[Lo.rt + (t << h) + e] = red_turns(v);
+        }
+    (void)hp;
+}
+}  // namespace
+
+void serialise_plan(const Plan& p, PlanBlob* blob) {
+    const int n = p.n;
+    size_t nops = 0, nmat = 0, ndiag = 0;
+    for (const HostPass& hp : p.passes)
+        for (const HostOp& o : hp.ops) {
+            ++nops;
+            if (o.kind == OP_DENSE) nmat += o.mat.size();
+            else ndiag += diag_doubles((int)hp.tile.size(), n - (int)hp.tile.size());
+        }
+    const size_t csz = p.dtype == SV_C64 ? 8 : 16;
+    blob->npasses = (int)p.passes.size();
+    blob->pass_off = 0;
+    blob->op_off = align16(sizeof(PassDev) * p.passes.size());
+    blob->mat_off = align16(blob->op_off + sizeof(OpDev) * nops);
+    blob->diag_off = align16(blob->mat_off + csz * nmat);
+    const size_t total = align16(blob->diag_off + sizeof(double) * ndiag);
+    blob->bytes.assign(total, 0);
+    unsigned char* base = blob->bytes.data();
+    PassDev* pd = (PassDev*)(base + blob->pass_off);
+    OpDev* od = (OpDev*)(base + blob->op_off);
+    double* dg = (double*)(base + blob->diag_off);
+    size_t oi = 0, mi = 0, di = 0;
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    for (size_t pi = 0; pi < p.passes.size(); ++pi) {
+        const HostPass& hp = p.passes[pi];
+        PassDev& P = pd[pi];
+        memset(&P, 0, sizeof(P));
+        P.m = (int)hp.tile.size();
+        P.L = hp.L;
+        P.op_begin = (int)oi;
+        int loc[64];
+        for (int i = 0; i < 64; ++i) loc[i] = -1;
+        for (int i = 0; i < P.m; ++i) {
+            P.tq[i] = hp.tile[i];
+            loc[hp.tile[i]] = i;
+        }
+        P.nother = 0;
+        for (int q = 0; q < n; ++q)
+            if (loc[q] < 0) P.oq[P.nother++] = q;
+        for (const HostOp& o : hp.ops) {
+            OpDev& O = od[oi++];
+            memset(&O, 0, sizeof(O));
+            O.kind = o.kind;
+            O.ngates = o.ngates;
+            if (o.kind == OP_DENSE) {
+                O.k = (int)o.qubits.size();
+                for (int i = 0; i < O.k; ++i) O.lq[i] = loc[o.qubits[i]];
+                O.mat_off = (int)mi;
+                if (p.dtype == SV_C64) {
+                    float* f = (float*)(base + blob->mat_off) + 2 * mi;
+                    for (size_t e = 0; e < o.mat.size(); ++e) {
+                        f[2 * e] = (float)o.mat[e].real();
+                        f[2 * e + 1] = (float)o.mat[e].imag();
+                    }
+                } else {
+                    double* f = (double*)(base + blob->mat_off) + 2 * mi;
+                    for (size_t e = 0; e < o.mat.size(); ++e) {
+                        f[2 * e] = o.mat[e].real();
+                        f[2 * e + 1] = o.mat[e].imag();
+                    }
+                }
+                mi += o.mat.size();
+            } else {
+                O.k = 0;
+                O.diag_off = (int)di;
+                write_diag(o.diag, n, hp, P, dg + di);
+                di += diag_doubles(P.m, P.nother);
+            }
+        }
+        P.op_end = (int)oi;
+    }
+}
+
+}  // namespace sv

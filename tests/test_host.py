@@ -1,0 +1,54 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports
+every symbol include/sv.h declares; the planner's host logic."""
+import numpy as np
+import pytest
+
+import paper_2504_03967_gb300 as S
+import workloads as W
+from paper_2504_03967_gb300 import build as B
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+
+
+def test_exports_every_declared_symbol():
+    decl = S.declared_symbols()
+    assert len(decl) >= 20
+    missing = sorted(set(decl) - set(S.exported_symbols()))
+    assert not missing, missing
+
+
+def test_version_and_feature_count():
+    assert S.sv_version() >= 100
+    assert S.sv_feature_count() == 32
+
+
+def test_plan_qft_counts():
+    info = S.sv_plan_circuit(28, S.C64, W.qft(28))
+    assert info["gates"] == 420
+    assert 1 <= info["passes"] <= 8
+    assert info["max_k"] <= 5
+    assert info["bytes_moved"] == info["passes"] * 16 * (1 << 28)
+    plain = S.sv_plan_circuit(28, S.C64, W.qft(28), planner=S.PLAN_PLAIN)
+    assert plain["passes"] == 420
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_plan_respects_k(k):
+    info = S.sv_plan_circuit(20, S.C64, W.random_u3_cx(20, 10, 3), k_max=k)
+    assert info["max_k"] <= k
+
+
+def test_plan_validation_errors():
+    with pytest.raises(S.SVError) as ei:
+        S.sv_plan_circuit(4, S.C64, W.gates_from_list([(W.H, (4,), ())]))
+    assert ei.value.code == -1
+    with pytest.raises(S.SVError):
+        S.sv_plan_circuit(0, S.C64, W.qft(3))
+    with pytest.raises(S.SVError):
+        S.sv_plan_circuit(34, S.C128, W.qft(3))
+    g = W.gates_from_list([(W.RX, (0,), (float("nan"),))])
+    with pytest.raises(S.SVError):
+        S.sv_plan_circuit(2, S.C64, g)
