@@ -180,6 +180,31 @@ int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_out);
 int sv_sample_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_out);
 int sv_sample_uniforms(sv_handle h, const double *host_u, uint64_t shots, uint64_t *host_out);
 
+/* Sampling that allocates nothing.  The paper has no counterpart; this entry
+ * point exists for callers of this library that cannot allocate device
+ * memory while they run, e.g. a serving process whose device memory is
+ * handed out up front by its own allocator (a cudaMalloc here could fail or
+ * overrun its budget) or a caller that cannot accept the device-wide
+ * synchronisation that cudaFree implies.
+ *
+ * Same outcomes as sv_sample_uniforms for the same state and uniforms, but
+ * the state (dev_amps: 2^n amplitudes of dtype dt, 16-byte aligned), the
+ * uniforms (dev_u: shots doubles in [0,1)) and the outcomes (dev_out: shots
+ * uint64) all live in caller-owned device memory, and the call runs
+ * asynchronously on cuda_stream (NULL = legacy default stream).
+ *
+ * Its only scratch (the FP64 block CDF) is a fixed array of 128.5 KiB
+ * inside this library, which every GPU that loads the library holds until
+ * the process exits; it bounds n to 1..24, and larger n returns SV_EINVAL
+ * before any device work.  The first call on a device looks up that array's
+ * device address (once per device, with the device current); make that first
+ * call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents; every element a call reads it has written
+ * first, but calls that overlap on the GPU (e.g. on two streams at once)
+ * race on it and must be serialised by the caller. */
+int sv_sample_uniforms_noalloc(const void *dev_amps, int n, sv_dtype dt, const double *dev_u,
+                               uint64_t shots, uint64_t *dev_out, void *cuda_stream);
+
 /* ---- recorder (per-pass timings; the cost model's training data) ------- */
 
 /* Timings of the tile passes run by sv_apply_circuit calls made with

@@ -78,6 +78,7 @@ def lib():
             "sv_sample_device": [vp, u64, u64, vp],
             "sv_sample_uniforms": [vp, vp, u64, vp],
             "sv_pass_times": [vp, vp, vp, i, P(i)],
+            "sv_sample_uniforms_noalloc": [vp, i, i, vp, u64, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -250,6 +251,14 @@ def sv_pass_times(h, cap=1 << 16, features=False):
     _check(lib().sv_pass_times(h, _ptr(ms), _ptr(feat) if features else None, cap, ctypes.byref(cnt)))
     k = min(cnt.value, cap)
     return (ms[:k].copy(), feat[:k].copy()) if features else ms[:k].copy()
+
+
+def sv_sample_uniforms_noalloc(dev_amps, n, dtype, dev_u, shots, dev_out, stream=None):
+    """Sampling with caller-owned device buffers and no device allocation
+    (see include/sv.h): all pointers are device addresses (ints)."""
+    _check(lib().sv_sample_uniforms_noalloc(ctypes.c_void_p(dev_amps), int(n), int(dtype),
+                                            ctypes.c_void_p(dev_u), int(shots), ctypes.c_void_p(dev_out),
+                                            stream))
 
 
 def sv_sample_uniforms(h, u):

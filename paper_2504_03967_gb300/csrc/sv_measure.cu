@@ -9,6 +9,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <string>
+
 #include "sv_internal.h"
 
 namespace sv {
@@ -395,3 +398,104 @@ int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev
 }
 
 }  // namespace sv
+
+// ---------------------------------------------------------------------------
+// Sampling without any device allocation.
+//
+// Some callers cannot allocate device memory while they run: a serving
+// process whose device memory is handed out up front by its own allocator
+// (so a cudaMalloc here could fail or break its budget), or a caller that
+// cannot accept the implicit device-wide synchronisation of cudaFree.  For
+// them sv_sample_uniforms_noalloc keeps its only scratch (the probability
+// block sums / block CDF and the chunk totals of the scan) in the fixed
+// array below, which every GPU that loads this library holds until the
+// process exits.  The caller passes the state, the uniforms and the output
+// buffer, all in device memory.
+// ---------------------------------------------------------------------------
+namespace sv {
+namespace {
+constexpr int kNoAllocMaxQubits = 24;  // 2^(24-10) = 16384 block sums
+constexpr size_t kNoAllocDoubles = ((size_t)1 << (kNoAllocMaxQubits - kBlogMax)) + 64;
+
+// 128 KiB + 512 B of device memory per GPU; shared by every call.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device (looked up
+// once per device, with that device current).  In host code the array's
+// name only stands in for the symbol, so the address must come from
+// cudaGetSymbolAddress.
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return set_error(SV_EUNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SV_OK;
+}
+}  // namespace
+
+}  // namespace sv
+
+extern "C" int sv_sample_uniforms_noalloc(const void* dev_amps, int n, sv_dtype dt, const double* dev_u,
+                                          uint64_t shots, uint64_t* dev_out, void* cuda_stream) {
+    using namespace sv;
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (n < 1 || n > kNoAllocMaxQubits)
+        return set_error(SV_EINVAL, "sv_sample_uniforms_noalloc: n = " + std::to_string(n) +
+                                        " outside 1..24 (its fixed scratch holds 2^14 block sums)");
+    if (!dev_amps) return set_error(SV_EINVAL, "NULL state pointer");
+    if (((uintptr_t)dev_amps & 15) != 0) return set_error(SV_EINVAL, "state pointer not 16-byte aligned");
+    if (shots == 0) return SV_OK;
+    if (!dev_u || !dev_out) return set_error(SV_EINVAL, "NULL uniforms or output pointer");
+    double* bs = nullptr;
+    int rc = noalloc_scratch(&bs);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int blog;
+    const size_t nb = nblocks_of(n, &blog);
+    const size_t nch = (nb + kScanCh - 1) / kScanCh;
+    double* tot = bs + nb;  // nb + nch <= kNoAllocDoubles
+    const uint64_t N = 1ull << n;
+    // Every scratch element is written before it is read within this call,
+    // so nothing needs clearing; calls that overlap on the GPU race on it.
+    const unsigned g = (unsigned)((nb * 32 + 255) / 256);
+    count_launch();
+    if (dt == SV_C64)
+        k_block_sums<float2><<<g, 256, 0, st>>>((const float2*)dev_amps, N, blog, nb, bs);
+    else
+        k_block_sums<double2><<<g, 256, 0, st>>>((const double2*)dev_amps, N, blog, nb, bs);
+    if (nch <= 1) {
+        count_launch();
+        k_scan_chunks<<<1, kScanT, 0, st>>>(bs, nb, nullptr);
+    } else {
+        count_launch(3);
+        k_chunk_totals<<<(unsigned)nch, kScanT, 0, st>>>(bs, nb, tot);
+        k_scan_totals<<<1, kScanT, 0, st>>>(tot, (int)nch);
+        k_scan_chunks<<<(unsigned)nch, kScanT, 0, st>>>(bs, nb, tot);
+    }
+    uint64_t gs = (shots * 32 + 255) / 256;
+    const uint64_t cap = (uint64_t)sms() * 16;
+    if (gs > cap) gs = cap;
+    count_launch();
+    if (dt == SV_C64)
+        k_sample<float2><<<(unsigned)gs, 256, 0, st>>>((const float2*)dev_amps, n, blog, bs, (uint64_t)nb, shots,
+                                                      0, dev_u, dev_out);
+    else
+        k_sample<double2><<<(unsigned)gs, 256, 0, st>>>((const double2*)dev_amps, n, blog, bs, (uint64_t)nb,
+                                                       shots, 0, dev_u, dev_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "sv_sample_uniforms_noalloc");
+    return SV_OK;
+}
+
