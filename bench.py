@@ -168,6 +168,7 @@ def main():
     ap.add_argument("--planner", default="greedy", choices=["greedy", "mlp", "plain"])
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--tile-m", type=int, default=0)
+    ap.add_argument("--tensor", type=int, default=0, help="1: tensor cores for c64 blocks of 3..5 qubits")
     ap.add_argument("--shots", type=int, default=100)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -206,7 +207,7 @@ def main():
 
     def step(i, pl, record):
         S.sv_init_basis(h, x)
-        S.sv_apply_circuit(h, g, planner=pl, k_max=args.k, tile_m=args.tile_m, record=record)
+        S.sv_apply_circuit(h, g, planner=pl, k_max=args.k, tile_m=args.tile_m, record=record, tensor=args.tensor)
         S.sv_sample_device(h, args.shots, 1000 + i, shots_out.data_ptr())
         S.sv_expect_z_device(h, ez_out.data_ptr())
 
@@ -268,7 +269,7 @@ def main():
         gh = np.ascontiguousarray(g)
         for i in range(2):
             S.sv_init_basis(h2, x)
-            S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m)
+            S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor)
             S.sv_sample(h2, args.shots, i)
             S.sv_expect_z(h2)
         torch.cuda.synchronize()
@@ -276,7 +277,7 @@ def main():
         K = max(3, args.steps // 2)
         for i in range(K):
             S.sv_init_basis(h2, x)
-            S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m)
+            S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor)
             S.sv_sample(h2, args.shots, 1000 + i)
             S.sv_expect_z(h2)
         e2e_ms = 1e3 * (time.perf_counter() - t0) / K
@@ -289,7 +290,7 @@ def main():
     if args.workload.startswith("qft"):
         st = state.view(torch.complex64 if dt == S.C64 else torch.complex128)
         S.sv_init_basis(h, x)
-        S.sv_apply_circuit(h, g, planner=planner, k_max=args.k, tile_m=args.tile_m)
+        S.sv_apply_circuit(h, g, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor)
         torch.cuda.synchronize()
         rng = np.random.default_rng(0)
         ys = rng.integers(0, 1 << n, size=1 << 16)

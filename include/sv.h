@@ -89,15 +89,18 @@ typedef enum {
 
 /* Options for sv_apply_circuit; pass NULL for defaults.  A zero field means
  * "default".  k_max: widest fused dense block, 1..5 (App. D.2: gate fusion =
- * 5); tile_m: qubits per shared-memory tile pass (c64 10..14, c128 9..13);
+ * 5); tile_m: qubits per shared-memory tile pass (c64 9..14, c128 9..13);
  * planner: sv_planner; record: store per-pass CUDA-event times for the cost
- * model (sv_record_*). */
+ * model (sv_pass_times); tensor: 1 = complex64 dense blocks of 3..5 qubits
+ * run on the tensor cores (3xTF32, FP32 accumulation), -1 = CUDA cores only,
+ * 0 = the library's default (CUDA cores; the cost-model planner may choose). */
 typedef struct {
     int k_max;
     int tile_m;
     int planner;
     int record;
-    int reserved[4];
+    int tensor;
+    int reserved[3];
 } sv_options;
 
 /* Plan summary returned by sv_plan_circuit (host only, no device work). */

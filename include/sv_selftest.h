@@ -1,0 +1,33 @@
+/*
+ * libsv self-test entry points (not part of the simulation API).  They check
+ * the hardware building blocks the simulator's kernels rely on, with inputs
+ * the caller supplies, so a test can compare against its own computation.
+ */
+#ifndef SV_SELFTEST_H_
+#define SV_SELFTEST_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One 5th-generation tensor-core product on the current device, the building
+ * block of the tensor-core dense apply (fused blocks of 4-5 qubits as dense
+ * 2^k x 2^k products, App. D.2 "gate fusion = 5"):
+ *   D[m][n] = sum_k A[m][k] * B[n][k],  m < 128, n < 64, k < 64,
+ * with A (host, 128 x 64 row-major) held in tensor memory, B (host, 64 x 64
+ * row-major, n-th row = K values) placed in shared memory in the no-swizzle
+ * K-major core-matrix layout with byte strides kstride (between 4-element K
+ * groups) and nstride (between 8-row groups), kind::tf32 inputs, FP32
+ * accumulation.  swap_fields = 1 puts the two strides into the descriptor's
+ * fields the other way round (for diagnosing the layout).  D (host, 128 x 64)
+ * receives the result; *host_status = 0 on success, 1 if the bounded wait for
+ * the tensor core gave up.  Returns SV_OK, SV_EINVAL (strides out of range)
+ * or SV_ECUDA. */
+int sv_selftest_tc_tf32(const float *host_a, const float *host_b, float *host_d, int kstride, int nstride,
+                        int swap_fields, int *host_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_SELFTEST_H_ */

@@ -38,7 +38,7 @@ class SVError(RuntimeError):
 
 class sv_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
-                ("record", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class sv_plan_info(ctypes.Structure):
@@ -112,9 +112,9 @@ def _check(rc):
     return rc
 
 
-def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0):
+def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0):
     o = sv_options()
-    o.k_max, o.tile_m, o.planner, o.record = k_max, tile_m, planner, record
+    o.k_max, o.tile_m, o.planner, o.record, o.tensor = k_max, tile_m, planner, record, tensor
     return o
 
 
@@ -186,15 +186,15 @@ def sv_store_state(h):
     return a
 
 
-def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0):
+def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, record)
+    o = _opts(k_max, tile_m, planner, record, tensor)
     _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
 
 
-def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY):
+def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, tensor=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner)
+    o = _opts(k_max, tile_m, planner, 0, tensor)
     info = sv_plan_info()
     _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}

@@ -108,10 +108,19 @@ int fail_state(sv_handle h, int rc) {
     return rc;
 }
 
+// Copy a result to the host and wait; also reads the device error word that
+// the kernels' bounded waits set when they give up (SV_ETIMEOUT).
 int sync_d2h(sv_handle h, void* host, const void* dev, size_t bytes, const char* what) {
+    int dev_err = 0;
     cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && h->err.ptr)
+        e = cudaMemcpyAsync(&dev_err, h->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, what));
+    if (dev_err) {
+        cudaMemsetAsync(h->err.ptr, 0, sizeof(int), h->stream);
+        return fail_state(h, set_error(SV_ETIMEOUT, "a bounded device wait gave up (tensor-core pass)"));
+    }
     return SV_OK;
 }
 
@@ -166,6 +175,7 @@ int sv_free(sv_handle h) {
     if (h->plan_dev.ptr) cudaFree(h->plan_dev.ptr);
     if (h->red.ptr) cudaFree(h->red.ptr);
     if (h->out_dev.ptr) cudaFree(h->out_dev.ptr);
+    if (h->err.ptr) cudaFree(h->err.ptr);
     if (h->host_pin.ptr) cudaFreeHost(h->host_pin.ptr);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->upload_ev) cudaEventDestroy(h->upload_ev);
@@ -279,6 +289,12 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     if (rc) return rc;
     rc = ensure_scratch(&h->plan_dev, blob.bytes.size(), h->stream);
     if (rc) return rc;
+    if (!h->err.ptr) {
+        rc = ensure_scratch(&h->err, 64, h->stream);
+        if (rc) return rc;
+        e = cudaMemsetAsync(h->err.ptr, 0, 64, h->stream);
+        if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "error word"));
+    }
     memcpy(h->host_pin.ptr, blob.bytes.data(), blob.bytes.size());
     e = cudaMemcpyAsync(h->plan_dev.ptr, h->host_pin.ptr, blob.bytes.size(), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "plan upload"));

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "sv_internal.h"
+#include "sv_tc.cuh"
 
 namespace sv {
 
@@ -300,21 +301,45 @@ __device__ __forceinline__ void tile_diag(V* __restrict__ tile, const PassDev& P
     }
     for (int e = tid; e < (mh << h); e += blockDim.x) Rt[e] = (R)dd[Lo.rt + e];
     __syncthreads();
-    const int lomask = (1 << h) - 1;
-#pragma unroll 4
-    for (int i = tid; i < (1 << m); i += blockDim.x) {
-        const int lo = i & lomask, hi = i >> h;
-        R ph = Llo[lo] + Lhi[hi];
+    // Amplitude i = tid + 256 k: its lo half (tid mod 2^h) is fixed per thread
+    // because 2^h divides the 256-thread block, and its hi half is
+    // hi0 + k * 2^(8-h).  The lo-hi coupling terms for this lo therefore sit
+    // in registers, and the coupling of the k bits is two table entries.
+    static_assert(kPassThreads == 256, "diagonal runs assume 256 threads");
+    const int lo = tid & ((1 << h) - 1);
+    const int sb = 8 - h;  // hi bits fixed per thread
+    const int hi0 = tid >> h;
+    R ph0 = Llo[lo];
+    for (int t = 0; t < sb && t < mh; ++t)
+        if ((hi0 >> t) & 1) ph0 += Rt[(t << h) + lo];
+    R Rk[7];  // coupling of bit b of k (hi bit sb + b) with this lo
 #pragma unroll
-        for (int t = 0; t < 7; ++t)
-            if (t < mh && ((hi >> t) & 1)) ph += Rt[(t << h) + lo];
-        ph = frac_r(ph);
-        R sn, cs;
-        sincos_turns(ph, &sn, &cs);
-        V f;
-        f.x = cs;
-        f.y = sn;
-        tile[i] = cmul(f, tile[i]);
+    for (int b = 0; b < 7; ++b) Rk[b] = (sb + b < mh) ? Rt[((sb + b) << h) + lo] : (R)0;
+    R C3[8];  // coupling of the three low bits of k
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        C3[j] = ((j & 1) ? Rk[0] : (R)0) + ((j & 2) ? Rk[1] : (R)0) + ((j & 4) ? Rk[2] : (R)0);
+    const int K = m >= 8 ? (1 << (m - 8)) : (tid < (1 << m) ? 1 : 0);
+    for (int kh = 0; kh < K; kh += 8) {
+        R chi = ph0;
+#pragma unroll
+        for (int b = 3; b < 7; ++b)
+            if ((kh >> b) & 1) chi += Rk[b];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = kh + j;
+            if (k < K) {
+                const int i = tid + (k << 8);
+                R ph = chi + C3[j] + Lhi[hi0 + (k << sb)];
+                ph = frac_r(ph);
+                R sn, cs;
+                sincos_turns(ph, &sn, &cs);
+                V f;
+                f.x = cs;
+                f.y = sn;
+                tile[i] = cmul(f, tile[i]);
+            }
+        }
     }
 }
 
@@ -351,17 +376,134 @@ __host__ __device__ inline int diag_table_elems(int m) {
     return (1 << h) + (1 << mh) + (mh << h);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kPassThreads) k_pass(typename CT<R>::V* __restrict__ psi, int n,
+// Tensor-core dense block of K qubits (complex64 only).  The CTA's 256
+// threads form two groups of four warps; each group owns 128 TMEM lanes and
+// 4*2^K columns (A_hi, A_lo: 2^K each; accumulator: 2^(K+1)).  Lane 2s+c of a
+// group holds component c (0 = real, 1 = imaginary) of slice s, so one MMA
+// round covers 64 slices per group:
+//   acc[(s,c)][n] = sum_j X_c[s][j] B[n][j],  B = [Ur; Ui]  (N = 2^(K+1))
+// with 3xTF32 products (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulate),
+// and the complex result y_r = (Ur Xr - Ui Xi) + i (Ui Xr + Ur Xi) is formed
+// by exchanging accumulator halves between the two lanes of each slice.
+template <int K>
+__device__ __forceinline__ void tile_dense_tc(float2* __restrict__ tile, int m, const OpDev& op,
+                                              const float* __restrict__ sB, uint32_t tmem_base, uint64_t* mbar,
+                                              uint32_t* phase, int* s_abort, int* __restrict__ err) {
+    constexpr int D = 1 << K;
+    constexpr int N = 2 * D;
+    constexpr uint32_t IDESC = tc::idesc_tf32(128, N);
+    constexpr uint32_t SBO = (uint32_t)(D / 4) * 128u;
+    constexpr int CH = D < 16 ? D : 16;  // TMEM columns per load/store
+    const int tid = threadIdx.x;
+    const int grp = tid >> 7;
+    const int row = tid & 127;
+    const int c = row & 1;
+    const uint32_t col0 = (uint32_t)grp * 4u * D;
+    const uint32_t lane_addr = tmem_base + ((uint32_t)(row & ~31) << 16);
+    int bitv[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) bitv[i] = 1 << op.lq[i];
+    const int nslices = 1 << (m - K);
+    float* tw = reinterpret_cast<float*>(tile);
+    const uint32_t sb_hi = tc::smem_u32(sB), sb_lo = sb_hi + (uint32_t)(N * D * 4);
+    for (int s0 = 0; s0 < nslices; s0 += 128) {
+        const int s = s0 + grp * 64 + (row >> 1);
+        const bool act = s < nslices;
+        int base = s;
+#pragma unroll
+        for (int i = 0; i < K; ++i) base = (int)insert_zero((uint64_t)base, op.lq[i]);
+#pragma unroll
+        for (int j0 = 0; j0 < D; j0 += CH) {
+            uint32_t vh[CH], vl[CH];
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                const int j = j0 + jj;
+                int o = 0;
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+                    if ((j >> i) & 1) o += bitv[i];
+                // 3xTF32 split with rounding to nearest, so the products are
+                // not biased toward zero (the tensor core itself truncates)
+                const float a = act ? tw[2 * (base + o) + c] : 0.0f;
+                const uint32_t ah = tc::to_tf32(a);
+                vh[jj] = ah;
+                vl[jj] = tc::to_tf32(a - __uint_as_float(ah));
+            }
+            if (CH == 16) {
+                tc::tmem_st16(lane_addr + col0 + j0, vh);
+                tc::tmem_st16(lane_addr + col0 + D + j0, vl);
+            } else {
+                tc::tmem_st8(lane_addr + col0 + j0, vh);
+                tc::tmem_st8(lane_addr + col0 + D + j0, vl);
+            }
+        }
+        tc::tmem_wait_st();
+        tc::fence_before();
+        tc::named_barrier(1 + grp, 128);
+        tc::fence_after();
+        if (s_abort[grp]) break;  // uniform across the group (read after the barrier)
+        if (row == 0) {
+            const uint32_t dcol = tmem_base + col0 + 2 * D, ah = tmem_base + col0, al = tmem_base + col0 + D;
+#pragma unroll
+            for (int kk = 0; kk < D / 8; ++kk)
+                tc::mma_tf32_ts(dcol, ah + 8 * kk, tc::sdesc_noswz(sb_hi + kk * 256, 128, SBO), IDESC, kk > 0);
+#pragma unroll
+            for (int kk = 0; kk < D / 8; ++kk)
+                tc::mma_tf32_ts(dcol, ah + 8 * kk, tc::sdesc_noswz(sb_lo + kk * 256, 128, SBO), IDESC, 1);
+#pragma unroll
+            for (int kk = 0; kk < D / 8; ++kk)
+                tc::mma_tf32_ts(dcol, al + 8 * kk, tc::sdesc_noswz(sb_hi + kk * 256, 128, SBO), IDESC, 1);
+            tc::mma_commit(&mbar[grp]);
+        }
+        const bool ok = tc::mbar_wait_bounded(&mbar[grp], *phase & 1u, 1u << 22);
+        *phase += 1;
+        tc::fence_after();
+        if (!ok) {
+            s_abort[grp] = 1;
+            atomicExch(err, 1);
+            continue;
+        }
+#pragma unroll
+        for (int r0 = 0; r0 < D; r0 += CH) {
+            uint32_t own[CH], oth[CH];
+            if (CH == 16) {
+                tc::tmem_ld16(lane_addr + col0 + 2 * D + r0, own);
+                tc::tmem_ld16(lane_addr + col0 + 3 * D + r0, oth);
+            } else {
+                tc::tmem_ld8(lane_addr + col0 + 2 * D + r0, own);
+                tc::tmem_ld8(lane_addr + col0 + 3 * D + r0, oth);
+            }
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int rr = 0; rr < CH; ++rr) {
+                const float partner = __shfl_xor_sync(0xffffffffu, __uint_as_float(oth[rr]), 1);
+                const float y = __uint_as_float(own[rr]) + (c ? partner : -partner);
+                const int r = r0 + rr;
+                int o = 0;
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+                    if ((r >> i) & 1) o += bitv[i];
+                if (act) tw[2 * (base + o) + c] = y;
+            }
+        }
+    }
+}
+
+template <typename R, bool TC>
+__global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R>::V* __restrict__ psi, int n,
                                                       const PassDev* __restrict__ pdp,
                                                       const OpDev* __restrict__ ops,
                                                       const typename CT<R>::V* __restrict__ mats,
-                                                      const double* __restrict__ diags) {
+                                                      const double* __restrict__ diags,
+                                                      const float* __restrict__ tcmats, int* __restrict__ err) {
     using V = typename CT<R>::V;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
     __shared__ R s_ap[kMaxTileM];
     __shared__ double s_c;
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ int s_abort[2];
     {
         const int* src = (const int*)pdp;
         int* dst = (int*)&P;
@@ -369,10 +511,35 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(typename CT<R>::V* __rest
     }
     __syncthreads();
     const int m = P.m, L = P.L;
+    const int tc_k = TC ? P.tc_k : 0;
+    const uint32_t tc_cols = tc_k ? (8u << tc_k) : 0u;  // two groups x 4 * 2^k columns
+    if (tc_k) {
+        if (threadIdx.x < 32) {
+            tc::tmem_alloc(&s_taddr, tc_cols);
+            tc::tmem_relinquish();
+        }
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&s_mbar[0], 1);
+            tc::mbar_init(&s_mbar[1], 1);
+            tc::fence_mbar_init();
+            s_abort[0] = s_abort[1] = 0;
+        }
+        tc::fence_before();
+    }
     V* tile = (V*)smem;
     uint32_t* rowoff = (uint32_t*)(smem + (sizeof(V) << m));
     const int nrows = 1 << (m - L);
-    R* work = (R*)(rowoff + ((nrows + 3) & ~3));
+    // [tile | rowoff | resident tensor-core B operands | work]
+    const size_t res_off = ((sizeof(V) << m) + 4 * (size_t)nrows + 127) & ~(size_t)127;
+    const int tc_res = TC ? P.tc_res : 0;
+    float* bres = (float*)(smem + res_off);
+    R* work = (R*)(smem + res_off + ((4 * (size_t)tc_res + 127) & ~(size_t)127));
+    if (tc_res) {
+        const float* src = tcmats + P.tc_base;
+        for (int e = threadIdx.x; e < tc_res / 4; e += blockDim.x) cp_async16(bres + 4 * e, src + 4 * e);
+        cp_async_wait_all();
+        tc::fence_proxy_async();
+    }
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
         uint32_t o = 0;
         for (int b = 0; b < m - L; ++b)
@@ -380,6 +547,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(typename CT<R>::V* __rest
         rowoff[r] = o;
     }
     __syncthreads();
+    if (tc_k) tc::fence_after();
+    const uint32_t tmem_base = tc_k ? s_taddr : 0u;
+    uint32_t phase = 0;
     const uint64_t ntiles = 1ull << (n - m);
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         uint64_t base = 0;
@@ -388,7 +558,26 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(typename CT<R>::V* __rest
         __syncthreads();
         for (int oi = P.op_begin; oi < P.op_end; ++oi) {
             const OpDev op = ops[oi];
-            if (op.kind == OP_DENSE) {
+            if (op.kind == OP_DENSE && op.tc) {
+                if constexpr (TC && sizeof(R) == 4) {
+                    const float* sB = bres + (op.tc_off - P.tc_base);
+                    if (!tc_res) {  // B operands [hi | lo] of this block into shared memory
+                        const int nch = tc_floats(op.k) / 4;
+                        const float* src = tcmats + op.tc_off;
+                        for (int e = threadIdx.x; e < nch; e += blockDim.x)
+                            cp_async16((float*)work + 4 * e, src + 4 * e);
+                        cp_async_wait_all();
+                        tc::fence_proxy_async();
+                        __syncthreads();
+                        sB = (const float*)work;
+                    }
+                    switch (op.k) {
+                    case 3: tile_dense_tc<3>(tile, m, op, sB, tmem_base, s_mbar, &phase, s_abort, err); break;
+                    case 4: tile_dense_tc<4>(tile, m, op, sB, tmem_base, s_mbar, &phase, s_abort, err); break;
+                    default: tile_dense_tc<5>(tile, m, op, sB, tmem_base, s_mbar, &phase, s_abort, err); break;
+                    }
+                }
+            } else if (op.kind == OP_DENSE) {
                 V* sU = (V*)work;
                 const int DD = 1 << (2 * op.k);
                 for (int e = threadIdx.x; e < DD; e += blockDim.x) sU[e] = mats[op.mat_off + e];
@@ -408,16 +597,28 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(typename CT<R>::V* __rest
         store_tile(tile, psi, base, rowoff, m, L);
         __syncthreads();
     }
+    if (tc_k) {
+        tc::fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tc::tmem_dealloc(tmem_base, tc_cols);
+    }
 }
 
-size_t pass_smem_bytes(int dtype, int m, int L) {
+size_t pass_smem_bytes(int dtype, int m, int L, int tc_k, int tc_res) {
     const size_t csz = dtype == SV_C64 ? 8 : 16;
     const size_t rsz = dtype == SV_C64 ? 4 : 8;
     const int nrows = 1 << (m - L);
     size_t work = csz * (1 << (2 * kMaxK));
     const size_t dt = rsz * diag_table_elems(m);
     if (dt > work) work = dt;
-    return (csz << m) + 4 * (size_t)((nrows + 3) & ~3) + work;
+    if (tc_k && !tc_res && (size_t)tc_floats(tc_k) * 4 > work) work = (size_t)tc_floats(tc_k) * 4;
+    size_t total = (((csz << m) + 4 * (size_t)nrows + 127) & ~(size_t)127) +
+                   ((4 * (size_t)tc_res + 127) & ~(size_t)127) + work;
+    // Blocks of 5 qubits take 256 TMEM columns per CTA: at most two CTAs may
+    // share an SM (512 columns), so such passes ask for enough shared memory
+    // to keep a third one away.
+    if (tc_k >= 5 && total < 80 * 1024) total = 80 * 1024;
+    return total;
 }
 
 // ---------------------------------------------------------------------------
@@ -497,36 +698,42 @@ cudaError_t launch_plain_op(sv_state* h, const PlainOp& op) {
     return plain_op_t<double2>(h, op);
 }
 
-template <typename R>
+template <typename R, bool TC>
 static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
     using V = typename CT<R>::V;
     const int m = (int)hp.tile.size();
-    const size_t smem = pass_smem_bytes(h->dtype, m, hp.L);
-    static bool attr_set[2] = {false, false};
-    const int di = h->dtype == SV_C64 ? 0 : 1;
-    if (!attr_set[di]) {
-        cudaError_t e = cudaFuncSetAttribute(k_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pass_smem_bytes(h->dtype, h->dtype == SV_C64 ? 14 : 13, 1));
+    const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    const size_t smem = pass_smem_bytes(h->dtype, m, hp.L, TC ? pdh->tc_k : 0, TC ? pdh->tc_res : 0);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_pass<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pass_smem_bytes(h->dtype, h->dtype == SV_C64 ? 14 : 13, 1, 5, kTcResidentFloats));
         if (e != cudaSuccess) return e;
-        attr_set[di] = true;
+        attr_set = true;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R>, kPassThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R, TC>, kPassThreads, smem);
     if (per_sm < 1) per_sm = 1;
+    if (TC && pdh->tc_k >= 5 && per_sm > 2) per_sm = 2;  // 256 TMEM columns per CTA
     const uint64_t ntiles = 1ull << (h->n - m);
     uint64_t grid = (uint64_t)num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
     const unsigned char* b = (const unsigned char*)blob_dev;
     count_launch();
-    k_pass<R><<<(unsigned)grid, kPassThreads, smem, h->stream>>>(
+    k_pass<R, TC><<<(unsigned)grid, kPassThreads, smem, h->stream>>>(
         (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, (const OpDev*)(b + blob.op_off),
-        (const V*)(b + blob.mat_off), (const double*)(b + blob.diag_off));
+        (const V*)(b + blob.mat_off), (const double*)(b + blob.diag_off), (const float*)(b + blob.tc_off),
+        (int*)h->err.ptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
-    if (h->dtype == SV_C64) return pass_t<float>(h, blob_dev, blob, pass, hp);
-    return pass_t<double>(h, blob_dev, blob, pass, hp);
+    const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    if (h->dtype == SV_C64) {
+        if (pdh->tc_k) return pass_t<float, true>(h, blob_dev, blob, pass, hp);
+        return pass_t<float, false>(h, blob_dev, blob, pass, hp);
+    }
+    return pass_t<double, false>(h, blob_dev, blob, pass, hp);
 }
 
 }  // namespace sv

@@ -98,12 +98,14 @@ struct Plan {
     std::vector<HostPass> passes;
     std::vector<PlainOp> plain_ops;
     int64_t gates = 0;
+    int tensor = -1;  // 0: dense blocks of k >= kMinTcK go to the tensor cores
 };
 
 struct PlanOptions {
     int k_max = 5;
     int tile_m = 13;
     int planner = SV_PLAN_GREEDY;
+    int tensor = -1;  // 0: tensor cores for c64 blocks of k >= 3; -1: CUDA cores only
 };
 
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
@@ -125,16 +127,34 @@ struct OpDev {
     int kind;
     int k;
     int mat_off;   // dense: element offset into the matrix array (complex units)
-    int diag_off;  // diag: offset (doubles) of [c, a[n], b[n*n]] in turns
+    int diag_off;  // diag: offset (doubles) of the run's tables (DiagLayout)
     int lq[kMaxK]; // dense: local tile positions, ascending
     int ngates;
+    int tc;        // dense on the tensor cores (c64, k >= 3)
+    int tc_off;    // float offset of its B operands [hi | lo] in the tc section
 };
+
+// Tensor-core dense block of k qubits (D = 2^k): B operand = [Ur; Ui], N = 2D
+// rows x K = D columns, FP32 values laid out as the tcgen05 no-swizzle
+// K-major canonical layout (8-row x 4-element core matrices of 128 bytes;
+// 128 bytes between K-adjacent core matrices, (K/4)*128 between 8-row
+// groups), stored twice: hi = value with the low 13 mantissa bits cleared
+// (what the tensor core reads from an FP32 input) and lo = value - hi.
+constexpr int kMinTcK = 3;
+constexpr int kTcResidentFloats = 8192;  // 32 KiB of B operands kept per CTA
+__host__ __device__ inline int tc_floats(int k) { return 2 * (2 << k) * (1 << k); }  // hi + lo
+__host__ __device__ inline int tc_kmajor_index(int n, int kk, int K) {
+    return ((n >> 3) * (K >> 2) + (kk >> 2)) * 32 + (n & 7) * 4 + (kk & 3);
+}
 
 struct PassDev {
     int m;
     int L;
     int op_begin;
     int op_end;
+    int tc_k;            // widest tensor-core block in the pass (0: none)
+    int tc_base;         // float offset of the pass's first tensor-core B operands
+    int tc_res;          // floats of B operands kept resident in shared memory (0: loaded per op)
     int tq[kMaxTileM];   // tile qubits ascending
     int nother;
     int oq[40];          // non-tile qubits ascending
@@ -165,7 +185,7 @@ __host__ __device__ inline size_t diag_doubles(int m, int no) { return (size_t)D
 
 struct PlanBlob {
     std::vector<unsigned char> bytes;
-    size_t pass_off = 0, op_off = 0, mat_off = 0, diag_off = 0;
+    size_t pass_off = 0, op_off = 0, mat_off = 0, diag_off = 0, tc_off = 0;
     int npasses = 0;
 };
 
@@ -192,6 +212,7 @@ struct sv_state {
     sv::Scratch red;         // reduction scratch (block sums, CDF, partials)
     sv::Scratch out_dev;     // device staging for host outputs
     sv::Scratch host_pin;    // pinned staging for plan uploads
+    sv::Scratch err;         // device error word of bounded waits (int)
     cudaEvent_t upload_ev;   // recorded after the last plan upload from host_pin
     bool upload_pending;
     // recorder: CUDA events around each pass of applies made with record=1
@@ -215,7 +236,7 @@ cudaError_t launch_init_basis(sv_state* h, uint64_t x);
 cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
                         const HostPass& hp);
-size_t pass_smem_bytes(int dtype, int m, int L);
+size_t pass_smem_bytes(int dtype, int m, int L, int tc_k, int tc_res);
 
 // Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
 int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks);

@@ -229,7 +229,9 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         if (opt->k_max > 0) po.k_max = opt->k_max;
         if (opt->tile_m > 0) po.tile_m = opt->tile_m;
         po.planner = opt->planner;
+        po.tensor = opt->tensor > 0 ? 0 : -1;
     }
+    if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
     const int mmax = dtype == SV_C64 ? 14 : 13;
     po.tile_m = std::max(1, std::min(mmax, po.tile_m));
@@ -243,6 +245,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     out->plain = false;
     out->passes.clear();
     out->gates = (int64_t)gates.size();
+    out->tensor = po.tensor;
     const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
     // the tile holds the row bits plus room for any two-qubit gate
     const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
@@ -502,6 +505,17 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p) {
 namespace {
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// FP32 -> TF32 value (10-bit mantissa) rounded to nearest, ties away from
+// zero: add half of the dropped 13-bit field to the magnitude, then clear it.
+float tf32_round(float v) {
+    uint32_t bits;
+    memcpy(&bits, &v, 4);
+    bits = (bits + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &bits, 4);
+    return r;
+}
+
 // Phase in turns reduced to [-0.5, 0.5).
 double red_turns(double rad) {
     const double t = rad / (2.0 * kPi);
@@ -555,12 +569,16 @@ void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, 
 
 void serialise_plan(const Plan& p, PlanBlob* blob) {
     const int n = p.n;
-    size_t nops = 0, nmat = 0, ndiag = 0;
+    size_t nops = 0, nmat = 0, ndiag = 0, ntc = 0;
+    auto use_tc = [&](const HostOp& o) {
+        return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
+    };
     for (const HostPass& hp : p.passes)
         for (const HostOp& o : hp.ops) {
             ++nops;
             if (o.kind == OP_DENSE) nmat += o.mat.size();
             else ndiag += diag_doubles((int)hp.tile.size(), n - (int)hp.tile.size());
+            if (use_tc(o)) ntc += (size_t)tc_floats((int)o.qubits.size());
         }
     const size_t csz = p.dtype == SV_C64 ? 8 : 16;
     blob->npasses = (int)p.passes.size();
@@ -568,9 +586,12 @@ void serialise_plan(const Plan& p, PlanBlob* blob) {
     blob->op_off = align16(sizeof(PassDev) * p.passes.size());
     blob->mat_off = align16(blob->op_off + sizeof(OpDev) * nops);
     blob->diag_off = align16(blob->mat_off + csz * nmat);
-    const size_t total = align16(blob->diag_off + sizeof(double) * ndiag);
+    blob->tc_off = align16(blob->diag_off + sizeof(double) * ndiag);
+    const size_t total = align16(blob->tc_off + sizeof(float) * ntc);
     blob->bytes.assign(total, 0);
     unsigned char* base = blob->bytes.data();
+    float* tcf = (float*)(base + blob->tc_off);
+    size_t ti = 0;
     PassDev* pd = (PassDev*)(base + blob->pass_off);
     OpDev* od = (OpDev*)(base + blob->op_off);
     double* dg = (double*)(base + blob->diag_off);
@@ -615,6 +636,27 @@ void serialise_plan(const Plan& p, PlanBlob* blob) {
                     }
                 }
                 mi += o.mat.size();
+                if (use_tc(o)) {
+                    // B = [Ur; Ui]: row n < D holds Re U[n][j], row D + n holds Im U[n][j]
+                    const int k = O.k, Dm = 1 << k, N = 2 * Dm, K = Dm;
+                    O.tc = 1;
+                    O.tc_off = (int)ti;
+                    float* hi = tcf + ti;
+                    float* lo = hi + N * K;
+                    for (int r = 0; r < N; ++r)
+                        for (int j = 0; j < K; ++j) {
+                            const cd u = o.mat[(size_t)(r % Dm) * Dm + j];
+                            const float v = (float)(r < Dm ? u.real() : u.imag());
+                            const float vh = tf32_round(v);
+                            const int idx = tc_kmajor_index(r, j, K);
+                            hi[idx] = vh;
+                            lo[idx] = tf32_round(v - vh);
+                        }
+                    if (!P.tc_k) P.tc_base = (int)ti;
+                    ti += (size_t)tc_floats(k);
+                    if (k > P.tc_k) P.tc_k = k;
+                    P.tc_res = (int)ti - P.tc_base;  // all of the pass's B operands so far
+                }
             } else {
                 O.k = 0;
                 O.diag_off = (int)di;
@@ -623,6 +665,7 @@ void serialise_plan(const Plan& p, PlanBlob* blob) {
             }
         }
         P.op_end = (int)oi;
+        if (P.tc_res > kTcResidentFloats) P.tc_res = 0;  // too large: staged per op and tile
     }
 }
 

@@ -76,6 +76,22 @@ def test_qft_basis_and_random(dtype, planner):
     U.assert_close(got, U.run_oracle(n, g, psi0), dtype, "qft random")
 
 
+@pytest.mark.parametrize("tensor", [1, -1], ids=["tcgen05", "cuda_cores"])
+@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("tile_m", [9, 11, 13, 14])
+def test_tensor_core_blocks(tensor, k, tile_m):
+    """complex64 dense blocks of 3..5 qubits on the tensor cores (3xTF32)
+    and on the CUDA cores, multi-tile, random circuit and QFT."""
+    n = 17
+    g = W.random_u3_cx(n, 6, 300 + k + tile_m)
+    got = U.run_gpu(n, g, S.C64, k_max=k, tile_m=tile_m, tensor=tensor)
+    U.assert_close(got, U.run_oracle(n, g), S.C64, "random k=%d m=%d tensor=%d" % (k, tile_m, tensor))
+    q = W.qft(n)
+    psi0 = W.random_state(n, 9)
+    got = U.run_gpu(n, q, S.C64, psi0=psi0, k_max=k, tile_m=tile_m, tensor=tensor)
+    U.assert_close(got, U.run_oracle(n, q, psi0), S.C64, "qft k=%d m=%d tensor=%d" % (k, tile_m, tensor))
+
+
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
 def test_qubit_position_sweep(dtype):
     """Every 1-qubit gate position and every ordered 2-qubit pair, n = 15
@@ -107,6 +123,16 @@ def test_reversal_returns_zero_state(dtype):
     got = U.run_gpu(n, gg, dtype)
     ref = oracle.basis_state(n, 0)
     U.assert_close(got, ref, dtype, "reversal")
+
+
+def test_reversal_tensor_cores():
+    """The circuit and its reversal (8 + 8 layers at n = 16) through 3xTF32
+    blocks of 5 qubits returns |0...0> within the complex64 bounds."""
+    n = 16
+    g = W.random_u3_cx(n, 4, 6)
+    gg = np.concatenate([g, W.inverse(g)])
+    got = U.run_gpu(n, gg, S.C64, k_max=5, tensor=1)
+    U.assert_close(got, oracle.basis_state(n, 0), S.C64, "reversal tcgen05")
 
 
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
