@@ -221,6 +221,41 @@ int sv_pass_times(sv_handle h, double *host_ms, float *host_feat, int cap, int *
 /* Length of one pass feature vector. */
 int sv_feature_count(void);
 
+/* ---- learned cost model (one per process) -------------------------------
+ * A small MLP (32 -> 64 -> 64 -> 1, ReLU) predicts the log time of a tile
+ * pass from its feature vector (the recorder's features: qubit count, dtype,
+ * tile width, fused blocks per width, diagonal runs, and the paper's one-hot
+ * gate-type encoding of App. D.1 Eq. "onehot" summed over the pass's gates).
+ * With planner = SV_PLAN_MLP, sv_apply_circuit plans each new circuit with
+ * every candidate fusion width k (2..5), tile width m and tensor-core choice,
+ * predicts the total time and keeps the fastest; the greedy fixed-width plan
+ * is the fallback when no model is loaded and the judge of the prediction:
+ * the first two calls for a circuit time the chosen and the greedy plan, and
+ * later calls use whichever measured faster.  Plans are exact either way. */
+
+/* Train on count recorded passes (features count x sv_feature_count()
+ * floats, times in ms) on the GPU with the library's own forward, backward and
+ * Adam kernels, full batch, for epochs steps of learning rate lr, weights
+ * initialised from seed.  The trained model becomes the process's model and
+ * is written to weights_path unless it is NULL.  *final_loss (may be NULL)
+ * receives the mean squared error on standardised log times. */
+int sv_cost_model_train(const float *host_feat, const double *host_ms, int count, int epochs, double lr,
+                        uint64_t seed, const char *weights_path, double *final_loss);
+int sv_cost_model_save(const char *path);
+int sv_cost_model_load(const char *path);
+int sv_cost_model_unload(void);
+/* 1 if a model is loaded, else 0. */
+int sv_cost_model_loaded(void);
+/* Predicted times (ms) for count feature rows, computed on the GPU. */
+int sv_cost_model_predict(const float *host_feat, int count, double *host_ms);
+/* The options SV_PLAN_MLP picks for a circuit and its predicted time, without
+ * running it (plans on the host, predicts on the GPU). */
+int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate *gates, size_t count, sv_options *chosen,
+                         double *predicted_ms);
+/* Counters: circuits planned by the model, and judged mispredictions (the
+ * greedy plan measured faster than the model's choice). */
+int sv_cost_model_stats(int64_t *planned, int64_t *mispredicted);
+
 /* ---- misc -------------------------------------------------------------- */
 
 /* Message for the calling thread's last failing call ("" if none). */

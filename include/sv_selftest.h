@@ -26,6 +26,20 @@ extern "C" {
 int sv_selftest_tc_tf32(const float *host_a, const float *host_b, float *host_d, int kstride, int nstride,
                         int swap_fields, int *host_status);
 
+/* The cost-model network's loss and gradient on the GPU (the training
+ * kernels' forward and backward passes) for flat parameters params
+ * (sv_mlp_param_count() floats: W1 64x32 row-major | b1 | W2 64x64 | b2 |
+ * w3 | b3), inputs x (B x 32) and standardised targets t (B).  Writes the mean
+ * squared error to *loss and the gradient to grads. */
+int sv_mlp_gradient(const float *params, const float *x, const float *t, int B, double *loss, float *grads);
+
+/* steps Adam updates (beta1 0.9, beta2 0.999, eps 1e-8, zero initial moments)
+ * with the fixed gradient grads, on the GPU; params updated in place. */
+int sv_mlp_adam(float *params, const float *grads, int steps, double lr);
+
+/* Number of network parameters (6337). */
+int sv_mlp_param_count(void);
+
 #ifdef __cplusplus
 }
 #endif

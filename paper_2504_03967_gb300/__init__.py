@@ -99,11 +99,15 @@ def exported_symbols():
 
 
 def declared_symbols():
+    """Entry points declared in every header under include/."""
+    import glob
     import re
-    hdr = os.path.join(os.path.dirname(HERE), "include", "sv.h")
-    with open(hdr) as f:
-        txt = f.read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*|uint64_t)\s*\*?\s*(sv_\w+)\s*\(", txt, re.M)))
+    names = set()
+    for hdr in glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")):
+        with open(hdr) as f:
+            txt = f.read()
+        names |= set(re.findall(r"^\s*(?:int|const char \*|uint64_t)\s*\*?\s*(sv_\w+)\s*\(", txt, re.M))
+    return sorted(names)
 
 
 def _check(rc):
@@ -266,3 +270,101 @@ def sv_sample_uniforms(h, u):
     out = np.empty(len(u), dtype=np.uint64)
     _check(lib().sv_sample_uniforms(h, _ptr(u), len(u), _ptr(out)))
     return out
+
+
+# ---- learned cost model ---------------------------------------------------
+def _cm_lib():
+    L = lib()
+    if not getattr(L, "_cm_ready", False):
+        vp, i, u64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+        P = ctypes.POINTER
+        for name, args in {
+            "sv_cost_model_train": [vp, vp, i, i, d, u64, ctypes.c_char_p, P(d)],
+            "sv_cost_model_save": [ctypes.c_char_p],
+            "sv_cost_model_load": [ctypes.c_char_p],
+            "sv_cost_model_unload": [],
+            "sv_cost_model_loaded": [],
+            "sv_cost_model_predict": [vp, i, vp],
+            "sv_cost_model_choose": [i, i, vp, ctypes.c_size_t, P(sv_options), P(d)],
+            "sv_cost_model_stats": [P(ctypes.c_int64), P(ctypes.c_int64)],
+            "sv_mlp_gradient": [vp, vp, vp, i, P(d), vp],
+            "sv_mlp_adam": [vp, vp, i, d],
+            "sv_mlp_param_count": [],
+            "sv_selftest_tc_tf32": [vp, vp, vp, i, i, i, P(i)],
+        }.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L._cm_ready = True
+    return L
+
+
+def sv_cost_model_train(feat, ms, epochs=2000, lr=3e-3, seed=0, weights_path=None):
+    """Train the cost model on recorded passes; returns the final loss."""
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    ms = np.ascontiguousarray(ms, dtype=np.float64)
+    assert feat.shape == (len(ms), sv_feature_count())
+    loss = ctypes.c_double()
+    path = weights_path.encode() if weights_path else None
+    _check(_cm_lib().sv_cost_model_train(_ptr(feat), _ptr(ms), len(ms), int(epochs), float(lr), int(seed),
+                                         path, ctypes.byref(loss)))
+    return loss.value
+
+
+def sv_cost_model_save(path):
+    _check(_cm_lib().sv_cost_model_save(path.encode()))
+
+
+def sv_cost_model_load(path):
+    _check(_cm_lib().sv_cost_model_load(path.encode()))
+
+
+def sv_cost_model_unload():
+    _check(_cm_lib().sv_cost_model_unload())
+
+
+def sv_cost_model_loaded():
+    return bool(_cm_lib().sv_cost_model_loaded())
+
+
+def sv_cost_model_predict(feat):
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    out = np.empty(len(feat), dtype=np.float64)
+    _check(_cm_lib().sv_cost_model_predict(_ptr(feat), len(feat), _ptr(out)))
+    return out
+
+
+def sv_cost_model_choose(n, dtype, gates):
+    """(options dict, predicted ms) the cost-model planner picks for a circuit."""
+    g = as_gates(gates)
+    o = sv_options()
+    ms = ctypes.c_double()
+    _check(_cm_lib().sv_cost_model_choose(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(ms)))
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
+
+
+def sv_cost_model_stats():
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(_cm_lib().sv_cost_model_stats(ctypes.byref(a), ctypes.byref(b)))
+    return {"planned": a.value, "mispredicted": b.value}
+
+
+def sv_mlp_param_count():
+    return _cm_lib().sv_mlp_param_count()
+
+
+def sv_mlp_gradient(params, x, t):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.empty(sv_mlp_param_count(), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_cm_lib().sv_mlp_gradient(_ptr(params), _ptr(x), _ptr(t), len(t), ctypes.byref(loss), _ptr(g)))
+    return loss.value, g
+
+
+def sv_mlp_adam(params, grads, steps, lr):
+    p = np.array(params, dtype=np.float32, copy=True)
+    g = np.ascontiguousarray(grads, dtype=np.float32)
+    _check(_cm_lib().sv_mlp_adam(_ptr(p), _ptr(g), int(steps), float(lr)))
+    return p

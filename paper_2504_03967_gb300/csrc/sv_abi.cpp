@@ -260,7 +260,7 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     if (canonicalise(h->n, gates, count, &cg, &bad) != SV_OK)
         return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
     if (cg.empty()) return SV_OK;
-    const PlanOptions po = resolve_options(h->n, h->dtype, opt);
+    PlanOptions po = resolve_options(h->n, h->dtype, opt);
     Plan plan;
     if (po.planner == SV_PLAN_PLAIN) {
         plan_plain(h->n, h->dtype, cg, &plan);
@@ -270,6 +270,8 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
         }
         return SV_OK;
     }
+    cudaEvent_t judge0 = nullptr, judge1 = nullptr;
+    if (po.planner == SV_PLAN_MLP) po = mlp_plan_options(h, gates, count, cg, po, &judge0, &judge1);
     plan_greedy(h->n, h->dtype, cg, po, &plan);
     PlanBlob blob;
     serialise_plan(plan, &blob);
@@ -302,6 +304,7 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
     h->upload_pending = true;
     const bool rec = opt && opt->record;
+    if (judge0) cudaEventRecord(judge0, h->stream);
     for (int p = 0; p < blob.npasses; ++p) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (rec && (e0 = next_event(h)) && (e1 = next_event(h))) cudaEventRecord(e0, h->stream);
@@ -309,9 +312,10 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
         if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "tile pass kernel"));
         if (rec && e1) {
             cudaEventRecord(e1, h->stream);
-            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p]));
+            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p], plan.tensor == 0));
         }
     }
+    if (judge1) cudaEventRecord(judge1, h->stream);
     return SV_OK;
 }
 

@@ -118,7 +118,12 @@ void plan_summary(const Plan& p, sv_plan_info* info);
 // type (the paper's one-hot gate-type encoding, App. D.1 Eq. "onehot",
 // summed over the pass), arithmetic and byte volume, and a bias input.
 constexpr int kFeatures = 32;
-std::vector<float> pass_features(int n, int dtype, const HostPass& p);
+std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tensor_cores);
+
+// Options for an apply under SV_PLAN_MLP; ev0/ev1 receive events to record
+// around the passes when the judge times this call (else nullptr).
+PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
+                             const PlanOptions& base, cudaEvent_t* ev0, cudaEvent_t* ev1);
 
 // ---------------------------------------------------------------------------
 // Device-side plan blob.  Layout: [PassDev x P][OpDev x O][mats][diag doubles]

@@ -467,7 +467,7 @@ void plan_summary(const Plan& p, sv_plan_info* info) {
     info->bytes_moved = (int64_t)bytes;
 }
 
-std::vector<float> pass_features(int n, int dtype, const HostPass& p) {
+std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tensor_cores) {
     std::vector<float> f(kFeatures, 0.0f);
     const int m = (int)p.tile.size();
     f[0] = n / 34.0f;
@@ -494,7 +494,7 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p) {
     for (int t = 0; t < 14; ++t) f[14 + t] = p.type_count[t] / 16.0f;  // f[14..27]
     f[28] = (float)(ldexp(1.0, n) * (dtype == SV_C64 ? 16.0 : 32.0) / ldexp(1.0, 36));
     f[29] = (n - m) / 34.0f;
-    f[30] = 0.0f;
+    f[30] = tensor_cores ? 1.0f : 0.0f;
     f[31] = 1.0f;
     return f;
 }

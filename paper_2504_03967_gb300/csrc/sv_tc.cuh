@@ -71,9 +71,9 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // FP32 -> TF32 (10-bit mantissa), round to nearest with ties away from zero;
 // the result is an FP32 bit pattern with the low 13 mantissa bits zero.
 __device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
+    // add half of the dropped 13-bit field to the magnitude, then clear it
+    // (two integer ALU operations; same result as cvt.rna.tf32.f32 for finite x)
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 // ---- descriptors -------------------------------------------------------------
