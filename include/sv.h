@@ -208,6 +208,25 @@ int sv_sample_uniforms(sv_handle h, const double *host_u, uint64_t shots, uint64
 int sv_sample_uniforms_noalloc(const void *dev_amps, int n, sv_dtype dt, const double *dev_u,
                                uint64_t shots, uint64_t *dev_out, void *cuda_stream);
 
+/* ---- batches of independent circuits ------------------------------------ */
+
+/* Run C independent circuits of uneven size (the paper's parallel mode of
+ * many small circuits, Sec. 2.4), each from |0...0>, and return their shots
+ * and <Z_i>.  Circuit c has n_qubits[c] qubits and the gate records
+ * gates[gate_offsets[c] .. gate_offsets[c] + gate_counts[c]); the fixed-size
+ * circuit tensor of App. B Lemma 2 (C circuits padded to d records) is the
+ * case gate_offsets[c] = c * d.  Circuit c draws its shots with seed + c
+ * (sv_sample's Philox convention).  host_samples (C x shots uint64, row c =
+ * circuit c) and host_expz (C x nmax doubles, row c holds n_qubits[c]
+ * values, nmax >= every n_qubits[c]) may each be NULL.
+ * Circuits of at most 13 (complex64) / 12 (complex128) qubits run entirely in
+ * shared memory inside one persistent kernel launched from a CUDA graph;
+ * larger ones run through the fused tile passes.  opt as for
+ * sv_apply_circuit (k_max defaults to 3 here).  Synchronous. */
+int sv_batch_run(int C, const int *n_qubits, const int64_t *gate_offsets, const int64_t *gate_counts,
+                 const sv_gate *gates, sv_dtype dt, uint64_t shots, uint64_t seed, const sv_options *opt,
+                 uint64_t *host_samples, double *host_expz, int nmax, void *cuda_stream);
+
 /* ---- recorder (per-pass timings; the cost model's training data) ------- */
 
 /* Timings of the tile passes run by sv_apply_circuit calls made with

@@ -368,3 +368,32 @@ def sv_mlp_adam(params, grads, steps, lr):
     g = np.ascontiguousarray(grads, dtype=np.float32)
     _check(_cm_lib().sv_mlp_adam(_ptr(p), _ptr(g), int(steps), float(lr)))
     return p
+
+
+# ---- batches ----------------------------------------------------------------
+def sv_batch_run(circuits, dtype=C64, shots=0, seed=0, expz=True, k_max=0, tile_m=0, stream=None):
+    """circuits: list of (n, gates).  Returns (samples C x shots uint64 or
+    None, expz C x nmax float64 or None)."""
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        vp = ctypes.c_void_p
+        L.sv_batch_run.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                   ctypes.POINTER(sv_options), vp, vp, ctypes.c_int, vp]
+        L.sv_batch_run.restype = ctypes.c_int
+        L._batch_ready = True
+    C = len(circuits)
+    ns = np.array([n for n, _ in circuits], dtype=np.int32)
+    counts = np.array([len(g) for _, g in circuits], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    allg = np.ascontiguousarray(np.concatenate([as_gates(g) for _, g in circuits]) if C else
+                                np.zeros(0, GATE_DTYPE))
+    if len(allg) == 0:
+        allg = np.zeros(1, GATE_DTYPE)
+    nmax = int(ns.max())
+    samp = np.empty((C, shots), dtype=np.uint64) if shots else None
+    ez = np.empty((C, nmax), dtype=np.float64) if expz else None
+    o = _opts(k_max, tile_m)
+    _check(L.sv_batch_run(C, _ptr(ns), _ptr(offs), _ptr(counts), _ptr(allg), dtype, int(shots), int(seed),
+                          ctypes.byref(o), _ptr(samp) if samp is not None else None,
+                          _ptr(ez) if ez is not None else None, nmax, stream))
+    return samp, ez

@@ -259,6 +259,16 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     size_t bad = 0;
     if (canonicalise(h->n, gates, count, &cg, &bad) != SV_OK)
         return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
+    return sv::apply_canonical(h, gates, count, cg, opt);
+}
+
+}  // extern "C"
+
+namespace sv {
+
+int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
+                    const sv_options* opt) {
+    int rc = SV_OK;
     if (cg.empty()) return SV_OK;
     PlanOptions po = resolve_options(h->n, h->dtype, opt);
     Plan plan;
@@ -318,6 +328,10 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     if (judge1) cudaEventRecord(judge1, h->stream);
     return SV_OK;
 }
+
+}  // namespace sv
+
+extern "C" {
 
 int sv_pass_times(sv_handle h, double* host_ms, float* host_feat, int cap, int* count) {
     if (!h || !count) return set_error(SV_EINVAL, "NULL argument");

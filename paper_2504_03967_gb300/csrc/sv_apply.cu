@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "sv_internal.h"
+#include "sv_philox.cuh"
 #include "sv_tc.cuh"
 
 namespace sv {
@@ -619,6 +620,202 @@ size_t pass_smem_bytes(int dtype, int m, int L, int tc_k, int tc_res) {
     // to keep a third one away.
     if (tc_k >= 5 && total < 80 * 1024) total = 80 * 1024;
     return total;
+}
+
+// ---------------------------------------------------------------------------
+// Batched circuits whose whole state fits one CTA's shared memory (the
+// paper's parallel mode of many small circuits, Sec. 2.4): one persistent
+// launch; each CTA takes circuits from a work counter, starts from |0...0>,
+// applies the circuit's single tile pass (every qubit in the tile), and
+// writes <Z_i> and the shots straight from shared memory.  Shots follow the
+// library's rule min{x : C_x > u C_{N-1}} with the CDF built over blocks of
+// 32 amplitudes in FP64; circuit c (index gidx[c] in the caller's batch)
+// draws its uniforms with seed + gidx[c].
+// ---------------------------------------------------------------------------
+template <typename V> __device__ __forceinline__ double prob_d(V a) {
+    const double x = (double)a.x, y = (double)a.y;
+    return fma(x, x, y * y);
+}
+
+size_t batch_small_smem_bytes(int dtype, int mmax) {
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    const size_t rsz = dtype == SV_C64 ? 4 : 8;
+    size_t work = csz * (1 << (2 * kMaxK));
+    const size_t dt = rsz * diag_table_elems(mmax);
+    if (dt > work) work = dt;
+    return (csz << mmax) + work + 8 * 256;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __restrict__ pd, int C,
+                                                             const OpDev* __restrict__ ops,
+                                                             const typename CT<R>::V* __restrict__ mats,
+                                                             const double* __restrict__ diags, int mmax,
+                                                             uint64_t shots, uint64_t seed,
+                                                             const int* __restrict__ gidx,
+                                                             uint64_t* __restrict__ samples,
+                                                             double* __restrict__ expz, int nmax,
+                                                             int* __restrict__ counter) {
+    using V = typename CT<R>::V;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ PassDev P;
+    __shared__ R s_ap[kMaxTileM];
+    __shared__ double s_c;
+    __shared__ int s_circ;
+    __shared__ double s_red[8][kMaxTileM + 2];
+    V* tile = (V*)smem;
+    R* work = (R*)(smem + (sizeof(V) << mmax));
+    double* cdf = (double*)(smem + (sizeof(V) << mmax) +
+                            ((size_t)(sizeof(V) << (2 * kMaxK)) > sizeof(R) * diag_table_elems(mmax)
+                                 ? (size_t)(sizeof(V) << (2 * kMaxK))
+                                 : sizeof(R) * diag_table_elems(mmax)));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_circ = atomicAdd(counter, 1);
+        __syncthreads();
+        const int c = s_circ;
+        if (c >= C) break;
+        {
+            const int* src = (const int*)(pd + c);
+            int* dst = (int*)&P;
+            for (int i = tid; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const int m = P.m;  // = the circuit's qubit count
+        const int N = 1 << m;
+        for (int i = tid; i < N; i += blockDim.x) {
+            V v = czero<V>();
+            if (i == 0) v.x = 1;
+            tile[i] = v;
+        }
+        __syncthreads();
+        for (int oi = P.op_begin; oi < P.op_end; ++oi) {
+            const OpDev op = ops[oi];
+            if (op.kind == OP_DENSE) {
+                V* sU = (V*)work;
+                const int DD = 1 << (2 * op.k);
+                for (int e = tid; e < DD; e += blockDim.x) sU[e] = mats[op.mat_off + e];
+                __syncthreads();
+                switch (op.k) {
+                case 1: tile_dense<V, 1>(tile, m, op, sU); break;
+                case 2: tile_dense<V, 2>(tile, m, op, sU); break;
+                case 3: tile_dense<V, 3>(tile, m, op, sU); break;
+                case 4: tile_dense<V, 4>(tile, m, op, sU); break;
+                default: tile_dense<V, 5>(tile, m, op, sU); break;
+                }
+            } else {
+                tile_diag<V, R>(tile, P, 0ull, diags + op.diag_off, work, s_ap, &s_c);
+            }
+            __syncthreads();
+        }
+        if (expz) {
+            double tot = 0.0, sb[kMaxTileM];
+#pragma unroll
+            for (int b = 0; b < kMaxTileM; ++b) sb[b] = 0.0;
+            for (int i = tid; i < N; i += blockDim.x) {
+                const double p = prob_d(tile[i]);
+                tot += p;
+#pragma unroll
+                for (int b = 0; b < kMaxTileM; ++b)
+                    if ((i >> b) & 1) sb[b] += p;
+            }
+#pragma unroll
+            for (int b = 0; b <= kMaxTileM; ++b) {
+                double v = b < kMaxTileM ? sb[b] : tot;
+#pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+                if (lane == 0) s_red[warp][b] = v;
+            }
+            __syncthreads();
+            if (tid < m) {
+                double s = 0.0, t = 0.0;
+                for (int w = 0; w < 8; ++w) {
+                    s += s_red[w][tid];
+                    t += s_red[w][kMaxTileM];
+                }
+                expz[(size_t)c * nmax + tid] = t - 2.0 * s;
+            }
+            __syncthreads();
+        }
+        if (samples && shots) {
+            const int blen = N < 32 ? N : 32;
+            const int nblk = N / blen;
+            for (int b = warp; b < nblk; b += 8) {
+                double p = lane < blen ? prob_d(tile[b * blen + lane]) : 0.0;
+#pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1) p += __shfl_xor_sync(0xffffffffu, p, sh);
+                if (lane == 0) cdf[b] = p;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0.0;
+                for (int b = 0; b < nblk; ++b) {
+                    a += cdf[b];
+                    cdf[b] = a;
+                }
+            }
+            __syncthreads();
+            const double S = cdf[nblk - 1];
+            for (uint64_t s = tid; s < shots; s += blockDim.x) {
+                const double t = philox_uniform(seed + (uint64_t)gidx[c], s) * S;
+                int lo = 0, hi = nblk - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cdf[mid] > t) hi = mid;
+                    else lo = mid + 1;
+                }
+                double acc = lo ? cdf[lo - 1] : 0.0;
+                int pick = -1, last_nz = lo * blen;
+                for (int l = 0; l < blen; ++l) {
+                    const double p = prob_d(tile[lo * blen + l]);
+                    if (p > 0.0) last_nz = lo * blen + l;
+                    acc += p;
+                    if (acc > t && p > 0.0) {
+                        pick = lo * blen + l;
+                        break;
+                    }
+                }
+                samples[(size_t)c * shots + s] = (uint64_t)(pick >= 0 ? pick : last_nz);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& blob, int C, int mmax,
+                               uint64_t shots, uint64_t seed, const int* gidx, uint64_t* samples, double* expz,
+                               int nmax, int* counter, cudaStream_t st) {
+    const size_t smem = batch_small_smem_bytes(dtype, mmax);
+    const unsigned char* b = (const unsigned char*)blob_dev;
+    int per_sm = 1;
+    cudaError_t e;
+    if (dtype == SV_C64) {
+        e = cudaFuncSetAttribute(k_batch_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_small<float>, kPassThreads, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_batch_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_small<double>, kPassThreads, smem);
+    }
+    if (per_sm < 1) per_sm = 1;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = sms * per_sm;
+    if (grid > C) grid = C;
+    count_launch();
+    if (dtype == SV_C64)
+        k_batch_small<float><<<grid, kPassThreads, smem, st>>>(
+            (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
+            (const float2*)(b + blob.mat_off), (const double*)(b + blob.diag_off), mmax, shots, seed, gidx,
+            samples, expz, nmax, counter);
+    else
+        k_batch_small<double><<<grid, kPassThreads, smem, st>>>(
+            (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
+            (const double2*)(b + blob.mat_off), (const double*)(b + blob.diag_off), mmax, shots, seed, gidx,
+            samples, expz, nmax, counter);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

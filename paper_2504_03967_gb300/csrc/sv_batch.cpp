@@ -1,0 +1,243 @@
+// Batched execution of many independent circuits of uneven size (the paper's
+// parallel mode, Sec. 2.4, where many small circuits run side by side, and
+// its fixed-size circuit tensor of App. B Lemma 2).
+//
+//  * circuits whose whole state fits one CTA's shared memory are planned on
+//    host threads into single-tile plans and run by ONE persistent kernel,
+//    launched from a CUDA graph: each CTA takes circuits from a device work
+//    counter and writes <Z_i> and the shots straight from shared memory;
+//  * larger circuits run through the fused tile-pass path, spread over a few
+//    streams that each own a state buffer, with the read-outs kept on the
+//    device until a single copy back at the end.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <thread>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+int small_limit(int dtype) { return dtype == SV_C64 ? 13 : 12; }
+
+template <typename F>
+void parallel_for(int n, F f) {
+    const int T = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t)
+        th.emplace_back([&]() {
+            for (int i; (i = next.fetch_add(1)) < n;) f(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    void* buf = nullptr;
+    sv_state h{};
+};
+
+}  // namespace
+}  // namespace sv
+
+using namespace sv;
+
+extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offsets, const int64_t* gate_counts,
+                            const sv_gate* gates, sv_dtype dt, uint64_t shots, uint64_t seed,
+                            const sv_options* opt, uint64_t* host_samples, double* host_expz, int nmax,
+                            void* cuda_stream) {
+    if (C < 1 || !n_qubits || !gate_offsets || !gate_counts || !gates)
+        return set_error(SV_EINVAL, "sv_batch_run: NULL argument or C < 1");
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (host_samples && shots == 0) host_samples = nullptr;
+    int nbig = 0;
+    for (int c = 0; c < C; ++c) {
+        const int n = n_qubits[c];
+        if (n < 1 || n > (dt == SV_C64 ? kMaxQubitsC64 : kMaxQubitsC128))
+            return set_error(SV_EINVAL, "circuit " + std::to_string(c) + ": n out of range");
+        if (gate_counts[c] < 0 || gate_offsets[c] < 0) return set_error(SV_EINVAL, "negative gate offset/count");
+        nbig = std::max(nbig, n);
+    }
+    if (host_expz && nmax < nbig) return set_error(SV_EINVAL, "nmax below the largest circuit");
+    if (!host_expz) nmax = 1;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    // 1. validate and canonicalise every circuit, on host threads
+    std::vector<std::vector<CGate>> cg(C);
+    std::vector<int> bad(C, 0);
+    parallel_for(C, [&](int c) {
+        size_t b = 0;
+        bad[c] = canonicalise(n_qubits[c], gates + gate_offsets[c], (size_t)gate_counts[c], &cg[c], &b) != SV_OK;
+    });
+    for (int c = 0; c < C; ++c)
+        if (bad[c]) return set_error(SV_EINVAL, "circuit " + std::to_string(c) + ": invalid gate record");
+
+    std::vector<int> small, large;
+    for (int c = 0; c < C; ++c) (n_qubits[c] <= small_limit(dt) ? small : large).push_back(c);
+    const int Cs = (int)small.size();
+
+    // device outputs in [small..., large...] order
+    uint64_t* d_samples = nullptr;
+    double* d_expz = nullptr;
+    int* d_counter = nullptr;
+    int* d_gidx = nullptr;
+    void* d_blob = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (host_samples) e = cudaMallocAsync((void**)&d_samples, sizeof(uint64_t) * (size_t)C * shots, st);
+    if (e == cudaSuccess && host_expz) e = cudaMallocAsync((void**)&d_expz, sizeof(double) * (size_t)C * nmax, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_counter, sizeof(int), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SV_ENOMEM, "sv_batch_run: output allocation failed");
+    }
+    int rc = SV_OK;
+    std::vector<Slot> slots;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    void* pin = nullptr;
+
+    // 2. small circuits: single-tile plans -> one persistent launch
+    if (Cs > 0) {
+        std::vector<Plan> plans(Cs);
+        int mmax = 1;
+        parallel_for(Cs, [&](int i) {
+            const int c = small[i];
+            PlanOptions po = resolve_options(n_qubits[c], dt, opt);
+            if (!opt || opt->k_max == 0) po.k_max = 3;  // CUDA-core blocks: k = 3 is the cheapest fused width
+            po.tile_m = n_qubits[c];
+            po.tensor = -1;
+            plan_greedy(n_qubits[c], dt, cg[c], po, &plans[i]);
+        });
+        std::vector<const Plan*> pp;
+        for (int i = 0; i < Cs; ++i) {
+            if (plans[i].passes.size() > 1) return set_error(SV_EINVAL, "internal: small circuit needs one pass");
+            if (plans[i].passes.empty()) {  // empty circuit: an identity pass
+                HostPass hp;
+                for (int q = 0; q < plans[i].n; ++q) hp.tile.push_back(q);
+                hp.L = std::min(plans[i].n, dt == SV_C64 ? 4 : 3);
+                plans[i].passes.push_back(hp);
+            }
+            mmax = std::max(mmax, plans[i].n);
+            pp.push_back(&plans[i]);
+        }
+        PlanBlob blob;
+        serialise_plans(pp, &blob);
+        const size_t gbytes = sizeof(int) * (size_t)Cs;
+        e = cudaMallocAsync(&d_blob, blob.bytes.size(), st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_gidx, gbytes, st);
+        if (e == cudaSuccess) e = cudaMallocHost(&pin, blob.bytes.size() + gbytes);
+        if (e == cudaSuccess) {
+            memcpy(pin, blob.bytes.data(), blob.bytes.size());
+            memcpy((char*)pin + blob.bytes.size(), small.data(), gbytes);
+            e = cudaMemcpyAsync(d_blob, pin, blob.bytes.size(), cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_gidx, (char*)pin + blob.bytes.size(), gbytes, cudaMemcpyHostToDevice, st);
+        // the persistent launch (and its work-counter reset) from a graph
+        cudaStream_t cs = nullptr;
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        cudaEvent_t ready = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(d_counter, 0, sizeof(int), cs);
+            launch_batch_small(dt, d_blob, blob, Cs, mmax, host_samples ? shots : 0, seed, d_gidx, d_samples, d_expz,
+                               nmax, d_counter, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gexec, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ready, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (ready) cudaEventDestroy(ready);
+        if (cs) cudaStreamDestroy(cs);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batched small circuits");
+    }
+
+    // 3. large circuits: fused passes on a few streams
+    if (rc == SV_OK && !large.empty()) {
+        int nl = 0;
+        for (int c : large) nl = std::max(nl, n_qubits[c]);
+        const size_t bytes = (size_t)(dt == SV_C64 ? 8 : 16) << nl;
+        size_t freeb = 0, totb = 0;
+        cudaMemGetInfo(&freeb, &totb);
+        int ns = (int)std::min<size_t>(std::min<size_t>(4, large.size()), std::max<size_t>(1, freeb / (2 * bytes)));
+        slots.resize(ns);
+        for (int s = 0; e == cudaSuccess && s < ns; ++s) {
+            e = cudaStreamCreateWithFlags(&slots[s].st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaMalloc(&slots[s].buf, bytes);
+            slots[s].h.dtype = dt;
+            slots[s].h.amps = slots[s].buf;
+            slots[s].h.stream = slots[s].st;
+            slots[s].h.owned = false;
+            slots[s].h.bad = false;
+            slots[s].h.ev_used = 0;
+            slots[s].h.upload_ev = nullptr;
+            slots[s].h.upload_pending = false;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(SV_ENOMEM, "sv_batch_run: large-circuit state buffers");
+        }
+        for (size_t i = 0; rc == SV_OK && i < large.size(); ++i) {
+            const int c = large[i];
+            const int idx = Cs + (int)i;
+            sv_state* h = &slots[i % slots.size()].h;
+            h->n = n_qubits[c];
+            if (launch_init_basis(h, 0) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "init");
+            if (rc == SV_OK) rc = apply_canonical(h, gates + gate_offsets[c], (size_t)gate_counts[c], cg[c], opt);
+            if (rc == SV_OK && host_samples)
+                rc = measure_sample(h, shots, seed + (uint64_t)c, nullptr, d_samples + (size_t)idx * shots);
+            if (rc == SV_OK && host_expz) rc = measure_expect_z(h, d_expz + (size_t)idx * nmax);
+        }
+    }
+
+    // 4. one copy back, then scatter to the caller's circuit order
+    for (auto& s : slots)
+        if (s.st) cudaStreamSynchronize(s.st);
+    e = cudaStreamSynchronize(st);
+    if (rc == SV_OK && e != cudaSuccess) rc = cuda_fail(e, "batch");
+    std::vector<int> order(small);
+    order.insert(order.end(), large.begin(), large.end());
+    if (rc == SV_OK && host_samples) {
+        std::vector<uint64_t> tmp((size_t)C * shots);
+        e = cudaMemcpy(tmp.data(), d_samples, sizeof(uint64_t) * tmp.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "samples readback");
+        for (int i = 0; rc == SV_OK && i < C; ++i)
+            memcpy(host_samples + (size_t)order[i] * shots, tmp.data() + (size_t)i * shots, sizeof(uint64_t) * shots);
+    }
+    if (rc == SV_OK && host_expz) {
+        std::vector<double> tmp((size_t)C * nmax);
+        e = cudaMemcpy(tmp.data(), d_expz, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "expz readback");
+        for (int i = 0; rc == SV_OK && i < C; ++i)
+            memcpy(host_expz + (size_t)order[i] * nmax, tmp.data() + (size_t)i * nmax, sizeof(double) * nmax);
+    }
+    for (auto& s : slots) {
+        if (s.h.plan_dev.ptr) cudaFree(s.h.plan_dev.ptr);
+        if (s.h.red.ptr) cudaFree(s.h.red.ptr);
+        if (s.h.err.ptr) cudaFree(s.h.err.ptr);
+        if (s.h.host_pin.ptr) cudaFreeHost(s.h.host_pin.ptr);
+        if (s.h.upload_ev) cudaEventDestroy(s.h.upload_ev);
+        for (cudaEvent_t ev : s.h.ev_pool) cudaEventDestroy(ev);
+        if (s.buf) cudaFree(s.buf);
+        if (s.st) cudaStreamDestroy(s.st);
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (pin) cudaFreeHost(pin);
+    if (d_blob) cudaFree(d_blob);
+    if (d_samples) cudaFree(d_samples);
+    if (d_expz) cudaFree(d_expz);
+    if (d_counter) cudaFree(d_counter);
+    if (d_gidx) cudaFree(d_gidx);
+    cudaGetLastError();
+    return rc;
+}

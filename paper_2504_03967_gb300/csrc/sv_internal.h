@@ -153,6 +153,7 @@ __host__ __device__ inline int tc_kmajor_index(int n, int kk, int K) {
 }
 
 struct PassDev {
+    int n;               // qubits of the state the pass runs on
     int m;
     int L;
     int op_begin;
@@ -195,6 +196,8 @@ struct PlanBlob {
 };
 
 void serialise_plan(const Plan& p, PlanBlob* blob);
+// Several plans (same dtype) in one blob, passes in order.
+void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob);
 
 // ---------------------------------------------------------------------------
 // Handle.
@@ -233,6 +236,10 @@ int set_error(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 void count_launch(uint64_t k = 1);
 
+// The body of sv_apply_circuit after validation: plan and launch on h's stream.
+int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
+                    const sv_options* opt);
+
 int ensure_scratch(Scratch* s, size_t bytes, cudaStream_t st);
 int ensure_pinned(Scratch* s, size_t bytes);
 
@@ -242,6 +249,13 @@ cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
                         const HostPass& hp);
 size_t pass_smem_bytes(int dtype, int m, int L, int tc_k, int tc_res);
+// One persistent launch for circuits of at most mmax qubits (single-tile
+// plans, one pass each, in blob order); outputs per circuit c at
+// samples + c*shots and expz + c*nmax (either may be NULL).
+cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& blob, int C, int mmax,
+                               uint64_t shots, uint64_t seed, const int* gidx, uint64_t* samples, double* expz,
+                               int nmax, int* counter, cudaStream_t st);
+size_t batch_small_smem_bytes(int dtype, int mmax);
 
 // Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
 int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks);

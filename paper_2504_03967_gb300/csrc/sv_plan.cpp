@@ -567,23 +567,28 @@ void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, 
 }
 }  // namespace
 
-void serialise_plan(const Plan& p, PlanBlob* blob) {
-    const int n = p.n;
-    size_t nops = 0, nmat = 0, ndiag = 0, ntc = 0;
-    auto use_tc = [&](const HostOp& o) {
+void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
+    size_t nops = 0, nmat = 0, ndiag = 0, ntc = 0, npass = 0;
+    auto use_tc = [&](const Plan& p, const HostOp& o) {
         return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
     };
-    for (const HostPass& hp : p.passes)
+    const int dtype = plans.empty() ? SV_C64 : plans[0]->dtype;
+    for (const Plan* pp : plans) {
+      const Plan& p = *pp;
+      const int n = p.n;
+      npass += p.passes.size();
+      for (const HostPass& hp : p.passes)
         for (const HostOp& o : hp.ops) {
             ++nops;
             if (o.kind == OP_DENSE) nmat += o.mat.size();
             else ndiag += diag_doubles((int)hp.tile.size(), n - (int)hp.tile.size());
-            if (use_tc(o)) ntc += (size_t)tc_floats((int)o.qubits.size());
+            if (use_tc(p, o)) ntc += (size_t)tc_floats((int)o.qubits.size());
         }
-    const size_t csz = p.dtype == SV_C64 ? 8 : 16;
-    blob->npasses = (int)p.passes.size();
+    }
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    blob->npasses = (int)npass;
     blob->pass_off = 0;
-    blob->op_off = align16(sizeof(PassDev) * p.passes.size());
+    blob->op_off = align16(sizeof(PassDev) * npass);
     blob->mat_off = align16(blob->op_off + sizeof(OpDev) * nops);
     blob->diag_off = align16(blob->mat_off + csz * nmat);
     blob->tc_off = align16(blob->diag_off + sizeof(double) * ndiag);
@@ -596,11 +601,15 @@ void serialise_plan(const Plan& p, PlanBlob* blob) {
     OpDev* od = (OpDev*)(base + blob->op_off);
     double* dg = (double*)(base + blob->diag_off);
     size_t oi = 0, mi = 0, di = 0;
-    const double inv2pi = 1.0 / (2.0 * kPi);
-    for (size_t pi = 0; pi < p.passes.size(); ++pi) {
+    size_t gpi = 0;
+    for (const Plan* pp : plans) {
+      const Plan& p = *pp;
+      const int n = p.n;
+      for (size_t pi = 0; pi < p.passes.size(); ++pi, ++gpi) {
         const HostPass& hp = p.passes[pi];
-        PassDev& P = pd[pi];
+        PassDev& P = pd[gpi];
         memset(&P, 0, sizeof(P));
+        P.n = n;
         P.m = (int)hp.tile.size();
         P.L = hp.L;
         P.op_begin = (int)oi;
@@ -636,7 +645,7 @@ void serialise_plan(const Plan& p, PlanBlob* blob) {
                     }
                 }
                 mi += o.mat.size();
-                if (use_tc(o)) {
+                if (use_tc(p, o)) {
                     // B = [Ur; Ui]: row n < D holds Re U[n][j], row D + n holds Im U[n][j]
                     const int k = O.k, Dm = 1 << k, N = 2 * Dm, K = Dm;
                     O.tc = 1;
@@ -666,7 +675,10 @@ void serialise_plan(const Plan& p, PlanBlob* blob) {
         }
         P.op_end = (int)oi;
         if (P.tc_res > kTcResidentFloats) P.tc_res = 0;  // too large: staged per op and tile
+      }
     }
 }
+
+void serialise_plan(const Plan& p, PlanBlob* blob) { serialise_plans({&p}, blob); }
 
 }  // namespace sv
