@@ -125,6 +125,36 @@ def cpu_baseline(n, gates, x, budget_s=12.0):
             "sample": "gates 2..%d of the %d-gate list at n=%d, FP64 complex128, %.1f s" % (G + 1, len(gates), n, dt)}
 
 
+def train_cost_model(S, dt, n):
+    """Record pass timings of circuits OTHER than the benchmarked one (QFT and
+    random circuits at n qubits, every candidate fusion width, tile width and
+    tensor-core choice) and train the cost model on them (GPU kernels)."""
+    h = S.sv_alloc(n, dt)
+    cands = [(k, m, t) for k in (2, 3, 4, 5) for m in (12, 13, 14) for t in (-1, 1)
+             if not (t == 1 and (k < 3 or dt != S.C64))]
+    circuits = [W.qft(n), W.random_u3_cx(n, 4, 2001), W.random_cx_blocks(n, 150, 2002),
+                W.qft(n - 2), W.random_u3_cx(n - 2, 4, 2003)]
+    feats, times = [], []
+    try:
+        for g in circuits:
+            nq = int(max(int(r["q"][:int(r["nq"])].max()) for r in g)) + 1
+            hh = h if nq == n else S.sv_alloc(nq, dt)
+            for k, m, t in cands:
+                S.sv_init_basis(hh, 0)
+                S.sv_apply_circuit(hh, g, k_max=k, tile_m=m, tensor=t, record=1)
+                ms, f = S.sv_pass_times(hh, features=True)
+                feats.append(f)
+                times.append(ms)
+            if hh is not h:
+                S.sv_free(hh)
+    finally:
+        S.sv_free(h)
+    F, T = np.concatenate(feats), np.concatenate(times)
+    loss = S.sv_cost_model_train(F, T, epochs=3000, lr=3e-3, seed=7)
+    return {"train_samples": int(len(T)), "train_loss": loss, "training_circuits": "QFT and random U3+CX / CX-block "
+            "circuits at %d and %d qubits (not the benchmarked circuit)" % (n, n - 2)}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -165,7 +195,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qft28")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--planner", default="greedy", choices=["greedy", "mlp", "plain"])
+    ap.add_argument("--planner", default="mlp", choices=["greedy", "mlp", "plain"])
+    ap.add_argument("--cm-n", type=int, default=26, help="qubits of the cost-model training circuits")
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--tile-m", type=int, default=0)
     ap.add_argument("--tensor", type=int, default=0, help="1: tensor cores for c64 blocks of 3..5 qubits")
@@ -208,8 +239,7 @@ def main():
     def step(i, pl, record):
         S.sv_init_basis(h, x)
         S.sv_apply_circuit(h, g, planner=pl, k_max=args.k, tile_m=args.tile_m, record=record, tensor=args.tensor)
-        S.sv_sample_device(h, args.shots, 1000 + i, shots_out.data_ptr())
-        S.sv_expect_z_device(h, ez_out.data_ptr())
+        S.sv_measure_device(h, args.shots, 1000 + i, shots_out.data_ptr(), ez_out.data_ptr())
 
     def barrier():
         if dist:
@@ -239,11 +269,24 @@ def main():
             ms = float(t.item())
         return ms, launches
 
+    cm = None
+    if planner == S.PLAN_MLP:
+        t0 = time.perf_counter()
+        cm = train_cost_model(S, dt, args.cm_n)
+        cm["seconds"] = time.perf_counter() - t0
+        chosen, pred = S.sv_cost_model_choose(n, dt, g)
+        cm["chosen"] = chosen
+        cm["predicted_ms"] = pred
     with Clocks(local) as clk:
         ms, launches = timed(planner, args.steps, args.warmup, 1)
     pass_ms = S.sv_pass_times(h)
-    plan = S.sv_plan_circuit(n, dt, g, k_max=args.k, tile_m=args.tile_m,
-                             planner=S.PLAN_PLAIN if planner == S.PLAN_PLAIN else S.PLAN_GREEDY)
+    if cm is not None:
+        cm["judge"] = S.sv_cost_model_stats()
+        po = cm["chosen"]
+        plan = S.sv_plan_circuit(n, dt, g, k_max=po["k_max"], tile_m=po["tile_m"], tensor=po["tensor"])
+    else:
+        plan = S.sv_plan_circuit(n, dt, g, k_max=args.k, tile_m=args.tile_m,
+                                 planner=S.PLAN_PLAIN if planner == S.PLAN_PLAIN else S.PLAN_GREEDY)
     value = world * updates / (ms / 1e3)
     hbm, src = peaks()
     # dominant kernel: the tile pass (one read + one write of 2^n amplitudes)
@@ -262,6 +305,11 @@ def main():
         pms, _ = timed(S.PLAN_PLAIN, max(2, args.steps // 3), 1, 0)
         plain = {"value": world * updates / (pms / 1e3), "ms_per_step": pms,
                  "fused_over_plain": pms / ms}
+    greedy = None
+    if planner == S.PLAN_MLP and not args.no_plain:
+        gms, _ = timed(S.PLAN_GREEDY, max(3, args.steps // 2), 2, 0)
+        greedy = {"value": world * updates / (gms / 1e3), "ms_per_step": gms, "k_max": 5,
+                  "learned_over_greedy": gms / ms}
 
     e2e = None
     if not args.no_e2e:
@@ -313,7 +361,7 @@ def main():
                        "passes": plan["passes"], "k_max": args.k or 5, "tile_m": args.tile_m or None,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state %d MiB)" % ((amp_b << n) >> 20)},
-            "roofline": roof, "plain": plain, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "plain": plain, "greedy": greedy, "cost_model": cm, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clk.summary(), "check": fid}
     print(json.dumps(line), flush=True)
     if dist:

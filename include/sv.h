@@ -183,6 +183,11 @@ int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_out);
 int sv_sample_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_out);
 int sv_sample_uniforms(sv_handle h, const double *host_u, uint64_t shots, uint64_t *host_out);
 
+/* Shots (as sv_sample_device) and <Z_i> (as sv_expect_z_device) from ONE
+ * pass over the state: the probability block statistics are computed once
+ * and serve both.  Either output may be NULL (shots then ignored). */
+int sv_measure_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_samples, double *dev_expz);
+
 /* Sampling that allocates nothing.  The paper has no counterpart; this entry
  * point exists for callers of this library that cannot allocate device
  * memory while they run, e.g. a serving process whose device memory is

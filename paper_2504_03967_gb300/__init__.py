@@ -242,6 +242,15 @@ def sv_sample_device(h, shots, seed, dev_out_ptr):
     _check(lib().sv_sample_device(h, int(shots), int(seed), ctypes.c_void_p(dev_out_ptr)))
 
 
+def sv_measure_device(h, shots, seed, dev_samples_ptr, dev_expz_ptr):
+    L = lib()
+    f = L.sv_measure_device
+    f.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(h, int(shots), int(seed), ctypes.c_void_p(dev_samples_ptr) if dev_samples_ptr else None,
+             ctypes.c_void_p(dev_expz_ptr) if dev_expz_ptr else None))
+
+
 def sv_feature_count():
     return lib().sv_feature_count()
 

@@ -438,3 +438,11 @@ int sv_sample_uniforms(sv_handle h, const double* host_u, uint64_t shots, uint64
 }
 
 }  // extern "C"
+
+extern "C" int sv_measure_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t* dev_samples,
+                                 double* dev_expz) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (shots && !dev_samples) return set_error(SV_EINVAL, "NULL samples output");
+    return fail_state(h, measure_readout(h, dev_samples ? shots : 0, seed, dev_samples, dev_expz));
+}

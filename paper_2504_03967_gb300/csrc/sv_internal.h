@@ -262,6 +262,8 @@ int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nbl
 cudaError_t launch_probs(sv_state* h, double* dev_out);
 int measure_norm(sv_state* h, double* host_out);
 int measure_expect_z(sv_state* h, double* dev_out);
+// Shots and <Z_i> from one pass over the state (either output may be NULL).
+int measure_readout(sv_state* h, uint64_t shots, uint64_t seed, uint64_t* dev_samples, double* dev_expz);
 int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev_u, uint64_t* dev_out);
 
 }  // namespace sv

@@ -31,19 +31,108 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// ---- block sums: one warp per block of 2^blog amplitudes -----------------
+// ---- block statistics: totals and within-block bit sums in one pass ------
+// One warp per block of 2^blog amplitudes; lane l takes amplitudes l + 32 j,
+// so index bits 0..4 are the lane and bits 5..9 the loop counter j.  For
+// complex64, |a|^2 is formed exactly as an unevaluated float pair (products
+// by fma, the sum by TwoSum) and accumulated in double-float, so the FP64
+// block value carries the same information as an FP64 sum, at FP32 speed
+// (this GPU's FP64 rate is a small fraction of its FP32 rate).  complex128
+// accumulates in FP64.  bits (optional, nblocks x 10) receives, for each
+// block, the probability mass with index bit i set, i < min(blog, 10).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ void ff_add(FF& a, float x, float xl) {
+    const float s = a.hi + x;
+    const float bb = s - a.hi;
+    a.lo += ((a.hi - (s - bb)) + (x - bb)) + xl;
+    a.hi = s;
+}
+__device__ __forceinline__ double ff_val(FF a) { return (double)a.hi + (double)a.lo; }
+
 template <typename V>
-__global__ void __launch_bounds__(256) k_block_sums(const V* __restrict__ psi, uint64_t N, int blog,
-                                                    uint64_t nblocks, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, int blog, uint64_t nblocks,
+                                                     double* __restrict__ tot, double* __restrict__ bits) {
     const int lane = threadIdx.x & 31;
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= nblocks) return;
     const uint64_t b0 = wid << blog;
-    const uint64_t len = 1ull << blog;
-    double acc = 0.0;
-    for (uint64_t i = lane; i < len; i += 32) acc += prob(psi[b0 + i]);
-    acc = warp_sum(acc);
-    if (lane == 0) out[wid] = acc;
+    const int len = 1 << blog;
+    const int jn = len >= 32 ? len / 32 : 1;
+    double t, bj[5];
+    if constexpr (sizeof(V) == 8) {
+        FF acc = {0.f, 0.f}, ab[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) ab[b] = FF{0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < jn && lane + 32 * j < len) {
+                const V v = psi[b0 + lane + 32 * j];
+                const float r2 = v.x * v.x, r2e = fmaf(v.x, v.x, -r2);
+                const float i2 = v.y * v.y, i2e = fmaf(v.y, v.y, -i2);
+                const float s = r2 + i2, bb = s - r2;
+                const float sl = ((r2 - (s - bb)) + (i2 - bb)) + r2e + i2e;
+                ff_add(acc, s, sl);
+#pragma unroll
+                for (int b = 0; b < 5; ++b)
+                    if ((j >> b) & 1) ff_add(ab[b], s, sl);
+            }
+        }
+        t = ff_val(acc);
+#pragma unroll
+        for (int b = 0; b < 5; ++b) bj[b] = ff_val(ab[b]);
+    } else {
+        t = 0.0;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) bj[b] = 0.0;
+        for (int j = 0; j < jn; ++j) {
+            if (lane + 32 * j < len) {
+                const double p = prob(psi[b0 + lane + 32 * j]);
+                t += p;
+#pragma unroll
+                for (int b = 0; b < 5; ++b)
+                    if ((j >> b) & 1) bj[b] += p;
+            }
+        }
+    }
+    const double total = warp_sum(t);
+    if (bits) {
+        double out[10];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) out[b] = warp_sum(((lane >> b) & 1) ? t : 0.0);
+#pragma unroll
+        for (int b = 0; b < 5; ++b) out[5 + b] = warp_sum(bj[b]);
+        if (lane == 0)
+            for (int b = 0; b < 10; ++b) bits[wid * 10 + b] = b < blog ? out[b] : 0.0;
+    }
+    if (lane == 0) tot[wid] = total;
+}
+
+// <Z_i> = S - 2 * (mass with bit i set) from the block records: one CTA per
+// qubit, fixed-order reductions.
+__global__ void __launch_bounds__(256) k_expz_blocks(const double* __restrict__ tot, const double* __restrict__ bits,
+                                                     uint64_t nblocks, int blog, double* __restrict__ out) {
+    __shared__ double s1[256], s2[256];
+    const int i = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (uint64_t k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        const double tk = tot[k];
+        a += tk;
+        if (i < blog) b += bits[k * 10 + i];
+        else if ((k >> (i - blog)) & 1) b += tk;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = s1[0] - 2.0 * s2[0];
 }
 
 // ---- inclusive scan of doubles -------------------------------------------
@@ -189,66 +278,6 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
     }
 }
 
-// ---- <Z_i>: warp-per-segment partial sums --------------------------------
-// Segment = 32 x 32 amplitudes.  Lane bits 0..4 are fixed per lane, so each
-// lane keeps its own total; bits >= 5 are constant over each 32-amplitude
-// row, whose warp sum is added to bit accumulators held one per lane.
-template <typename V>
-__global__ void __launch_bounds__(256) k_expz_partial(const V* __restrict__ psi, int n, uint64_t N,
-                                                      double* __restrict__ part /* [grid][n+1] */) {
-    __shared__ double sh[8][40];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    double lane_tot = 0.0;   // sum over this lane's amplitudes
-    double bitacc = 0.0;     // lane b: sum of rows with bit (5 + b) set
-    double bitacc2 = 0.0;    // lane b: bit (37 + b) (unused for n <= 37)
-    const uint64_t rows = N >= 32 ? N / 32 : 1;
-    for (uint64_t r = gw; r < rows; r += nw) {
-        const uint64_t x = r * 32 + lane;
-        const double p = x < N ? prob(psi[x]) : 0.0;
-        lane_tot += p;
-        const double rs = warp_sum(p);
-        const uint64_t xb = r * 32;
-        if (lane + 5 < n && ((xb >> (lane + 5)) & 1)) bitacc += rs;
-        (void)bitacc2;
-    }
-    sh[w][lane] = bitacc;
-    // totals of lane bits: bit i (< 5) set lanes
-    for (int i = 0; i < 5; ++i) {
-        const double v = warp_sum(((lane >> i) & 1) ? lane_tot : 0.0);
-        if (lane == 0) sh[w][32 + i] = v;
-    }
-    const double tot = warp_sum(lane_tot);
-    if (lane == 0) sh[w][37] = tot;
-    __syncthreads();
-    if (threadIdx.x < 40) {
-        double v = 0.0;
-        for (int k = 0; k < 8; ++k) v += sh[k][threadIdx.x];
-        // layout per CTA: [0..n-1] = sum of p with bit i set, [n] = total
-        const int t = threadIdx.x;
-        double* P = part + (uint64_t)blockIdx.x * (n + 1);
-        if (t < 32) {
-            if (t + 5 < n) P[t + 5] = v;
-        } else if (t < 37) {
-            if (t - 32 < n) P[t - 32] = v;
-        } else if (t == 37) {
-            P[n] = v;
-        }
-    }
-}
-
-__global__ void k_expz_final(const double* __restrict__ part, int nparts, int n, double* __restrict__ out) {
-    const int i = threadIdx.x;
-    if (i >= n) return;
-    double s1 = 0.0, tot = 0.0;
-    for (int k = 0; k < nparts; ++k) {
-        s1 += part[(uint64_t)k * (n + 1) + i];
-        tot += part[(uint64_t)k * (n + 1) + n];
-    }
-    out[i] = tot - 2.0 * s1;
-}
-
 template <typename V>
 __global__ void __launch_bounds__(256) k_probs(const V* __restrict__ psi, uint64_t N, double* __restrict__ out) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -273,38 +302,49 @@ size_t nblocks_of(int n, int* blog) {
 }
 }  // namespace
 
-// Block sums -> inclusive block CDF, in h->red.
-int measure_block_sums(sv_state* h, double** cdf, int* blog_out, int64_t* nb_out) {
+// Block statistics in h->red: [raw block totals: nb][inclusive CDF: nb]
+// [chunk totals: nch][bit sums: 10 nb, when asked for].
+static int block_stats(sv_state* h, bool want_bits, double** tot_out, double** cdf_out, double** bits_out,
+                       int* blog_out, int64_t* nb_out) {
     int blog;
     const size_t nb = nblocks_of(h->n, &blog);
     const size_t nch = (nb + kScanCh - 1) / kScanCh;
-    const size_t need = sizeof(double) * (nb + nch + 64);
+    const size_t need = sizeof(double) * (2 * nb + nch + 64 + (want_bits ? 10 * nb : 0));
     int rc = ensure_scratch(&h->red, need, h->stream);
     if (rc) return rc;
-    double* bs = (double*)h->red.ptr;
-    double* tot = bs + nb;
-    const uint64_t N = 1ull << h->n;
+    double* tot = (double*)h->red.ptr;
+    double* cdf = tot + nb;
+    double* chunks = cdf + nb;
+    double* bits = want_bits ? chunks + nch + 64 : nullptr;
     const unsigned g = (unsigned)((nb * 32 + 255) / 256);
     count_launch();
     if (h->dtype == SV_C64)
-        k_block_sums<float2><<<g, 256, 0, h->stream>>>((const float2*)h->amps, N, blog, nb, bs);
+        k_block_stats<float2><<<g, 256, 0, h->stream>>>((const float2*)h->amps, blog, nb, tot, bits);
     else
-        k_block_sums<double2><<<g, 256, 0, h->stream>>>((const double2*)h->amps, N, blog, nb, bs);
+        k_block_stats<double2><<<g, 256, 0, h->stream>>>((const double2*)h->amps, blog, nb, tot, bits);
+    cudaError_t e = cudaMemcpyAsync(cdf, tot, sizeof(double) * nb, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "block totals copy");
     if (nch <= 1) {
         count_launch();
-        k_scan_chunks<<<1, kScanT, 0, h->stream>>>(bs, nb, nullptr);
+        k_scan_chunks<<<1, kScanT, 0, h->stream>>>(cdf, nb, nullptr);
     } else {
         count_launch(3);
-        k_chunk_totals<<<(unsigned)nch, kScanT, 0, h->stream>>>(bs, nb, tot);
-        k_scan_totals<<<1, kScanT, 0, h->stream>>>(tot, (int)nch);
-        k_scan_chunks<<<(unsigned)nch, kScanT, 0, h->stream>>>(bs, nb, tot);
+        k_chunk_totals<<<(unsigned)nch, kScanT, 0, h->stream>>>(cdf, nb, chunks);
+        k_scan_totals<<<1, kScanT, 0, h->stream>>>(chunks, (int)nch);
+        k_scan_chunks<<<(unsigned)nch, kScanT, 0, h->stream>>>(cdf, nb, chunks);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "block sums");
-    *cdf = bs;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "block statistics");
+    if (tot_out) *tot_out = tot;
+    *cdf_out = cdf;
+    if (bits_out) *bits_out = bits;
     *blog_out = blog;
     *nb_out = (int64_t)nb;
     return SV_OK;
+}
+
+int measure_block_sums(sv_state* h, double** cdf, int* blog_out, int64_t* nb_out) {
+    return block_stats(h, false, nullptr, cdf, nullptr, blog_out, nb_out);
 }
 
 cudaError_t launch_probs(sv_state* h, double* dev_out) {
@@ -331,34 +371,8 @@ int measure_norm(sv_state* h, double* host_out) {
     return SV_OK;
 }
 
-int measure_expect_z(sv_state* h, double* dev_out) {
-    const uint64_t N = 1ull << h->n;
-    const uint64_t rows = N >= 32 ? N / 32 : 1;
-    uint64_t g = (rows + 7) / 8;
-    const uint64_t cap = (uint64_t)sms() * 8;
-    if (g > cap) g = cap;
-    const size_t need = sizeof(double) * (size_t)g * (h->n + 1);
-    int rc = ensure_scratch(&h->red, need, h->stream);
-    if (rc) return rc;
-    double* part = (double*)h->red.ptr;
-    count_launch(2);
-    if (h->dtype == SV_C64)
-        k_expz_partial<float2><<<(unsigned)g, 256, 0, h->stream>>>((const float2*)h->amps, h->n, N, part);
-    else
-        k_expz_partial<double2><<<(unsigned)g, 256, 0, h->stream>>>((const double2*)h->amps, h->n, N, part);
-    k_expz_final<<<1, 64, 0, h->stream>>>(part, (int)g, h->n, dev_out);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "expect_z");
-    return SV_OK;
-}
-
-int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev_u, uint64_t* dev_out) {
-    if (shots == 0) return SV_OK;
-    double* cdf;
-    int blog;
-    int64_t nb;
-    int rc = measure_block_sums(h, &cdf, &blog, &nb);
-    if (rc) return rc;
+static cudaError_t launch_sample(sv_state* h, int blog, const double* cdf, int64_t nb, uint64_t shots,
+                                 uint64_t seed, const double* dev_u, uint64_t* dev_out) {
     uint64_t g = (shots * 32 + 255) / 256;
     const uint64_t cap = (uint64_t)sms() * 16;
     if (g > cap) g = cap;
@@ -369,7 +383,36 @@ int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev
     else
         k_sample<double2><<<(unsigned)g, 256, 0, h->stream>>>((const double2*)h->amps, h->n, blog, cdf,
                                                              (uint64_t)nb, shots, seed, dev_u, dev_out);
+    return cudaGetLastError();
+}
+
+// Shots and <Z_i> from ONE pass over the state (either output may be NULL).
+int measure_readout(sv_state* h, uint64_t shots, uint64_t seed, uint64_t* dev_samples, double* dev_expz) {
+    double *tot, *cdf, *bits;
+    int blog;
+    int64_t nb;
+    int rc = block_stats(h, dev_expz != nullptr, &tot, &cdf, &bits, &blog, &nb);
+    if (rc) return rc;
+    if (dev_expz) {
+        count_launch();
+        k_expz_blocks<<<h->n, 256, 0, h->stream>>>(tot, bits, (uint64_t)nb, blog, dev_expz);
+    }
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && dev_samples && shots) e = launch_sample(h, blog, cdf, nb, shots, seed, nullptr, dev_samples);
+    if (e != cudaSuccess) return cuda_fail(e, "read-out");
+    return SV_OK;
+}
+
+int measure_expect_z(sv_state* h, double* dev_out) { return measure_readout(h, 0, 0, nullptr, dev_out); }
+
+int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev_u, uint64_t* dev_out) {
+    if (shots == 0) return SV_OK;
+    double* cdf;
+    int blog;
+    int64_t nb;
+    int rc = measure_block_sums(h, &cdf, &blog, &nb);
+    if (rc) return rc;
+    cudaError_t e = launch_sample(h, blog, cdf, nb, shots, seed, dev_u, dev_out);
     if (e != cudaSuccess) return cuda_fail(e, "sample");
     return SV_OK;
 }
@@ -443,15 +486,14 @@ extern "C" int sv_sample_uniforms_noalloc(const void* dev_amps, int n, sv_dtype 
     const size_t nb = nblocks_of(n, &blog);
     const size_t nch = (nb + kScanCh - 1) / kScanCh;
     double* tot = bs + nb;  // nb + nch <= kNoAllocDoubles
-    const uint64_t N = 1ull << n;
     // Every scratch element is written before it is read within this call,
     // so nothing needs clearing; calls that overlap on the GPU race on it.
     const unsigned g = (unsigned)((nb * 32 + 255) / 256);
     count_launch();
     if (dt == SV_C64)
-        k_block_sums<float2><<<g, 256, 0, st>>>((const float2*)dev_amps, N, blog, nb, bs);
+        k_block_stats<float2><<<g, 256, 0, st>>>((const float2*)dev_amps, blog, nb, bs, nullptr);
     else
-        k_block_sums<double2><<<g, 256, 0, st>>>((const double2*)dev_amps, N, blog, nb, bs);
+        k_block_stats<double2><<<g, 256, 0, st>>>((const double2*)dev_amps, blog, nb, bs, nullptr);
     if (nch <= 1) {
         count_launch();
         k_scan_chunks<<<1, kScanT, 0, st>>>(bs, nb, nullptr);

@@ -182,6 +182,29 @@ def test_sampler_oracle_uniforms(dtype, n):
 
 
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
+@pytest.mark.parametrize("n", [4, 10, 15])
+def test_measure_device_one_pass(dtype, n):
+    """Shots and <Z> from one pass equal the separate entry points."""
+    torch = pytest.importorskip("torch")
+    g = W.random_u3_cx(n, 3, 90 + n)
+    h = S.sv_alloc(n, dtype)
+    try:
+        S.sv_init_basis(h, 0)
+        S.sv_apply_circuit(h, g)
+        ds = torch.zeros(3000, dtype=torch.int64, device="cuda")
+        dz = torch.zeros(n, dtype=torch.float64, device="cuda")
+        S.sv_measure_device(h, 3000, 42, ds.data_ptr(), dz.data_ptr())
+        torch.cuda.synchronize()
+        assert np.array_equal(ds.cpu().numpy().view(np.uint64), S.sv_sample(h, 3000, 42))
+        ez = S.sv_expect_z(h)
+        assert np.array_equal(dz.cpu().numpy(), ez)
+        ref = U.run_oracle(n, g)
+        assert np.abs(ez - oracle.expect_z(ref)).max() <= (1e-5 if dtype == S.C64 else 1e-12)
+    finally:
+        S.sv_free(h)
+
+
+@pytest.mark.parametrize("dtype", DT, ids=DTN.get)
 def test_sampler_philox_matches_oracle_uniforms(dtype):
     n = 10
     g = W.random_u3_cx(n, 3, 8)
