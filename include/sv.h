@@ -277,8 +277,14 @@ int sv_cost_model_predict(const float *host_feat, int count, double *host_ms);
 int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate *gates, size_t count, sv_options *chosen,
                          double *predicted_ms);
 /* Counters: circuits planned by the model, and judged mispredictions (the
- * greedy plan measured faster than the model's choice). */
+ * model's first choice was not the fastest of the plans the judge timed: its
+ * top three and the greedy plan). */
 int sv_cost_model_stats(int64_t *planned, int64_t *mispredicted);
+/* The options the judge settled on for a circuit already applied with
+ * SV_PLAN_MLP (the model's first choice until all judged calls are done) and
+ * that plan's measured time in ms (-1 if not timed yet). */
+int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate *gates, size_t count, sv_options *out,
+                         double *measured_ms);
 
 /* ---- misc -------------------------------------------------------------- */
 

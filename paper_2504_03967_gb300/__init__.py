@@ -352,6 +352,19 @@ def sv_cost_model_choose(n, dtype, gates):
     return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
 
 
+def sv_cost_model_judged(n, dtype, gates):
+    L = _cm_lib()
+    f = L.sv_cost_model_judged
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(sv_options),
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    g = as_gates(gates)
+    o = sv_options()
+    ms = ctypes.c_double()
+    _check(f(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(ms)))
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
+
+
 def sv_cost_model_stats():
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(_cm_lib().sv_cost_model_stats(ctypes.byref(a), ctypes.byref(b)))

@@ -3,15 +3,18 @@
 // For a new circuit every candidate plan is built on the host: greedy tile
 // passes for each fusion width k in 2..5 (App. D.2, "gate fusion = 5" as the
 // upper bound), tile width m, and (complex64, k >= 3) tensor cores on or off.
-// The MLP predicts each pass's time from its features, the candidate with the
-// smallest predicted total wins.  The greedy fixed-width plan is the fallback
-// when no model is loaded and the judge of the prediction: the first call
-// for a circuit runs the model's choice, the second the greedy plan, both
-// timed with CUDA events, and later calls keep whichever measured faster.
+// The MLP predicts each pass's time from its features and ranks the
+// candidates by predicted total.  The greedy fixed-width plan is the fallback
+// when no model is loaded and the judge of the prediction: the first calls
+// for a circuit time the model's top few candidates and the greedy plan with
+// CUDA events, and later calls keep whichever measured fastest.  A
+// misprediction is counted when the model's first choice was not the fastest.
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <numeric>
 #include <unordered_map>
 
 #include "sv_internal.h"
@@ -21,6 +24,8 @@ namespace sv {
 bool cost_model_predict(const std::vector<float>& feat, int count, std::vector<double>* ms);
 
 namespace {
+
+constexpr int kExplore = 3;  // model candidates timed by the judge
 
 uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
     const unsigned char* p = (const unsigned char*)data;
@@ -32,14 +37,13 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
 }
 
 struct Choice {
-    PlanOptions chosen, greedy;
+    std::vector<PlanOptions> trial;  // model's top candidates, then the greedy plan
+    std::vector<double> measured;    // ms per trial (-1: not yet)
     double predicted = 0.0;
-    int calls = 0;            // applies made with this entry
-    double t_chosen = -1.0;   // measured ms of the model's plan
-    double t_greedy = -1.0;   // measured ms of the greedy plan
-    bool use_greedy = false;  // judged: greedy measured faster
+    int calls = 0;
+    int best = 0;  // index into trial once judged
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int pending = -1;         // 0: events time the chosen plan, 1: the greedy plan
+    int pending = -1;  // trial timed by the events of the last call
 };
 
 std::mutex g_mu;
@@ -48,9 +52,9 @@ int64_t g_planned = 0, g_mispredicted = 0;
 
 }  // namespace
 
-// Predicted time of every candidate; returns the index of the best (or -1).
-int choose_options(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& base,
-                   PlanOptions* best, double* best_ms) {
+// Candidates ranked by predicted time (best first); false without a model.
+bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& base,
+                  std::vector<PlanOptions>* ranked, std::vector<double>* ranked_ms) {
     std::vector<PlanOptions> cands;
     const int ms_c64[] = {12, 13, 14}, ms_c128[] = {11, 12, 13};
     for (int k = 2; k <= kMaxK; ++k)
@@ -75,28 +79,27 @@ int choose_options(int n, int dtype, const std::vector<CGate>& gates, const Plan
         Plan p;
         plan_greedy(n, dtype, gates, cands[c], &p);
         for (HostPass& hp : p.passes) {
-            // the features must describe how the pass will run: mark blocks
-            // that would go to the tensor cores
             const std::vector<float> f = pass_features(n, dtype, hp, cands[c].tensor == 0);
             feat.insert(feat.end(), f.begin(), f.end());
             owner.push_back((int)c);
         }
     }
     std::vector<double> ms;
-    if (!cost_model_predict(feat, (int)owner.size(), &ms)) return -1;
+    if (!cost_model_predict(feat, (int)owner.size(), &ms)) return false;
     std::vector<double> tot(cands.size(), 0.0);
     for (size_t i = 0; i < owner.size(); ++i) tot[owner[i]] += ms[i];
-    int bi = 0;
-    for (size_t c = 1; c < cands.size(); ++c)
-        if (tot[c] < tot[bi]) bi = (int)c;
-    *best = cands[bi];
-    *best_ms = tot[bi];
-    return bi;
+    std::vector<int> idx(cands.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return tot[a] < tot[b]; });
+    ranked->clear();
+    ranked_ms->clear();
+    for (int i : idx) {
+        ranked->push_back(cands[i]);
+        ranked_ms->push_back(tot[i]);
+    }
+    return true;
 }
 
-// Options for this apply under SV_PLAN_MLP (and bookkeeping for the judge).
-// *timing_slot is set to the Choice's event pair to record around the passes,
-// or nullptr.
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
                              const PlanOptions& base, cudaEvent_t* ev0, cudaEvent_t* ev1) {
     *ev0 = *ev1 = nullptr;
@@ -106,30 +109,33 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
     if (it == g_cache.end()) {
+        std::vector<PlanOptions> ranked;
+        std::vector<double> rms;
+        if (!rank_options(h->n, h->dtype, cg, base, &ranked, &rms)) return base;  // no model: greedy
         Choice c;
-        c.greedy = base;
-        if (choose_options(h->n, h->dtype, cg, base, &c.chosen, &c.predicted) < 0) return base;  // no model
+        for (int i = 0; i < kExplore && i < (int)ranked.size(); ++i) c.trial.push_back(ranked[i]);
+        c.trial.push_back(base);
+        c.measured.assign(c.trial.size(), -1.0);
+        c.predicted = rms[0];
         ++g_planned;
         if (g_cache.size() > 4096) g_cache.clear();
         it = g_cache.emplace(key, c).first;
     }
     Choice& c = it->second;
-    // collect the timing of the previous judged call
-    if (c.pending >= 0 && c.e1) {
+    if (c.pending >= 0 && c.e1) {  // collect the previous judged call
         float ms = 0.f;
-        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess) {
-            if (c.pending == 0) c.t_chosen = ms;
-            else c.t_greedy = ms;
-        }
+        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess)
+            c.measured[c.pending] = ms;
         cudaGetLastError();
         c.pending = -1;
-        if (c.t_chosen >= 0 && c.t_greedy >= 0) {
-            c.use_greedy = c.t_greedy < c.t_chosen;
-            if (c.use_greedy) ++g_mispredicted;
+        if (c.calls == (int)c.trial.size()) {
+            c.best = (int)(std::min_element(c.measured.begin(), c.measured.end()) - c.measured.begin());
+            if (c.best != 0) ++g_mispredicted;
         }
     }
-    const int call = c.calls++;
-    if (call < 2) {
+    const int call = c.calls;
+    if (call < (int)c.trial.size()) {
+        ++c.calls;
         if (!c.e0) {
             cudaEventCreate(&c.e0);
             cudaEventCreate(&c.e1);
@@ -137,9 +143,9 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
         c.pending = call;
         *ev0 = c.e0;
         *ev1 = c.e1;
-        return call == 0 ? c.chosen : c.greedy;
+        return c.trial[call];
     }
-    return c.use_greedy ? c.greedy : c.chosen;
+    return c.trial[c.best];
 }
 
 }  // namespace sv
@@ -156,15 +162,15 @@ extern "C" int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate* gates, si
     if (canonicalise(n, gates, count, &cg, &bad) != SV_OK)
         return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
     const PlanOptions base = resolve_options(n, dt, nullptr);
-    PlanOptions best;
-    double ms = 0.0;
-    if (choose_options(n, dt, cg, base, &best, &ms) < 0) return set_error(SV_EINVAL, "no cost model loaded");
+    std::vector<PlanOptions> ranked;
+    std::vector<double> rms;
+    if (!rank_options(n, dt, cg, base, &ranked, &rms)) return set_error(SV_EINVAL, "no cost model loaded");
     memset(chosen, 0, sizeof(*chosen));
-    chosen->k_max = best.k_max;
-    chosen->tile_m = best.tile_m;
+    chosen->k_max = ranked[0].k_max;
+    chosen->tile_m = ranked[0].tile_m;
     chosen->planner = SV_PLAN_GREEDY;
-    chosen->tensor = best.tensor == 0 ? 1 : -1;
-    *predicted_ms = ms;
+    chosen->tensor = ranked[0].tensor == 0 ? 1 : -1;
+    *predicted_ms = rms[0];
     return SV_OK;
 }
 
@@ -172,5 +178,38 @@ extern "C" int sv_cost_model_stats(int64_t* planned, int64_t* mispredicted) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (planned) *planned = g_planned;
     if (mispredicted) *mispredicted = g_mispredicted;
+    return SV_OK;
+}
+
+// The options the judge settled on for a circuit (after its timed calls), or
+// the model's first choice before that.
+extern "C" int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate* gates, size_t count, sv_options* out,
+                                    double* measured_ms) {
+    if (!out || (count && !gates)) return set_error(SV_EINVAL, "bad arguments");
+    uint64_t key = fnv1a(gates, count * sizeof(sv_gate), 1469598103934665603ull);
+    const PlanOptions base = resolve_options(n, dt, nullptr);
+    const int meta[3] = {n, (int)dt, base.tensor};
+    key = fnv1a(meta, sizeof(meta), key);
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) return set_error(SV_EINVAL, "circuit not planned by the cost model yet");
+    Choice& c = it->second;
+    if (c.pending >= 0 && c.e1) {  // finish the last judged call
+        float ms = 0.f;
+        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess)
+            c.measured[c.pending] = ms;
+        cudaGetLastError();
+        c.pending = -1;
+        if (c.calls == (int)c.trial.size()) {
+            c.best = (int)(std::min_element(c.measured.begin(), c.measured.end()) - c.measured.begin());
+            if (c.best != 0) ++g_mispredicted;
+        }
+    }
+    const PlanOptions& po = c.trial[c.calls == (int)c.trial.size() ? c.best : 0];
+    memset(out, 0, sizeof(*out));
+    out->k_max = po.k_max;
+    out->tile_m = po.tile_m;
+    out->tensor = po.tensor == 0 ? 1 : -1;
+    if (measured_ms) *measured_ms = c.measured[c.calls == (int)c.trial.size() ? c.best : 0];
     return SV_OK;
 }
