@@ -112,6 +112,8 @@ typedef struct {
     int64_t max_k;        /* widest dense block */
     int64_t bytes_moved;  /* algorithmic HBM bytes: sum over passes of the
                              amplitudes each pass reads and writes */
+    int64_t gate_ops;     /* of dense_ops, the blocks applied as their gate
+                             sequence in registers instead of a 2^k matrix */
 } sv_plan_info;
 
 /* ---- state lifetime (App. A, Eq. "hilbert") ---------------------------- */

@@ -43,7 +43,8 @@ class sv_options(ctypes.Structure):
 
 class sv_plan_info(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_ops", ctypes.c_int64),
-                ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64)]
+                ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64),
+                ("gate_ops", ctypes.c_int64)]
 
 
 _lib = None

@@ -231,6 +231,177 @@ __device__ __forceinline__ void tile_dense(V* __restrict__ tile, int m, const Op
     }
 }
 
+// ---------------------------------------------------------------------------
+// Gate-sequence block: one thread holds a whole 2^K-amplitude slice in
+// registers and applies the block's gates one after the other, each with
+// code unrolled for its (compile-time) position inside the block:
+//   GR_U   2x2 complex matrix on position a        8 FMA per amplitude
+//   GR_UR  2x2 real matrix on position a           4
+//   GR_DT  2^K-entry diagonal (phase) table        one complex product
+//   GR_CX  controlled-NOT (control a, target b)    register moves
+//   GR_SWAP                                        register moves
+// ---------------------------------------------------------------------------
+template <typename V, int K, int P>
+__device__ __forceinline__ void reg_u(V* v, V u00, V u01, V u10, V u11) {
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if (!((j >> P) & 1)) {
+            const V a = v[j], b = v[j | (1 << P)];
+            v[j] = cfma(u00, a, cmul(u01, b));
+            v[j | (1 << P)] = cfma(u10, a, cmul(u11, b));
+        }
+}
+template <typename V, int K, int P, typename R>
+__device__ __forceinline__ void reg_ur(V* v, R u00, R u01, R u10, R u11) {
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if (!((j >> P) & 1)) {
+            const V a = v[j], b = v[j | (1 << P)];
+            V x, y;
+            x.x = fma(u00, a.x, u01 * b.x);
+            x.y = fma(u00, a.y, u01 * b.y);
+            y.x = fma(u10, a.x, u11 * b.x);
+            y.y = fma(u10, a.y, u11 * b.y);
+            v[j] = x;
+            v[j | (1 << P)] = y;
+        }
+}
+template <typename V, int K, int C, int T>
+__device__ __forceinline__ void reg_cx(V* v) {
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if (((j >> C) & 1) && !((j >> T) & 1)) {
+            const V a = v[j];
+            v[j] = v[j | (1 << T)];
+            v[j | (1 << T)] = a;
+        }
+}
+template <typename V, int K, int A, int B>
+__device__ __forceinline__ void reg_swap(V* v) {
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if (((j >> A) & 1) && !((j >> B) & 1)) {
+            const V a = v[j];
+            v[j] = v[j ^ (1 << A) ^ (1 << B)];
+            v[j ^ (1 << A) ^ (1 << B)] = a;
+        }
+}
+
+template <typename V, int K>
+__device__ __forceinline__ void reg_u_any(V* v, int p, V u00, V u01, V u10, V u11) {
+    switch (p) {
+    case 0: reg_u<V, K, 0>(v, u00, u01, u10, u11); break;
+    case 1: if constexpr (K > 1) reg_u<V, K, 1>(v, u00, u01, u10, u11); break;
+    case 2: if constexpr (K > 2) reg_u<V, K, 2>(v, u00, u01, u10, u11); break;
+    case 3: if constexpr (K > 3) reg_u<V, K, 3>(v, u00, u01, u10, u11); break;
+    default: if constexpr (K > 4) reg_u<V, K, 4>(v, u00, u01, u10, u11); break;
+    }
+}
+template <typename V, int K, typename R>
+__device__ __forceinline__ void reg_ur_any(V* v, int p, R u00, R u01, R u10, R u11) {
+    switch (p) {
+    case 0: reg_ur<V, K, 0>(v, u00, u01, u10, u11); break;
+    case 1: if constexpr (K > 1) reg_ur<V, K, 1>(v, u00, u01, u10, u11); break;
+    case 2: if constexpr (K > 2) reg_ur<V, K, 2>(v, u00, u01, u10, u11); break;
+    case 3: if constexpr (K > 3) reg_ur<V, K, 3>(v, u00, u01, u10, u11); break;
+    default: if constexpr (K > 4) reg_ur<V, K, 4>(v, u00, u01, u10, u11); break;
+    }
+}
+// (a, b) -> compile-time pair; a != b, both < K
+template <typename V, int K, int A>
+__device__ __forceinline__ void reg_cx_b(V* v, int b) {
+    switch (b) {
+    case 0: if constexpr (A != 0) reg_cx<V, K, A, 0>(v); break;
+    case 1: if constexpr (A != 1 && K > 1) reg_cx<V, K, A, 1>(v); break;
+    case 2: if constexpr (A != 2 && K > 2) reg_cx<V, K, A, 2>(v); break;
+    case 3: if constexpr (A != 3 && K > 3) reg_cx<V, K, A, 3>(v); break;
+    default: if constexpr (A != 4 && K > 4) reg_cx<V, K, A, 4>(v); break;
+    }
+}
+template <typename V, int K>
+__device__ __forceinline__ void reg_cx_any(V* v, int a, int b) {
+    switch (a) {
+    case 0: reg_cx_b<V, K, 0>(v, b); break;
+    case 1: if constexpr (K > 1) reg_cx_b<V, K, 1>(v, b); break;
+    case 2: if constexpr (K > 2) reg_cx_b<V, K, 2>(v, b); break;
+    case 3: if constexpr (K > 3) reg_cx_b<V, K, 3>(v, b); break;
+    default: if constexpr (K > 4) reg_cx_b<V, K, 4>(v, b); break;
+    }
+}
+template <typename V, int K, int A>
+__device__ __forceinline__ void reg_swap_b(V* v, int b) {
+    switch (b) {
+    case 0: if constexpr (A != 0) reg_swap<V, K, A, 0>(v); break;
+    case 1: if constexpr (A != 1 && K > 1) reg_swap<V, K, A, 1>(v); break;
+    case 2: if constexpr (A != 2 && K > 2) reg_swap<V, K, A, 2>(v); break;
+    case 3: if constexpr (A != 3 && K > 3) reg_swap<V, K, A, 3>(v); break;
+    default: if constexpr (A != 4 && K > 4) reg_swap<V, K, A, 4>(v); break;
+    }
+}
+template <typename V, int K>
+__device__ __forceinline__ void reg_swap_any(V* v, int a, int b) {
+    switch (a) {
+    case 0: reg_swap_b<V, K, 0>(v, b); break;
+    case 1: if constexpr (K > 1) reg_swap_b<V, K, 1>(v, b); break;
+    case 2: if constexpr (K > 2) reg_swap_b<V, K, 2>(v, b); break;
+    case 3: if constexpr (K > 3) reg_swap_b<V, K, 3>(v, b); break;
+    default: if constexpr (K > 4) reg_swap_b<V, K, 4>(v, b); break;
+    }
+}
+
+// recs/sdata: the op's gate records and matrices/tables (shared memory).
+template <typename V, int K>
+__device__ __forceinline__ void tile_gates(V* __restrict__ tile, int m, const OpDev& op, const GateRec* recs,
+                                           const V* __restrict__ sdata) {
+    constexpr int D = 1 << K;
+    using R = decltype(V().x);
+    int bitv[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) bitv[i] = 1 << op.lq[i];
+    const int nslices = 1 << (m - K);
+    const int nrec = op.nrec;
+    for (int s = threadIdx.x; s < nslices; s += blockDim.x) {
+        int base = s;
+#pragma unroll
+        for (int i = 0; i < K; ++i) base = (int)insert_zero((uint64_t)base, op.lq[i]);
+        V v[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            int o = 0;
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+                if ((j >> i) & 1) o += bitv[i];
+            v[j] = tile[base + o];
+        }
+        for (int r = 0; r < nrec; ++r) {
+            const GateRec g = recs[r];
+            switch (g.kind) {
+            case GR_U:
+                reg_u_any<V, K>(v, g.a, sdata[g.off], sdata[g.off + 1], sdata[g.off + 2], sdata[g.off + 3]);
+                break;
+            case GR_UR:
+                reg_ur_any<V, K, R>(v, g.a, sdata[g.off].x, sdata[g.off + 1].x, sdata[g.off + 2].x,
+                                    sdata[g.off + 3].x);
+                break;
+            case GR_DT:
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[j] = cmul(sdata[g.off + j], v[j]);
+                break;
+            case GR_CX: reg_cx_any<V, K>(v, g.a, g.b); break;
+            default: reg_swap_any<V, K>(v, g.a, g.b); break;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            int o = 0;
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+                if ((j >> i) & 1) o += bitv[i];
+            tile[base + o] = v[j];
+        }
+    }
+}
+
 template <typename R> __device__ __forceinline__ R frac_r(R v) { return v - rint(v); }
 
 __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
@@ -496,7 +667,8 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
                                                       const OpDev* __restrict__ ops,
                                                       const typename CT<R>::V* __restrict__ mats,
                                                       const double* __restrict__ diags,
-                                                      const float* __restrict__ tcmats, int* __restrict__ err) {
+                                                      const float* __restrict__ tcmats, int* __restrict__ err,
+                                                      const GateRec* __restrict__ grecs) {
     using V = typename CT<R>::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
@@ -578,6 +750,18 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
                     default: tile_dense_tc<5>(tile, m, op, sB, tmem_base, s_mbar, &phase, s_abort, err); break;
                     }
                 }
+            } else if (op.kind == OP_GATES) {
+                V* sd = (V*)work;
+                GateRec* sr = (GateRec*)(sd + kMaxGateData);
+                for (int e = threadIdx.x; e < op.ndata; e += blockDim.x) sd[e] = mats[op.mat_off + e];
+                for (int e = threadIdx.x; e < op.nrec; e += blockDim.x) sr[e] = grecs[op.rec_off + e];
+                __syncthreads();
+                switch (op.k) {  // k <= max_gates_k: 4 (complex64), 3 (complex128)
+                case 1: tile_gates<V, 1>(tile, m, op, sr, sd); break;
+                case 2: tile_gates<V, 2>(tile, m, op, sr, sd); break;
+                case 3: tile_gates<V, 3>(tile, m, op, sr, sd); break;
+                default: if constexpr (sizeof(V) == 8) tile_gates<V, 4>(tile, m, op, sr, sd); break;
+                }
             } else if (op.kind == OP_DENSE) {
                 V* sU = (V*)work;
                 const int DD = 1 << (2 * op.k);
@@ -650,7 +834,8 @@ template <typename R>
 __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __restrict__ pd, int C,
                                                              const OpDev* __restrict__ ops,
                                                              const typename CT<R>::V* __restrict__ mats,
-                                                             const double* __restrict__ diags, int mmax,
+                                                             const double* __restrict__ diags,
+                                                             const GateRec* __restrict__ grecs, int mmax,
                                                              uint64_t shots, uint64_t seed,
                                                              const int* __restrict__ gidx,
                                                              uint64_t* __restrict__ samples,
@@ -691,7 +876,19 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
         __syncthreads();
         for (int oi = P.op_begin; oi < P.op_end; ++oi) {
             const OpDev op = ops[oi];
-            if (op.kind == OP_DENSE) {
+            if (op.kind == OP_GATES) {
+                V* sd = (V*)work;
+                GateRec* sr = (GateRec*)(sd + kMaxGateData);
+                for (int e = tid; e < op.ndata; e += blockDim.x) sd[e] = mats[op.mat_off + e];
+                for (int e = tid; e < op.nrec; e += blockDim.x) sr[e] = grecs[op.rec_off + e];
+                __syncthreads();
+                switch (op.k) {  // k <= max_gates_k: 4 (complex64), 3 (complex128)
+                case 1: tile_gates<V, 1>(tile, m, op, sr, sd); break;
+                case 2: tile_gates<V, 2>(tile, m, op, sr, sd); break;
+                case 3: tile_gates<V, 3>(tile, m, op, sr, sd); break;
+                default: if constexpr (sizeof(V) == 8) tile_gates<V, 4>(tile, m, op, sr, sd); break;
+                }
+            } else if (op.kind == OP_DENSE) {
                 V* sU = (V*)work;
                 const int DD = 1 << (2 * op.k);
                 for (int e = tid; e < DD; e += blockDim.x) sU[e] = mats[op.mat_off + e];
@@ -808,12 +1005,14 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
     if (dtype == SV_C64)
         k_batch_small<float><<<grid, kPassThreads, smem, st>>>(
             (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
-            (const float2*)(b + blob.mat_off), (const double*)(b + blob.diag_off), mmax, shots, seed, gidx,
+            (const float2*)(b + blob.mat_off), (const double*)(b + blob.diag_off),
+            (const GateRec*)(b + blob.rec_off), mmax, shots, seed, gidx,
             samples, expz, nmax, counter);
     else
         k_batch_small<double><<<grid, kPassThreads, smem, st>>>(
             (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
-            (const double2*)(b + blob.mat_off), (const double*)(b + blob.diag_off), mmax, shots, seed, gidx,
+            (const double2*)(b + blob.mat_off), (const double*)(b + blob.diag_off),
+            (const GateRec*)(b + blob.rec_off), mmax, shots, seed, gidx,
             samples, expz, nmax, counter);
     return cudaGetLastError();
 }
@@ -920,7 +1119,7 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     k_pass<R, TC><<<(unsigned)grid, kPassThreads, smem, h->stream>>>(
         (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, (const OpDev*)(b + blob.op_off),
         (const V*)(b + blob.mat_off), (const double*)(b + blob.diag_off), (const float*)(b + blob.tc_off),
-        (int*)h->err.ptr);
+        (int*)h->err.ptr, (const GateRec*)(b + blob.rec_off));
     return cudaGetLastError();
 }
 

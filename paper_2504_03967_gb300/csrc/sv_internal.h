@@ -46,7 +46,19 @@ int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out,
 // 2^L amplitudes is contiguous), applies its ops in shared memory and writes
 // the tile back: one HBM read and one write of the state per pass.
 // ---------------------------------------------------------------------------
-enum OpKind { OP_DENSE = 0, OP_DIAG = 1 };
+enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2 };
+
+// Gate-sequence block records (positions are block-local bits, data offsets
+// index the op's own complex values).
+enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4 };
+struct GateRec {
+    int kind, a, b, off;
+};
+constexpr int kMaxGateRecs = 64;     // records per gate-sequence op
+constexpr int kMaxGateData = 768;    // complex values per gate-sequence op
+// Widest gate-sequence block: its 2^k amplitudes per thread must stay in
+// registers under the pass kernel's 80-register budget.
+inline int max_gates_k(int dtype) { return dtype == SV_C64 ? 4 : 3; }
 
 struct DiagForm {
     // phase(x) = c + sum_q a[q] x_q + sum_{p<q} b[p*n+q] x_p x_q  (radians)
@@ -68,9 +80,10 @@ struct DiagForm {
 
 struct HostOp {
     int kind;
-    std::vector<int> qubits;  // dense: sorted ascending, block bit i <-> qubits[i]
-    std::vector<cd> mat;      // dense: 2^k x 2^k row-major
+    std::vector<int> qubits;  // dense / gates: sorted ascending, block bit i <-> qubits[i]
+    std::vector<cd> mat;      // dense: 2^k x 2^k row-major; gates: the records' data
     DiagForm diag;            // diag
+    std::vector<GateRec> recs;  // gates
     int ngates = 0;           // logical gates folded into the op
 };
 
@@ -137,6 +150,9 @@ struct OpDev {
     int ngates;
     int tc;        // dense on the tensor cores (c64, k >= 3)
     int tc_off;    // float offset of its B operands [hi | lo] in the tc section
+    int nrec;      // gates: number of records
+    int rec_off;   // gates: index of the first record in the record section
+    int ndata;     // gates: complex values at mat_off
 };
 
 // Tensor-core dense block of k qubits (D = 2^k): B operand = [Ur; Ui], N = 2D
@@ -191,7 +207,7 @@ __host__ __device__ inline size_t diag_doubles(int m, int no) { return (size_t)D
 
 struct PlanBlob {
     std::vector<unsigned char> bytes;
-    size_t pass_off = 0, op_off = 0, mat_off = 0, diag_off = 0, tc_off = 0;
+    size_t pass_off = 0, op_off = 0, mat_off = 0, diag_off = 0, tc_off = 0, rec_off = 0;
     int npasses = 0;
 };
 

@@ -84,6 +84,7 @@ void make_canonical(const sv_gate& g, CGate* c) {
 struct Block {
     std::vector<int> qubits;  // sorted
     std::vector<cd> mat;
+    std::vector<CGate> seq;   // the gates multiplied into mat, in order
     int ngates = 0;
     bool active() const { return !qubits.empty(); }
     int pos(int q) const {
@@ -191,6 +192,75 @@ bool touches(const DiagForm& D, const CGate& g) {
     for (int i = 0; i < g.nq; ++i)
         if (D.support[g.q[i]]) return true;
     return false;
+}
+
+// Estimated CUDA-core instructions per amplitude of a block of k qubits as a
+// dense 2^k x 2^k product, and as a gate sequence applied in registers.
+double dense_cost(int k) { return 4.0 * (double)(1 << k) + 2.0; }
+double gate_sequence_cost(const std::vector<GateRec>& recs) {
+    double c = 2.0;
+    for (const GateRec& r : recs) c += r.kind == GR_U ? 8.0 : r.kind == GR_UR ? 4.0 : r.kind == GR_DT ? 5.0 : 1.0;
+    return c;
+}
+
+bool is_real(const cd* m, int cnt) {
+    for (int i = 0; i < cnt; ++i)
+        if (m[i].imag() != 0.0) return false;
+    return true;
+}
+
+// The block as a sequence on block-local positions: consecutive one-qubit
+// gates on one position multiplied together, runs of diagonal gates folded
+// into one 2^k-entry phase table, CX and SWAP kept as permutations.  False
+// when the block holds a gate this form does not cover or exceeds the
+// record limits.
+bool gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<cd>* data) {
+    recs->clear();
+    data->clear();
+    const int k = (int)B.qubits.size(), D = 1 << k;
+    std::vector<double> ph(D, 0.0);
+    bool dpend = false;
+    auto flush_diag = [&]() {
+        if (!dpend) return;
+        recs->push_back(GateRec{GR_DT, 0, 0, (int)data->size()});
+        for (int j = 0; j < D; ++j) data->push_back(std::polar(1.0, ph[j]));
+        std::fill(ph.begin(), ph.end(), 0.0);
+        dpend = false;
+    };
+    for (const CGate& g : B.seq) {
+        if (g.kind == GK_DIAG) {
+            const int p0 = B.pos(g.q[0]), p1 = g.nq > 1 ? B.pos(g.q[1]) : 0;
+            for (int j = 0; j < D; ++j) {
+                int li = (j >> p0) & 1;
+                if (g.nq > 1) li |= ((j >> p1) & 1) << 1;
+                ph[j] += g.ph[li];
+            }
+            dpend = true;
+            continue;
+        }
+        flush_diag();
+        if (g.nq == 1) {
+            const int p = B.pos(g.q[0]);
+            if (!recs->empty() && (recs->back().kind == GR_U || recs->back().kind == GR_UR) && recs->back().a == p) {
+                cd* Mp = data->data() + recs->back().off;  // merge: M = G * M_prev
+                const cd M[4] = {g.m[0] * Mp[0] + g.m[1] * Mp[2], g.m[0] * Mp[1] + g.m[1] * Mp[3],
+                                 g.m[2] * Mp[0] + g.m[3] * Mp[2], g.m[2] * Mp[1] + g.m[3] * Mp[3]};
+                for (int i = 0; i < 4; ++i) Mp[i] = M[i];
+                recs->back().kind = is_real(Mp, 4) ? GR_UR : GR_U;
+            } else {
+                recs->push_back(GateRec{is_real(g.m, 4) ? GR_UR : GR_U, p, 0, (int)data->size()});
+                for (int i = 0; i < 4; ++i) data->push_back(g.m[i]);
+            }
+        } else if (g.type == SV_CX) {
+            recs->push_back(GateRec{GR_CX, B.pos(g.q[0]), B.pos(g.q[1]), 0});
+        } else if (g.type == SV_SWAP) {
+            recs->push_back(GateRec{GR_SWAP, B.pos(g.q[0]), B.pos(g.q[1]), 0});
+        } else {
+            return false;
+        }
+    }
+    flush_diag();
+    return (int)recs->size() <= kMaxGateRecs && (int)data->size() <= kMaxGateData;
 }
 
 }  // namespace
@@ -320,10 +390,19 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
         auto flushB = [&]() {
             if (!B.active()) return;
             HostOp op;
-            op.kind = OP_DENSE;
             op.qubits = B.qubits;
-            op.mat = B.mat;
             op.ngates = B.ngates;
+            // the cheaper representation: the dense 2^k matrix, or the gate
+            // sequence applied in registers (tensor-core blocks stay dense)
+            const bool tc_block = po.tensor == 0 && dtype == SV_C64 && (int)B.qubits.size() >= kMinTcK;
+            if (!tc_block && (int)B.qubits.size() <= max_gates_k(dtype) && gate_sequence(B, &op.recs, &op.mat) &&
+                gate_sequence_cost(op.recs) <= dense_cost((int)B.qubits.size())) {
+                op.kind = OP_GATES;
+            } else {
+                op.kind = OP_DENSE;
+                op.recs.clear();
+                op.mat = B.mat;
+            }
             pass.ops.push_back(std::move(op));
             B = Block();
         };
@@ -364,6 +443,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                 }
                 if (inB || widen) {
                     block_apply_diag(&B, g);
+                    B.seq.push_back(g);
                     B.ngates++;
                 } else {
                     diag_add(&D, n, g);
@@ -387,6 +467,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
             }
             expand_block(&B, u);
             block_apply_dense(&B, g);
+            B.seq.push_back(g);
             B.ngates++;
         }
         flushB();
@@ -455,8 +536,9 @@ void plan_summary(const Plan& p, sv_plan_info* info) {
         for (const HostPass& hp : p.passes) {
             bytes += 2.0 * N * s;
             for (const HostOp& o : hp.ops) {
-                if (o.kind == OP_DENSE) {
+                if (o.kind == OP_DENSE || o.kind == OP_GATES) {
                     info->dense_ops++;
+                    info->gate_ops += o.kind == OP_GATES;
                     info->max_k = std::max<int64_t>(info->max_k, (int64_t)o.qubits.size());
                 } else {
                     info->diag_ops++;
@@ -477,10 +559,10 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tenso
     double flops = 0.0, msize = 0.0;
     int ndiag = 0;
     for (const HostOp& o : p.ops) {
-        if (o.kind == OP_DENSE) {
+        if (o.kind == OP_DENSE || o.kind == OP_GATES) {
             const int k = (int)o.qubits.size();
             f[3 + k] += 1.0f / 8.0f;  // f[4..8]: dense blocks of width 1..5
-            flops += ldexp(1.0, k);
+            flops += (o.kind == OP_GATES ? gate_sequence_cost(o.recs) : dense_cost(k)) / 4.0;
             msize += ldexp(1.0, 2 * k);
         } else {
             ++ndiag;
@@ -568,7 +650,7 @@ void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, 
 }  // namespace
 
 void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
-    size_t nops = 0, nmat = 0, ndiag = 0, ntc = 0, npass = 0;
+    size_t nops = 0, nmat = 0, ndiag = 0, ntc = 0, npass = 0, nrecs = 0;
     auto use_tc = [&](const Plan& p, const HostOp& o) {
         return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
     };
@@ -580,8 +662,9 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
       for (const HostPass& hp : p.passes)
         for (const HostOp& o : hp.ops) {
             ++nops;
-            if (o.kind == OP_DENSE) nmat += o.mat.size();
+            if (o.kind == OP_DENSE || o.kind == OP_GATES) nmat += o.mat.size();
             else ndiag += diag_doubles((int)hp.tile.size(), n - (int)hp.tile.size());
+            if (o.kind == OP_GATES) nrecs += o.recs.size();
             if (use_tc(p, o)) ntc += (size_t)tc_floats((int)o.qubits.size());
         }
     }
@@ -592,11 +675,13 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
     blob->mat_off = align16(blob->op_off + sizeof(OpDev) * nops);
     blob->diag_off = align16(blob->mat_off + csz * nmat);
     blob->tc_off = align16(blob->diag_off + sizeof(double) * ndiag);
-    const size_t total = align16(blob->tc_off + sizeof(float) * ntc);
+    blob->rec_off = align16(blob->tc_off + sizeof(float) * ntc);
+    const size_t total = align16(blob->rec_off + sizeof(GateRec) * nrecs);
     blob->bytes.assign(total, 0);
     unsigned char* base = blob->bytes.data();
     float* tcf = (float*)(base + blob->tc_off);
-    size_t ti = 0;
+    size_t ti = 0, ri = 0;
+    GateRec* rg = (GateRec*)(base + blob->rec_off);
     PassDev* pd = (PassDev*)(base + blob->pass_off);
     OpDev* od = (OpDev*)(base + blob->op_off);
     double* dg = (double*)(base + blob->diag_off);
@@ -627,7 +712,13 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
             memset(&O, 0, sizeof(O));
             O.kind = o.kind;
             O.ngates = o.ngates;
-            if (o.kind == OP_DENSE) {
+            if (o.kind == OP_GATES) {
+                O.nrec = (int)o.recs.size();
+                O.rec_off = (int)ri;
+                O.ndata = (int)o.mat.size();
+                for (const GateRec& r : o.recs) rg[ri++] = r;
+            }
+            if (o.kind == OP_DENSE || o.kind == OP_GATES) {
                 O.k = (int)o.qubits.size();
                 for (int i = 0; i < O.k; ++i) O.lq[i] = loc[o.qubits[i]];
                 O.mat_off = (int)mi;

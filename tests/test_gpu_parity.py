@@ -64,6 +64,23 @@ def test_mixed_all_gate_types(dtype, planner, n):
 
 
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+@pytest.mark.parametrize("kind", ["mixed", "qft", "cx_blocks"])
+def test_gate_sequence_blocks(dtype, k, kind):
+    """Blocks applied as their gate sequence in registers (2x2 complex and
+    real matrices, phase tables, CX and SWAP moves) next to dense blocks."""
+    n = 15
+    rng = np.random.default_rng(300 + k)
+    g = {"mixed": lambda: random_mixed_circuit(n, 120, rng), "qft": lambda: W.qft(n),
+         "cx_blocks": lambda: W.random_cx_blocks(n, 40, 9 + k)}[kind]()
+    info = S.sv_plan_circuit(n, dtype, g, k_max=k, tile_m=12)
+    assert info["gate_ops"] > 0 or k == 5
+    psi0 = W.random_state(n, 17 + k)
+    got = U.run_gpu(n, g, dtype, psi0=psi0, k_max=k, tile_m=12)
+    U.assert_close(got, U.run_oracle(n, g, psi0), dtype, "%s k=%d" % (kind, k))
+
+
+@pytest.mark.parametrize("dtype", DT, ids=DTN.get)
 @pytest.mark.parametrize("planner", [S.PLAN_PLAIN, S.PLAN_GREEDY])
 def test_qft_basis_and_random(dtype, planner):
     n = 18
