@@ -245,7 +245,7 @@ def main():
         if dist:
             dist.barrier()
 
-    def timed(pl, steps, warmup, record):
+    def timed(pl, steps, warmup, record, tag="timed_steps"):
         for i in range(warmup):
             step(i, pl, 0)
         torch.cuda.synchronize()
@@ -255,11 +255,13 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = S.sv_launch_count()
+        torch.cuda.nvtx.range_push(tag)  # lets a profiler select the timed launches
         e0.record(stream)
         for i in range(steps):
             step(i, pl, record)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         launches = S.sv_launch_count() - l0
         barrier()
         ms = e0.elapsed_time(e1) / steps
@@ -291,9 +293,13 @@ def main():
         cm["judge"] = S.sv_cost_model_stats()
         po = cm["chosen"]
         plan = S.sv_plan_circuit(n, dt, g, k_max=po["k_max"], tile_m=po["tile_m"], tensor=po["tensor"])
+        plan_opts = {"k_max": po["k_max"], "tile_m": po["tile_m"], "tensor": po["tensor"], "source": "cost model + judge"}
     else:
-        plan = S.sv_plan_circuit(n, dt, g, k_max=args.k, tile_m=args.tile_m,
+        plan = S.sv_plan_circuit(n, dt, g, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
                                  planner=S.PLAN_PLAIN if planner == S.PLAN_PLAIN else S.PLAN_GREEDY)
+        plan_opts = {"k_max": args.k or 5, "tile_m": args.tile_m or "default", "tensor": args.tensor,
+                     "source": args.planner}
+    plan_opts.update({"dense_ops": plan["dense_ops"], "gate_ops": plan["gate_ops"], "diag_ops": plan["diag_ops"]})
     value = world * updates / (ms / 1e3)
     hbm, src = peaks()
     # dominant kernel: the tile pass (one read + one write of 2^n amplitudes)
@@ -309,12 +315,12 @@ def main():
 
     plain = None
     if not args.no_plain and planner != S.PLAN_PLAIN:
-        pms, _ = timed(S.PLAN_PLAIN, max(2, args.steps // 3), 1, 0)
+        pms, _ = timed(S.PLAN_PLAIN, max(2, args.steps // 3), 1, 0, "plain_steps")
         plain = {"value": world * updates / (pms / 1e3), "ms_per_step": pms,
                  "fused_over_plain": pms / ms}
     greedy = None
     if planner == S.PLAN_MLP and not args.no_plain:
-        gms, _ = timed(S.PLAN_GREEDY, max(3, args.steps // 2), 2, 0)
+        gms, _ = timed(S.PLAN_GREEDY, max(3, args.steps // 2), 2, 0, "greedy_steps")
         greedy = {"value": world * updates / (gms / 1e3), "ms_per_step": gms, "k_max": 5,
                   "learned_over_greedy": gms / ms}
 
@@ -365,7 +371,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": len(g), "shots": args.shots, "planner": args.planner,
-                       "passes": plan["passes"], "k_max": args.k or 5, "tile_m": args.tile_m or None,
+                       "passes": plan["passes"], "plan_options": plan_opts,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state %d MiB)" % ((amp_b << n) >> 20)},
             "roofline": roof, "plain": plain, "greedy": greedy, "cost_model": cm, "e2e": e2e, "cpu_baseline": cpu,

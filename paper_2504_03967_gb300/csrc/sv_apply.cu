@@ -177,6 +177,16 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Shared-memory position of tile amplitude i: the 16-byte chunks of each
+// 128-byte row are XOR-permuted by the row number (mod 8), so that a warp
+// reading one amplitude from each of 8 consecutive rows (slices of a block on
+// the low tile qubits) hits 8 different bank groups.  The map is linear over
+// XOR: swz(a ^ b) = swz(a) ^ swz(b), so slice offsets can be swizzled once.
+template <typename V> __device__ __forceinline__ int swz(int i) {
+    if constexpr (sizeof(V) == 8) return i ^ (((i >> 4) & 7) << 1);  // 2 amplitudes per chunk
+    else return i ^ ((i >> 3) & 7);                                   // 1 amplitude per chunk
+}
+
 // Dense k-qubit block on tile positions lq[0..K-1] (ascending).  A round
 // covers blockDim/G whole slices; thread t takes row group g = t / (blockDim/G)
 // (uniform across each warp, so matrix reads are shared-memory broadcasts)
@@ -187,9 +197,9 @@ __device__ __forceinline__ void tile_dense(V* __restrict__ tile, int m, const Op
     constexpr int D = 1 << K;
     constexpr int RG = D < 8 ? D : 8;
     constexpr int G = D / RG;
-    int bitv[K];
+    int bitv[K];  // swizzled offsets of the block's bits
 #pragma unroll
-    for (int i = 0; i < K; ++i) bitv[i] = 1 << op.lq[i];
+    for (int i = 0; i < K; ++i) bitv[i] = swz<V>(1 << op.lq[i]);
     const int nslices = 1 << (m - K);
     const int per_round = blockDim.x / G;
     const int g = threadIdx.x / per_round;
@@ -200,6 +210,7 @@ __device__ __forceinline__ void tile_dense(V* __restrict__ tile, int m, const Op
         int base = s;
 #pragma unroll
         for (int i = 0; i < K; ++i) base = (int)insert_zero((uint64_t)base, op.lq[i]);
+        base = swz<V>(base);
         V acc[RG];
 #pragma unroll
         for (int r = 0; r < RG; ++r) acc[r] = czero<V>();
@@ -209,8 +220,8 @@ __device__ __forceinline__ void tile_dense(V* __restrict__ tile, int m, const Op
                 int o = 0;
 #pragma unroll
                 for (int i = 0; i < K; ++i)
-                    if ((j >> i) & 1) o += bitv[i];
-                const V x = tile[base + o];
+                    if ((j >> i) & 1) o ^= bitv[i];
+                const V x = tile[base ^ o];
 #pragma unroll
                 for (int r = 0; r < RG; ++r) acc[r] = cfma(sU[(g * RG + r) * D + j], x, acc[r]);
             }
@@ -223,8 +234,8 @@ __device__ __forceinline__ void tile_dense(V* __restrict__ tile, int m, const Op
                 int o = 0;
 #pragma unroll
                 for (int i = 0; i < K; ++i)
-                    if ((row >> i) & 1) o += bitv[i];
-                tile[base + o] = acc[r];
+                    if ((row >> i) & 1) o ^= bitv[i];
+                tile[base ^ o] = acc[r];
             }
         }
         if (G > 1) __syncthreads();
@@ -355,23 +366,24 @@ __device__ __forceinline__ void tile_gates(V* __restrict__ tile, int m, const Op
                                            const V* __restrict__ sdata) {
     constexpr int D = 1 << K;
     using R = decltype(V().x);
-    int bitv[K];
+    int bitv[K];  // swizzled offsets of the block's bits
 #pragma unroll
-    for (int i = 0; i < K; ++i) bitv[i] = 1 << op.lq[i];
+    for (int i = 0; i < K; ++i) bitv[i] = swz<V>(1 << op.lq[i]);
     const int nslices = 1 << (m - K);
     const int nrec = op.nrec;
     for (int s = threadIdx.x; s < nslices; s += blockDim.x) {
         int base = s;
 #pragma unroll
         for (int i = 0; i < K; ++i) base = (int)insert_zero((uint64_t)base, op.lq[i]);
+        base = swz<V>(base);
         V v[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             int o = 0;
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if ((j >> i) & 1) o += bitv[i];
-            v[j] = tile[base + o];
+                if ((j >> i) & 1) o ^= bitv[i];
+            v[j] = tile[base ^ o];
         }
         for (int r = 0; r < nrec; ++r) {
             const GateRec g = recs[r];
@@ -396,83 +408,87 @@ __device__ __forceinline__ void tile_gates(V* __restrict__ tile, int m, const Op
             int o = 0;
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if ((j >> i) & 1) o += bitv[i];
-            tile[base + o] = v[j];
+                if ((j >> i) & 1) o ^= bitv[i];
+            tile[base ^ o] = v[j];
         }
     }
 }
 
-template <typename R> __device__ __forceinline__ R frac_r(R v) { return v - rint(v); }
-
-__device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
-    __sincosf(6.28318530717958647692f * t, s, c);  // |t| <= 0.5 after reduction
-}
-__device__ __forceinline__ void sincos_turns(double t, double* s, double* c) { sincospi(2.0 * t, s, c); }
-
 // Diagonal-phase run: psi_x *= exp(2 pi i phase(x)), phase(x) = c + sum_q a_q
-// x_q + sum_{p<q} b_pq x_p x_q (turns).  For the tile with non-tile bits
+// x_q + sum_{p<q} b_pq x_p x_q (turns).  Coefficients arrive as fixed-point
+// turns (2^-64 turn units, so integer addition is addition modulo one turn);
+// the complex64 path uses the top 32 bits.  For the tile with non-tile bits
 // "base" the non-tile part folds into a constant C and per-tile linear
-// coefficients a'_t; the tile-internal quadratic part comes precomputed per
-// pass (Qlo, Qhi over the lo/hi halves of the tile index, Rt coupling them),
-// so each amplitude costs a few table lookups and one sincos.
+// coefficients a'_t, all in integer arithmetic; the tile-internal quadratic
+// part comes precomputed per pass (Qlo, Qhi over the lo/hi halves of the tile
+// index, Rt coupling them), so each amplitude costs two integer adds, one
+// table lookup, one conversion and one sincos.
+template <typename R> struct Turns;
+template <> struct Turns<float> {
+    using U = uint32_t;
+    static __device__ __forceinline__ U coef(uint64_t x) { return (U)((x + 0x80000000ull) >> 32); }
+    static __device__ __forceinline__ void sincos(U ph, float* s, float* c) {
+        __sincosf((float)(int32_t)ph * 1.46291807926715968e-09f, s, c);  // 2 pi / 2^32
+    }
+};
+template <> struct Turns<double> {
+    using U = uint64_t;
+    static __device__ __forceinline__ U coef(uint64_t x) { return x; }
+    static __device__ __forceinline__ void sincos(U ph, double* s, double* c) {
+        sincospi((double)(int64_t)ph * 1.08420217248550443e-19, s, c);  // 2 / 2^64
+    }
+};
+
 template <typename V, typename R>
 __device__ __forceinline__ void tile_diag(V* __restrict__ tile, const PassDev& P, uint64_t base,
-                                          const double* __restrict__ dd, R* tabs, R* s_ap, double* s_c) {
+                                          const uint64_t* __restrict__ dd, R* tabs, uint64_t* s_ap,
+                                          uint64_t* s_c) {
+    using T = Turns<R>;
+    using U = typename T::U;
     const int m = P.m, no = P.nother;
     const DiagLayout Lo(m, no);
     const int h = Lo.h, mh = Lo.mh;
     const int tid = threadIdx.x;
-    // One round trip each: every load of the row is independent (unrolled to
-    // the 32-qubit bound and predicated), then summed in order.
+    // a'_t = a_t + sum_o b_to x_o for the tile bits (thread t), and the
+    // non-tile constant C = c + sum_o a_o x_o + sum_{o2<o} b_oo2 x_o x_o2
+    // (warp 1, one non-tile bit per lane).  Loads are unrolled to the 32-bit
+    // bound and predicated so that they are all in flight together.
     if (tid < m) {
-        const double* row = dd + Lo.bo + tid * no;
-        double r[32];
+        const uint64_t* row = dd + Lo.bo + tid * no;
+        U r[32];
 #pragma unroll
-        for (int o = 0; o < 32; ++o) r[o] = (o < no && ((base >> P.oq[o]) & 1)) ? row[o] : 0.0;
-        double v = dd[Lo.at + tid];
+        for (int o = 0; o < 32; ++o) r[o] = (o < no && ((base >> P.oq[o]) & 1)) ? T::coef(row[o]) : (U)0;
+        U v = T::coef(dd[Lo.at + tid]);
 #pragma unroll
         for (int o = 0; o < 32; ++o) v += r[o];
-        s_ap[tid] = (R)(v - floor(v + 0.5));
+        s_ap[tid] = v;
     }
     if (tid >= 32 && tid < 64) {
         const int o = tid - 32;
         const bool set = o < no && ((base >> P.oq[o < no ? o : 0]) & 1);
-        double v = 0.0;
+        U v = 0;
         if (set) {
-            const double* row = dd + Lo.boo + o * no;
-            double r[32];
+            const uint64_t* row = dd + Lo.boo + o * no;
+            U r[32];
 #pragma unroll
-            for (int o2 = 0; o2 < 32; ++o2) r[o2] = (o2 < o && ((base >> P.oq[o2]) & 1)) ? row[o2] : 0.0;
-            v = dd[Lo.ao + o];
+            for (int o2 = 0; o2 < 32; ++o2) r[o2] = (o2 < o && ((base >> P.oq[o2]) & 1)) ? T::coef(row[o2]) : (U)0;
+            v = T::coef(dd[Lo.ao + o]);
 #pragma unroll
             for (int o2 = 0; o2 < 32; ++o2) v += r[o2];
         }
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-        if (o == 0) {
-            v += dd[Lo.c];
-            *s_c = v - floor(v + 0.5);
-        }
+        if (o == 0) *s_c = v + T::coef(dd[Lo.c]);
     }
     __syncthreads();
-    R* Llo = tabs;
-    R* Lhi = Llo + (1 << h);
-    R* Rt = Lhi + (1 << mh);
-    for (int e = tid; e < (1 << h); e += blockDim.x) {
-        R v = (R)dd[Lo.qlo + e];
-        for (int b = 0; b < h; ++b)
-            if ((e >> b) & 1) v += s_ap[b];
-        Llo[e] = frac_r(v);
-    }
-    const R cc = (R)*s_c;
+    U* Lhi = reinterpret_cast<U*>(tabs);
+    const U cc = (U)*s_c;
     for (int e = tid; e < (1 << mh); e += blockDim.x) {
-        R v = (R)dd[Lo.qhi + e] + cc;
+        U v = T::coef(dd[Lo.qhi + e]) + cc;
         for (int b = 0; b < mh; ++b)
-            if ((e >> b) & 1) v += s_ap[h + b];
-        Lhi[e] = frac_r(v);
+            if ((e >> b) & 1) v += (U)s_ap[h + b];
+        Lhi[e] = v;
     }
-    for (int e = tid; e < (mh << h); e += blockDim.x) Rt[e] = (R)dd[Lo.rt + e];
-    __syncthreads();
     // Amplitude i = tid + 256 k: its lo half (tid mod 2^h) is fixed per thread
     // because 2^h divides the 256-thread block, and its hi half is
     // hi0 + k * 2^(8-h).  The lo-hi coupling terms for this lo therefore sit
@@ -481,19 +497,23 @@ __device__ __forceinline__ void tile_diag(V* __restrict__ tile, const PassDev& P
     const int lo = tid & ((1 << h) - 1);
     const int sb = 8 - h;  // hi bits fixed per thread
     const int hi0 = tid >> h;
-    R ph0 = Llo[lo];
+    U ph0 = T::coef(dd[Lo.qlo + lo]);
+    for (int b = 0; b < h; ++b)
+        if ((lo >> b) & 1) ph0 += (U)s_ap[b];
     for (int t = 0; t < sb && t < mh; ++t)
-        if ((hi0 >> t) & 1) ph0 += Rt[(t << h) + lo];
-    R Rk[7];  // coupling of bit b of k (hi bit sb + b) with this lo
+        if ((hi0 >> t) & 1) ph0 += T::coef(dd[Lo.rt + (t << h) + lo]);
+    U Rk[7];  // coupling of bit b of k (hi bit sb + b) with this lo
 #pragma unroll
-    for (int b = 0; b < 7; ++b) Rk[b] = (sb + b < mh) ? Rt[((sb + b) << h) + lo] : (R)0;
-    R C3[8];  // coupling of the three low bits of k
+    for (int b = 0; b < 7; ++b) Rk[b] = (sb + b < mh) ? T::coef(dd[Lo.rt + ((sb + b) << h) + lo]) : (U)0;
+    U C3[8];  // coupling of the three low bits of k
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-        C3[j] = ((j & 1) ? Rk[0] : (R)0) + ((j & 2) ? Rk[1] : (R)0) + ((j & 4) ? Rk[2] : (R)0);
+        C3[j] = ((j & 1) ? Rk[0] : (U)0) + ((j & 2) ? Rk[1] : (U)0) + ((j & 4) ? Rk[2] : (U)0);
+    __syncthreads();
     const int K = m >= 8 ? (1 << (m - 8)) : (tid < (1 << m) ? 1 : 0);
+    const int stid = swz<V>(tid);  // swz(tid + (k << 8)) = swz(tid) + (k << 8)
     for (int kh = 0; kh < K; kh += 8) {
-        R chi = ph0;
+        U chi = ph0;
 #pragma unroll
         for (int b = 3; b < 7; ++b)
             if ((kh >> b) & 1) chi += Rk[b];
@@ -501,11 +521,9 @@ __device__ __forceinline__ void tile_diag(V* __restrict__ tile, const PassDev& P
         for (int j = 0; j < 8; ++j) {
             const int k = kh + j;
             if (k < K) {
-                const int i = tid + (k << 8);
-                R ph = chi + C3[j] + Lhi[hi0 + (k << sb)];
-                ph = frac_r(ph);
+                const int i = stid + (k << 8);
                 R sn, cs;
-                sincos_turns(ph, &sn, &cs);
+                T::sincos(chi + C3[j] + Lhi[hi0 + (k << sb)], &sn, &cs);
                 V f;
                 f.x = cs;
                 f.y = sn;
@@ -524,7 +542,7 @@ __device__ __forceinline__ void load_tile(V* tile, const V* __restrict__ psi, ui
     for (int c = threadIdx.x; c < nch; c += blockDim.x) {
         const int i = c * PER;
         const uint64_t g = base + ((uint64_t)rowoff[i >> L] << L) + (uint64_t)(i & rmask);
-        cp_async16(tile + i, psi + g);
+        cp_async16(tile + swz<V>(i), psi + g);
     }
     cp_async_wait_all();
 }
@@ -538,14 +556,14 @@ __device__ __forceinline__ void store_tile(const V* tile, V* __restrict__ psi, u
     for (int c = threadIdx.x; c < nch; c += blockDim.x) {
         const int i = c * PER;
         const uint64_t g = base + ((uint64_t)rowoff[i >> L] << L) + (uint64_t)(i & rmask);
-        *(float4*)(psi + g) = *(const float4*)(tile + i);
+        *(float4*)(psi + g) = *(const float4*)(tile + swz<V>(i));
     }
 }
 
+// Shared-memory words (8 bytes) of a diagonal run's per-tile table Lhi.
 __host__ __device__ inline int diag_table_elems(int m) {
     const int h = m < 7 ? m : 7;
-    const int mh = m - h;
-    return (1 << h) + (1 << mh) + (mh << h);
+    return 1 << (m - h);
 }
 
 // Tensor-core dense block of K qubits (complex64 only).  The CTA's 256
@@ -572,9 +590,9 @@ __device__ __forceinline__ void tile_dense_tc(float2* __restrict__ tile, int m, 
     const int c = row & 1;
     const uint32_t col0 = (uint32_t)grp * 4u * D;
     const uint32_t lane_addr = tmem_base + ((uint32_t)(row & ~31) << 16);
-    int bitv[K];
+    int bitv[K];  // swizzled offsets of the block's bits
 #pragma unroll
-    for (int i = 0; i < K; ++i) bitv[i] = 1 << op.lq[i];
+    for (int i = 0; i < K; ++i) bitv[i] = swz<float2>(1 << op.lq[i]);
     const int nslices = 1 << (m - K);
     float* tw = reinterpret_cast<float*>(tile);
     const uint32_t sb_hi = tc::smem_u32(sB), sb_lo = sb_hi + (uint32_t)(N * D * 4);
@@ -584,6 +602,7 @@ __device__ __forceinline__ void tile_dense_tc(float2* __restrict__ tile, int m, 
         int base = s;
 #pragma unroll
         for (int i = 0; i < K; ++i) base = (int)insert_zero((uint64_t)base, op.lq[i]);
+        base = swz<float2>(base);
 #pragma unroll
         for (int j0 = 0; j0 < D; j0 += CH) {
             uint32_t vh[CH], vl[CH];
@@ -593,10 +612,10 @@ __device__ __forceinline__ void tile_dense_tc(float2* __restrict__ tile, int m, 
                 int o = 0;
 #pragma unroll
                 for (int i = 0; i < K; ++i)
-                    if ((j >> i) & 1) o += bitv[i];
+                    if ((j >> i) & 1) o ^= bitv[i];
                 // 3xTF32 split with rounding to nearest, so the products are
                 // not biased toward zero (the tensor core itself truncates)
-                const float a = act ? tw[2 * (base + o) + c] : 0.0f;
+                const float a = act ? tw[2 * (base ^ o) + c] : 0.0f;
                 const uint32_t ah = tc::to_tf32(a);
                 vh[jj] = ah;
                 vl[jj] = tc::to_tf32(a - __uint_as_float(ah));
@@ -654,8 +673,8 @@ __device__ __forceinline__ void tile_dense_tc(float2* __restrict__ tile, int m, 
                 int o = 0;
 #pragma unroll
                 for (int i = 0; i < K; ++i)
-                    if ((r >> i) & 1) o += bitv[i];
-                if (act) tw[2 * (base + o) + c] = y;
+                    if ((r >> i) & 1) o ^= bitv[i];
+                if (act) tw[2 * (base ^ o) + c] = y;
             }
         }
     }
@@ -666,14 +685,14 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
                                                       const PassDev* __restrict__ pdp,
                                                       const OpDev* __restrict__ ops,
                                                       const typename CT<R>::V* __restrict__ mats,
-                                                      const double* __restrict__ diags,
+                                                      const uint64_t* __restrict__ diags,
                                                       const float* __restrict__ tcmats, int* __restrict__ err,
                                                       const GateRec* __restrict__ grecs) {
     using V = typename CT<R>::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
-    __shared__ R s_ap[kMaxTileM];
-    __shared__ double s_c;
+    __shared__ uint64_t s_ap[kMaxTileM];
+    __shared__ uint64_t s_c;
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ int s_abort[2];
@@ -834,7 +853,7 @@ template <typename R>
 __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __restrict__ pd, int C,
                                                              const OpDev* __restrict__ ops,
                                                              const typename CT<R>::V* __restrict__ mats,
-                                                             const double* __restrict__ diags,
+                                                             const uint64_t* __restrict__ diags,
                                                              const GateRec* __restrict__ grecs, int mmax,
                                                              uint64_t shots, uint64_t seed,
                                                              const int* __restrict__ gidx,
@@ -844,8 +863,8 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
     using V = typename CT<R>::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
-    __shared__ R s_ap[kMaxTileM];
-    __shared__ double s_c;
+    __shared__ uint64_t s_ap[kMaxTileM];
+    __shared__ uint64_t s_c;
     __shared__ int s_circ;
     __shared__ double s_red[8][kMaxTileM + 2];
     V* tile = (V*)smem;
@@ -871,7 +890,7 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
         for (int i = tid; i < N; i += blockDim.x) {
             V v = czero<V>();
             if (i == 0) v.x = 1;
-            tile[i] = v;
+            tile[swz<V>(i)] = v;
         }
         __syncthreads();
         for (int oi = P.op_begin; oi < P.op_end; ++oi) {
@@ -910,7 +929,7 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
 #pragma unroll
             for (int b = 0; b < kMaxTileM; ++b) sb[b] = 0.0;
             for (int i = tid; i < N; i += blockDim.x) {
-                const double p = prob_d(tile[i]);
+                const double p = prob_d(tile[swz<V>(i)]);
                 tot += p;
 #pragma unroll
                 for (int b = 0; b < kMaxTileM; ++b)
@@ -938,7 +957,7 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
             const int blen = N < 32 ? N : 32;
             const int nblk = N / blen;
             for (int b = warp; b < nblk; b += 8) {
-                double p = lane < blen ? prob_d(tile[b * blen + lane]) : 0.0;
+                double p = lane < blen ? prob_d(tile[swz<V>(b * blen + lane)]) : 0.0;
 #pragma unroll
                 for (int sh = 16; sh > 0; sh >>= 1) p += __shfl_xor_sync(0xffffffffu, p, sh);
                 if (lane == 0) cdf[b] = p;
@@ -964,7 +983,7 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
                 double acc = lo ? cdf[lo - 1] : 0.0;
                 int pick = -1, last_nz = lo * blen;
                 for (int l = 0; l < blen; ++l) {
-                    const double p = prob_d(tile[lo * blen + l]);
+                    const double p = prob_d(tile[swz<V>(lo * blen + l)]);
                     if (p > 0.0) last_nz = lo * blen + l;
                     acc += p;
                     if (acc > t && p > 0.0) {
@@ -1005,13 +1024,13 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
     if (dtype == SV_C64)
         k_batch_small<float><<<grid, kPassThreads, smem, st>>>(
             (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
-            (const float2*)(b + blob.mat_off), (const double*)(b + blob.diag_off),
+            (const float2*)(b + blob.mat_off), (const uint64_t*)(b + blob.diag_off),
             (const GateRec*)(b + blob.rec_off), mmax, shots, seed, gidx,
             samples, expz, nmax, counter);
     else
         k_batch_small<double><<<grid, kPassThreads, smem, st>>>(
             (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
-            (const double2*)(b + blob.mat_off), (const double*)(b + blob.diag_off),
+            (const double2*)(b + blob.mat_off), (const uint64_t*)(b + blob.diag_off),
             (const GateRec*)(b + blob.rec_off), mmax, shots, seed, gidx,
             samples, expz, nmax, counter);
     return cudaGetLastError();
@@ -1118,7 +1137,7 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     count_launch();
     k_pass<R, TC><<<(unsigned)grid, kPassThreads, smem, h->stream>>>(
         (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, (const OpDev*)(b + blob.op_off),
-        (const V*)(b + blob.mat_off), (const double*)(b + blob.diag_off), (const float*)(b + blob.tc_off),
+        (const V*)(b + blob.mat_off), (const uint64_t*)(b + blob.diag_off), (const float*)(b + blob.tc_off),
         (int*)h->err.ptr, (const GateRec*)(b + blob.rec_off));
     return cudaGetLastError();
 }

@@ -182,7 +182,8 @@ struct PassDev {
     int oq[40];          // non-tile qubits ascending
 };
 
-// Layout (in doubles, phases in turns) of one diagonal run inside a pass
+// Layout (in 8-byte words of fixed-point turns, 2^-64 turn units) of one
+// diagonal run inside a pass
 // with m tile qubits and no = n - m other qubits:
 //   c | a_t[m] | a_o[no] | Bo[m][no] | Boo[no][no] | Qlo[2^h] | Qhi[2^(m-h)]
 //   | Rt[(m-h)][2^h]

@@ -598,52 +598,57 @@ float tf32_round(float v) {
     return r;
 }
 
-// Phase in turns reduced to [-0.5, 0.5).
-double red_turns(double rad) {
-    const double t = rad / (2.0 * kPi);
-    return t - floor(t + 0.5);
+// Phase (radians) as fixed-point turns: the fraction of a turn in units of
+// 2^-64, so that sums of coefficients wrap exactly modulo one turn.  The
+// FP64 phase carries 53 significant bits; the fraction is rounded to 2^-53.
+uint64_t fx_turns(double rad) {
+    double t = rad / (2.0 * kPi);
+    t -= floor(t);  // [0, 1)
+    const uint64_t q = (uint64_t)llround(ldexp(t, 53)) & ((1ull << 53) - 1ull);
+    return q << 11;
 }
 
 // A diagonal run, split for pass P (layout in DiagLayout).  Everything that
-// does not depend on the tile's non-tile bits is precomputed here in FP64:
-// the tile-internal quadratic tables over the lo (h bits) and hi (m-h bits)
-// halves of the tile index and the lo-hi coupling table.
-void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, double* d) {
+// does not depend on the tile's non-tile bits is precomputed here: the
+// tile-internal quadratic tables over the lo (h bits) and hi (m-h bits)
+// halves of the tile index and the lo-hi coupling table, each entry the
+// exact (modulo one turn) sum of its fixed-point terms.
+void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, uint64_t* d) {
     const int m = P.m, no = P.nother;
     const DiagLayout Lo(m, no);
     auto B = [&](int qa, int qb) {
-        if (qa == qb) return 0.0;
+        if (qa == qb) return (uint64_t)0;
         const int lo = qa < qb ? qa : qb, hi = qa < qb ? qb : qa;
-        return D.b[(size_t)lo * n + hi];
+        return fx_turns(D.b[(size_t)lo * n + hi]);
     };
-    d[Lo.c] = red_turns(D.c);
-    for (int t = 0; t < m; ++t) d[Lo.at + t] = red_turns(D.a[P.tq[t]]);
-    for (int o = 0; o < no; ++o) d[Lo.ao + o] = red_turns(D.a[P.oq[o]]);
+    d[Lo.c] = fx_turns(D.c);
+    for (int t = 0; t < m; ++t) d[Lo.at + t] = fx_turns(D.a[P.tq[t]]);
+    for (int o = 0; o < no; ++o) d[Lo.ao + o] = fx_turns(D.a[P.oq[o]]);
     for (int t = 0; t < m; ++t)
-        for (int o = 0; o < no; ++o) d[Lo.bo + t * no + o] = red_turns(B(P.tq[t], P.oq[o]));
+        for (int o = 0; o < no; ++o) d[Lo.bo + t * no + o] = B(P.tq[t], P.oq[o]);
     for (int o = 0; o < no; ++o)
-        for (int o2 = 0; o2 < no; ++o2) d[Lo.boo + o * no + o2] = red_turns(B(P.oq[o], P.oq[o2]));
+        for (int o2 = 0; o2 < no; ++o2) d[Lo.boo + o * no + o2] = B(P.oq[o], P.oq[o2]);
     const int h = Lo.h, mh = Lo.mh;
     for (int e = 0; e < (1 << h); ++e) {
-        double v = 0.0;
+        uint64_t v = 0;
         for (int b = 0; b < h; ++b)
             for (int b2 = 0; b2 < b; ++b2)
                 if (((e >> b) & 1) && ((e >> b2) & 1)) v += B(P.tq[b], P.tq[b2]);
-        d[Lo.qlo + e] = red_turns(v);
+        d[Lo.qlo + e] = v;
     }
     for (int e = 0; e < (1 << mh); ++e) {
-        double v = 0.0;
+        uint64_t v = 0;
         for (int b = 0; b < mh; ++b)
             for (int b2 = 0; b2 < b; ++b2)
                 if (((e >> b) & 1) && ((e >> b2) & 1)) v += B(P.tq[h + b], P.tq[h + b2]);
-        d[Lo.qhi + e] = red_turns(v);
+        d[Lo.qhi + e] = v;
     }
     for (int t = 0; t < mh; ++t)
         for (int e = 0; e < (1 << h); ++e) {
-            double v = 0.0;
+            uint64_t v = 0;
             for (int b = 0; b < h; ++b)
                 if ((e >> b) & 1) v += B(P.tq[b], P.tq[h + t]);
-            d[Lo.rt + (t << h) + e] = red_turns(v);
+            d[Lo.rt + (t << h) + e] = v;
         }
     (void)hp;
 }
@@ -674,7 +679,7 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
     blob->op_off = align16(sizeof(PassDev) * npass);
     blob->mat_off = align16(blob->op_off + sizeof(OpDev) * nops);
     blob->diag_off = align16(blob->mat_off + csz * nmat);
-    blob->tc_off = align16(blob->diag_off + sizeof(double) * ndiag);
+    blob->tc_off = align16(blob->diag_off + sizeof(uint64_t) * ndiag);
     blob->rec_off = align16(blob->tc_off + sizeof(float) * ntc);
     const size_t total = align16(blob->rec_off + sizeof(GateRec) * nrecs);
     blob->bytes.assign(total, 0);
@@ -684,7 +689,7 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
     GateRec* rg = (GateRec*)(base + blob->rec_off);
     PassDev* pd = (PassDev*)(base + blob->pass_off);
     OpDev* od = (OpDev*)(base + blob->op_off);
-    double* dg = (double*)(base + blob->diag_off);
+    uint64_t* dg = (uint64_t*)(base + blob->diag_off);
     size_t oi = 0, mi = 0, di = 0;
     size_t gpi = 0;
     for (const Plan* pp : plans) {
