@@ -247,6 +247,26 @@ int sv_pass_times(sv_handle h, double *host_ms, float *host_feat, int cap, int *
 /* Length of one pass feature vector. */
 int sv_feature_count(void);
 
+/* ---- autotuner ---------------------------------------------------------- */
+
+/* Time every candidate plan of this circuit on h's state and return the
+ * fastest: fusion width k_max 2..5 (App. D.2's "gate fusion = 5" as the
+ * bound) x tile width (11..14 qubits for complex64, 10..13 for complex128,
+ * at most n) x, for complex64, tensor cores on or off (blocks of 3..5
+ * qubits).  Each candidate runs twice on h's stream and keeps its faster
+ * CUDA-event time.  h's amplitudes serve as scratch: their content is
+ * undefined afterwards.  cache_path (may be NULL) names a JSON-lines file of
+ * earlier results, one object per line {"key", "k_max", "tile_m", "tensor",
+ * "ms"}; the key holds n, dtype, the gate count, a 64-bit FNV-1a hash of the
+ * records and the device name and SM count.  When the file has a line for
+ * this key its result is returned without any device work; otherwise the
+ * new result is appended (the file is created if missing; a write failure
+ * is ignored).  *best receives planner = SV_PLAN_GREEDY and the winning
+ * k_max, tile_m and tensor (1 or -1), ready for sv_apply_circuit; *best_ms
+ * (may be NULL) its time in milliseconds.  Synchronous. */
+int sv_autotune(sv_handle h, const sv_gate *gates, size_t count, const char *cache_path, sv_options *best,
+                double *best_ms);
+
 /* ---- learned cost model (one per process) -------------------------------
  * A small MLP (32 -> 64 -> 64 -> 1, ReLU) predicts the log time of a tile
  * pass from its feature vector (the recorder's features: qubit count, dtype,
@@ -256,8 +276,9 @@ int sv_feature_count(void);
  * every candidate fusion width k (2..5), tile width m and tensor-core choice,
  * predicts the total time and keeps the fastest; the greedy fixed-width plan
  * is the fallback when no model is loaded and the judge of the prediction:
- * the first two calls for a circuit time the chosen and the greedy plan, and
- * later calls use whichever measured faster.  Plans are exact either way. */
+ * the first calls for a circuit time the model's three best candidates and
+ * the greedy plan with CUDA events, and later calls use whichever measured
+ * fastest.  Plans are exact either way. */
 
 /* Train on count recorded passes (features count x sv_feature_count()
  * floats, times in ms) on the GPU with the library's own forward, backward and

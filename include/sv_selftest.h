@@ -26,6 +26,16 @@ extern "C" {
 int sv_selftest_tc_tf32(const float *host_a, const float *host_b, float *host_d, int kstride, int nstride,
                         int swap_fields, int *host_status);
 
+/* Failure detection without a GPU fault: a one-CTA kernel waits on an
+ * mbarrier that nothing ever arrives at, with the bounded wait of the
+ * tensor-core pass (limit try-wait rounds, 1..2^22), then records the expiry
+ * in a device status word and returns normally, so the context stays usable.
+ * *host_status = 1 when the wait gave up (the expected outcome), 0 if it
+ * completed.  Returns SV_OK, SV_EINVAL or SV_ECUDA.  The simulator's own
+ * passes report such an expiry as SV_ETIMEOUT from the next call that
+ * synchronises. */
+int sv_selftest_wait_timeout(unsigned limit, int *host_status);
+
 /* The cost-model network's loss and gradient on the GPU (the training
  * kernels' forward and backward passes) for flat parameters params
  * (sv_mlp_param_count() floats: W1 64x32 row-major | b1 | W2 64x64 | b2 |

@@ -267,6 +267,22 @@ def sv_pass_times(h, cap=1 << 16, features=False):
     return (ms[:k].copy(), feat[:k].copy()) if features else ms[:k].copy()
 
 
+def sv_autotune(h, gates, cache_path=None):
+    """Fastest plan options for this circuit on h's state (h's amplitudes are
+    scratch afterwards); returns (options dict, ms)."""
+    L = lib()
+    f = L.sv_autotune
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_char_p, ctypes.POINTER(sv_options),
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    g = as_gates(gates)
+    o = sv_options()
+    ms = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(f(h, _ptr(g), len(g), path, ctypes.byref(o), ctypes.byref(ms)))
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
+
+
 def sv_sample_uniforms_noalloc(dev_amps, n, dtype, dev_u, shots, dev_out, stream=None):
     """Sampling with caller-owned device buffers and no device allocation
     (see include/sv.h): all pointers are device addresses (ints)."""

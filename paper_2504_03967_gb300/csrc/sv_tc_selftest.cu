@@ -134,3 +134,41 @@ extern "C" int sv_selftest_tc_tf32(const float* host_a, const float* host_b, flo
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 self-test");
     return SV_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Failure detection without a fault: one CTA waits on an mbarrier that no
+// thread or copy ever arrives at, through the same bounded wait the
+// tensor-core pass uses, and records the expiry in a device status word
+// before returning normally.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_wait_selftest(uint32_t limit, int* __restrict__ status) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) {
+        sv::tc::mbar_init(&mbar, 1);
+        sv::tc::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = sv::tc::mbar_wait_bounded(&mbar, 0u, limit);
+    if (!ok && threadIdx.x == 0) atomicExch(status, 1);
+}
+}  // namespace
+
+extern "C" int sv_selftest_wait_timeout(unsigned limit, int* host_status) {
+    using namespace sv;
+    if (!host_status) return set_error(SV_EINVAL, "NULL argument");
+    if (limit == 0 || limit > (1u << 22)) return set_error(SV_EINVAL, "limit must be in 1..2^22");
+    int* dS = nullptr;
+    cudaError_t e = cudaMalloc(&dS, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(dS, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        count_launch();
+        k_wait_selftest<<<1, 32>>>((uint32_t)limit, dS);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host_status, dS, sizeof(int), cudaMemcpyDeviceToHost);
+    if (dS) cudaFree(dS);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    return SV_OK;
+}
