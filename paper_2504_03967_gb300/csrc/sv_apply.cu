@@ -534,20 +534,6 @@ __device__ __forceinline__ void tile_diag(V* __restrict__ tile, const PassDev& P
 }
 
 template <typename V>
-__device__ __forceinline__ void load_tile(V* tile, const V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
-                                          int m, int L) {
-    constexpr int PER = 16 / sizeof(V);  // amplitudes per 16-byte chunk
-    const int nch = (1 << m) / PER;
-    const int rmask = (1 << L) - 1;
-    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
-        const int i = c * PER;
-        const uint64_t g = base + ((uint64_t)rowoff[i >> L] << L) + (uint64_t)(i & rmask);
-        cp_async16(tile + swz<V>(i), psi + g);
-    }
-    cp_async_wait_all();
-}
-
-template <typename V>
 __device__ __forceinline__ void store_tile(const V* tile, V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
                                            int m, int L) {
     constexpr int PER = 16 / sizeof(V);
@@ -680,14 +666,52 @@ __device__ __forceinline__ void tile_dense_tc(float2* __restrict__ tile, int m, 
     }
 }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Start the 16-byte copies of a tile (no wait).
+template <typename V>
+__device__ __forceinline__ void issue_tile(V* tile, const V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
+                                           int m, int L) {
+    constexpr int PER = 16 / sizeof(V);
+    const int nch = (1 << m) / PER;
+    const int rmask = (1 << L) - 1;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        const int i = c * PER;
+        const uint64_t g = base + ((uint64_t)rowoff[i >> L] << L) + (uint64_t)(i & rmask);
+        cp_async16(tile + swz<V>(i), psi + g);
+    }
+}
+
+// Shared-memory layout of one pass CTA, computed on the host:
+//   [tile buffer 0 | tile buffer 1 (nbuf = 2) | row offsets | resident
+//    tensor-core B operands | staged pass region | work]
+// With the whole region staged, every op reads its matrix, records or phase
+// words from shared memory for all of the CTA's tiles; otherwise only the
+// OpDev array is staged and each op copies its payload into the work area.
+// With two tile buffers the next tile's copies are in flight while the
+// current one is processed.
+struct PassLayout {
+    int nbuf;
+    int tile_bytes;
+    int rowoff_off;
+    int bres_off;
+    int stage_off;
+    int tc_res;       // floats of tensor-core B operands kept resident (0: copied per op)
+    int stage_bytes;  // bytes of the region copied (region or its OpDev array)
+    int staged;       // 1: the whole region is in shared memory
+    int work_off;
+    int total;
+};
+
 template <typename R, bool TC>
-__global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R>::V* __restrict__ psi, int n,
+__global__ void __launch_bounds__(kPassThreads, 2) k_pass(typename CT<R>::V* __restrict__ psi, int n,
                                                       const PassDev* __restrict__ pdp,
-                                                      const OpDev* __restrict__ ops,
-                                                      const typename CT<R>::V* __restrict__ mats,
-                                                      const uint64_t* __restrict__ diags,
+                                                      const unsigned char* __restrict__ blob,
                                                       const float* __restrict__ tcmats, int* __restrict__ err,
-                                                      const GateRec* __restrict__ grecs) {
+                                                      const PassLayout lay) {
     using V = typename CT<R>::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
@@ -718,47 +742,75 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
         }
         tc::fence_before();
     }
-    V* tile = (V*)smem;
-    uint32_t* rowoff = (uint32_t*)(smem + (sizeof(V) << m));
+    V* tiles[2] = {(V*)smem, (V*)(smem + (lay.nbuf == 2 ? lay.tile_bytes : 0))};
+    uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
+    float* bres = (float*)(smem + lay.bres_off);
+    unsigned char* stage = smem + lay.stage_off;
+    R* work = (R*)(smem + lay.work_off);
+    const unsigned char* greg = blob + P.region_off;
     const int nrows = 1 << (m - L);
-    // [tile | rowoff | resident tensor-core B operands | work]
-    const size_t res_off = ((sizeof(V) << m) + 4 * (size_t)nrows + 127) & ~(size_t)127;
-    const int tc_res = TC ? P.tc_res : 0;
-    float* bres = (float*)(smem + res_off);
-    R* work = (R*)(smem + res_off + ((4 * (size_t)tc_res + 127) & ~(size_t)127));
+    // the pass region (or its OpDev array) and the resident B operands
+    for (int e = threadIdx.x; e < lay.stage_bytes / 16; e += blockDim.x) cp_async16(stage + 16 * e, greg + 16 * e);
+    const int tc_res = TC ? lay.tc_res : 0;
     if (tc_res) {
         const float* src = tcmats + P.tc_base;
         for (int e = threadIdx.x; e < tc_res / 4; e += blockDim.x) cp_async16(bres + 4 * e, src + 4 * e);
-        cp_async_wait_all();
-        tc::fence_proxy_async();
     }
+    cp_async_commit();
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
         uint32_t o = 0;
         for (int b = 0; b < m - L; ++b)
             if ((r >> b) & 1) o |= 1u << (P.tq[L + b] - L);
         rowoff[r] = o;
     }
+    cp_async_wait_group<0>();
+    if (tc_res) tc::fence_proxy_async();
     __syncthreads();
     if (tc_k) tc::fence_after();
+    const OpDev* opsp = (const OpDev*)(lay.stage_bytes >= P.ops_bytes ? (const unsigned char*)stage : greg);
+    const unsigned char* reg = lay.staged ? (const unsigned char*)stage : greg;
     const uint32_t tmem_base = tc_k ? s_taddr : 0u;
     uint32_t phase = 0;
     const uint64_t ntiles = 1ull << (n - m);
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = 0;
+        for (int i = 0; i < P.nother; ++i) b |= ((t >> i) & 1ull) << P.oq[i];
+        return b;
+    };
+    int cur = 0;
+    if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
+        issue_tile(tiles[0], psi, tile_base(blockIdx.x), rowoff, m, L);
+        cp_async_commit();
+    }
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        uint64_t base = 0;
-        for (int b = 0; b < P.nother; ++b) base |= ((t >> b) & 1ull) << P.oq[b];
-        load_tile(tile, psi, base, rowoff, m, L);
+        const uint64_t base = tile_base(t);
+        const uint64_t tn = t + gridDim.x;
+        if (lay.nbuf == 2) {
+            if (tn < ntiles) {
+                issue_tile(tiles[cur ^ 1], psi, tile_base(tn), rowoff, m, L);
+                cp_async_commit();
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+        } else {
+            issue_tile(tiles[0], psi, base, rowoff, m, L);
+            cp_async_commit();
+            cp_async_wait_group<0>();
+        }
         __syncthreads();
-        for (int oi = P.op_begin; oi < P.op_end; ++oi) {
-            const OpDev op = ops[oi];
-            if (op.kind == OP_DENSE && op.tc) {
+        V* tile = tiles[cur];
+        for (int oi = 0; oi < P.nops; ++oi) {
+            const OpDev& op = opsp[oi];
+            const int kind = op.kind;
+            if (kind == OP_DENSE && op.tc) {
                 if constexpr (TC && sizeof(R) == 4) {
                     const float* sB = bres + (op.tc_off - P.tc_base);
                     if (!tc_res) {  // B operands [hi | lo] of this block into shared memory
                         const int nch = tc_floats(op.k) / 4;
                         const float* src = tcmats + op.tc_off;
                         for (int e = threadIdx.x; e < nch; e += blockDim.x)
-                            cp_async16((float*)work + 4 * e, src + 4 * e);
-                        cp_async_wait_all();
+                            *(float4*)((float*)work + 4 * e) = *(const float4*)(src + 4 * e);
                         tc::fence_proxy_async();
                         __syncthreads();
                         sB = (const float*)work;
@@ -769,23 +821,33 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
                     default: tile_dense_tc<5>(tile, m, op, sB, tmem_base, s_mbar, &phase, s_abort, err); break;
                     }
                 }
-            } else if (op.kind == OP_GATES) {
-                V* sd = (V*)work;
-                GateRec* sr = (GateRec*)(sd + kMaxGateData);
-                for (int e = threadIdx.x; e < op.ndata; e += blockDim.x) sd[e] = mats[op.mat_off + e];
-                for (int e = threadIdx.x; e < op.nrec; e += blockDim.x) sr[e] = grecs[op.rec_off + e];
-                __syncthreads();
+            } else if (kind == OP_GATES) {
+                const V* sd = (const V*)(reg + op.mat_off);
+                const GateRec* sr = (const GateRec*)(reg + op.rec_off);
+                if (!lay.staged) {
+                    V* wd = (V*)work;
+                    GateRec* wr = (GateRec*)(wd + kMaxGateData);
+                    for (int e = threadIdx.x; e < op.ndata; e += blockDim.x) wd[e] = sd[e];
+                    for (int e = threadIdx.x; e < op.nrec; e += blockDim.x) wr[e] = sr[e];
+                    __syncthreads();
+                    sd = wd;
+                    sr = wr;
+                }
                 switch (op.k) {  // k <= max_gates_k: 4 (complex64), 3 (complex128)
                 case 1: tile_gates<V, 1>(tile, m, op, sr, sd); break;
                 case 2: tile_gates<V, 2>(tile, m, op, sr, sd); break;
                 case 3: tile_gates<V, 3>(tile, m, op, sr, sd); break;
                 default: if constexpr (sizeof(V) == 8) tile_gates<V, 4>(tile, m, op, sr, sd); break;
                 }
-            } else if (op.kind == OP_DENSE) {
-                V* sU = (V*)work;
-                const int DD = 1 << (2 * op.k);
-                for (int e = threadIdx.x; e < DD; e += blockDim.x) sU[e] = mats[op.mat_off + e];
-                __syncthreads();
+            } else if (kind == OP_DENSE) {
+                const V* sU = (const V*)(reg + op.mat_off);
+                if (!lay.staged) {
+                    V* wU = (V*)work;
+                    const int DD = 1 << (2 * op.k);
+                    for (int e = threadIdx.x; e < DD; e += blockDim.x) wU[e] = sU[e];
+                    __syncthreads();
+                    sU = wU;
+                }
                 switch (op.k) {
                 case 1: tile_dense<V, 1>(tile, m, op, sU); break;
                 case 2: tile_dense<V, 2>(tile, m, op, sU); break;
@@ -794,12 +856,13 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
                 default: tile_dense<V, 5>(tile, m, op, sU); break;
                 }
             } else {
-                tile_diag<V, R>(tile, P, base, diags + op.diag_off, work, s_ap, &s_c);
+                tile_diag<V, R>(tile, P, base, (const uint64_t*)(reg + op.diag_off), work, s_ap, &s_c);
             }
             __syncthreads();
         }
         store_tile(tile, psi, base, rowoff, m, L);
         __syncthreads();
+        if (lay.nbuf == 2) cur ^= 1;
     }
     if (tc_k) {
         tc::fence_before();
@@ -808,21 +871,52 @@ __global__ void __launch_bounds__(kPassThreads, TC ? 2 : 3) k_pass(typename CT<R
     }
 }
 
-size_t pass_smem_bytes(int dtype, int m, int L, int tc_k, int tc_res) {
+// Shared memory a pass may stage (its region) and the CTA budget that keeps
+// two CTAs per SM when the tile is double-buffered.
+constexpr int kStageCap = 48 * 1024;
+constexpr int kTwoCtaBudget = 112 * 1024;
+constexpr int kMaxDynSmem = 225 * 1024;  // 227 KB per block less the kernel's static variables
+
+static int round128(size_t v) { return (int)((v + 127) & ~(size_t)127); }
+
+PassLayout pass_layout(int dtype, const PassDev& P) {
     const size_t csz = dtype == SV_C64 ? 8 : 16;
-    const size_t rsz = dtype == SV_C64 ? 4 : 8;
-    const int nrows = 1 << (m - L);
-    size_t work = csz * (1 << (2 * kMaxK));
-    const size_t dt = rsz * diag_table_elems(m);
-    if (dt > work) work = dt;
-    if (tc_k && !tc_res && (size_t)tc_floats(tc_k) * 4 > work) work = (size_t)tc_floats(tc_k) * 4;
-    size_t total = (((csz << m) + 4 * (size_t)nrows + 127) & ~(size_t)127) +
-                   ((4 * (size_t)tc_res + 127) & ~(size_t)127) + work;
+    const size_t usz = dtype == SV_C64 ? 4 : 8;
+    const int m = P.m;
+    const int nrows = 1 << (m - P.L);
+    PassLayout lay;
+    lay.tile_bytes = round128(csz << m);
+    lay.tc_res = P.tc_res;
+    lay.staged = P.region_bytes <= kStageCap;
+    // Drop the staged payloads, then the resident B operands, until the CTA
+    // fits the per-block shared-memory limit (static variables included).
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        lay.stage_bytes = lay.staged ? P.region_bytes : (P.ops_bytes <= kStageCap ? P.ops_bytes : 0);
+        // work: the diagonal runs' per-tile table, non-resident tensor-core B
+        // operands, and without staging the per-op payload copies
+        size_t work = usz * (size_t)diag_table_elems(m);
+        if (P.tc_k && !lay.tc_res) work = std::max(work, (size_t)tc_floats(P.tc_k) * 4);
+        if (!lay.staged) {
+            work = std::max(work, csz * (size_t)(1 << (2 * kMaxK)));
+            work = std::max(work, csz * kMaxGateData + sizeof(GateRec) * kMaxGateRecs);
+        }
+        const int rest = round128(4 * (size_t)nrows) + round128(4 * (size_t)lay.tc_res) + round128(lay.stage_bytes) +
+                         round128(work);
+        lay.nbuf = 2 * lay.tile_bytes + rest <= kTwoCtaBudget ? 2 : 1;
+        lay.rowoff_off = lay.nbuf * lay.tile_bytes;
+        lay.bres_off = lay.rowoff_off + round128(4 * (size_t)nrows);
+        lay.stage_off = lay.bres_off + round128(4 * (size_t)lay.tc_res);
+        lay.work_off = lay.stage_off + round128(lay.stage_bytes);
+        lay.total = lay.work_off + round128(work);
+        if (lay.total <= kMaxDynSmem) break;
+        if (attempt == 0) lay.staged = 0;
+        else lay.tc_res = 0;
+    }
     // Blocks of 5 qubits take 256 TMEM columns per CTA: at most two CTAs may
     // share an SM (512 columns), so such passes ask for enough shared memory
     // to keep a third one away.
-    if (tc_k >= 5 && total < 80 * 1024) total = 80 * 1024;
-    return total;
+    if (P.tc_k >= 5 && lay.total < 80 * 1024) lay.total = 80 * 1024;
+    return lay;
 }
 
 // ---------------------------------------------------------------------------
@@ -851,10 +945,7 @@ size_t batch_small_smem_bytes(int dtype, int mmax) {
 
 template <typename R>
 __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __restrict__ pd, int C,
-                                                             const OpDev* __restrict__ ops,
-                                                             const typename CT<R>::V* __restrict__ mats,
-                                                             const uint64_t* __restrict__ diags,
-                                                             const GateRec* __restrict__ grecs, int mmax,
+                                                             const unsigned char* __restrict__ blob, int mmax,
                                                              uint64_t shots, uint64_t seed,
                                                              const int* __restrict__ gidx,
                                                              uint64_t* __restrict__ samples,
@@ -893,13 +984,17 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
             tile[swz<V>(i)] = v;
         }
         __syncthreads();
-        for (int oi = P.op_begin; oi < P.op_end; ++oi) {
+        const unsigned char* greg = blob + P.region_off;
+        const OpDev* ops = (const OpDev*)greg;
+        for (int oi = 0; oi < P.nops; ++oi) {
             const OpDev op = ops[oi];
             if (op.kind == OP_GATES) {
                 V* sd = (V*)work;
                 GateRec* sr = (GateRec*)(sd + kMaxGateData);
-                for (int e = tid; e < op.ndata; e += blockDim.x) sd[e] = mats[op.mat_off + e];
-                for (int e = tid; e < op.nrec; e += blockDim.x) sr[e] = grecs[op.rec_off + e];
+                const V* gd = (const V*)(greg + op.mat_off);
+                const GateRec* gr = (const GateRec*)(greg + op.rec_off);
+                for (int e = tid; e < op.ndata; e += blockDim.x) sd[e] = gd[e];
+                for (int e = tid; e < op.nrec; e += blockDim.x) sr[e] = gr[e];
                 __syncthreads();
                 switch (op.k) {  // k <= max_gates_k: 4 (complex64), 3 (complex128)
                 case 1: tile_gates<V, 1>(tile, m, op, sr, sd); break;
@@ -910,7 +1005,8 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
             } else if (op.kind == OP_DENSE) {
                 V* sU = (V*)work;
                 const int DD = 1 << (2 * op.k);
-                for (int e = tid; e < DD; e += blockDim.x) sU[e] = mats[op.mat_off + e];
+                const V* gU = (const V*)(greg + op.mat_off);
+                for (int e = tid; e < DD; e += blockDim.x) sU[e] = gU[e];
                 __syncthreads();
                 switch (op.k) {
                 case 1: tile_dense<V, 1>(tile, m, op, sU); break;
@@ -920,7 +1016,7 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
                 default: tile_dense<V, 5>(tile, m, op, sU); break;
                 }
             } else {
-                tile_diag<V, R>(tile, P, 0ull, diags + op.diag_off, work, s_ap, &s_c);
+                tile_diag<V, R>(tile, P, 0ull, (const uint64_t*)(greg + op.diag_off), work, s_ap, &s_c);
             }
             __syncthreads();
         }
@@ -1023,15 +1119,11 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
     count_launch();
     if (dtype == SV_C64)
         k_batch_small<float><<<grid, kPassThreads, smem, st>>>(
-            (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
-            (const float2*)(b + blob.mat_off), (const uint64_t*)(b + blob.diag_off),
-            (const GateRec*)(b + blob.rec_off), mmax, shots, seed, gidx,
+            (const PassDev*)(b + blob.pass_off), C, b, mmax, shots, seed, gidx,
             samples, expz, nmax, counter);
     else
         k_batch_small<double><<<grid, kPassThreads, smem, st>>>(
-            (const PassDev*)(b + blob.pass_off), C, (const OpDev*)(b + blob.op_off),
-            (const double2*)(b + blob.mat_off), (const uint64_t*)(b + blob.diag_off),
-            (const GateRec*)(b + blob.rec_off), mmax, shots, seed, gidx,
+            (const PassDev*)(b + blob.pass_off), C, b, mmax, shots, seed, gidx,
             samples, expz, nmax, counter);
     return cudaGetLastError();
 }
@@ -1118,16 +1210,15 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     using V = typename CT<R>::V;
     const int m = (int)hp.tile.size();
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
-    const size_t smem = pass_smem_bytes(h->dtype, m, hp.L, TC ? pdh->tc_k : 0, TC ? pdh->tc_res : 0);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_pass<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pass_smem_bytes(h->dtype, h->dtype == SV_C64 ? 14 : 13, 1, 5, kTcResidentFloats));
+    const PassLayout lay = pass_layout(h->dtype, *pdh);
+    static int attr_bytes = 0;  // dynamic shared memory the kernel is currently allowed
+    if (lay.total > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_pass<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_bytes = lay.total;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R, TC>, kPassThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R, TC>, kPassThreads, lay.total);
     if (per_sm < 1) per_sm = 1;
     if (TC && pdh->tc_k >= 5 && per_sm > 2) per_sm = 2;  // 256 TMEM columns per CTA
     const uint64_t ntiles = 1ull << (h->n - m);
@@ -1135,10 +1226,9 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     if (grid > ntiles) grid = ntiles;
     const unsigned char* b = (const unsigned char*)blob_dev;
     count_launch();
-    k_pass<R, TC><<<(unsigned)grid, kPassThreads, smem, h->stream>>>(
-        (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, (const OpDev*)(b + blob.op_off),
-        (const V*)(b + blob.mat_off), (const uint64_t*)(b + blob.diag_off), (const float*)(b + blob.tc_off),
-        (int*)h->err.ptr, (const GateRec*)(b + blob.rec_off));
+    k_pass<R, TC><<<(unsigned)grid, kPassThreads, lay.total, h->stream>>>(
+        (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, b, (const float*)(b + blob.tc_off),
+        (int*)h->err.ptr, lay);
     return cudaGetLastError();
 }
 

@@ -139,21 +139,27 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
                              const PlanOptions& base, cudaEvent_t* ev0, cudaEvent_t* ev1);
 
 // ---------------------------------------------------------------------------
-// Device-side plan blob.  Layout: [PassDev x P][OpDev x O][mats][diag doubles]
+// Device-side plan blob: [PassDev x P][tensor-core B operands][pass regions].
+// Each pass owns one contiguous region [OpDev x nops | payloads], every piece
+// 16-byte aligned, so a CTA can copy the whole region into shared memory once
+// and run all its tiles from there.  Payload offsets are bytes from the start
+// of the region.
 // ---------------------------------------------------------------------------
 struct OpDev {
     int kind;
     int k;
-    int mat_off;   // dense: element offset into the matrix array (complex units)
-    int diag_off;  // diag: offset (doubles) of the run's tables (DiagLayout)
-    int lq[kMaxK]; // dense: local tile positions, ascending
+    int mat_off;   // dense / gates: byte offset of the matrix / the records' complex data
+    int diag_off;  // diag: byte offset of the run's words (DiagLayout)
+    int lq[kMaxK]; // dense / gates: local tile positions, ascending
     int ngates;
     int tc;        // dense on the tensor cores (c64, k >= 3)
     int tc_off;    // float offset of its B operands [hi | lo] in the tc section
     int nrec;      // gates: number of records
-    int rec_off;   // gates: index of the first record in the record section
+    int rec_off;   // gates: byte offset of the records
     int ndata;     // gates: complex values at mat_off
+    int pad;
 };
+static_assert(sizeof(OpDev) % 16 == 0, "OpDev array must keep 16-byte alignment");
 
 // Tensor-core dense block of k qubits (D = 2^k): B operand = [Ur; Ui], N = 2D
 // rows x K = D columns, FP32 values laid out as the tcgen05 no-swizzle
@@ -172,8 +178,10 @@ struct PassDev {
     int n;               // qubits of the state the pass runs on
     int m;
     int L;
-    int op_begin;
-    int op_end;
+    int nops;            // ops in the pass's region
+    int region_off;      // byte offset of the region in the blob
+    int region_bytes;    // its size (multiple of 16)
+    int ops_bytes;       // size of its OpDev array (multiple of 16)
     int tc_k;            // widest tensor-core block in the pass (0: none)
     int tc_base;         // float offset of the pass's first tensor-core B operands
     int tc_res;          // floats of B operands kept resident in shared memory (0: loaded per op)
@@ -208,8 +216,9 @@ __host__ __device__ inline size_t diag_doubles(int m, int no) { return (size_t)D
 
 struct PlanBlob {
     std::vector<unsigned char> bytes;
-    size_t pass_off = 0, op_off = 0, mat_off = 0, diag_off = 0, tc_off = 0, rec_off = 0;
+    size_t pass_off = 0, tc_off = 0;
     int npasses = 0;
+    int max_region = 0;  // largest pass region (bytes)
 };
 
 void serialise_plan(const Plan& p, PlanBlob* blob);
@@ -265,7 +274,6 @@ cudaError_t launch_init_basis(sv_state* h, uint64_t x);
 cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
                         const HostPass& hp);
-size_t pass_smem_bytes(int dtype, int m, int L, int tc_k, int tc_res);
 // One persistent launch for circuits of at most mmax qubits (single-tile
 // plans, one pass each, in blob order); outputs per circuit c at
 // samples + c*shots and expz + c*nmax (either may be NULL).

@@ -655,43 +655,39 @@ void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, 
 }  // namespace
 
 void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
-    size_t nops = 0, nmat = 0, ndiag = 0, ntc = 0, npass = 0, nrecs = 0;
     auto use_tc = [&](const Plan& p, const HostOp& o) {
         return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
     };
     const int dtype = plans.empty() ? SV_C64 : plans[0]->dtype;
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    // sizes: one region per pass
+    size_t ntc = 0, npass = 0, nregion = 0;
+    std::vector<size_t> rsize;
     for (const Plan* pp : plans) {
-      const Plan& p = *pp;
-      const int n = p.n;
-      npass += p.passes.size();
-      for (const HostPass& hp : p.passes)
-        for (const HostOp& o : hp.ops) {
-            ++nops;
-            if (o.kind == OP_DENSE || o.kind == OP_GATES) nmat += o.mat.size();
-            else ndiag += diag_doubles((int)hp.tile.size(), n - (int)hp.tile.size());
-            if (o.kind == OP_GATES) nrecs += o.recs.size();
-            if (use_tc(p, o)) ntc += (size_t)tc_floats((int)o.qubits.size());
+        const Plan& p = *pp;
+        npass += p.passes.size();
+        for (const HostPass& hp : p.passes) {
+            size_t r = align16(sizeof(OpDev) * hp.ops.size());
+            for (const HostOp& o : hp.ops) {
+                if (o.kind == OP_DENSE || o.kind == OP_GATES) r += align16(csz * o.mat.size());
+                else r += align16(sizeof(uint64_t) * diag_doubles((int)hp.tile.size(), p.n - (int)hp.tile.size()));
+                if (o.kind == OP_GATES) r += align16(sizeof(GateRec) * o.recs.size());
+                if (use_tc(p, o)) ntc += (size_t)tc_floats((int)o.qubits.size());
+            }
+            rsize.push_back(r);
+            nregion += r;
         }
     }
-    const size_t csz = dtype == SV_C64 ? 8 : 16;
     blob->npasses = (int)npass;
     blob->pass_off = 0;
-    blob->op_off = align16(sizeof(PassDev) * npass);
-    blob->mat_off = align16(blob->op_off + sizeof(OpDev) * nops);
-    blob->diag_off = align16(blob->mat_off + csz * nmat);
-    blob->tc_off = align16(blob->diag_off + sizeof(uint64_t) * ndiag);
-    blob->rec_off = align16(blob->tc_off + sizeof(float) * ntc);
-    const size_t total = align16(blob->rec_off + sizeof(GateRec) * nrecs);
-    blob->bytes.assign(total, 0);
+    blob->tc_off = align16(sizeof(PassDev) * npass);
+    size_t roff = align16(blob->tc_off + sizeof(float) * ntc);
+    blob->bytes.assign(roff + nregion, 0);
+    blob->max_region = 0;
     unsigned char* base = blob->bytes.data();
     float* tcf = (float*)(base + blob->tc_off);
-    size_t ti = 0, ri = 0;
-    GateRec* rg = (GateRec*)(base + blob->rec_off);
     PassDev* pd = (PassDev*)(base + blob->pass_off);
-    OpDev* od = (OpDev*)(base + blob->op_off);
-    uint64_t* dg = (uint64_t*)(base + blob->diag_off);
-    size_t oi = 0, mi = 0, di = 0;
-    size_t gpi = 0;
+    size_t ti = 0, gpi = 0;
     for (const Plan* pp : plans) {
       const Plan& p = *pp;
       const int n = p.n;
@@ -702,7 +698,14 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
         P.n = n;
         P.m = (int)hp.tile.size();
         P.L = hp.L;
-        P.op_begin = (int)oi;
+        P.nops = (int)hp.ops.size();
+        P.region_off = (int)roff;
+        P.region_bytes = (int)rsize[gpi];
+        P.ops_bytes = (int)align16(sizeof(OpDev) * hp.ops.size());
+        blob->max_region = std::max(blob->max_region, P.region_bytes);
+        unsigned char* reg = base + roff;
+        size_t off = (size_t)P.ops_bytes;
+        roff += rsize[gpi];
         int loc[64];
         for (int i = 0; i < 64; ++i) loc[i] = -1;
         for (int i = 0; i < P.m; ++i) {
@@ -712,35 +715,39 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
         P.nother = 0;
         for (int q = 0; q < n; ++q)
             if (loc[q] < 0) P.oq[P.nother++] = q;
-        for (const HostOp& o : hp.ops) {
-            OpDev& O = od[oi++];
+        OpDev* od = (OpDev*)reg;
+        for (size_t oi = 0; oi < hp.ops.size(); ++oi) {
+            const HostOp& o = hp.ops[oi];
+            OpDev& O = od[oi];
             memset(&O, 0, sizeof(O));
             O.kind = o.kind;
             O.ngates = o.ngates;
-            if (o.kind == OP_GATES) {
-                O.nrec = (int)o.recs.size();
-                O.rec_off = (int)ri;
-                O.ndata = (int)o.mat.size();
-                for (const GateRec& r : o.recs) rg[ri++] = r;
-            }
             if (o.kind == OP_DENSE || o.kind == OP_GATES) {
                 O.k = (int)o.qubits.size();
                 for (int i = 0; i < O.k; ++i) O.lq[i] = loc[o.qubits[i]];
-                O.mat_off = (int)mi;
+                O.mat_off = (int)off;
                 if (p.dtype == SV_C64) {
-                    float* f = (float*)(base + blob->mat_off) + 2 * mi;
+                    float* f = (float*)(reg + off);
                     for (size_t e = 0; e < o.mat.size(); ++e) {
                         f[2 * e] = (float)o.mat[e].real();
                         f[2 * e + 1] = (float)o.mat[e].imag();
                     }
                 } else {
-                    double* f = (double*)(base + blob->mat_off) + 2 * mi;
+                    double* f = (double*)(reg + off);
                     for (size_t e = 0; e < o.mat.size(); ++e) {
                         f[2 * e] = o.mat[e].real();
                         f[2 * e + 1] = o.mat[e].imag();
                     }
                 }
-                mi += o.mat.size();
+                off += align16(csz * o.mat.size());
+                if (o.kind == OP_GATES) {
+                    O.nrec = (int)o.recs.size();
+                    O.ndata = (int)o.mat.size();
+                    O.rec_off = (int)off;
+                    GateRec* rg = (GateRec*)(reg + off);
+                    for (size_t r = 0; r < o.recs.size(); ++r) rg[r] = o.recs[r];
+                    off += align16(sizeof(GateRec) * o.recs.size());
+                }
                 if (use_tc(p, o)) {
                     // B = [Ur; Ui]: row n < D holds Re U[n][j], row D + n holds Im U[n][j]
                     const int k = O.k, Dm = 1 << k, N = 2 * Dm, K = Dm;
@@ -764,12 +771,11 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
                 }
             } else {
                 O.k = 0;
-                O.diag_off = (int)di;
-                write_diag(o.diag, n, hp, P, dg + di);
-                di += diag_doubles(P.m, P.nother);
+                O.diag_off = (int)off;
+                write_diag(o.diag, n, hp, P, (uint64_t*)(reg + off));
+                off += align16(sizeof(uint64_t) * diag_doubles(P.m, P.nother));
             }
         }
-        P.op_end = (int)oi;
         if (P.tc_res > kTcResidentFloats) P.tc_res = 0;  // too large: staged per op and tile
       }
     }
