@@ -93,14 +93,19 @@ typedef enum {
  * planner: sv_planner; record: store per-pass CUDA-event times for the cost
  * model (sv_pass_times); tensor: 1 = complex64 dense blocks of 3..5 qubits
  * run on the tensor cores (3xTF32, FP32 accumulation), -1 = CUDA cores only,
- * 0 = the library's default (CUDA cores; the cost-model planner may choose). */
+ * 0 = the library's default (CUDA cores; the cost-model planner may choose).
+ * pass_kernel: 0 = default (passes run register-resident where they can:
+ * every thread keeps 2^5 (c64) / 2^4 (c128) amplitudes of the tile in
+ * registers), 1 = always the shared-memory pass kernel.  Results agree within
+ * rounding either way.  reserved: must be zero. */
 typedef struct {
     int k_max;
     int tile_m;
     int planner;
     int record;
     int tensor;
-    int reserved[3];
+    int pass_kernel;
+    int reserved[2];
 } sv_options;
 
 /* Plan summary returned by sv_plan_circuit (host only, no device work). */
@@ -114,6 +119,9 @@ typedef struct {
                              amplitudes each pass reads and writes */
     int64_t gate_ops;     /* of dense_ops, the blocks applied as their gate
                              sequence in registers instead of a 2^k matrix */
+    int64_t reg_passes;   /* passes run by the register-resident kernel */
+    int64_t remaps;       /* register-layout exchanges over all such passes
+                             (per tile) */
 } sv_plan_info;
 
 /* ---- state lifetime (App. A, Eq. "hilbert") ---------------------------- */

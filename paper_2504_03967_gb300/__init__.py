@@ -38,13 +38,14 @@ class SVError(RuntimeError):
 
 class sv_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
-                ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("pass_kernel", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class sv_plan_info(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_ops", ctypes.c_int64),
                 ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64),
-                ("gate_ops", ctypes.c_int64)]
+                ("gate_ops", ctypes.c_int64), ("reg_passes", ctypes.c_int64), ("remaps", ctypes.c_int64)]
 
 
 _lib = None
@@ -117,9 +118,10 @@ def _check(rc):
     return rc
 
 
-def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0):
+def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0):
     o = sv_options()
     o.k_max, o.tile_m, o.planner, o.record, o.tensor = k_max, tile_m, planner, record, tensor
+    o.pass_kernel = pass_kernel
     return o
 
 
@@ -191,15 +193,15 @@ def sv_store_state(h):
     return a
 
 
-def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0):
+def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, record, tensor)
+    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel)
     _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
 
 
-def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, tensor=0):
+def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, tensor=0, pass_kernel=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, 0, tensor)
+    o = _opts(k_max, tile_m, planner, 0, tensor, pass_kernel)
     info = sv_plan_info()
     _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}

@@ -248,6 +248,17 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
     else plan_greedy(n, dt, cg, po, &plan);
     plan.gates = (int64_t)count;
     plan_summary(plan, info);
+    if (!plan.plain) {  // which passes the register-resident kernel takes
+        PlanBlob blob;
+        serialise_plan(plan, &blob);
+        const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off);
+        for (int i = 0; i < blob.npasses; ++i) {
+            if (!pd[i].rmode) continue;
+            info->reg_passes++;
+            const OpDev* od = (const OpDev*)(blob.bytes.data() + pd[i].region_off);
+            for (int o = 0; o < pd[i].nops; ++o) info->remaps += od[o].kind == OP_REMAP;
+        }
+    }
     return SV_OK;
 }
 

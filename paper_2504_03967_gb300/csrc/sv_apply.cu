@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_pass(typename CT<R>::V* __r
                     sd = wd;
                     sr = wr;
                 }
-                switch (op.k) {  // k <= max_gates_k: 4 (complex64), 3 (complex128)
+                switch (op.k) {  // k <= smem_gates_max_k: 4 (complex64), 3 (complex128)
                 case 1: tile_gates<V, 1>(tile, m, op, sr, sd); break;
                 case 2: tile_gates<V, 2>(tile, m, op, sr, sd); break;
                 case 3: tile_gates<V, 3>(tile, m, op, sr, sd); break;
@@ -873,7 +873,6 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_pass(typename CT<R>::V* __r
 
 // Shared memory a pass may stage (its region) and the CTA budget that keeps
 // two CTAs per SM when the tile is double-buffered.
-constexpr int kStageCap = 48 * 1024;
 constexpr int kTwoCtaBudget = 112 * 1024;
 constexpr int kMaxDynSmem = 225 * 1024;  // 227 KB per block less the kernel's static variables
 
@@ -916,6 +915,318 @@ PassLayout pass_layout(int dtype, const PassDev& P) {
     // share an SM (512 columns), so such passes ask for enough shared memory
     // to keep a third one away.
     if (P.tc_k >= 5 && lay.total < 80 * 1024) lay.total = 80 * 1024;
+    return lay;
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident tile pass.  Thread t of a CTA of 2^(m-RB) threads holds
+// the 2^RB amplitudes of the tile whose register bits (tile positions
+// rpos[0..RB-1]) vary and whose other bits are the bits of t (tile positions
+// tpos[]).  Gate records, dense blocks (on register bits 0..k-1) and diagonal
+// runs act on the registers directly; shared memory is used only to load and
+// store the tile and to exchange amplitudes when the plan changes the
+// register layout (remap).  The layouts are chosen on the host.
+// ---------------------------------------------------------------------------
+template <typename V, int RB> struct RegLayout {
+    int sbase;     // swizzled tile offset of this thread's register 0
+    int sbit[RB];  // swizzled offset of register bit b
+};
+
+template <typename V, int RB>
+__device__ __forceinline__ void reg_layout(RegLayout<V, RB>& L, const int* rpos, const int* tpos, int tb) {
+    int base = 0;
+    for (int t = 0; t < tb; ++t) base |= ((int)(threadIdx.x >> t) & 1) << tpos[t];
+    L.sbase = swz<V>(base);
+#pragma unroll
+    for (int b = 0; b < RB; ++b) L.sbit[b] = swz<V>(1 << rpos[b]);
+}
+
+template <typename V, int RB>
+__device__ __forceinline__ void reg_read(V* v, const V* tile, const RegLayout<V, RB>& L) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); ++k) {
+        int o = L.sbase;
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+            if ((k >> b) & 1) o ^= L.sbit[b];
+        v[k] = tile[o];
+    }
+}
+
+template <typename V, int RB>
+__device__ __forceinline__ void reg_write(const V* v, V* tile, const RegLayout<V, RB>& L) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); ++k) {
+        int o = L.sbase;
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+            if ((k >> b) & 1) o ^= L.sbit[b];
+        tile[o] = v[k];
+    }
+}
+
+// Dense 2^K x 2^K block on register bits 0..K-1.
+template <typename V, int RB, int K>
+__device__ __forceinline__ void reg_dense(V* v, const V* __restrict__ U) {
+    constexpr int D = 1 << K;
+#pragma unroll
+    for (int hi = 0; hi < (1 << (RB - K)); ++hi) {
+        V x[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = v[hi * D + j];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            V a = czero<V>();
+#pragma unroll
+            for (int j = 0; j < D; ++j) a = cfma(U[r * D + j], x[j], a);
+            v[hi * D + r] = a;
+        }
+    }
+}
+
+template <typename V, int RB>
+__device__ __forceinline__ void reg_gates(V* v, const GateRec* __restrict__ recs, int nrec, const V* __restrict__ sd) {
+    using R = decltype(V().x);
+    for (int r = 0; r < nrec; ++r) {
+        const GateRec g = recs[r];
+        switch (g.kind) {
+        case GR_U: reg_u_any<V, RB>(v, g.a, sd[g.off], sd[g.off + 1], sd[g.off + 2], sd[g.off + 3]); break;
+        case GR_UR:
+            reg_ur_any<V, RB, R>(v, g.a, sd[g.off].x, sd[g.off + 1].x, sd[g.off + 2].x, sd[g.off + 3].x);
+            break;
+        case GR_DT:
+#pragma unroll
+            for (int j = 0; j < (1 << RB); ++j) v[j] = cmul(sd[g.off + j], v[j]);
+            break;
+        case GR_CX: reg_cx_any<V, RB>(v, g.a, g.b); break;
+        default: reg_swap_any<V, RB>(v, g.a, g.b); break;
+        }
+    }
+}
+
+// Diagonal run on the registers.  fold = the run's per-tile linear
+// coefficients a'_j (tile positions j < m) and constant C (at m); dw = the
+// run's RDiagLayout words for the current layout.
+template <typename V, typename R, int RB>
+__device__ __forceinline__ void reg_diag(V* v, const uint64_t* __restrict__ dw, const uint64_t* fold, int m, int no,
+                                         const int* rpos, const int* tpos, int tb) {
+    using T = Turns<R>;
+    using U = typename T::U;
+    const RDiagLayout Lr(m, no);
+    const int tid = threadIdx.x, lo = tid & 15, hi = tid >> 4;
+    U phT = (U)fold[m] + T::coef(dw[Lr.tqlo + lo]) + T::coef(dw[Lr.tqhi + hi]);
+    for (int t = 0; t < tb; ++t)
+        if ((tid >> t) & 1) phT += (U)fold[tpos[t]];
+    for (int t = 4; t < tb; ++t)
+        if ((tid >> t) & 1) phT += T::coef(dw[Lr.tr + (t - 4) * 16 + lo]);
+    U al[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b)
+        al[b] = (U)fold[rpos[b]] + T::coef(dw[Lr.talo + b * 16 + lo]) + T::coef(dw[Lr.tahi + b * 32 + hi]);
+    U be[RB][RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int b2 = b + 1; b2 < RB; ++b2) be[b][b2] = T::coef(dw[Lr.beta + b * 5 + b2]);
+    constexpr int LB = (RB + 1) / 2, HB = RB - LB;
+    U PL[1 << LB];
+#pragma unroll
+    for (int u = 0; u < (1 << LB); ++u) {
+        U s = 0;
+#pragma unroll
+        for (int b = 0; b < LB; ++b)
+            if ((u >> b) & 1) {
+                s += al[b];
+#pragma unroll
+                for (int b2 = b + 1; b2 < LB; ++b2)
+                    if ((u >> b2) & 1) s += be[b][b2];
+            }
+        PL[u] = s;
+    }
+#pragma unroll
+    for (int w = 0; w < (1 << HB); ++w) {
+        U PH = phT;
+        U cb[LB];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) cb[b] = 0;
+#pragma unroll
+        for (int c = 0; c < HB; ++c)
+            if ((w >> c) & 1) {
+                PH += al[LB + c];
+#pragma unroll
+                for (int c2 = c + 1; c2 < HB; ++c2)
+                    if ((w >> c2) & 1) PH += be[LB + c][LB + c2];
+#pragma unroll
+                for (int b = 0; b < LB; ++b) cb[b] += be[b][LB + c];
+            }
+#pragma unroll
+        for (int u = 0; u < (1 << LB); ++u) {
+            U ph = PH + PL[u];
+#pragma unroll
+            for (int b = 0; b < LB; ++b)
+                if ((u >> b) & 1) ph += cb[b];
+            R sn, cs;
+            T::sincos(ph, &sn, &cs);
+            V f;
+            f.x = cs;
+            f.y = sn;
+            const int k = (w << LB) | u;
+            v[k] = cmul(f, v[k]);
+        }
+    }
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(512, 1) k_rpass(typename CT<R>::V* __restrict__ psi, int n,
+                                                  const PassDev* __restrict__ pdp,
+                                                  const unsigned char* __restrict__ blob, const PassLayout lay) {
+    using V = typename CT<R>::V;
+    using T = Turns<R>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ PassDev P;
+    {
+        const int* src = (const int*)pdp;
+        int* dst = (int*)&P;
+        for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int m = P.m, L = P.L, tb = m - RB, no = P.nother, nd = P.ndiag;
+    V* tiles[2] = {(V*)smem, (V*)(smem + (lay.nbuf == 2 ? lay.tile_bytes : 0))};
+    uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
+    unsigned char* stage = smem + lay.stage_off;
+    uint64_t* fold = (uint64_t*)(smem + lay.work_off);  // nd x (m + 1)
+    int* dofs = (int*)(fold + (size_t)nd * (m + 1));   // diag word offsets by ordinal
+    const unsigned char* greg = blob + P.region_off;
+    for (int e = threadIdx.x; e < lay.stage_bytes / 16; e += blockDim.x) cp_async16(stage + 16 * e, greg + 16 * e);
+    cp_async_commit();
+    const int nrows = 1 << (m - L);
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+        uint32_t o = 0;
+        for (int b = 0; b < m - L; ++b)
+            if ((r >> b) & 1) o |= 1u << (P.tq[L + b] - L);
+        rowoff[r] = o;
+    }
+    cp_async_wait_group<0>();
+    __syncthreads();
+    const OpDev* ops = (const OpDev*)stage;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < P.nops; ++i)
+            if (ops[i].kind == OP_DIAG) dofs[ops[i].ord] = ops[i].diag_off;
+    const uint64_t ntiles = 1ull << (n - m);
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = 0;
+        for (int i = 0; i < no; ++i) b |= ((t >> i) & 1ull) << P.oq[i];
+        return b;
+    };
+    int cur = 0;
+    if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
+        issue_tile(tiles[0], psi, tile_base(blockIdx.x), rowoff, m, L);
+        cp_async_commit();
+    }
+    V v[1 << RB];
+    RegLayout<V, RB> Lg;
+    const int* rpos = nullptr;
+    const int* tpos = nullptr;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t base = tile_base(t);
+        const uint64_t tn = t + gridDim.x;
+        if (lay.nbuf == 2) {
+            if (tn < ntiles) {
+                issue_tile(tiles[cur ^ 1], psi, tile_base(tn), rowoff, m, L);
+                cp_async_commit();
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+        } else {
+            issue_tile(tiles[0], psi, base, rowoff, m, L);
+            cp_async_commit();
+            cp_async_wait_group<0>();
+        }
+        __syncthreads();
+        V* tile = tiles[cur];
+        // per-tile fold of every diagonal run: a'_j = a_j + sum_o b_jo x_o and
+        // C = c + sum_o a_o x_o + sum_{o2<o} b_oo2 x_o x_o2 (x_o = bit o of t)
+        for (int idx = threadIdx.x; idx < nd * (m + 1); idx += blockDim.x) {
+            const int d = idx / (m + 1), j = idx - d * (m + 1);
+            const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
+            const RDiagLayout Lr(m, no);
+            uint64_t a;
+            if (j < m) {
+                a = dw[Lr.at + j];
+                for (int o = 0; o < no; ++o)
+                    if ((t >> o) & 1) a += dw[Lr.bo + j * no + o];
+            } else {
+                a = dw[Lr.c];
+                for (int o = 0; o < no; ++o)
+                    if ((t >> o) & 1) {
+                        a += dw[Lr.ao + o];
+                        for (int o2 = 0; o2 < o; ++o2)
+                            if ((t >> o2) & 1) a += dw[Lr.boo + o * no + o2];
+                    }
+            }
+            fold[idx] = T::coef(a);
+        }
+        bool in_regs = false;
+        for (int oi = 0; oi < P.nops; ++oi) {
+            const OpDev& op = ops[oi];
+            switch (op.kind) {
+            case OP_REMAP:
+                if (in_regs) {
+                    __syncthreads();
+                    reg_write<V, RB>(v, tile, Lg);
+                }
+                __syncthreads();
+                rpos = op.lq;
+                tpos = (const int*)(stage + op.mat_off);
+                reg_layout<V, RB>(Lg, rpos, tpos, tb);
+                reg_read<V, RB>(v, tile, Lg);
+                in_regs = true;
+                break;
+            case OP_GATES:
+                reg_gates<V, RB>(v, (const GateRec*)(stage + op.rec_off), op.nrec, (const V*)(stage + op.mat_off));
+                break;
+            case OP_DENSE: {
+                const V* U = (const V*)(stage + op.mat_off);
+                switch (op.k) {
+                case 1: reg_dense<V, RB, 1>(v, U); break;
+                case 2: reg_dense<V, RB, 2>(v, U); break;
+                default: reg_dense<V, RB, 3>(v, U); break;
+                }
+                break;
+            }
+            default:
+                reg_diag<V, R, RB>(v, (const uint64_t*)(stage + op.diag_off), fold + (size_t)op.ord * (m + 1), m, no,
+                                   rpos, tpos, tb);
+                break;
+            }
+        }
+        __syncthreads();
+        reg_write<V, RB>(v, tile, Lg);
+        __syncthreads();
+        store_tile(tile, psi, base, rowoff, m, L);
+        __syncthreads();
+        if (lay.nbuf == 2) cur ^= 1;
+    }
+}
+
+PassLayout rpass_layout(int dtype, const PassDev& P) {
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    const int m = P.m;
+    const int nrows = 1 << (m - P.L);
+    PassLayout lay;
+    memset(&lay, 0, sizeof(lay));
+    lay.tile_bytes = round128(csz << m);
+    lay.staged = 1;
+    lay.stage_bytes = P.region_bytes;
+    const size_t work = sizeof(uint64_t) * (size_t)P.ndiag * (m + 1) + sizeof(int) * (size_t)P.ndiag;
+    const int rest = round128(4 * (size_t)nrows) + round128(lay.stage_bytes) + round128(work);
+    lay.nbuf = 2 * lay.tile_bytes + rest <= kTwoCtaBudget ? 2 : 1;
+    lay.rowoff_off = lay.nbuf * lay.tile_bytes;
+    lay.bres_off = lay.rowoff_off + round128(4 * (size_t)nrows);
+    lay.stage_off = lay.bres_off;
+    lay.work_off = lay.stage_off + round128(lay.stage_bytes);
+    lay.total = lay.work_off + round128(work);
     return lay;
 }
 
@@ -996,7 +1307,7 @@ __global__ void __launch_bounds__(kPassThreads) k_batch_small(const PassDev* __r
                 for (int e = tid; e < op.ndata; e += blockDim.x) sd[e] = gd[e];
                 for (int e = tid; e < op.nrec; e += blockDim.x) sr[e] = gr[e];
                 __syncthreads();
-                switch (op.k) {  // k <= max_gates_k: 4 (complex64), 3 (complex128)
+                switch (op.k) {  // k <= smem_gates_max_k: 4 (complex64), 3 (complex128)
                 case 1: tile_gates<V, 1>(tile, m, op, sr, sd); break;
                 case 2: tile_gates<V, 2>(tile, m, op, sr, sd); break;
                 case 3: tile_gates<V, 3>(tile, m, op, sr, sd); break;
@@ -1232,8 +1543,38 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     return cudaGetLastError();
 }
 
+template <typename R, int RB>
+static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass) {
+    using V = typename CT<R>::V;
+    const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    const PassLayout lay = rpass_layout(h->dtype, *pdh);
+    if (lay.total > kMaxDynSmem) return cudaErrorInvalidValue;
+    static int attr_bytes = 0;
+    if (lay.total > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_rpass<R, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+        if (e != cudaSuccess) return e;
+        attr_bytes = lay.total;
+    }
+    const int threads = 1 << (pdh->m - RB);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass<R, RB>, threads, lay.total);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t ntiles = 1ull << (h->n - pdh->m);
+    uint64_t grid = (uint64_t)num_sms() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const unsigned char* b = (const unsigned char*)blob_dev;
+    count_launch();
+    k_rpass<R, RB><<<(unsigned)grid, threads, lay.total, h->stream>>>(
+        (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, b, lay);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    if (pdh->rmode) {
+        if (h->dtype == SV_C64) return rpass_t<float, 5>(h, blob_dev, blob, pass);
+        return rpass_t<double, 4>(h, blob_dev, blob, pass);
+    }
     if (h->dtype == SV_C64) {
         if (pdh->tc_k) return pass_t<float, true>(h, blob_dev, blob, pass, hp);
         return pass_t<float, false>(h, blob_dev, blob, pass, hp);

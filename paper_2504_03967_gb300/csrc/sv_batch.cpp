@@ -122,6 +122,7 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
                 plans[i].passes.push_back(hp);
             }
             mmax = std::max(mmax, plans[i].n);
+            plans[i].no_register_passes = true;  // the batch kernel reads the shared-memory region format
             pp.push_back(&plans[i]);
         }
         PlanBlob blob;

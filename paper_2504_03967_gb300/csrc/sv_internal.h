@@ -46,7 +46,13 @@ int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out,
 // 2^L amplitudes is contiguous), applies its ops in shared memory and writes
 // the tile back: one HBM read and one write of the state per pass.
 // ---------------------------------------------------------------------------
-enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2 };
+enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2, OP_REMAP = 3 };
+
+// Register-resident passes: each thread holds 2^kRegBits amplitudes of the
+// tile in registers; the other m - kRegBits tile bits index the thread.
+__host__ __device__ inline int reg_bits(int dtype) { return dtype == SV_C64 ? 5 : 4; }
+constexpr int kRegDenseMaxK = 3;  // dense blocks in registers (wider ones run as gate sequences)
+constexpr int kStageCap = 48 * 1024;  // bytes of a pass region staged in shared memory
 
 // Gate-sequence block records (positions are block-local bits, data offsets
 // index the op's own complex values).
@@ -56,9 +62,12 @@ struct GateRec {
 };
 constexpr int kMaxGateRecs = 64;     // records per gate-sequence op
 constexpr int kMaxGateData = 768;    // complex values per gate-sequence op
-// Widest gate-sequence block: its 2^k amplitudes per thread must stay in
-// registers under the pass kernel's 80-register budget.
-inline int max_gates_k(int dtype) { return dtype == SV_C64 ? 4 : 3; }
+// Widest gate-sequence block: its 2^k amplitudes per thread stay in
+// registers (64 registers of data at the bound, for both dtypes).  The
+// shared-memory pass kernel, which holds more state per thread, takes one
+// qubit less and runs wider blocks from their dense matrix.
+inline int max_gates_k(int dtype) { return dtype == SV_C64 ? 5 : 4; }
+inline int smem_gates_max_k(int dtype) { return dtype == SV_C64 ? 4 : 3; }
 
 struct DiagForm {
     // phase(x) = c + sum_q a[q] x_q + sum_{p<q} b[p*n+q] x_p x_q  (radians)
@@ -81,7 +90,8 @@ struct DiagForm {
 struct HostOp {
     int kind;
     std::vector<int> qubits;  // dense / gates: sorted ascending, block bit i <-> qubits[i]
-    std::vector<cd> mat;      // dense: 2^k x 2^k row-major; gates: the records' data
+    std::vector<cd> mat;      // dense and gates: the block's 2^k x 2^k matrix, row-major
+    std::vector<cd> gdata;    // gates: the records' complex data
     DiagForm diag;            // diag
     std::vector<GateRec> recs;  // gates
     int ngates = 0;           // logical gates folded into the op
@@ -112,6 +122,7 @@ struct Plan {
     std::vector<PlainOp> plain_ops;
     int64_t gates = 0;
     int tensor = -1;  // 0: dense blocks of k >= kMinTcK go to the tensor cores
+    bool no_register_passes = false;
 };
 
 struct PlanOptions {
@@ -119,6 +130,7 @@ struct PlanOptions {
     int tile_m = 13;
     int planner = SV_PLAN_GREEDY;
     int tensor = -1;  // 0: tensor cores for c64 blocks of k >= 3; -1: CUDA cores only
+    int pass_kernel = 0;  // 1: shared-memory pass kernel only
 };
 
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
@@ -157,7 +169,7 @@ struct OpDev {
     int nrec;      // gates: number of records
     int rec_off;   // gates: byte offset of the records
     int ndata;     // gates: complex values at mat_off
-    int pad;
+    int ord;       // register passes, diag: ordinal of the run within the pass
 };
 static_assert(sizeof(OpDev) % 16 == 0, "OpDev array must keep 16-byte alignment");
 
@@ -178,6 +190,8 @@ struct PassDev {
     int n;               // qubits of the state the pass runs on
     int m;
     int L;
+    int rmode;           // 1: register-resident pass (region in the register format)
+    int ndiag;           // register passes: diagonal runs (each folded once per tile)
     int nops;            // ops in the pass's region
     int region_off;      // byte offset of the region in the blob
     int region_bytes;    // its size (multiple of 16)
@@ -213,6 +227,32 @@ struct DiagLayout {
     }
 };
 __host__ __device__ inline size_t diag_doubles(int m, int no) { return (size_t)DiagLayout(m, no).total; }
+
+// Diagonal run of a register pass (8-byte words of fixed-point turns), for
+// the register layout in force: rpos[b] = tile position of register bit b,
+// tpos[t] = tile position of thread bit t (t < m - r; lo = thread bits 0..3,
+// hi = the rest, at most 5):
+//   c | a_t[m] | a_o[no] | Bo[m][no] | Boo[no][no]        (per-tile fold)
+//   | TQlo[16] | TQhi[32] | TR[5][16]                       (thread-thread couplings)
+//   | TAlo[5][16] | TAhi[5][32]                             (register-thread couplings)
+//   | beta[5][5]                                            (register-register couplings)
+struct RDiagLayout {
+    int c, at, ao, bo, boo, tqlo, tqhi, tr, talo, tahi, beta, total;
+    __host__ __device__ RDiagLayout(int m, int no) {
+        c = 0;
+        at = 1;
+        ao = at + m;
+        bo = ao + no;
+        boo = bo + m * no;
+        tqlo = boo + no * no;
+        tqhi = tqlo + 16;
+        tr = tqhi + 32;
+        talo = tr + 5 * 16;
+        tahi = talo + 5 * 16;
+        beta = tahi + 5 * 32;
+        total = beta + 25;
+    }
+};
 
 struct PlanBlob {
     std::vector<unsigned char> bytes;

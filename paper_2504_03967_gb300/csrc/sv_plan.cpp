@@ -300,6 +300,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         if (opt->tile_m > 0) po.tile_m = opt->tile_m;
         po.planner = opt->planner;
         po.tensor = opt->tensor > 0 ? 0 : -1;
+        po.pass_kernel = opt->pass_kernel == 1 ? 1 : 0;
     }
     if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
@@ -316,6 +317,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     out->passes.clear();
     out->gates = (int64_t)gates.size();
     out->tensor = po.tensor;
+    out->no_register_passes = po.pass_kernel == 1;
     const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
     // the tile holds the row bits plus room for any two-qubit gate
     const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
@@ -395,13 +397,14 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
             // the cheaper representation: the dense 2^k matrix, or the gate
             // sequence applied in registers (tensor-core blocks stay dense)
             const bool tc_block = po.tensor == 0 && dtype == SV_C64 && (int)B.qubits.size() >= kMinTcK;
-            if (!tc_block && (int)B.qubits.size() <= max_gates_k(dtype) && gate_sequence(B, &op.recs, &op.mat) &&
+            op.mat = B.mat;
+            if (!tc_block && (int)B.qubits.size() <= max_gates_k(dtype) && gate_sequence(B, &op.recs, &op.gdata) &&
                 gate_sequence_cost(op.recs) <= dense_cost((int)B.qubits.size())) {
                 op.kind = OP_GATES;
             } else {
                 op.kind = OP_DENSE;
                 op.recs.clear();
-                op.mat = B.mat;
+                op.gdata.clear();
             }
             pass.ops.push_back(std::move(op));
             B = Block();
@@ -654,131 +657,348 @@ void write_diag(const DiagForm& D, int n, const HostPass& hp, const PassDev& P, 
 }
 }  // namespace
 
-void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
-    auto use_tc = [&](const Plan& p, const HostOp& o) {
-        return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
-    };
-    const int dtype = plans.empty() ? SV_C64 : plans[0]->dtype;
-    const size_t csz = dtype == SV_C64 ? 8 : 16;
-    // sizes: one region per pass
-    size_t ntc = 0, npass = 0, nregion = 0;
-    std::vector<size_t> rsize;
-    for (const Plan* pp : plans) {
-        const Plan& p = *pp;
-        npass += p.passes.size();
-        for (const HostPass& hp : p.passes) {
-            size_t r = align16(sizeof(OpDev) * hp.ops.size());
-            for (const HostOp& o : hp.ops) {
-                if (o.kind == OP_DENSE || o.kind == OP_GATES) r += align16(csz * o.mat.size());
-                else r += align16(sizeof(uint64_t) * diag_doubles((int)hp.tile.size(), p.n - (int)hp.tile.size()));
-                if (o.kind == OP_GATES) r += align16(sizeof(GateRec) * o.recs.size());
-                if (use_tc(p, o)) ntc += (size_t)tc_floats((int)o.qubits.size());
-            }
-            rsize.push_back(r);
-            nregion += r;
-        }
+namespace {
+
+// Payload bytes of one region, 16-byte aligned pieces; offsets are bytes
+// from the start of the payload until the OpDev array is put in front.
+struct Payload {
+    std::vector<unsigned char> b;
+    size_t put(const void* p, size_t n) {
+        const size_t off = b.size();
+        b.resize(off + align16(n), 0);
+        if (n) memcpy(b.data() + off, p, n);
+        return off;
     }
+    size_t put_cplx(const std::vector<cd>& v, int dtype) {
+        if (dtype == SV_C64) {
+            std::vector<float> f(2 * v.size());
+            for (size_t e = 0; e < v.size(); ++e) {
+                f[2 * e] = (float)v[e].real();
+                f[2 * e + 1] = (float)v[e].imag();
+            }
+            return put(f.data(), sizeof(float) * f.size());
+        }
+        std::vector<double> f(2 * v.size());
+        for (size_t e = 0; e < v.size(); ++e) {
+            f[2 * e] = v[e].real();
+            f[2 * e + 1] = v[e].imag();
+        }
+        return put(f.data(), sizeof(double) * f.size());
+    }
+};
+
+void assemble(std::vector<OpDev>& ops, const Payload& pay, PassDev* P, std::vector<unsigned char>* out) {
+    const size_t ob = align16(sizeof(OpDev) * ops.size());
+    for (OpDev& O : ops) {
+        if (O.kind == OP_DENSE || O.kind == OP_GATES || O.kind == OP_REMAP) O.mat_off += (int)ob;
+        if (O.kind == OP_GATES) O.rec_off += (int)ob;
+        if (O.kind == OP_DIAG) O.diag_off += (int)ob;
+    }
+    out->assign(ob + pay.b.size(), 0);
+    if (!ops.empty()) memcpy(out->data(), ops.data(), sizeof(OpDev) * ops.size());
+    if (!pay.b.empty()) memcpy(out->data() + ob, pay.b.data(), pay.b.size());
+    P->nops = (int)ops.size();
+    P->ops_bytes = (int)ob;
+    P->region_bytes = (int)out->size();
+}
+
+bool use_tc(const Plan& p, const HostOp& o) {
+    return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
+}
+
+// Region for the shared-memory pass kernel: dense blocks, gate sequences of
+// at most smem_gates_max_k qubits (wider ones as their dense matrix) and
+// diagonal runs in the DiagLayout form.
+void smem_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, float* tcf, size_t* ti,
+                 std::vector<unsigned char>* out) {
+    std::vector<OpDev> ops;
+    Payload pay;
+    for (const HostOp& o : hp.ops) {
+        OpDev O;
+        memset(&O, 0, sizeof(O));
+        O.ngates = o.ngates;
+        if (o.kind == OP_DENSE || o.kind == OP_GATES) {
+            O.k = (int)o.qubits.size();
+            for (int i = 0; i < O.k; ++i) O.lq[i] = loc[o.qubits[i]];
+            const bool gates = o.kind == OP_GATES && O.k <= smem_gates_max_k(p.dtype);
+            O.kind = gates ? OP_GATES : OP_DENSE;
+            if (gates) {
+                O.mat_off = (int)pay.put_cplx(o.gdata, p.dtype);
+                O.ndata = (int)o.gdata.size();
+                O.nrec = (int)o.recs.size();
+                O.rec_off = (int)pay.put(o.recs.data(), sizeof(GateRec) * o.recs.size());
+            } else {
+                O.mat_off = (int)pay.put_cplx(o.mat, p.dtype);
+            }
+            if (use_tc(p, o)) {
+                // B = [Ur; Ui]: row n < D holds Re U[n][j], row D + n holds Im U[n][j]
+                const int k = O.k, Dm = 1 << k, N = 2 * Dm, K = Dm;
+                O.tc = 1;
+                O.tc_off = (int)*ti;
+                float* hi = tcf + *ti;
+                float* lo = hi + N * K;
+                for (int r = 0; r < N; ++r)
+                    for (int j = 0; j < K; ++j) {
+                        const cd u = o.mat[(size_t)(r % Dm) * Dm + j];
+                        const float v = (float)(r < Dm ? u.real() : u.imag());
+                        const float vh = tf32_round(v);
+                        const int idx = tc_kmajor_index(r, j, K);
+                        hi[idx] = vh;
+                        lo[idx] = tf32_round(v - vh);
+                    }
+                if (!P->tc_k) P->tc_base = (int)*ti;
+                *ti += (size_t)tc_floats(k);
+                if (k > P->tc_k) P->tc_k = k;
+                P->tc_res = (int)*ti - P->tc_base;  // all of the pass's B operands so far
+            }
+        } else {
+            O.kind = OP_DIAG;
+            std::vector<uint64_t> w(diag_doubles(P->m, P->nother));
+            write_diag(o.diag, p.n, hp, *P, w.data());
+            O.diag_off = (int)pay.put(w.data(), sizeof(uint64_t) * w.size());
+        }
+        ops.push_back(O);
+    }
+    if (P->tc_res > kTcResidentFloats) P->tc_res = 0;  // too large: staged per op and tile
+    assemble(ops, pay, P, out);
+}
+
+// Region for the register-resident pass kernel, or false when the pass
+// needs the shared-memory kernel (tensor-core blocks, dense blocks wider than
+// kRegDenseMaxK, a thread count outside 32..512, or a region too large to
+// stage).  Register layouts are chosen here: before a block whose qubits are
+// not all in registers, a remap brings them in (for dense blocks, in block
+// order at register bits 0..k-1) and fills the other register bits with the
+// tile positions the following blocks use soonest.
+bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, std::vector<unsigned char>* out) {
+    const int r = reg_bits(p.dtype), m = P->m, tb = m - r, nops = (int)hp.ops.size();
+    if (tb < 5 || tb > 9) return false;
+    std::vector<std::vector<int>> used(nops);
+    for (int i = 0; i < nops; ++i) {
+        const HostOp& o = hp.ops[i];
+        if (o.kind == OP_DIAG) continue;
+        if (use_tc(p, o)) return false;
+        if (o.kind == OP_DENSE && (int)o.qubits.size() > kRegDenseMaxK) return false;
+        if ((int)o.qubits.size() > r) return false;
+        for (int q : o.qubits) used[i].push_back(loc[q]);
+    }
+    auto next_use = [&](int pos, int from) {
+        for (int j = from; j < nops; ++j)
+            if (std::find(used[j].begin(), used[j].end(), pos) != used[j].end()) return j;
+        return nops + 1;
+    };
+    std::vector<OpDev> ops;
+    Payload pay;
+    std::vector<int> rpos, tpos;
+    auto remap = [&](int i, const std::vector<int>& PQ) {
+        std::vector<int> cand;
+        for (int q = 0; q < m; ++q)
+            if (std::find(PQ.begin(), PQ.end(), q) == PQ.end()) cand.push_back(q);
+        std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+            const int na = next_use(a, i + 1), nb = next_use(b, i + 1);
+            if (na != nb) return na < nb;
+            const bool ia = std::find(rpos.begin(), rpos.end(), a) != rpos.end();
+            const bool ib = std::find(rpos.begin(), rpos.end(), b) != rpos.end();
+            return ia && !ib;
+        });
+        std::vector<int> slots = PQ;
+        for (size_t c = 0; c < cand.size() && (int)slots.size() < r; ++c) slots.push_back(cand[c]);
+        std::sort(slots.begin() + PQ.size(), slots.end());
+        rpos = slots;
+        tpos.clear();
+        for (int q = 0; q < m; ++q)
+            if (std::find(rpos.begin(), rpos.end(), q) == rpos.end()) tpos.push_back(q);
+        OpDev O;
+        memset(&O, 0, sizeof(O));
+        O.kind = OP_REMAP;
+        O.k = r;
+        for (int b = 0; b < r; ++b) O.lq[b] = rpos[b];
+        int tp[16];
+        for (int t = 0; t < 16; ++t) tp[t] = t < (int)tpos.size() ? tpos[t] : -1;
+        O.mat_off = (int)pay.put(tp, sizeof(tp));
+        ops.push_back(O);
+    };
+    auto slot = [&](int pos) { return (int)(std::find(rpos.begin(), rpos.end(), pos) - rpos.begin()); };
+    int nd = 0;
+    for (int i = 0; i < nops; ++i) {
+        const HostOp& o = hp.ops[i];
+        if (o.kind == OP_DIAG) {
+            if (rpos.empty()) {
+                std::vector<int> PQ;
+                for (int j = i + 1; j < nops; ++j)
+                    if (!used[j].empty()) {
+                        PQ = used[j];
+                        break;
+                    }
+                remap(i, PQ);
+            }
+            OpDev O;
+            memset(&O, 0, sizeof(O));
+            O.kind = OP_DIAG;
+            O.ngates = o.ngates;
+            O.ord = nd++;
+            const RDiagLayout Lr(m, P->nother);
+            std::vector<uint64_t> w(Lr.total, 0);
+            std::vector<uint64_t> full(diag_doubles(m, P->nother));
+            write_diag(o.diag, p.n, hp, *P, full.data());  // c, a_t, a_o, Bo, Boo come first in both layouts
+            for (int e = 0; e < Lr.tqlo; ++e) w[e] = full[e];
+            auto B = [&](int pa, int pb) {
+                if (pa == pb) return (uint64_t)0;
+                const int qa = P->tq[pa], qb = P->tq[pb];
+                return fx_turns(o.diag.b[(size_t)std::min(qa, qb) * p.n + std::max(qa, qb)]);
+            };
+            const int nlo = std::min(4, tb);
+            for (int e = 0; e < 16; ++e) {
+                uint64_t v = 0;
+                for (int t = 0; t < nlo; ++t)
+                    for (int t2 = 0; t2 < t; ++t2)
+                        if (((e >> t) & 1) && ((e >> t2) & 1)) v += B(tpos[t], tpos[t2]);
+                w[Lr.tqlo + e] = v;
+            }
+            for (int e = 0; e < 32; ++e) {
+                uint64_t v = 0;
+                for (int t = 4; t < tb; ++t)
+                    for (int t2 = 4; t2 < t; ++t2)
+                        if (((e >> (t - 4)) & 1) && ((e >> (t2 - 4)) & 1)) v += B(tpos[t], tpos[t2]);
+                w[Lr.tqhi + e] = v;
+            }
+            for (int t = 4; t < tb; ++t)
+                for (int e = 0; e < 16; ++e) {
+                    uint64_t v = 0;
+                    for (int t2 = 0; t2 < nlo; ++t2)
+                        if ((e >> t2) & 1) v += B(tpos[t], tpos[t2]);
+                    w[Lr.tr + (t - 4) * 16 + e] = v;
+                }
+            for (int b = 0; b < r; ++b) {
+                for (int e = 0; e < 16; ++e) {
+                    uint64_t v = 0;
+                    for (int t = 0; t < nlo; ++t)
+                        if ((e >> t) & 1) v += B(rpos[b], tpos[t]);
+                    w[Lr.talo + b * 16 + e] = v;
+                }
+                for (int e = 0; e < 32; ++e) {
+                    uint64_t v = 0;
+                    for (int t = 4; t < tb; ++t)
+                        if ((e >> (t - 4)) & 1) v += B(rpos[b], tpos[t]);
+                    w[Lr.tahi + b * 32 + e] = v;
+                }
+                for (int b2 = 0; b2 < r; ++b2) w[Lr.beta + b * 5 + b2] = B(rpos[b], rpos[b2]);
+            }
+            O.diag_off = (int)pay.put(w.data(), sizeof(uint64_t) * w.size());
+            ops.push_back(O);
+            continue;
+        }
+        const std::vector<int>& PQ = used[i];
+        bool ok = !rpos.empty();
+        for (size_t j = 0; ok && j < PQ.size(); ++j)
+            ok = o.kind == OP_DENSE ? rpos[j] == PQ[j] : slot(PQ[j]) < r;
+        if (!ok) remap(i, PQ);
+        OpDev O;
+        memset(&O, 0, sizeof(O));
+        O.kind = o.kind;
+        O.ngates = o.ngates;
+        O.k = (int)PQ.size();
+        for (int j = 0; j < O.k; ++j) O.lq[j] = slot(PQ[j]);
+        if (o.kind == OP_DENSE) {
+            O.mat_off = (int)pay.put_cplx(o.mat, p.dtype);
+        } else {
+            std::vector<GateRec> recs;
+            std::vector<cd> data;
+            for (const GateRec& g : o.recs) {
+                GateRec t = g;
+                if (g.kind == GR_DT) {
+                    t.off = (int)data.size();
+                    for (int v = 0; v < (1 << r); ++v) {
+                        int idx = 0;
+                        for (int j = 0; j < O.k; ++j) idx |= ((v >> O.lq[j]) & 1) << j;
+                        data.push_back(o.gdata[(size_t)g.off + idx]);
+                    }
+                } else {
+                    t.a = O.lq[g.a];
+                    if (g.kind == GR_CX || g.kind == GR_SWAP) t.b = O.lq[g.b];
+                    if (g.kind == GR_U || g.kind == GR_UR) {
+                        t.off = (int)data.size();
+                        for (int e = 0; e < 4; ++e) data.push_back(o.gdata[(size_t)g.off + e]);
+                    }
+                }
+                recs.push_back(t);
+            }
+            O.mat_off = (int)pay.put_cplx(data, p.dtype);
+            O.ndata = (int)data.size();
+            O.nrec = (int)recs.size();
+            O.rec_off = (int)pay.put(recs.data(), sizeof(GateRec) * recs.size());
+        }
+        ops.push_back(O);
+    }
+    if (rpos.empty()) remap(0, {});
+    assemble(ops, pay, P, out);
+    P->rmode = 1;
+    P->ndiag = nd;
+    return P->region_bytes <= kStageCap;
+}
+
+}  // namespace
+
+void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
+    const int dtype = plans.empty() ? SV_C64 : plans[0]->dtype;
+    size_t ntc = 0, npass = 0;
+    for (const Plan* pp : plans) {
+        npass += pp->passes.size();
+        for (const HostPass& hp : pp->passes)
+            for (const HostOp& o : hp.ops)
+                if (use_tc(*pp, o)) ntc += (size_t)tc_floats((int)o.qubits.size());
+    }
+    (void)dtype;
     blob->npasses = (int)npass;
     blob->pass_off = 0;
     blob->tc_off = align16(sizeof(PassDev) * npass);
-    size_t roff = align16(blob->tc_off + sizeof(float) * ntc);
-    blob->bytes.assign(roff + nregion, 0);
-    blob->max_region = 0;
-    unsigned char* base = blob->bytes.data();
-    float* tcf = (float*)(base + blob->tc_off);
-    PassDev* pd = (PassDev*)(base + blob->pass_off);
+    const size_t roff0 = align16(blob->tc_off + sizeof(float) * ntc);
+    std::vector<PassDev> pds(npass);
+    std::vector<std::vector<unsigned char>> regions(npass);
+    std::vector<float> tcf(ntc);
     size_t ti = 0, gpi = 0;
     for (const Plan* pp : plans) {
-      const Plan& p = *pp;
-      const int n = p.n;
-      for (size_t pi = 0; pi < p.passes.size(); ++pi, ++gpi) {
-        const HostPass& hp = p.passes[pi];
-        PassDev& P = pd[gpi];
-        memset(&P, 0, sizeof(P));
-        P.n = n;
-        P.m = (int)hp.tile.size();
-        P.L = hp.L;
-        P.nops = (int)hp.ops.size();
-        P.region_off = (int)roff;
-        P.region_bytes = (int)rsize[gpi];
-        P.ops_bytes = (int)align16(sizeof(OpDev) * hp.ops.size());
-        blob->max_region = std::max(blob->max_region, P.region_bytes);
-        unsigned char* reg = base + roff;
-        size_t off = (size_t)P.ops_bytes;
-        roff += rsize[gpi];
-        int loc[64];
-        for (int i = 0; i < 64; ++i) loc[i] = -1;
-        for (int i = 0; i < P.m; ++i) {
-            P.tq[i] = hp.tile[i];
-            loc[hp.tile[i]] = i;
-        }
-        P.nother = 0;
-        for (int q = 0; q < n; ++q)
-            if (loc[q] < 0) P.oq[P.nother++] = q;
-        OpDev* od = (OpDev*)reg;
-        for (size_t oi = 0; oi < hp.ops.size(); ++oi) {
-            const HostOp& o = hp.ops[oi];
-            OpDev& O = od[oi];
-            memset(&O, 0, sizeof(O));
-            O.kind = o.kind;
-            O.ngates = o.ngates;
-            if (o.kind == OP_DENSE || o.kind == OP_GATES) {
-                O.k = (int)o.qubits.size();
-                for (int i = 0; i < O.k; ++i) O.lq[i] = loc[o.qubits[i]];
-                O.mat_off = (int)off;
-                if (p.dtype == SV_C64) {
-                    float* f = (float*)(reg + off);
-                    for (size_t e = 0; e < o.mat.size(); ++e) {
-                        f[2 * e] = (float)o.mat[e].real();
-                        f[2 * e + 1] = (float)o.mat[e].imag();
-                    }
-                } else {
-                    double* f = (double*)(reg + off);
-                    for (size_t e = 0; e < o.mat.size(); ++e) {
-                        f[2 * e] = o.mat[e].real();
-                        f[2 * e + 1] = o.mat[e].imag();
-                    }
-                }
-                off += align16(csz * o.mat.size());
-                if (o.kind == OP_GATES) {
-                    O.nrec = (int)o.recs.size();
-                    O.ndata = (int)o.mat.size();
-                    O.rec_off = (int)off;
-                    GateRec* rg = (GateRec*)(reg + off);
-                    for (size_t r = 0; r < o.recs.size(); ++r) rg[r] = o.recs[r];
-                    off += align16(sizeof(GateRec) * o.recs.size());
-                }
-                if (use_tc(p, o)) {
-                    // B = [Ur; Ui]: row n < D holds Re U[n][j], row D + n holds Im U[n][j]
-                    const int k = O.k, Dm = 1 << k, N = 2 * Dm, K = Dm;
-                    O.tc = 1;
-                    O.tc_off = (int)ti;
-                    float* hi = tcf + ti;
-                    float* lo = hi + N * K;
-                    for (int r = 0; r < N; ++r)
-                        for (int j = 0; j < K; ++j) {
-                            const cd u = o.mat[(size_t)(r % Dm) * Dm + j];
-                            const float v = (float)(r < Dm ? u.real() : u.imag());
-                            const float vh = tf32_round(v);
-                            const int idx = tc_kmajor_index(r, j, K);
-                            hi[idx] = vh;
-                            lo[idx] = tf32_round(v - vh);
-                        }
-                    if (!P.tc_k) P.tc_base = (int)ti;
-                    ti += (size_t)tc_floats(k);
-                    if (k > P.tc_k) P.tc_k = k;
-                    P.tc_res = (int)ti - P.tc_base;  // all of the pass's B operands so far
-                }
-            } else {
-                O.k = 0;
-                O.diag_off = (int)off;
-                write_diag(o.diag, n, hp, P, (uint64_t*)(reg + off));
-                off += align16(sizeof(uint64_t) * diag_doubles(P.m, P.nother));
+        const Plan& p = *pp;
+        const int n = p.n;
+        for (size_t pi = 0; pi < p.passes.size(); ++pi, ++gpi) {
+            const HostPass& hp = p.passes[pi];
+            PassDev& P = pds[gpi];
+            memset(&P, 0, sizeof(P));
+            P.n = n;
+            P.m = (int)hp.tile.size();
+            P.L = hp.L;
+            int loc[64];
+            for (int i = 0; i < 64; ++i) loc[i] = -1;
+            for (int i = 0; i < P.m; ++i) {
+                P.tq[i] = hp.tile[i];
+                loc[hp.tile[i]] = i;
             }
+            P.nother = 0;
+            for (int q = 0; q < n; ++q)
+                if (loc[q] < 0) P.oq[P.nother++] = q;
+            if (!p.no_register_passes) {
+                PassDev R = P;
+                if (reg_region(p, hp, &R, loc, &regions[gpi])) {
+                    P = R;
+                    continue;
+                }
+            }
+            smem_region(p, hp, &P, loc, tcf.data(), &ti, &regions[gpi]);
         }
-        if (P.tc_res > kTcResidentFloats) P.tc_res = 0;  // too large: staged per op and tile
-      }
     }
+    size_t roff = roff0;
+    blob->max_region = 0;
+    for (size_t i = 0; i < npass; ++i) {
+        pds[i].region_off = (int)roff;
+        roff += regions[i].size();
+        blob->max_region = std::max(blob->max_region, pds[i].region_bytes);
+    }
+    blob->bytes.assign(roff, 0);
+    unsigned char* base = blob->bytes.data();
+    if (npass) memcpy(base + blob->pass_off, pds.data(), sizeof(PassDev) * npass);
+    if (ntc) memcpy(base + blob->tc_off, tcf.data(), sizeof(float) * ntc);
+    for (size_t i = 0; i < npass; ++i)
+        if (!regions[i].empty()) memcpy(base + pds[i].region_off, regions[i].data(), regions[i].size());
 }
 
 void serialise_plan(const Plan& p, PlanBlob* blob) { serialise_plans({&p}, blob); }

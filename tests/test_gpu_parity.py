@@ -81,6 +81,30 @@ def test_gate_sequence_blocks(dtype, k, kind):
 
 
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
+@pytest.mark.parametrize("tb", [5, 6, 8, 9])
+@pytest.mark.parametrize("kind", ["mixed", "qft", "random", "cx_blocks"])
+def test_register_passes(dtype, tb, kind):
+    """Register-resident passes (2^5 / 2^4 amplitudes per thread, remaps
+    through shared memory, diagonal runs from the register layout) at every
+    thread count, against the oracle and against the shared-memory kernel."""
+    rb = 5 if dtype == S.C64 else 4
+    m = rb + tb
+    n = max(m + 3, 15)
+    rng = np.random.default_rng(500 + tb)
+    g = {"mixed": lambda: random_mixed_circuit(n, 150, rng), "qft": lambda: W.qft(n),
+         "random": lambda: W.random_u3_cx(n, 4, 40 + tb), "cx_blocks": lambda: W.random_cx_blocks(n, 60, 7 + tb)}[kind]()
+    psi0 = W.random_state(n, 70 + tb)
+    ref = U.run_oracle(n, g, psi0)
+    for k in (3, 4):
+        info = S.sv_plan_circuit(n, dtype, g, k_max=k, tile_m=m)
+        assert info["reg_passes"] > 0 and (k > 3 or info["reg_passes"] == info["passes"])
+        got = U.run_gpu(n, g, dtype, psi0=psi0, k_max=k, tile_m=m)
+        U.assert_close(got, ref, dtype, "%s register k=%d m=%d" % (kind, k, m))
+        smem = U.run_gpu(n, g, dtype, psi0=psi0, k_max=k, tile_m=m, pass_kernel=1)
+        U.assert_close(smem, ref, dtype, "%s shared-memory k=%d m=%d" % (kind, k, m))
+
+
+@pytest.mark.parametrize("dtype", DT, ids=DTN.get)
 @pytest.mark.parametrize("planner", [S.PLAN_PLAIN, S.PLAN_GREEDY])
 def test_qft_basis_and_random(dtype, planner):
     n = 18
