@@ -994,9 +994,10 @@ __device__ __forceinline__ void reg_gates(V* v, const GateRec* __restrict__ recs
         case GR_UR:
             reg_ur_any<V, RB, R>(v, g.a, sd[g.off].x, sd[g.off + 1].x, sd[g.off + 2].x, sd[g.off + 3].x);
             break;
-        case GR_DT:
+        case GR_DT:  // b: entries that differ from 1
 #pragma unroll
-            for (int j = 0; j < (1 << RB); ++j) v[j] = cmul(sd[g.off + j], v[j]);
+            for (int j = 0; j < (1 << RB); ++j)
+                if ((g.b >> j) & 1) v[j] = cmul(sd[g.off + j], v[j]);
             break;
         case GR_CX: reg_cx_any<V, RB>(v, g.a, g.b); break;
         default: reg_swap_any<V, RB>(v, g.a, g.b); break;
@@ -1076,8 +1077,11 @@ __device__ __forceinline__ void reg_diag(V* v, const uint64_t* __restrict__ dw, 
     }
 }
 
-template <typename R, int RB>
-__global__ void __launch_bounds__(512, 1) k_rpass(typename CT<R>::V* __restrict__ psi, int n,
+// MAXT/MINB: launch bounds of the instance (up to 128 threads: registers are
+// not capped below 255, so the 2^RB amplitudes and the op state never spill;
+// 256 and 512 threads: 128 registers).
+template <typename R, int RB, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restrict__ psi, int n,
                                                   const PassDev* __restrict__ pdp,
                                                   const unsigned char* __restrict__ blob, const PassLayout lay) {
     using V = typename CT<R>::V;
@@ -1145,27 +1149,33 @@ __global__ void __launch_bounds__(512, 1) k_rpass(typename CT<R>::V* __restrict_
         }
         __syncthreads();
         V* tile = tiles[cur];
-        // per-tile fold of every diagonal run: a'_j = a_j + sum_o b_jo x_o and
-        // C = c + sum_o a_o x_o + sum_{o2<o} b_oo2 x_o x_o2 (x_o = bit o of t)
-        for (int idx = threadIdx.x; idx < nd * (m + 1); idx += blockDim.x) {
-            const int d = idx / (m + 1), j = idx - d * (m + 1);
-            const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
+        // per-tile fold of every diagonal run: a'_j = a_j + sum_o b_jo x_o (one
+        // thread per run and tile position) and C = c + sum_o x_o (a_o +
+        // sum_{o2<o} b_oo2 x_o2) (one warp per run, one non-tile bit per lane),
+        // with x_o = bit o of t
+        {
             const RDiagLayout Lr(m, no);
-            uint64_t a;
-            if (j < m) {
-                a = dw[Lr.at + j];
+            for (int idx = threadIdx.x; idx < nd * m; idx += blockDim.x) {
+                const int d = idx / m, j = idx - d * m;
+                const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
+                uint64_t a = dw[Lr.at + j];
                 for (int o = 0; o < no; ++o)
                     if ((t >> o) & 1) a += dw[Lr.bo + j * no + o];
-            } else {
-                a = dw[Lr.c];
-                for (int o = 0; o < no; ++o)
-                    if ((t >> o) & 1) {
-                        a += dw[Lr.ao + o];
-                        for (int o2 = 0; o2 < o; ++o2)
-                            if ((t >> o2) & 1) a += dw[Lr.boo + o * no + o2];
-                    }
+                fold[d * (m + 1) + j] = T::coef(a);
             }
-            fold[idx] = T::coef(a);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+            for (int d = warp; d < nd; d += nwarps) {
+                const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
+                uint64_t a = 0;
+                if (lane < no && ((t >> lane) & 1)) {
+                    a = dw[Lr.ao + lane];
+                    for (int o2 = 0; o2 < lane; ++o2)
+                        if ((t >> o2) & 1) a += dw[Lr.boo + lane * no + o2];
+                }
+#pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1) a += __shfl_xor_sync(0xffffffffu, a, sh);
+                if (lane == 0) fold[d * (m + 1) + m] = T::coef(a + dw[Lr.c]);
+            }
         }
         bool in_regs = false;
         for (int oi = 0; oi < P.nops; ++oi) {
@@ -1543,7 +1553,7 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     return cudaGetLastError();
 }
 
-template <typename R, int RB>
+template <typename R, int RB, int MAXT, int MINB>
 static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass) {
     using V = typename CT<R>::V;
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
@@ -1551,29 +1561,39 @@ static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& bl
     if (lay.total > kMaxDynSmem) return cudaErrorInvalidValue;
     static int attr_bytes = 0;
     if (lay.total > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_rpass<R, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+        cudaError_t e = cudaFuncSetAttribute(k_rpass<R, RB, MAXT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             lay.total);
         if (e != cudaSuccess) return e;
         attr_bytes = lay.total;
     }
     const int threads = 1 << (pdh->m - RB);
+    if (threads > MAXT) return cudaErrorInvalidValue;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass<R, RB>, threads, lay.total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass<R, RB, MAXT, MINB>, threads, lay.total);
     if (per_sm < 1) per_sm = 1;
     const uint64_t ntiles = 1ull << (h->n - pdh->m);
     uint64_t grid = (uint64_t)num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
     const unsigned char* b = (const unsigned char*)blob_dev;
     count_launch();
-    k_rpass<R, RB><<<(unsigned)grid, threads, lay.total, h->stream>>>(
+    k_rpass<R, RB, MAXT, MINB><<<(unsigned)grid, threads, lay.total, h->stream>>>(
         (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, b, lay);
     return cudaGetLastError();
+}
+
+template <typename R, int RB>
+static cudaError_t rpass_any(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, int m) {
+    const int tb = m - RB;
+    if (tb <= 7) return rpass_t<R, RB, 128, 2>(h, blob_dev, blob, pass);
+    if (tb == 8) return rpass_t<R, RB, 256, 2>(h, blob_dev, blob, pass);
+    return rpass_t<R, RB, 512, 1>(h, blob_dev, blob, pass);
 }
 
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
     if (pdh->rmode) {
-        if (h->dtype == SV_C64) return rpass_t<float, 5>(h, blob_dev, blob, pass);
-        return rpass_t<double, 4>(h, blob_dev, blob, pass);
+        if (h->dtype == SV_C64) return rpass_any<float, 5>(h, blob_dev, blob, pass, pdh->m);
+        return rpass_any<double, 4>(h, blob_dev, blob, pass, pdh->m);
     }
     if (h->dtype == SV_C64) {
         if (pdh->tc_k) return pass_t<float, true>(h, blob_dev, blob, pass, hp);

@@ -907,11 +907,16 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
             for (const GateRec& g : o.recs) {
                 GateRec t = g;
                 if (g.kind == GR_DT) {
+                    // the table over all 2^r register values; b = mask of the
+                    // entries that are not exactly 1 (the others are skipped)
                     t.off = (int)data.size();
+                    t.b = 0;
                     for (int v = 0; v < (1 << r); ++v) {
                         int idx = 0;
                         for (int j = 0; j < O.k; ++j) idx |= ((v >> O.lq[j]) & 1) << j;
-                        data.push_back(o.gdata[(size_t)g.off + idx]);
+                        const cd e = o.gdata[(size_t)g.off + idx];
+                        data.push_back(e);
+                        if (e != cd(1.0, 0.0)) t.b |= 1 << v;
                     }
                 } else {
                     t.a = O.lq[g.a];
