@@ -96,8 +96,10 @@ typedef enum {
  * 0 = the library's default (CUDA cores; the cost-model planner may choose).
  * pass_kernel: 0 = default (passes run register-resident where they can:
  * every thread keeps 2^5 (c64) / 2^4 (c128) amplitudes of the tile in
- * registers), 1 = always the shared-memory pass kernel.  Results agree within
- * rounding either way.  reserved: must be zero. */
+ * registers; tiles move by 16-byte cp.async copies), 1 = always the
+ * shared-memory pass kernel, 2 = register-resident passes whose tiles move by
+ * TMA tensor copies through a ring of tile slots (one CTA per SM).  Results
+ * agree within rounding whichever kernel runs.  reserved: zero. */
 typedef struct {
     int k_max;
     int tile_m;

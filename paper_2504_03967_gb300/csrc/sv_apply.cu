@@ -9,6 +9,7 @@
 //    diagonal-phase runs to each 2^m-amplitude tile held in shared memory.
 //    Tiles are gathered with 16-byte cp.async copies of contiguous rows of
 //    2^L amplitudes (128 bytes), so every HBM access is a full line.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1077,6 +1078,81 @@ __device__ __forceinline__ void reg_diag(V* v, const uint64_t* __restrict__ dw, 
     }
 }
 
+// One tile of a register pass: fold the diagonal runs for tile t, then run the
+// pass's ops on the registers (remaps exchange through the tile buffer).  On
+// return the amplitudes are in registers in the last layout (Lg).
+template <typename V, typename R, int RB>
+__device__ __forceinline__ void rpass_tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,
+                                           uint64_t* fold, const int* dofs, uint64_t t, RegLayout<V, RB>& Lg) {
+    using T = Turns<R>;
+    const int m = P.m, tb = m - RB, no = P.nother, nd = P.ndiag;
+    const OpDev* ops = (const OpDev*)stage;
+    const int* rpos = nullptr;
+    const int* tpos = nullptr;
+    // per-tile fold of every diagonal run: a'_j = a_j + sum_o b_jo x_o (one
+    // thread per run and tile position) and C = c + sum_o x_o (a_o +
+    // sum_{o2<o} b_oo2 x_o2) (one warp per run, one non-tile bit per lane),
+    // with x_o = bit o of t
+    {
+        const RDiagLayout Lr(m, no);
+        for (int idx = threadIdx.x; idx < nd * m; idx += blockDim.x) {
+            const int d = idx / m, j = idx - d * m;
+            const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
+            uint64_t a = dw[Lr.at + j];
+            for (int o = 0; o < no; ++o)
+                if ((t >> o) & 1) a += dw[Lr.bo + j * no + o];
+            fold[d * (m + 1) + j] = T::coef(a);
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int d = warp; d < nd; d += nwarps) {
+            const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
+            uint64_t a = 0;
+            if (lane < no && ((t >> lane) & 1)) {
+                a = dw[Lr.ao + lane];
+                for (int o2 = 0; o2 < lane; ++o2)
+                    if ((t >> o2) & 1) a += dw[Lr.boo + lane * no + o2];
+            }
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) a += __shfl_xor_sync(0xffffffffu, a, sh);
+            if (lane == 0) fold[d * (m + 1) + m] = T::coef(a + dw[Lr.c]);
+        }
+    }
+    bool in_regs = false;
+    for (int oi = 0; oi < P.nops; ++oi) {
+        const OpDev& op = ops[oi];
+        switch (op.kind) {
+        case OP_REMAP:
+            if (in_regs) {
+                __syncthreads();
+                reg_write<V, RB>(v, tile, Lg);
+            }
+            __syncthreads();
+            rpos = op.lq;
+            tpos = (const int*)(stage + op.mat_off);
+            reg_layout<V, RB>(Lg, rpos, tpos, tb);
+            reg_read<V, RB>(v, tile, Lg);
+            in_regs = true;
+            break;
+        case OP_GATES:
+            reg_gates<V, RB>(v, (const GateRec*)(stage + op.rec_off), op.nrec, (const V*)(stage + op.mat_off));
+            break;
+        case OP_DENSE: {
+            const V* U = (const V*)(stage + op.mat_off);
+            switch (op.k) {
+            case 1: reg_dense<V, RB, 1>(v, U); break;
+            case 2: reg_dense<V, RB, 2>(v, U); break;
+            default: reg_dense<V, RB, 3>(v, U); break;
+            }
+            break;
+        }
+        default:
+            reg_diag<V, R, RB>(v, (const uint64_t*)(stage + op.diag_off), fold + (size_t)op.ord * (m + 1), m, no,
+                               rpos, tpos, tb);
+            break;
+        }
+    }
+}
+
 // MAXT/MINB: launch bounds of the instance (up to 128 threads: registers are
 // not capped below 255, so the 2^RB amplitudes and the op state never spill;
 // 256 and 512 threads: 128 registers).
@@ -1085,7 +1161,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
                                                   const PassDev* __restrict__ pdp,
                                                   const unsigned char* __restrict__ blob, const PassLayout lay) {
     using V = typename CT<R>::V;
-    using T = Turns<R>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
     {
@@ -1094,7 +1169,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
         for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const int m = P.m, L = P.L, tb = m - RB, no = P.nother, nd = P.ndiag;
+    const int m = P.m, L = P.L, no = P.nother, nd = P.ndiag;
     V* tiles[2] = {(V*)smem, (V*)(smem + (lay.nbuf == 2 ? lay.tile_bytes : 0))};
     uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
     unsigned char* stage = smem + lay.stage_off;
@@ -1129,8 +1204,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
     }
     V v[1 << RB];
     RegLayout<V, RB> Lg;
-    const int* rpos = nullptr;
-    const int* tpos = nullptr;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint64_t base = tile_base(t);
         const uint64_t tn = t + gridDim.x;
@@ -1149,74 +1222,141 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
         }
         __syncthreads();
         V* tile = tiles[cur];
-        // per-tile fold of every diagonal run: a'_j = a_j + sum_o b_jo x_o (one
-        // thread per run and tile position) and C = c + sum_o x_o (a_o +
-        // sum_{o2<o} b_oo2 x_o2) (one warp per run, one non-tile bit per lane),
-        // with x_o = bit o of t
-        {
-            const RDiagLayout Lr(m, no);
-            for (int idx = threadIdx.x; idx < nd * m; idx += blockDim.x) {
-                const int d = idx / m, j = idx - d * m;
-                const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
-                uint64_t a = dw[Lr.at + j];
-                for (int o = 0; o < no; ++o)
-                    if ((t >> o) & 1) a += dw[Lr.bo + j * no + o];
-                fold[d * (m + 1) + j] = T::coef(a);
-            }
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-            for (int d = warp; d < nd; d += nwarps) {
-                const uint64_t* dw = (const uint64_t*)(stage + dofs[d]);
-                uint64_t a = 0;
-                if (lane < no && ((t >> lane) & 1)) {
-                    a = dw[Lr.ao + lane];
-                    for (int o2 = 0; o2 < lane; ++o2)
-                        if ((t >> o2) & 1) a += dw[Lr.boo + lane * no + o2];
-                }
-#pragma unroll
-                for (int sh = 16; sh > 0; sh >>= 1) a += __shfl_xor_sync(0xffffffffu, a, sh);
-                if (lane == 0) fold[d * (m + 1) + m] = T::coef(a + dw[Lr.c]);
-            }
-        }
-        bool in_regs = false;
-        for (int oi = 0; oi < P.nops; ++oi) {
-            const OpDev& op = ops[oi];
-            switch (op.kind) {
-            case OP_REMAP:
-                if (in_regs) {
-                    __syncthreads();
-                    reg_write<V, RB>(v, tile, Lg);
-                }
-                __syncthreads();
-                rpos = op.lq;
-                tpos = (const int*)(stage + op.mat_off);
-                reg_layout<V, RB>(Lg, rpos, tpos, tb);
-                reg_read<V, RB>(v, tile, Lg);
-                in_regs = true;
-                break;
-            case OP_GATES:
-                reg_gates<V, RB>(v, (const GateRec*)(stage + op.rec_off), op.nrec, (const V*)(stage + op.mat_off));
-                break;
-            case OP_DENSE: {
-                const V* U = (const V*)(stage + op.mat_off);
-                switch (op.k) {
-                case 1: reg_dense<V, RB, 1>(v, U); break;
-                case 2: reg_dense<V, RB, 2>(v, U); break;
-                default: reg_dense<V, RB, 3>(v, U); break;
-                }
-                break;
-            }
-            default:
-                reg_diag<V, R, RB>(v, (const uint64_t*)(stage + op.diag_off), fold + (size_t)op.ord * (m + 1), m, no,
-                                   rpos, tpos, tb);
-                break;
-            }
-        }
+        rpass_tile<V, R, RB>(v, tile, P, stage, fold, dofs, t, Lg);
         __syncthreads();
         reg_write<V, RB>(v, tile, Lg);
         __syncthreads();
         store_tile(tile, psi, base, rowoff, m, L);
         __syncthreads();
         if (lay.nbuf == 2) cur ^= 1;
+    }
+}
+
+// Register pass fed by TMA.  The CTA keeps a ring of S tile slots: warp 0
+// issues the tensor copies of a tile's rows into a free slot (completion
+// counted in bytes on the slot's mbarrier) S-1 tiles ahead, every thread
+// works on the oldest loaded slot in registers, and warp 0 writes the slot
+// back with tensor stores, whose shared-memory reads are awaited before the
+// slot is loaded again.  The copies use the 128-byte swizzle, which places
+// each 16-byte chunk exactly where swz() puts it.  All waits are bounded; on
+// expiry the kernel records an error, lets its copies in flight land and
+// returns.
+constexpr int kMaxSlots = 4;
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
+
+struct RingLayout {
+    int slots;
+    int tile_bytes;
+    int box_rows;   // rows per tensor copy
+    int rowoff_off;
+    int stage_off;
+    int stage_bytes;
+    int work_off;
+    int total;
+};
+
+template <typename R, int RB, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __restrict__ pdp,
+                                                       const unsigned char* __restrict__ blob,
+                                                       const __grid_constant__ CUtensorMap tmap, const RingLayout lay,
+                                                       int* __restrict__ err) {
+    using V = typename CT<R>::V;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // slots start on a 1024-byte boundary (the period of the 128-byte swizzle);
+    // the layout reserves the kilobyte this may skip
+    unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ PassDev P;
+    __shared__ __align__(8) uint64_t full[kMaxSlots];
+    {
+        const int* src = (const int*)pdp;
+        int* dst = (int*)&P;
+        for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int m = P.m, L = P.L, no = P.nother, nd = P.ndiag, S = lay.slots;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
+    unsigned char* stage = smem + lay.stage_off;
+    uint64_t* fold = (uint64_t*)(smem + lay.work_off);  // nd x (m + 1)
+    int* dofs = (int*)(fold + (size_t)nd * (m + 1));
+    const unsigned char* greg = blob + P.region_off;
+    for (int e = tid; e < lay.stage_bytes / 16; e += blockDim.x) cp_async16(stage + 16 * e, greg + 16 * e);
+    cp_async_commit();
+    const int nrows = 1 << (m - L);
+    for (int r = tid; r < nrows; r += blockDim.x) {
+        uint32_t o = 0;
+        for (int b = 0; b < m - L; ++b)
+            if ((r >> b) & 1) o |= 1u << (P.tq[L + b] - L);
+        rowoff[r] = o;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) tc::mbar_init(&full[s], 1);
+        tc::fence_mbar_init();
+    }
+    cp_async_wait_group<0>();
+    __syncthreads();
+    const OpDev* ops = (const OpDev*)stage;
+    if (tid == 0)
+        for (int i = 0; i < P.nops; ++i)
+            if (ops[i].kind == OP_DIAG) dofs[ops[i].ord] = ops[i].diag_off;
+    const uint64_t ntiles = 1ull << (n - m);
+    const int nloc = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // this CTA's tiles
+    const int BR = lay.box_rows, ngroups = nrows / BR;
+    auto tile_of = [&](int j) { return (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x; };
+    auto row0_of = [&](uint64_t t) {
+        uint64_t b = 0;
+        for (int i = 0; i < no; ++i) b |= ((t >> i) & 1ull) << P.oq[i];
+        return (int)(b >> L);
+    };
+    auto issue_load = [&](int j) {  // warp 0: tile j of this CTA into slot j % S
+        const int s = j % S;
+        if (lane == 0) tma::mbar_arrive_expect_tx(&full[s], (uint32_t)lay.tile_bytes);
+        __syncwarp();
+        const int row0 = row0_of(tile_of(j));
+        unsigned char* dst = smem + (size_t)s * lay.tile_bytes;
+        for (int g = lane; g < ngroups; g += 32)
+            tma::load_2d(dst + (size_t)g * BR * 128, &tmap, 0, row0 + (int)rowoff[g * BR], &full[s]);
+    };
+    if (warp == 0)
+        for (int j = 0; j < S - 1 && j < nloc; ++j) issue_load(j);
+    __syncthreads();  // the expect_tx arrivals precede any wait
+    V v[1 << RB];
+    RegLayout<V, RB> Lg;
+    int done = 0;  // tiles whose slots were consumed
+    bool aborted = false;
+    for (int j = 0; j < nloc; ++j) {
+        const int s = j % S;
+        if (warp == 0 && j + S - 1 < nloc) {
+            if (j >= 1) tma::store_wait_read();  // the store of tile j-1 has left slot (j+S-1) % S
+            __syncwarp();
+            issue_load(j + S - 1);
+        }
+        const bool ok = tc::mbar_wait_bounded(&full[s], (uint32_t)((j / S) & 1), kTmaWaitLimit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            aborted = true;
+            break;
+        }
+        const uint64_t t = tile_of(j);
+        V* tile = (V*)(smem + (size_t)s * lay.tile_bytes);
+        rpass_tile<V, R, RB>(v, tile, P, stage, fold, dofs, t, Lg);
+        __syncthreads();
+        reg_write<V, RB>(v, tile, Lg);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (warp == 0) {
+            const int row0 = row0_of(t);
+            for (int g = lane; g < ngroups; g += 32)
+                tma::store_2d(&tmap, 0, row0 + (int)rowoff[g * BR], (const unsigned char*)tile + (size_t)g * BR * 128);
+            tma::store_commit();
+        }
+        done = j + 1;
+    }
+    if (warp == 0) {
+        tma::store_wait_all();
+        if (aborted)  // let the loads already issued land before the CTA's shared memory goes away
+            for (int j = done; j < nloc && j < done + S - 1; ++j)
+                tc::mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), kTmaWaitLimit);
     }
 }
 
@@ -1589,9 +1729,129 @@ static cudaError_t rpass_any(sv_state* h, const void* blob_dev, const PlanBlob& 
     return rpass_t<R, RB, 512, 1>(h, blob_dev, blob, pass);
 }
 
+// ---- TMA-fed register passes: tensor map and ring layout -----------------
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Rows of 128 bytes (2^L amplitudes) per tensor copy: the run of tile qubits
+// L, L+1, ... makes consecutive tile rows consecutive in global memory.
+int box_rows(const PassDev& P) {
+    int run = 0;
+    while (P.L + run < P.m && P.tq[P.L + run] == P.L + run) ++run;
+    return 1 << std::min(run, 8);
+}
+}  // namespace
+
+// The ring: as many slots (2..4) as keep the most warps per SM busy.
+static bool ring_layout(int dtype, const PassDev& P, RingLayout* out, int* ctas_per_sm) {
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    const int m = P.m, nrows = 1 << (m - P.L), threads = 1 << (m - reg_bits(dtype));
+    RingLayout lay;
+    memset(&lay, 0, sizeof(lay));
+    lay.tile_bytes = (int)(csz << m);
+    if (lay.tile_bytes % 1024) return false;  // slots must stay 1024-byte aligned for the swizzle
+    lay.box_rows = std::min(box_rows(P), nrows);
+    lay.stage_bytes = P.region_bytes;
+    const size_t work = sizeof(uint64_t) * (size_t)P.ndiag * (m + 1) + sizeof(int) * (size_t)P.ndiag;
+    const int rest = round128(4 * (size_t)nrows) + round128(lay.stage_bytes) + round128(work) + 1024;
+    int best_score = -1;
+    for (int S = kMaxSlots; S >= 2; --S) {
+        const int total = S * lay.tile_bytes + rest;
+        if (total > kMaxDynSmem) continue;
+        const int ctas = std::max(1, std::min(8, (228 * 1024) / (total + 1024)));
+        const int warps = std::min(16, ctas * threads / 32);
+        const int score = warps * 8 + S;
+        if (score > best_score) {
+            best_score = score;
+            lay.slots = S;
+            *ctas_per_sm = ctas;
+        }
+    }
+    if (best_score < 0) return false;
+    lay.rowoff_off = lay.slots * lay.tile_bytes;
+    lay.stage_off = lay.rowoff_off + round128(4 * (size_t)nrows);
+    lay.work_off = lay.stage_off + round128(lay.stage_bytes);
+    lay.total = lay.work_off + round128(work) + 1024;  // + alignment of the slots
+    *out = lay;
+    return true;
+}
+
+template <typename R, int RB, int MAXT>
+static cudaError_t rpass_tma_t(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, bool* used) {
+    *used = false;
+    const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    RingLayout lay;
+    int ctas = 1;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || !ring_layout(h->dtype, *pdh, &lay, &ctas)) return cudaSuccess;
+    const int threads = 1 << (pdh->m - RB);
+    if (threads > MAXT || ((uintptr_t)h->amps & 15)) return cudaSuccess;
+    const size_t csz = h->dtype == SV_C64 ? 8 : 16;
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {16, (cuuint64_t)((csz << h->n) / 128)};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {16, (cuuint32_t)lay.box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, h->amps, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return cudaSuccess;  // not expressible: the caller falls back to the copy-based kernel
+    static int attr_bytes = 0;
+    if (lay.total > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_rpass_tma<R, RB, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             lay.total);
+        if (e != cudaSuccess) return e;
+        attr_bytes = lay.total;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass_tma<R, RB, MAXT>, threads, lay.total);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t ntiles = 1ull << (h->n - pdh->m);
+    uint64_t grid = (uint64_t)num_sms() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const unsigned char* b = (const unsigned char*)blob_dev;
+    count_launch();
+    k_rpass_tma<R, RB, MAXT><<<(unsigned)grid, threads, lay.total, h->stream>>>(
+        h->n, (const PassDev*)(b + blob.pass_off) + pass, b, tmap, lay, (int*)h->err.ptr);
+    *used = true;
+    return cudaGetLastError();
+}
+
+template <typename R, int RB>
+static cudaError_t rpass_tma_any(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, int m, bool* used) {
+    const int tb = m - RB;
+    if (tb <= 7) return rpass_tma_t<R, RB, 128>(h, blob_dev, blob, pass, used);
+    if (tb == 8) return rpass_tma_t<R, RB, 256>(h, blob_dev, blob, pass, used);
+    return rpass_tma_t<R, RB, 512>(h, blob_dev, blob, pass, used);
+}
+
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
     if (pdh->rmode) {
+        bool used = false;
+        cudaError_t e = cudaSuccess;
+        if (pdh->rmode == 2) {  // the TMA-fed register kernel was asked for
+            e = h->dtype == SV_C64 ? rpass_tma_any<float, 5>(h, blob_dev, blob, pass, pdh->m, &used)
+                                   : rpass_tma_any<double, 4>(h, blob_dev, blob, pass, pdh->m, &used);
+            if (e != cudaSuccess || used) return e;
+        }
         if (h->dtype == SV_C64) return rpass_any<float, 5>(h, blob_dev, blob, pass, pdh->m);
         return rpass_any<double, 4>(h, blob_dev, blob, pass, pdh->m);
     }

@@ -123,6 +123,7 @@ struct Plan {
     int64_t gates = 0;
     int tensor = -1;  // 0: dense blocks of k >= kMinTcK go to the tensor cores
     bool no_register_passes = false;
+    bool use_tma = false;  // register passes move tiles with TMA tensor copies
 };
 
 struct PlanOptions {
@@ -130,7 +131,7 @@ struct PlanOptions {
     int tile_m = 13;
     int planner = SV_PLAN_GREEDY;
     int tensor = -1;  // 0: tensor cores for c64 blocks of k >= 3; -1: CUDA cores only
-    int pass_kernel = 0;  // 1: shared-memory pass kernel only
+    int pass_kernel = 0;  // 1: shared-memory pass kernel only; 2: register passes fed by TMA
 };
 
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
@@ -190,7 +191,8 @@ struct PassDev {
     int n;               // qubits of the state the pass runs on
     int m;
     int L;
-    int rmode;           // 1: register-resident pass (region in the register format)
+    int rmode;           // register-resident pass (region in the register format): 1 fed by
+                         // cp.async copies, 2 by TMA tensor copies; 0: shared-memory kernel
     int ndiag;           // register passes: diagonal runs (each folded once per tile)
     int nops;            // ops in the pass's region
     int region_off;      // byte offset of the region in the blob

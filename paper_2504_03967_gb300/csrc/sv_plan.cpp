@@ -300,7 +300,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         if (opt->tile_m > 0) po.tile_m = opt->tile_m;
         po.planner = opt->planner;
         po.tensor = opt->tensor > 0 ? 0 : -1;
-        po.pass_kernel = opt->pass_kernel == 1 ? 1 : 0;
+        po.pass_kernel = opt->pass_kernel == 1 || opt->pass_kernel == 2 ? opt->pass_kernel : 0;
     }
     if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
@@ -318,6 +318,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     out->gates = (int64_t)gates.size();
     out->tensor = po.tensor;
     out->no_register_passes = po.pass_kernel == 1;
+    out->use_tma = po.pass_kernel == 2;
     const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
     // the tile holds the row bits plus room for any two-qubit gate
     const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
@@ -937,7 +938,7 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
     }
     if (rpos.empty()) remap(0, {});
     assemble(ops, pay, P, out);
-    P->rmode = 1;
+    P->rmode = p.use_tma ? 2 : 1;
     P->ndiag = nd;
     return P->region_bytes <= kStageCap;
 }

@@ -138,3 +138,36 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parit
 
 }  // namespace tc
 }  // namespace sv
+
+// ---- TMA (tensor copies between global and shared memory) -------------------
+// The tensor map lives in kernel parameter space (__grid_constant__); its
+// generic address is what the copy instructions take.
+namespace sv {
+namespace tma {
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+// 2-D tile load global -> shared, completion counted in bytes on mbar.
+__device__ __forceinline__ void load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(tc::smem_u32(smem_dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(tc::smem_u32(mbar))
+        : "memory");
+}
+// 2-D tile store shared -> global, tracked by this thread's bulk async-group.
+__device__ __forceinline__ void store_2d(const void* tmap, int x, int y, const void* smem_src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(tmap),
+                 "r"(x), "r"(y), "r"(tc::smem_u32(smem_src))
+                 : "memory");
+}
+__device__ __forceinline__ void store_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// wait until this thread's committed stores no longer read shared memory
+__device__ __forceinline__ void store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// wait until they are complete
+__device__ __forceinline__ void store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+}  // namespace tma
+}  // namespace sv

@@ -86,7 +86,8 @@ def test_gate_sequence_blocks(dtype, k, kind):
 def test_register_passes(dtype, tb, kind):
     """Register-resident passes (2^5 / 2^4 amplitudes per thread, remaps
     through shared memory, diagonal runs from the register layout) at every
-    thread count, against the oracle and against the shared-memory kernel."""
+    thread count, fed by TMA tensor copies and by cp.async copies, and the
+    shared-memory kernel, all against the oracle."""
     rb = 5 if dtype == S.C64 else 4
     m = rb + tb
     n = max(m + 3, 15)
@@ -98,10 +99,9 @@ def test_register_passes(dtype, tb, kind):
     for k in (3, 4):
         info = S.sv_plan_circuit(n, dtype, g, k_max=k, tile_m=m)
         assert info["reg_passes"] > 0 and (k > 3 or info["reg_passes"] == info["passes"])
-        got = U.run_gpu(n, g, dtype, psi0=psi0, k_max=k, tile_m=m)
-        U.assert_close(got, ref, dtype, "%s register k=%d m=%d" % (kind, k, m))
-        smem = U.run_gpu(n, g, dtype, psi0=psi0, k_max=k, tile_m=m, pass_kernel=1)
-        U.assert_close(smem, ref, dtype, "%s shared-memory k=%d m=%d" % (kind, k, m))
+        for pk, what in ((0, "register"), (2, "register+TMA"), (1, "shared-memory")):
+            got = U.run_gpu(n, g, dtype, psi0=psi0, k_max=k, tile_m=m, pass_kernel=pk)
+            U.assert_close(got, ref, dtype, "%s %s k=%d m=%d" % (kind, what, k, m))
 
 
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
