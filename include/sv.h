@@ -99,7 +99,9 @@ typedef enum {
  * registers; tiles move by 16-byte cp.async copies), 1 = always the
  * shared-memory pass kernel, 2 = register-resident passes whose tiles move by
  * TMA tensor copies through a ring of tile slots (one CTA per SM).  Results
- * agree within rounding whichever kernel runs.  reserved: zero. */
+ * agree within rounding whichever kernel runs.  relabel: 1 = SWAP gates
+ * become a relabelling of the state's qubits instead of data movement (see
+ * sv_qubit_map); 0 = SWAPs move amplitudes.  reserved: zero. */
 typedef struct {
     int k_max;
     int tile_m;
@@ -107,7 +109,8 @@ typedef struct {
     int record;
     int tensor;
     int pass_kernel;
-    int reserved[2];
+    int relabel;
+    int reserved[1];
 } sv_options;
 
 /* Plan summary returned by sv_plan_circuit (host only, no device work). */
@@ -148,6 +151,26 @@ int sv_set_stream(sv_handle h, void *cuda_stream);
 
 /* Number of qubits / dtype / device pointer of the state (for interop). */
 int sv_info(sv_handle h, int *n, int *dtype, void **dev_amps);
+
+/* Qubit relabelling.  After an apply with opt->relabel = 1 the amplitude of
+ * logical basis state x may sit at a permuted index in device memory: logical
+ * qubit q is stored at bit map[q].  Every read-out (probabilities, norm, <Z>,
+ * shots, sv_store_state) and every later sv_apply_circuit honours the map, so
+ * results are those of the logical circuit; only code that reads the device
+ * buffer directly (sv_info, sv_attach memory, sv_sample_uniforms_noalloc)
+ * sees the physical order.  sv_init_basis and sv_load_state reset the map to
+ * the identity.  Shots under a non-identity map follow the sampling rule
+ * over the stored order and are reported in logical labels: the distribution
+ * is exactly |a_x|^2, but the outcome drawn for a given uniform is the one of
+ * the stored order (sv_materialize first to reproduce identity-map draws).
+ * sv_qubit_map writes map[0..n-1]; sv_materialize moves the amplitudes into
+ * logical order (fused SWAP passes) and resets the map. */
+int sv_qubit_map(sv_handle h, int *map);
+int sv_materialize(sv_handle h);
+
+/* Options the last sv_apply_circuit on h planned with (for SV_PLAN_MLP, the
+ * candidate the cost model and its judge picked for that call). */
+int sv_last_plan(sv_handle h, sv_options *out);
 
 /* |x>: all amplitudes 0 except a_x = 1.  SV_EINVAL if x >= 2^n. */
 int sv_init_basis(sv_handle h, uint64_t x);
@@ -263,16 +286,17 @@ int sv_feature_count(void);
  * fastest: fusion width k_max 2..5 (App. D.2's "gate fusion = 5" as the
  * bound) x tile width (11..14 qubits for complex64, 10..13 for complex128,
  * at most n) x, for complex64, tensor cores on or off (blocks of 3..5
- * qubits).  Each candidate runs twice on h's stream and keeps its faster
+ * qubits) x pass kernel (register-resident where it can run, or the
+ * shared-memory kernel).  Each candidate runs twice on h's stream and keeps its faster
  * CUDA-event time.  h's amplitudes serve as scratch: their content is
  * undefined afterwards.  cache_path (may be NULL) names a JSON-lines file of
  * earlier results, one object per line {"key", "k_max", "tile_m", "tensor",
- * "ms"}; the key holds n, dtype, the gate count, a 64-bit FNV-1a hash of the
+ * "pass_kernel", "ms"}; the key holds n, dtype, the gate count, a 64-bit FNV-1a hash of the
  * records and the device name and SM count.  When the file has a line for
  * this key its result is returned without any device work; otherwise the
  * new result is appended (the file is created if missing; a write failure
  * is ignored).  *best receives planner = SV_PLAN_GREEDY and the winning
- * k_max, tile_m and tensor (1 or -1), ready for sv_apply_circuit; *best_ms
+ * k_max, tile_m, tensor (1 or -1) and pass_kernel, ready for sv_apply_circuit; *best_ms
  * (may be NULL) its time in milliseconds.  Synchronous. */
 int sv_autotune(sv_handle h, const sv_gate *gates, size_t count, const char *cache_path, sv_options *best,
                 double *best_ms);

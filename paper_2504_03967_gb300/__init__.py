@@ -39,7 +39,7 @@ class SVError(RuntimeError):
 class sv_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
                 ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("relabel", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class sv_plan_info(ctypes.Structure):
@@ -66,6 +66,9 @@ def lib():
             "sv_free": [vp],
             "sv_set_stream": [vp, vp],
             "sv_info": [vp, P(i), P(i), P(vp)],
+            "sv_qubit_map": [vp, vp],
+            "sv_materialize": [vp],
+            "sv_last_plan": [vp, vp],
             "sv_init_basis": [vp, u64],
             "sv_load_state": [vp, vp],
             "sv_store_state": [vp, vp],
@@ -118,10 +121,10 @@ def _check(rc):
     return rc
 
 
-def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0):
+def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0):
     o = sv_options()
     o.k_max, o.tile_m, o.planner, o.record, o.tensor = k_max, tile_m, planner, record, tensor
-    o.pass_kernel = pass_kernel
+    o.pass_kernel, o.relabel = pass_kernel, relabel
     return o
 
 
@@ -193,9 +196,9 @@ def sv_store_state(h):
     return a
 
 
-def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0):
+def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel)
+    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel)
     _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
 
 
@@ -205,6 +208,25 @@ def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, ten
     info = sv_plan_info()
     _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}
+
+
+def sv_qubit_map(h):
+    """Physical bit of each logical qubit (identity unless relabelled)."""
+    n, _, _ = sv_info(h)
+    m = (ctypes.c_int * max(1, n))()
+    _check(lib().sv_qubit_map(h, m))
+    return [m[i] for i in range(n)]
+
+
+def sv_materialize(h):
+    _check(lib().sv_materialize(h))
+
+
+def sv_last_plan(h):
+    o = sv_options()
+    _check(lib().sv_last_plan(h, ctypes.byref(o)))
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "planner": o.planner, "tensor": o.tensor,
+            "pass_kernel": o.pass_kernel, "relabel": o.relabel}
 
 
 def sv_probs(h):
@@ -282,7 +304,7 @@ def sv_autotune(h, gates, cache_path=None):
     ms = ctypes.c_double()
     path = cache_path.encode() if cache_path else None
     _check(f(h, _ptr(g), len(g), path, ctypes.byref(o), ctypes.byref(ms)))
-    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor, "pass_kernel": o.pass_kernel}, ms.value
 
 
 def sv_sample_uniforms_noalloc(dev_amps, n, dtype, dev_u, shots, dev_out, stream=None):
@@ -368,7 +390,7 @@ def sv_cost_model_choose(n, dtype, gates):
     o = sv_options()
     ms = ctypes.c_double()
     _check(_cm_lib().sv_cost_model_choose(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(ms)))
-    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor, "pass_kernel": o.pass_kernel}, ms.value
 
 
 def sv_cost_model_judged(n, dtype, gates):
@@ -381,7 +403,7 @@ def sv_cost_model_judged(n, dtype, gates):
     o = sv_options()
     ms = ctypes.c_double()
     _check(f(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(ms)))
-    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor}, ms.value
+    return {"k_max": o.k_max, "tile_m": o.tile_m, "tensor": o.tensor, "pass_kernel": o.pass_kernel}, ms.value
 
 
 def sv_cost_model_stats():

@@ -26,6 +26,18 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+void reset_perm(sv_state* h) {
+    for (int q = 0; q < 64; ++q) h->perm[q] = q;
+    h->permuted = false;
+}
+
+QubitMap qubit_map(const sv_state* h) {
+    QubitMap m;
+    m.n = h->n;
+    for (int q = 0; q < 40; ++q) m.phys[q] = q < h->n ? h->perm[q] : q;
+    return m;
+}
+
 int ensure_scratch(Scratch* s, size_t bytes, cudaStream_t st) {
     if (s->cap >= bytes) return SV_OK;
     if (s->ptr) {
@@ -89,6 +101,8 @@ int make_handle(int n, sv_dtype dt, void* amps, bool owned, void* stream, sv_han
     h->ev_used = 0;
     h->upload_ev = nullptr;
     h->upload_pending = false;
+    reset_perm(h);
+    memset(&h->last_opts, 0, sizeof(h->last_opts));
     *out = h;
     return SV_OK;
 }
@@ -176,6 +190,7 @@ int sv_free(sv_handle h) {
     if (h->red.ptr) cudaFree(h->red.ptr);
     if (h->out_dev.ptr) cudaFree(h->out_dev.ptr);
     if (h->err.ptr) cudaFree(h->err.ptr);
+    if (h->perm_tmp.ptr) cudaFree(h->perm_tmp.ptr);
     if (h->host_pin.ptr) cudaFreeHost(h->host_pin.ptr);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->upload_ev) cudaEventDestroy(h->upload_ev);
@@ -208,6 +223,7 @@ int sv_init_basis(sv_handle h, uint64_t x) {
         return cuda_fail(e, "init_basis");
     }
     h->bad = false;
+    reset_perm(h);
     return SV_OK;
 }
 
@@ -222,6 +238,7 @@ int sv_load_state(sv_handle h, const void* host_amps) {
         return cuda_fail(e, "load_state");
     }
     h->bad = false;
+    reset_perm(h);
     return SV_OK;
 }
 
@@ -229,7 +246,19 @@ int sv_store_state(sv_handle h, void* host_amps) {
     int rc = check_handle(h);
     if (rc) return rc;
     if (!host_amps) return set_error(SV_EINVAL, "NULL host buffer");
-    return sync_d2h(h, host_amps, h->amps, amp_bytes(h->dtype) << h->n, "store_state");
+    if (!h->permuted) return sync_d2h(h, host_amps, h->amps, amp_bytes(h->dtype) << h->n, "store_state");
+    // relabelled qubits: gather logical order chunk by chunk through device staging
+    const uint64_t N = 1ull << h->n, chunk = std::min<uint64_t>(N, 1ull << 22);
+    rc = ensure_scratch(&h->out_dev, amp_bytes(h->dtype) * chunk, h->stream);
+    if (rc) return rc;
+    for (uint64_t x0 = 0; x0 < N; x0 += chunk) {
+        cudaError_t e = launch_gather_logical(h, x0, chunk, h->out_dev.ptr);
+        if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "store_state gather"));
+        rc = sync_d2h(h, (char*)host_amps + amp_bytes(h->dtype) * x0, h->out_dev.ptr, amp_bytes(h->dtype) * chunk,
+                      "store_state");
+        if (rc) return rc;
+    }
+    return SV_OK;
 }
 
 int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, const sv_options* opt,
@@ -282,9 +311,37 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     int rc = SV_OK;
     if (cg.empty()) return SV_OK;
     PlanOptions po = resolve_options(h->n, h->dtype, opt);
+    memset(&h->last_opts, 0, sizeof(h->last_opts));
+    // Relabelling: gates act on the physical bits of their logical qubits; with
+    // relabel on, a SWAP only exchanges two entries of the map.
+    uint64_t salt = 0;
+    std::vector<CGate> mapped;
+    const std::vector<CGate>* gl = &cg;
+    if (po.relabel || h->permuted) {
+        if (h->permuted) {
+            salt = 1469598103934665603ull;
+            for (int q = 0; q < h->n; ++q) salt = (salt ^ (uint64_t)h->perm[q]) * 1099511628211ull;
+        }
+        if (po.relabel) salt ^= 0x9e3779b97f4a7c15ull;
+        mapped.reserve(cg.size());
+        for (const CGate& g : cg) {
+            if (po.relabel && g.type == SV_SWAP) {
+                std::swap(h->perm[g.q[0]], h->perm[g.q[1]]);
+                continue;
+            }
+            CGate x = g;
+            for (int i = 0; i < g.nq; ++i) x.q[i] = h->perm[g.q[i]];
+            mapped.push_back(x);
+        }
+        h->permuted = false;
+        for (int q = 0; q < h->n; ++q) h->permuted |= h->perm[q] != q;
+        gl = &mapped;
+        if (mapped.empty()) return SV_OK;
+    }
+    const std::vector<CGate>& cgm = *gl;
     Plan plan;
     if (po.planner == SV_PLAN_PLAIN) {
-        plan_plain(h->n, h->dtype, cg, &plan);
+        plan_plain(h->n, h->dtype, cgm, &plan);
         for (const PlainOp& op : plan.plain_ops) {
             cudaError_t e = launch_plain_op(h, op);
             if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "plain gate kernel"));
@@ -292,8 +349,14 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
         return SV_OK;
     }
     cudaEvent_t judge0 = nullptr, judge1 = nullptr;
-    if (po.planner == SV_PLAN_MLP) po = mlp_plan_options(h, gates, count, cg, po, &judge0, &judge1);
-    plan_greedy(h->n, h->dtype, cg, po, &plan);
+    if (po.planner == SV_PLAN_MLP) po = mlp_plan_options(h, gates, count, cgm, po, salt, &judge0, &judge1);
+    plan_greedy(h->n, h->dtype, cgm, po, &plan);
+    h->last_opts.k_max = po.k_max;
+    h->last_opts.tile_m = po.tile_m;
+    h->last_opts.planner = opt ? opt->planner : SV_PLAN_GREEDY;
+    h->last_opts.tensor = po.tensor == 0 ? 1 : -1;
+    h->last_opts.pass_kernel = po.pass_kernel;
+    h->last_opts.relabel = po.relabel;
     PlanBlob blob;
     serialise_plan(plan, &blob);
     // Stage through pinned memory; only the previous upload from it has to
@@ -333,7 +396,8 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
         if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "tile pass kernel"));
         if (rec && e1) {
             cudaEventRecord(e1, h->stream);
-            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p], plan.tensor == 0));
+            const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
+            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p], plan.tensor == 0, pd->rmode != 0));
         }
     }
     if (judge1) cudaEventRecord(judge1, h->stream);
@@ -446,6 +510,52 @@ int sv_sample_uniforms(sv_handle h, const double* host_u, uint64_t shots, uint64
     rc = measure_sample(h, shots, 0, du, dout);
     if (rc) return fail_state(h, rc);
     return sync_d2h(h, host_out, dout, sizeof(uint64_t) * shots, "sample readback");
+}
+
+
+int sv_qubit_map(sv_handle h, int* map) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (!map) return set_error(SV_EINVAL, "NULL output");
+    for (int q = 0; q < h->n; ++q) map[q] = h->perm[q];
+    return SV_OK;
+}
+
+int sv_materialize(sv_handle h) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->permuted) return SV_OK;
+    // physical SWAPs that bring every logical qubit to its own bit
+    int perm[64];
+    for (int q = 0; q < h->n; ++q) perm[q] = h->perm[q];
+    std::vector<sv_gate> sw;
+    for (int q = 0; q < h->n; ++q) {
+        if (perm[q] == q) continue;
+        int q2 = 0;
+        while (perm[q2] != q) ++q2;  // the logical qubit stored at bit q
+        sv_gate g;
+        memset(&g, 0, sizeof(g));
+        g.type = SV_SWAP;
+        g.nq = 2;
+        g.q[0] = (uint32_t)perm[q];
+        g.q[1] = (uint32_t)q;
+        sw.push_back(g);
+        perm[q2] = perm[q];
+        perm[q] = q;
+    }
+    std::vector<CGate> cg;
+    size_t bad = 0;
+    if (canonicalise(h->n, sw.data(), sw.size(), &cg, &bad) != SV_OK) return set_error(SV_EINVAL, "internal: swap list");
+    reset_perm(h);  // the swaps below act on physical bits
+    sv_options o;
+    memset(&o, 0, sizeof(o));
+    return apply_canonical(h, sw.data(), sw.size(), cg, &o);
+}
+
+int sv_last_plan(sv_handle h, sv_options* out) {
+    if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (!out) return set_error(SV_EINVAL, "NULL output");
+    *out = h->last_opts;
+    return SV_OK;
 }
 
 }  // extern "C"

@@ -61,6 +61,9 @@ bool cache_lookup(const char* path, const std::string& key, sv_options* o, doubl
         const char* pm = strstr(line, "\"tile_m\": ");
         const char* pt = strstr(line, "\"tensor\": ");
         const char* pv = strstr(line, "\"ms\": ");
+        const char* pp = strstr(line, "\"pass_kernel\": ");
+        int kern = 0;
+        if (pp && sscanf(pp + 15, "%d", &kern) != 1) kern = 0;
         if (pk && pm && pt && pv && sscanf(pk + 9, "%d", &k) == 1 && sscanf(pm + 10, "%d", &m) == 1 &&
             sscanf(pt + 10, "%d", &t) == 1 && sscanf(pv + 6, "%lf", &v) == 1 && k >= 1 && k <= kMaxK &&
             m >= 1 && m <= kMaxTileM && (t == 1 || t == -1)) {
@@ -68,6 +71,7 @@ bool cache_lookup(const char* path, const std::string& key, sv_options* o, doubl
             o->k_max = k;
             o->tile_m = m;
             o->tensor = t;
+            o->pass_kernel = kern == 1 ? 1 : 0;
             o->planner = SV_PLAN_GREEDY;
             *ms = v;
             found = true;  // the last matching line wins
@@ -81,8 +85,8 @@ void cache_append(const char* path, const std::string& key, const sv_options& o,
     std::lock_guard<std::mutex> lk(g_file_mu);
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"k_max\": %d, \"tile_m\": %d, \"tensor\": %d, \"ms\": %.6f}\n", key.c_str(),
-            o.k_max, o.tile_m, o.tensor, ms);
+    fprintf(f, "{\"key\": \"%s\", \"k_max\": %d, \"tile_m\": %d, \"tensor\": %d, \"pass_kernel\": %d, \"ms\": %.6f}\n",
+            key.c_str(), o.k_max, o.tile_m, o.tensor, o.pass_kernel, ms);
     fclose(f);
 }
 
@@ -111,18 +115,22 @@ extern "C" int sv_autotune(sv_handle h, const sv_gate* gates, size_t count, cons
     const int m0 = h->dtype == SV_C64 ? 11 : 10;
     for (int k = 2; k <= kMaxK; ++k)
         for (int m = m0; m < m0 + 4; ++m)
-            for (int t = -1; t <= 1; t += 2) {
-                if (t == 1 && (h->dtype != SV_C64 || k < kMinTcK)) continue;
-                sv_options o;
-                memset(&o, 0, sizeof(o));
-                o.k_max = k;
-                o.tile_m = std::min(m, h->n);
-                o.tensor = t;
-                o.planner = SV_PLAN_GREEDY;
-                bool dup = false;
-                for (const sv_options& c : cands) dup |= c.k_max == o.k_max && c.tile_m == o.tile_m && c.tensor == o.tensor;
-                if (!dup) cands.push_back(o);
-            }
+            for (int t = -1; t <= 1; t += 2)
+                for (int pk = 0; pk <= 1; ++pk) {
+                    if (t == 1 && (h->dtype != SV_C64 || k < kMinTcK)) continue;
+                    sv_options o;
+                    memset(&o, 0, sizeof(o));
+                    o.k_max = k;
+                    o.tile_m = std::min(m, h->n);
+                    o.tensor = t;
+                    o.pass_kernel = pk;
+                    o.planner = SV_PLAN_GREEDY;
+                    bool dup = false;
+                    for (const sv_options& c : cands)
+                        dup |= c.k_max == o.k_max && c.tile_m == o.tile_m && c.tensor == o.tensor &&
+                               c.pass_kernel == o.pass_kernel;
+                    if (!dup) cands.push_back(o);
+                }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);

@@ -61,17 +61,20 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanO
         for (int mi = 0; mi < 3; ++mi) {
             int m = dtype == SV_C64 ? ms_c64[mi] : ms_c128[mi];
             if (m > n) m = n;
-            for (int tensor = -1; tensor <= 0; ++tensor) {
-                if (tensor == 0 && (dtype != SV_C64 || k < kMinTcK)) continue;
-                PlanOptions po = base;
-                po.k_max = k;
-                po.tile_m = m;
-                po.tensor = tensor;
-                bool dup = false;
-                for (const PlanOptions& c : cands)
-                    dup |= c.k_max == po.k_max && c.tile_m == po.tile_m && c.tensor == po.tensor;
-                if (!dup) cands.push_back(po);
-            }
+            for (int tensor = -1; tensor <= 0; ++tensor)
+                for (int pk = 0; pk <= 1; ++pk) {
+                    if (tensor == 0 && (dtype != SV_C64 || k < kMinTcK)) continue;
+                    PlanOptions po = base;
+                    po.k_max = k;
+                    po.tile_m = m;
+                    po.tensor = tensor;
+                    po.pass_kernel = pk;
+                    bool dup = false;
+                    for (const PlanOptions& c : cands)
+                        dup |= c.k_max == po.k_max && c.tile_m == po.tile_m && c.tensor == po.tensor &&
+                               c.pass_kernel == po.pass_kernel;
+                    if (!dup) cands.push_back(po);
+                }
         }
     std::vector<float> feat;
     std::vector<int> owner;
@@ -79,7 +82,8 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanO
         Plan p;
         plan_greedy(n, dtype, gates, cands[c], &p);
         for (HostPass& hp : p.passes) {
-            const std::vector<float> f = pass_features(n, dtype, hp, cands[c].tensor == 0);
+            const std::vector<float> f =
+                pass_features(n, dtype, hp, cands[c].tensor == 0, register_pass_eligible(p, hp));
             feat.insert(feat.end(), f.begin(), f.end());
             owner.push_back((int)c);
         }
@@ -101,11 +105,12 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanO
 }
 
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
-                             const PlanOptions& base, cudaEvent_t* ev0, cudaEvent_t* ev1) {
+                             const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0, cudaEvent_t* ev1) {
     *ev0 = *ev1 = nullptr;
     uint64_t key = fnv1a(g, count * sizeof(sv_gate), 1469598103934665603ull);
     const int meta[3] = {h->n, h->dtype, base.tensor};
     key = fnv1a(meta, sizeof(meta), key);
+    if (salt) key = fnv1a(&salt, sizeof(salt), key);  // relabelling / a non-identity qubit map
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
     if (it == g_cache.end()) {
@@ -170,6 +175,7 @@ extern "C" int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate* gates, si
     chosen->tile_m = ranked[0].tile_m;
     chosen->planner = SV_PLAN_GREEDY;
     chosen->tensor = ranked[0].tensor == 0 ? 1 : -1;
+    chosen->pass_kernel = ranked[0].pass_kernel;
     *predicted_ms = rms[0];
     return SV_OK;
 }
@@ -210,6 +216,7 @@ extern "C" int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate* gates, si
     out->k_max = po.k_max;
     out->tile_m = po.tile_m;
     out->tensor = po.tensor == 0 ? 1 : -1;
+    out->pass_kernel = po.pass_kernel;
     if (measured_ms) *measured_ms = c.measured[c.calls == (int)c.trial.size() ? c.best : 0];
     return SV_OK;
 }

@@ -132,6 +132,7 @@ struct PlanOptions {
     int planner = SV_PLAN_GREEDY;
     int tensor = -1;  // 0: tensor cores for c64 blocks of k >= 3; -1: CUDA cores only
     int pass_kernel = 0;  // 1: shared-memory pass kernel only; 2: register passes fed by TMA
+    int relabel = 0;      // SWAP gates relabel qubits
 };
 
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
@@ -144,12 +145,15 @@ void plan_summary(const Plan& p, sv_plan_info* info);
 // type (the paper's one-hot gate-type encoding, App. D.1 Eq. "onehot",
 // summed over the pass), arithmetic and byte volume, and a bias input.
 constexpr int kFeatures = 32;
-std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tensor_cores);
+std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tensor_cores, bool register_pass);
+// Whether the register-resident kernel can take the pass (the serialiser's
+// structural conditions; a region too large to stage is checked there).
+bool register_pass_eligible(const Plan& p, const HostPass& hp);
 
 // Options for an apply under SV_PLAN_MLP; ev0/ev1 receive events to record
 // around the passes when the judge times this call (else nullptr).
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
-                             const PlanOptions& base, cudaEvent_t* ev0, cudaEvent_t* ev1);
+                             const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0, cudaEvent_t* ev1);
 
 // ---------------------------------------------------------------------------
 // Device-side plan blob: [PassDev x P][tensor-core B operands][pass regions].
@@ -295,9 +299,21 @@ struct sv_state {
     std::vector<cudaEvent_t> ev_pool;
     int ev_used;             // events in use (pairs: begin, end)
     std::vector<std::vector<float>> rec_feat;  // per recorded pass features
+    int perm[64];            // logical qubit -> physical bit of the stored amplitudes
+    bool permuted;           // perm is not the identity
+    sv::Scratch perm_tmp;    // device scratch of the permuted read-outs
+    sv_options last_opts;    // options of the last planned apply
 };
 
 namespace sv {
+
+// Logical -> physical qubit map handed to the read-out kernels by value.
+struct QubitMap {
+    int n;
+    int phys[40];
+};
+void reset_perm(sv_state* h);
+QubitMap qubit_map(const sv_state* h);
 
 // Error handling (thread-local message).
 int set_error(int code, const std::string& msg);
@@ -327,6 +343,8 @@ size_t batch_small_smem_bytes(int dtype, int mmax);
 // Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
 int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks);
 cudaError_t launch_probs(sv_state* h, double* dev_out);
+// Amplitudes of logical indices x0 .. x0+cnt-1 into dev_out (the handle's dtype).
+cudaError_t launch_gather_logical(sv_state* h, uint64_t x0, uint64_t cnt, void* dev_out);
 int measure_norm(sv_state* h, double* host_out);
 int measure_expect_z(sv_state* h, double* dev_out);
 // Shots and <Z_i> from one pass over the state (either output may be NULL).

@@ -343,6 +343,95 @@ static int block_stats(sv_state* h, bool want_bits, double** tot_out, double** c
     return SV_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Relabelled qubits: logical qubit q is stored at bit map.phys[q].  The
+// logical index x lives at P(x) = sum_q x_q 2^phys[q]; P is evaluated with
+// per-byte tables of x in shared memory.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ void build_byte_tables(uint64_t (*T)[256], const QubitMap& map) {
+    for (int e = threadIdx.x; e < 5 * 256; e += blockDim.x) {
+        const int b = e >> 8, v = e & 255;
+        uint64_t o = 0;
+        for (int i = 0; i < 8; ++i) {
+            const int q = 8 * b + i;
+            if (q < map.n && ((v >> i) & 1)) o |= 1ull << map.phys[q];
+        }
+        T[b][v] = o;
+    }
+}
+__device__ __forceinline__ uint64_t phys_index(const uint64_t (*T)[256], uint64_t x) {
+    return T[0][x & 255] | T[1][(x >> 8) & 255] | T[2][(x >> 16) & 255] | T[3][(x >> 24) & 255] |
+           T[4][(x >> 32) & 255];
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_probs_logical(const V* __restrict__ psi, uint64_t N, double* __restrict__ out,
+                                                       const QubitMap map) {
+    __shared__ uint64_t T[5][256];
+    build_byte_tables(T, map);
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += stride) {
+        const V a = psi[phys_index(T, x)];
+        const double re = (double)a.x, im = (double)a.y;
+        out[x] = fma(re, re, im * im);
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_gather_logical(const V* __restrict__ psi, uint64_t x0, uint64_t cnt,
+                                                        V* __restrict__ out, const QubitMap map) {
+    __shared__ uint64_t T[5][256];
+    build_byte_tables(T, map);
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride)
+        out[i] = psi[phys_index(T, x0 + i)];
+}
+
+// physical outcome y -> logical x (bit q of x = bit phys[q] of y), in place
+__global__ void k_logical_samples(uint64_t* __restrict__ s, uint64_t shots, const QubitMap map) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < shots; i += stride) {
+        const uint64_t y = s[i];
+        uint64_t x = 0;
+        for (int q = 0; q < map.n; ++q) x |= ((y >> map.phys[q]) & 1ull) << q;
+        s[i] = x;
+    }
+}
+
+__global__ void k_logical_expz(const double* __restrict__ phys, double* __restrict__ out, const QubitMap map) {
+    const int q = threadIdx.x;
+    if (q < map.n) out[q] = phys[map.phys[q]];
+}
+
+unsigned grid_n(uint64_t n, int cap_per_sm) {
+    uint64_t g = (n + 255) / 256;
+    const uint64_t cap = (uint64_t)sms() * cap_per_sm;
+    if (g > cap) g = cap;
+    return (unsigned)(g ? g : 1);
+}
+
+cudaError_t to_logical_samples(sv_state* h, uint64_t* dev_samples, uint64_t shots) {
+    if (!h->permuted || !shots) return cudaSuccess;
+    count_launch();
+    k_logical_samples<<<grid_n(shots, 4), 256, 0, h->stream>>>(dev_samples, shots, qubit_map(h));
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_gather_logical(sv_state* h, uint64_t x0, uint64_t cnt, void* dev_out) {
+    count_launch();
+    if (h->dtype == SV_C64)
+        k_gather_logical<float2><<<grid_n(cnt, 16), 256, 0, h->stream>>>((const float2*)h->amps, x0, cnt,
+                                                                        (float2*)dev_out, qubit_map(h));
+    else
+        k_gather_logical<double2><<<grid_n(cnt, 16), 256, 0, h->stream>>>((const double2*)h->amps, x0, cnt,
+                                                                          (double2*)dev_out, qubit_map(h));
+    return cudaGetLastError();
+}
+
 int measure_block_sums(sv_state* h, double** cdf, int* blog_out, int64_t* nb_out) {
     return block_stats(h, false, nullptr, cdf, nullptr, blog_out, nb_out);
 }
@@ -352,6 +441,13 @@ cudaError_t launch_probs(sv_state* h, double* dev_out) {
     unsigned g = (unsigned)((N + 255) / 256);
     if (g > (unsigned)sms() * 16) g = (unsigned)sms() * 16;
     count_launch();
+    if (h->permuted) {
+        if (h->dtype == SV_C64)
+            k_probs_logical<float2><<<g, 256, 0, h->stream>>>((const float2*)h->amps, N, dev_out, qubit_map(h));
+        else
+            k_probs_logical<double2><<<g, 256, 0, h->stream>>>((const double2*)h->amps, N, dev_out, qubit_map(h));
+        return cudaGetLastError();
+    }
     if (h->dtype == SV_C64)
         k_probs<float2><<<g, 256, 0, h->stream>>>((const float2*)h->amps, N, dev_out);
     else
@@ -394,11 +490,24 @@ int measure_readout(sv_state* h, uint64_t shots, uint64_t seed, uint64_t* dev_sa
     int rc = block_stats(h, dev_expz != nullptr, &tot, &cdf, &bits, &blog, &nb);
     if (rc) return rc;
     if (dev_expz) {
+        double* ez = dev_expz;
+        if (h->permuted) {  // physical bits first, then reordered to logical qubits
+            rc = ensure_scratch(&h->perm_tmp, sizeof(double) * 64, h->stream);
+            if (rc) return rc;
+            ez = (double*)h->perm_tmp.ptr;
+        }
         count_launch();
-        k_expz_blocks<<<h->n, 256, 0, h->stream>>>(tot, bits, (uint64_t)nb, blog, dev_expz);
+        k_expz_blocks<<<h->n, 256, 0, h->stream>>>(tot, bits, (uint64_t)nb, blog, ez);
+        if (h->permuted) {
+            count_launch();
+            k_logical_expz<<<1, 64, 0, h->stream>>>(ez, dev_expz, qubit_map(h));
+        }
     }
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && dev_samples && shots) e = launch_sample(h, blog, cdf, nb, shots, seed, nullptr, dev_samples);
+    if (e == cudaSuccess && dev_samples && shots) {
+        e = launch_sample(h, blog, cdf, nb, shots, seed, nullptr, dev_samples);
+        if (e == cudaSuccess) e = to_logical_samples(h, dev_samples, shots);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "read-out");
     return SV_OK;
 }
@@ -413,6 +522,7 @@ int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev
     int rc = measure_block_sums(h, &cdf, &blog, &nb);
     if (rc) return rc;
     cudaError_t e = launch_sample(h, blog, cdf, nb, shots, seed, dev_u, dev_out);
+    if (e == cudaSuccess) e = to_logical_samples(h, dev_out, shots);
     if (e != cudaSuccess) return cuda_fail(e, "sample");
     return SV_OK;
 }

@@ -301,6 +301,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         po.planner = opt->planner;
         po.tensor = opt->tensor > 0 ? 0 : -1;
         po.pass_kernel = opt->pass_kernel == 1 || opt->pass_kernel == 2 ? opt->pass_kernel : 0;
+        po.relabel = opt->relabel == 1 ? 1 : 0;
     }
     if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
@@ -553,7 +554,7 @@ void plan_summary(const Plan& p, sv_plan_info* info) {
     info->bytes_moved = (int64_t)bytes;
 }
 
-std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tensor_cores) {
+std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tensor_cores, bool register_pass) {
     std::vector<float> f(kFeatures, 0.0f);
     const int m = (int)p.tile.size();
     f[0] = n / 34.0f;
@@ -579,7 +580,7 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tenso
     f[13] = (float)p.ops.size() / 16.0f;
     for (int t = 0; t < 14; ++t) f[14 + t] = p.type_count[t] / 16.0f;  // f[14..27]
     f[28] = (float)(ldexp(1.0, n) * (dtype == SV_C64 ? 16.0 : 32.0) / ldexp(1.0, 36));
-    f[29] = (n - m) / 34.0f;
+    f[29] = register_pass ? 1.0f : 0.0f;  // kernel: register-resident or shared-memory
     f[30] = tensor_cores ? 1.0f : 0.0f;
     f[31] = 1.0f;
     return f;
@@ -944,6 +945,19 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
 }
 
 }  // namespace
+
+bool register_pass_eligible(const Plan& p, const HostPass& hp) {
+    if (p.no_register_passes) return false;
+    const int r = reg_bits(p.dtype), tb = (int)hp.tile.size() - r;
+    if (tb < 5 || tb > 9) return false;
+    for (const HostOp& o : hp.ops) {
+        if (o.kind == OP_DIAG) continue;
+        if (use_tc(p, o)) return false;
+        if (o.kind == OP_DENSE && (int)o.qubits.size() > kRegDenseMaxK) return false;
+        if ((int)o.qubits.size() > r) return false;
+    }
+    return true;
+}
 
 void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
     const int dtype = plans.empty() ? SV_C64 : plans[0]->dtype;

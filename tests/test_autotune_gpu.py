@@ -36,7 +36,8 @@ def test_autotune_choice_and_cache(dtype, tmp_path):
         lines = open(cache).read().strip().splitlines()
         assert len(lines) == 1
         rec = json.loads(lines[0])
-        assert (rec["k_max"], rec["tile_m"], rec["tensor"]) == (opts["k_max"], opts["tile_m"], opts["tensor"])
+        assert (rec["k_max"], rec["tile_m"], rec["tensor"], rec["pass_kernel"]) == (
+            opts["k_max"], opts["tile_m"], opts["tensor"], opts["pass_kernel"])
         # second call: served from the file, nothing appended
         opts2, ms2 = S.sv_autotune(h, g, cache)
         assert opts2 == opts and abs(ms2 - ms) < 1e-3
