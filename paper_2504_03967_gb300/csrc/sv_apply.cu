@@ -278,6 +278,21 @@ __device__ __forceinline__ void reg_ur(V* v, R u00, R u01, R u10, R u11) {
             v[j | (1 << P)] = y;
         }
 }
+template <typename V, int K, int P>
+__device__ __forceinline__ void reg_h(V* v) {  // unscaled butterfly (a + b, a - b)
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if (!((j >> P) & 1)) {
+            const V a = v[j], b = v[j | (1 << P)];
+            V x, y;
+            x.x = a.x + b.x;
+            x.y = a.y + b.y;
+            y.x = a.x - b.x;
+            y.y = a.y - b.y;
+            v[j] = x;
+            v[j | (1 << P)] = y;
+        }
+}
 template <typename V, int K, int C, int T>
 __device__ __forceinline__ void reg_cx(V* v) {
 #pragma unroll
@@ -317,6 +332,16 @@ __device__ __forceinline__ void reg_ur_any(V* v, int p, R u00, R u01, R u10, R u
     case 2: if constexpr (K > 2) reg_ur<V, K, 2>(v, u00, u01, u10, u11); break;
     case 3: if constexpr (K > 3) reg_ur<V, K, 3>(v, u00, u01, u10, u11); break;
     default: if constexpr (K > 4) reg_ur<V, K, 4>(v, u00, u01, u10, u11); break;
+    }
+}
+template <typename V, int K>
+__device__ __forceinline__ void reg_h_any(V* v, int p) {
+    switch (p) {
+    case 0: reg_h<V, K, 0>(v); break;
+    case 1: if constexpr (K > 1) reg_h<V, K, 1>(v); break;
+    case 2: if constexpr (K > 2) reg_h<V, K, 2>(v); break;
+    case 3: if constexpr (K > 3) reg_h<V, K, 3>(v); break;
+    default: if constexpr (K > 4) reg_h<V, K, 4>(v); break;
     }
 }
 // (a, b) -> compile-time pair; a != b, both < K
@@ -1001,9 +1026,58 @@ __device__ __forceinline__ void reg_gates(V* v, const GateRec* __restrict__ recs
                 if ((g.b >> j) & 1) v[j] = cmul(sd[g.off + j], v[j]);
             break;
         case GR_CX: reg_cx_any<V, RB>(v, g.a, g.b); break;
+        case GR_H: reg_h_any<V, RB>(v, g.a); break;
         default: reg_swap_any<V, RB>(v, g.a, g.b); break;
         }
     }
+}
+
+// Tile copies of a register pass: every thread moves exactly 16 chunks of 16
+// bytes (2^RB amplitudes), chunk k of thread t being tile chunk t + k * blockDim,
+// so the row and in-row offsets advance by compile-time multiples.
+template <typename V>
+__device__ __forceinline__ void rissue_tile(V* tile, const V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
+                                            int L) {
+    constexpr int PER = 16 / sizeof(V);
+    const int i0 = PER * (int)threadIdx.x, istep = PER * (int)blockDim.x;
+    const int ioff = i0 & ((1 << L) - 1);
+    const V* src = psi + base + ioff;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int i = i0 + k * istep;
+        cp_async16(tile + swz<V>(i), src + ((uint64_t)rowoff[i >> L] << L));
+    }
+}
+template <typename V>
+__device__ __forceinline__ void rstore_tile(const V* tile, V* __restrict__ psi, uint64_t base, const uint32_t* rowoff,
+                                            int L) {
+    constexpr int PER = 16 / sizeof(V);
+    const int i0 = PER * (int)threadIdx.x, istep = PER * (int)blockDim.x;
+    const int ioff = i0 & ((1 << L) - 1);
+    V* dst = psi + base + ioff;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int i = i0 + k * istep;
+        *(float4*)(dst + ((uint64_t)rowoff[i >> L] << L)) = *(const float4*)(tile + swz<V>(i));
+    }
+}
+
+// Global index of a tile's first amplitude from its number t: the bits of t
+// scattered to the non-tile qubits, via per-byte tables (entries in units of
+// 2^L amplitudes; at most 24 non-tile qubits here).
+__device__ __forceinline__ void build_base_tables(uint32_t (*tb)[256], const PassDev& P) {
+    for (int e = threadIdx.x; e < 3 * 256; e += blockDim.x) {
+        const int b = e >> 8, v = e & 255;
+        uint32_t o = 0;
+        for (int i = 0; i < 8; ++i) {
+            const int q = 8 * b + i;
+            if (q < P.nother && ((v >> i) & 1)) o |= 1u << (P.oq[q] - P.L);
+        }
+        tb[b][v] = o;
+    }
+}
+__device__ __forceinline__ uint64_t table_base(const uint32_t (*tb)[256], uint64_t t, int L) {
+    return (uint64_t)(tb[0][t & 255] | tb[1][(t >> 8) & 255] | tb[2][(t >> 16) & 255]) << L;
 }
 
 // Diagonal run on the registers.  fold = the run's per-tile linear
@@ -1163,13 +1237,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
     using V = typename CT<R>::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
+    __shared__ uint32_t tbase[3][256];
     {
         const int* src = (const int*)pdp;
         int* dst = (int*)&P;
         for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const int m = P.m, L = P.L, no = P.nother, nd = P.ndiag;
+    const int m = P.m, L = P.L, nd = P.ndiag;
     V* tiles[2] = {(V*)smem, (V*)(smem + (lay.nbuf == 2 ? lay.tile_bytes : 0))};
     uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
     unsigned char* stage = smem + lay.stage_off;
@@ -1185,6 +1260,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
             if ((r >> b) & 1) o |= 1u << (P.tq[L + b] - L);
         rowoff[r] = o;
     }
+    build_base_tables(tbase, P);
     cp_async_wait_group<0>();
     __syncthreads();
     const OpDev* ops = (const OpDev*)stage;
@@ -1192,14 +1268,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
         for (int i = 0; i < P.nops; ++i)
             if (ops[i].kind == OP_DIAG) dofs[ops[i].ord] = ops[i].diag_off;
     const uint64_t ntiles = 1ull << (n - m);
-    auto tile_base = [&](uint64_t t) {
-        uint64_t b = 0;
-        for (int i = 0; i < no; ++i) b |= ((t >> i) & 1ull) << P.oq[i];
-        return b;
-    };
+    auto tile_base = [&](uint64_t t) { return table_base(tbase, t, L); };
     int cur = 0;
     if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
-        issue_tile(tiles[0], psi, tile_base(blockIdx.x), rowoff, m, L);
+        rissue_tile(tiles[0], psi, tile_base(blockIdx.x), rowoff, L);
         cp_async_commit();
     }
     V v[1 << RB];
@@ -1209,24 +1281,32 @@ __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restr
         const uint64_t tn = t + gridDim.x;
         if (lay.nbuf == 2) {
             if (tn < ntiles) {
-                issue_tile(tiles[cur ^ 1], psi, tile_base(tn), rowoff, m, L);
+                rissue_tile(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L);
                 cp_async_commit();
                 cp_async_wait_group<1>();
             } else {
                 cp_async_wait_group<0>();
             }
         } else {
-            issue_tile(tiles[0], psi, base, rowoff, m, L);
+            rissue_tile(tiles[0], psi, base, rowoff, L);
             cp_async_commit();
             cp_async_wait_group<0>();
         }
         __syncthreads();
         V* tile = tiles[cur];
         rpass_tile<V, R, RB>(v, tile, P, stage, fold, dofs, t, Lg);
+        if (P.scale != 1.0) {
+            const R sc = (R)P.scale;
+#pragma unroll
+            for (int k = 0; k < (1 << RB); ++k) {
+                v[k].x *= sc;
+                v[k].y *= sc;
+            }
+        }
         __syncthreads();
         reg_write<V, RB>(v, tile, Lg);
         __syncthreads();
-        store_tile(tile, psi, base, rowoff, m, L);
+        rstore_tile(tile, psi, base, rowoff, L);
         __syncthreads();
         if (lay.nbuf == 2) cur ^= 1;
     }
@@ -1267,13 +1347,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
     unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ PassDev P;
     __shared__ __align__(8) uint64_t full[kMaxSlots];
+    __shared__ uint32_t tbase[3][256];
     {
         const int* src = (const int*)pdp;
         int* dst = (int*)&P;
         for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const int m = P.m, L = P.L, no = P.nother, nd = P.ndiag, S = lay.slots;
+    const int m = P.m, L = P.L, nd = P.ndiag, S = lay.slots;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
     unsigned char* stage = smem + lay.stage_off;
@@ -1289,6 +1370,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
             if ((r >> b) & 1) o |= 1u << (P.tq[L + b] - L);
         rowoff[r] = o;
     }
+    build_base_tables(tbase, P);
     if (tid == 0) {
         for (int s = 0; s < S; ++s) tc::mbar_init(&full[s], 1);
         tc::fence_mbar_init();
@@ -1303,11 +1385,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
     const int nloc = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // this CTA's tiles
     const int BR = lay.box_rows, ngroups = nrows / BR;
     auto tile_of = [&](int j) { return (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x; };
-    auto row0_of = [&](uint64_t t) {
-        uint64_t b = 0;
-        for (int i = 0; i < no; ++i) b |= ((t >> i) & 1ull) << P.oq[i];
-        return (int)(b >> L);
-    };
+    auto row0_of = [&](uint64_t t) { return (int)(table_base(tbase, t, L) >> L); };
     auto issue_load = [&](int j) {  // warp 0: tile j of this CTA into slot j % S
         const int s = j % S;
         if (lane == 0) tma::mbar_arrive_expect_tx(&full[s], (uint32_t)lay.tile_bytes);
@@ -1340,6 +1418,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
         const uint64_t t = tile_of(j);
         V* tile = (V*)(smem + (size_t)s * lay.tile_bytes);
         rpass_tile<V, R, RB>(v, tile, P, stage, fold, dofs, t, Lg);
+        if (P.scale != 1.0) {
+            const R sc = (R)P.scale;
+#pragma unroll
+            for (int k = 0; k < (1 << RB); ++k) {
+                v[k].x *= sc;
+                v[k].y *= sc;
+            }
+        }
         __syncthreads();
         reg_write<V, RB>(v, tile, Lg);
         tc::fence_proxy_async();

@@ -56,7 +56,10 @@ constexpr int kStageCap = 48 * 1024;  // bytes of a pass region staged in shared
 
 // Gate-sequence block records (positions are block-local bits, data offsets
 // index the op's own complex values).
-enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4 };
+enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4, GR_H = 5 };
+// GR_H (register passes only): the Hadamard without its 1/sqrt(2), a + b and
+// a - b; the pass multiplies its amplitudes by the product of the dropped
+// factors once, when it writes them back (PassDev::scale).
 struct GateRec {
     int kind, a, b, off;
 };
@@ -192,6 +195,7 @@ __host__ __device__ inline int tc_kmajor_index(int n, int kk, int K) {
 }
 
 struct PassDev {
+    double scale;        // register passes: factor applied at write-back (1 unless GR_H records)
     int n;               // qubits of the state the pass runs on
     int m;
     int L;

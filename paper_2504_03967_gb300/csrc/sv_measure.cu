@@ -50,6 +50,15 @@ __device__ __forceinline__ void ff_add(FF& a, float x, float xl) {
     a.hi = s;
 }
 __device__ __forceinline__ double ff_val(FF a) { return (double)a.hi + (double)a.lo; }
+// Sum over the warp in double-float (every lane gets it); no FP64 instruction.
+__device__ __forceinline__ FF ff_allreduce(FF a) {
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, a.hi, sh), l = __shfl_xor_sync(0xffffffffu, a.lo, sh);
+        ff_add(a, h, l);
+    }
+    return a;
+}
 
 template <typename V>
 __global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, int blog, uint64_t nblocks,
@@ -60,7 +69,6 @@ __global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, 
     const uint64_t b0 = wid << blog;
     const int len = 1 << blog;
     const int jn = len >= 32 ? len / 32 : 1;
-    double t, bj[5];
     if constexpr (sizeof(V) == 8) {
         FF acc = {0.f, 0.f}, ab[5];
 #pragma unroll
@@ -79,11 +87,23 @@ __global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, 
                     if ((j >> b) & 1) ff_add(ab[b], s, sl);
             }
         }
-        t = ff_val(acc);
+        // Warp sums in double-float; lane 0 converts the total and lanes 1..10
+        // the bit sums, so each block costs one FP64 conversion instruction.
+        FF mine = ff_allreduce(acc);
+        if (bits) {
 #pragma unroll
-        for (int b = 0; b < 5; ++b) bj[b] = ff_val(ab[b]);
+            for (int b = 0; b < 5; ++b) {
+                const FF lb = ff_allreduce(((lane >> b) & 1) ? acc : FF{0.f, 0.f});
+                const FF jb = ff_allreduce(ab[b]);
+                if (lane == 1 + b) mine = lb;
+                if (lane == 6 + b) mine = jb;
+            }
+        }
+        const double val = ff_val(mine);
+        if (lane == 0) tot[wid] = val;
+        if (bits && lane >= 1 && lane <= 10) bits[wid * 10 + lane - 1] = lane - 1 < blog ? val : 0.0;
     } else {
-        t = 0.0;
+        double t = 0.0, bj[5];
 #pragma unroll
         for (int b = 0; b < 5; ++b) bj[b] = 0.0;
         for (int j = 0; j < jn; ++j) {
@@ -95,28 +115,32 @@ __global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, 
                     if ((j >> b) & 1) bj[b] += p;
             }
         }
-    }
-    const double total = warp_sum(t);
-    if (bits) {
-        double out[10];
+        const double total = warp_sum(t);
+        if (bits) {
+            double out[10];
 #pragma unroll
-        for (int b = 0; b < 5; ++b) out[b] = warp_sum(((lane >> b) & 1) ? t : 0.0);
+            for (int b = 0; b < 5; ++b) out[b] = warp_sum(((lane >> b) & 1) ? t : 0.0);
 #pragma unroll
-        for (int b = 0; b < 5; ++b) out[5 + b] = warp_sum(bj[b]);
-        if (lane == 0)
-            for (int b = 0; b < 10; ++b) bits[wid * 10 + b] = b < blog ? out[b] : 0.0;
+            for (int b = 0; b < 5; ++b) out[5 + b] = warp_sum(bj[b]);
+            if (lane == 0)
+                for (int b = 0; b < 10; ++b) bits[wid * 10 + b] = b < blog ? out[b] : 0.0;
+        }
+        if (lane == 0) tot[wid] = total;
     }
-    if (lane == 0) tot[wid] = total;
 }
 
-// <Z_i> = S - 2 * (mass with bit i set) from the block records: one CTA per
-// qubit, fixed-order reductions.
+// <Z_i> = S - 2 * (mass with bit i set) from the block records.  Stage 1:
+// CTA (i, g) reduces chunk g of the block records for qubit i (fixed order);
+// stage 2: one thread per qubit adds its chunk partials in order.
+constexpr int kExpzChunks = 64;
 __global__ void __launch_bounds__(256) k_expz_blocks(const double* __restrict__ tot, const double* __restrict__ bits,
-                                                     uint64_t nblocks, int blog, double* __restrict__ out) {
+                                                     uint64_t nblocks, int blog, double* __restrict__ part) {
     __shared__ double s1[256], s2[256];
-    const int i = blockIdx.x;
+    const int i = blockIdx.x, g = blockIdx.y;
+    const uint64_t per = (nblocks + kExpzChunks - 1) / kExpzChunks;
+    const uint64_t k0 = (uint64_t)g * per, k1 = k0 + per < nblocks ? k0 + per : nblocks;
     double a = 0.0, b = 0.0;
-    for (uint64_t k = threadIdx.x; k < nblocks; k += blockDim.x) {
+    for (uint64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const double tk = tot[k];
         a += tk;
         if (i < blog) b += bits[k * 10 + i];
@@ -132,7 +156,20 @@ __global__ void __launch_bounds__(256) k_expz_blocks(const double* __restrict__ 
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[i] = s1[0] - 2.0 * s2[0];
+    if (threadIdx.x == 0) {
+        part[2 * (i * kExpzChunks + g)] = s1[0];
+        part[2 * (i * kExpzChunks + g) + 1] = s2[0];
+    }
+}
+__global__ void k_expz_final(const double* __restrict__ part, int n, double* __restrict__ out) {
+    const int i = threadIdx.x;
+    if (i >= n) return;
+    double a = 0.0, b = 0.0;
+    for (int g = 0; g < kExpzChunks; ++g) {
+        a += part[2 * (i * kExpzChunks + g)];
+        b += part[2 * (i * kExpzChunks + g) + 1];
+    }
+    out[i] = a - 2.0 * b;
 }
 
 // ---- inclusive scan of doubles -------------------------------------------
@@ -490,14 +527,14 @@ int measure_readout(sv_state* h, uint64_t shots, uint64_t seed, uint64_t* dev_sa
     int rc = block_stats(h, dev_expz != nullptr, &tot, &cdf, &bits, &blog, &nb);
     if (rc) return rc;
     if (dev_expz) {
-        double* ez = dev_expz;
-        if (h->permuted) {  // physical bits first, then reordered to logical qubits
-            rc = ensure_scratch(&h->perm_tmp, sizeof(double) * 64, h->stream);
-            if (rc) return rc;
-            ez = (double*)h->perm_tmp.ptr;
-        }
-        count_launch();
-        k_expz_blocks<<<h->n, 256, 0, h->stream>>>(tot, bits, (uint64_t)nb, blog, ez);
+        // chunk partials, then (relabelled qubits) the physical-bit values
+        rc = ensure_scratch(&h->perm_tmp, sizeof(double) * (2 * 64 * kExpzChunks + 64), h->stream);
+        if (rc) return rc;
+        double* part = (double*)h->perm_tmp.ptr;
+        double* ez = h->permuted ? part + 2 * 64 * kExpzChunks : dev_expz;
+        count_launch(2);
+        k_expz_blocks<<<dim3(h->n, kExpzChunks), 256, 0, h->stream>>>(tot, bits, (uint64_t)nb, blog, part);
+        k_expz_final<<<1, 64, 0, h->stream>>>(part, h->n, ez);
         if (h->permuted) {
             count_launch();
             k_logical_expz<<<1, 64, 0, h->stream>>>(ez, dev_expz, qubit_map(h));

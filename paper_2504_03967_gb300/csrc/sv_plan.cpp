@@ -923,9 +923,16 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
                 } else {
                     t.a = O.lq[g.a];
                     if (g.kind == GR_CX || g.kind == GR_SWAP) t.b = O.lq[g.b];
-                    if (g.kind == GR_U || g.kind == GR_UR) {
+                    const cd* gm = g.kind == GR_U || g.kind == GR_UR ? &o.gdata[(size_t)g.off] : nullptr;
+                    const double hs = 1.0 / std::sqrt(2.0);
+                    if (g.kind == GR_UR && gm[0] == cd(hs, 0.0) && gm[1] == cd(hs, 0.0) && gm[2] == cd(hs, 0.0) &&
+                        gm[3] == cd(-hs, 0.0)) {
+                        t.kind = GR_H;  // butterfly; the factor goes to the pass's write-back scale
+                        t.off = 0;
+                        P->scale *= hs;
+                    } else if (gm) {
                         t.off = (int)data.size();
-                        for (int e = 0; e < 4; ++e) data.push_back(o.gdata[(size_t)g.off + e]);
+                        for (int e = 0; e < 4; ++e) data.push_back(gm[e]);
                     }
                 }
                 recs.push_back(t);
@@ -984,6 +991,7 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
             const HostPass& hp = p.passes[pi];
             PassDev& P = pds[gpi];
             memset(&P, 0, sizeof(P));
+            P.scale = 1.0;
             P.n = n;
             P.m = (int)hp.tile.size();
             P.L = hp.L;

@@ -81,3 +81,45 @@ def test_batch_variational_sweep():
     circuits = [(n, W.hea(n, layers, params[s])) for s in range(len(params))]
     _, ez = S.sv_batch_run(circuits, dtype=S.C64, shots=0)
     _check_expz(ez, circuits, S.C64)
+
+
+def test_batch_qcrank_full_size():
+    """Config-3 sizes: 512 QCrank circuits, a ~ U{8..14}, d ~ U{4..10}
+    (n = 12..24), 10^5 shots each, complex64, one call.  Pinned on sampled
+    circuits: <Z> of every qubit against the oracle (the smaller circuits) and,
+    for every circuit, the address marginal (uniform, 2^-a) and the data
+    qubits' mean conditional closed form sin^2(pi pixel / 2) from the shots."""
+    batch = W.qcrank_batch(512, W.SEED[3])
+    circuits = [(a + d, W.qcrank(a, d, pix)) for a, d, pix in batch]
+    shots = 100000
+    samp, ez = S.sv_batch_run(circuits, dtype=S.C64, shots=shots, seed=31)
+    assert samp.shape == (512, shots)
+    # <Z_data_k> = mean over addresses of cos(pi pixel) for every circuit
+    for c, (a, d, pix) in enumerate(batch):
+        want = np.cos(np.pi * pix).mean(axis=0)
+        assert np.abs(ez[c, a:a + d] - want).max() < 1e-5, c
+        assert np.abs(ez[c, :a]).max() < 1e-5, c  # address qubits stay uniform
+    # shots of a few circuits against their closed-form data marginals
+    for c in range(0, 512, 97):
+        a, d, pix = batch[c]
+        s = samp[c].astype(np.int64)
+        for k in range(d):
+            p1 = ((s >> (a + k)) & 1).mean()
+            want = (np.sin(np.pi * pix[:, k] / 2) ** 2).mean()
+            assert abs(p1 - want) < 5.0 / np.sqrt(shots), (c, k)
+    # exact <Z> against the oracle on the smallest circuits
+    small = sorted(range(512), key=lambda c: circuits[c][0])[:4]
+    _check_expz(ez[small], [circuits[c] for c in small], S.C64)
+
+
+def test_batch_variational_full_size():
+    """Config-5 sizes: hardware-efficient ansatz at n = 20, 8 layers, 4096
+    parameter sets in one call (large-circuit path), <Z_i> for every qubit;
+    32 sampled sets against the oracle."""
+    n, layers = 20, 8
+    params = W.hea_params(4096, n, layers, W.SEED[5])
+    circuits = [(n, W.hea(n, layers, params[s])) for s in range(len(params))]
+    _, ez = S.sv_batch_run(circuits, dtype=S.C64, shots=0)
+    assert ez.shape[0] == 4096
+    pick = np.random.default_rng(3).choice(4096, 32, replace=False)
+    _check_expz(ez[pick], [circuits[c] for c in pick], S.C64)

@@ -161,16 +161,24 @@ def qcrank(a, d, pixels):
     assert pixels.shape == (L, d)
     theta = np.pi * np.asarray(pixels, dtype=np.float64)
     tp = qcrank_angles(a, theta)
-    ctrl = [(_gray(i) ^ _gray((i + 1) % L)).bit_length() - 1 for i in range(L)]
-    b = _Builder(a + 2 * d * L)
-    for q in range(a):
-        b.add(H, (q,))
-    for k in range(d):
-        t = a + k
-        for i in range(L):
-            b.add(RY, (t,), (float(tp[i, k]),))
-            b.add(CX, (ctrl[i], t))
-    return b.done()
+    ctrl = np.array([(_gray(i) ^ _gray((i + 1) % L)).bit_length() - 1 for i in range(L)], dtype=np.uint32)
+    # H on every address qubit, then for each data qubit t = a + k the ladder
+    # RY(theta'_i) on t, CX(ctrl_i, t) for i = 0 .. L-1 (filled column-wise)
+    g = np.zeros(a + 2 * d * L, dtype=GATE_DTYPE)
+    g["type"][:a] = H
+    g["nq"][:a] = 1
+    g["q"][:a, 0] = np.arange(a, dtype=np.uint32)
+    lad = g[a:].reshape(d, L, 2)
+    t = (a + np.arange(d, dtype=np.uint32))[:, None]
+    lad["type"][:, :, 0] = RY
+    lad["nq"][:, :, 0] = 1
+    lad["q"][:, :, 0, 0] = t
+    lad["p"][:, :, 0, 0] = tp.T
+    lad["type"][:, :, 1] = CX
+    lad["nq"][:, :, 1] = 2
+    lad["q"][:, :, 1, 0] = ctrl[None, :]
+    lad["q"][:, :, 1, 1] = t
+    return g
 
 
 def qcrank_batch(circuits, seed, a_range=(8, 14), d_range=(4, 10)):
