@@ -101,7 +101,12 @@ typedef enum {
  * TMA tensor copies through a ring of tile slots (one CTA per SM).  Results
  * agree within rounding whichever kernel runs.  relabel: 1 = SWAP gates
  * become a relabelling of the state's qubits instead of data movement (see
- * sv_qubit_map); 0 = SWAPs move amplitudes.  reserved: zero. */
+ * sv_qubit_map); 0 = SWAPs move amplitudes.  drop_phase_below: the
+ * approximation for negligible rotations (App. D.2): P, RZ and CP gates whose
+ * angle, reduced to (-pi, pi], is smaller in magnitude than this many radians
+ * are left out; the result then differs from the exact circuit by at most
+ * the sum of the dropped angles over 2 in norm (0, a negative value or NaN =
+ * exact).  reserved: zero. */
 typedef struct {
     int k_max;
     int tile_m;
@@ -111,11 +116,12 @@ typedef struct {
     int pass_kernel;
     int relabel;
     int reserved[1];
+    double drop_phase_below;
 } sv_options;
 
 /* Plan summary returned by sv_plan_circuit (host only, no device work). */
 typedef struct {
-    int64_t gates;        /* gate records given (MEASURE included) */
+    int64_t gates;        /* gate records given (MEASURE included), less those drop_phase_below removes */
     int64_t passes;       /* HBM passes the plan makes over the state */
     int64_t dense_ops;    /* fused dense blocks over all passes */
     int64_t diag_ops;     /* diagonal-phase runs over all passes */

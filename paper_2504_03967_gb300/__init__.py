@@ -39,7 +39,7 @@ class SVError(RuntimeError):
 class sv_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
                 ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("relabel", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("relabel", ctypes.c_int), ("reserved", ctypes.c_int * 1), ("drop_phase_below", ctypes.c_double)]
 
 
 class sv_plan_info(ctypes.Structure):
@@ -121,10 +121,10 @@ def _check(rc):
     return rc
 
 
-def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0):
+def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0, drop_phase_below=0.0):
     o = sv_options()
     o.k_max, o.tile_m, o.planner, o.record, o.tensor = k_max, tile_m, planner, record, tensor
-    o.pass_kernel, o.relabel = pass_kernel, relabel
+    o.pass_kernel, o.relabel, o.drop_phase_below = pass_kernel, relabel, drop_phase_below
     return o
 
 
@@ -196,15 +196,17 @@ def sv_store_state(h):
     return a
 
 
-def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0):
+def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0,
+                     drop_phase_below=0.0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel)
+    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel, drop_phase_below)
     _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
 
 
-def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, tensor=0, pass_kernel=0):
+def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, tensor=0, pass_kernel=0,
+                    drop_phase_below=0.0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, 0, tensor, pass_kernel)
+    o = _opts(k_max, tile_m, planner, 0, tensor, pass_kernel, 0, drop_phase_below)
     info = sv_plan_info()
     _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}

@@ -272,10 +272,12 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
     if (canonicalise(n, gates, count, &cg, &bad) != SV_OK)
         return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
     const PlanOptions po = resolve_options(n, dt, opt);
+    const size_t before = cg.size();
+    drop_small_phases(&cg, po.drop_phase_below);
     Plan plan;
     if (po.planner == SV_PLAN_PLAIN) plan_plain(n, dt, cg, &plan);
     else plan_greedy(n, dt, cg, po, &plan);
-    plan.gates = (int64_t)count;
+    plan.gates = (int64_t)(count - (before - cg.size()));
     plan_summary(plan, info);
     if (!plan.plain) {  // which passes the register-resident kernel takes
         PlanBlob blob;
@@ -317,14 +319,22 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     uint64_t salt = 0;
     std::vector<CGate> mapped;
     const std::vector<CGate>* gl = &cg;
+    std::vector<CGate> approx;
+    if (po.drop_phase_below > 0.0) {
+        approx = cg;
+        drop_small_phases(&approx, po.drop_phase_below);
+        gl = &approx;
+        salt ^= 0x51ed270b27f1c0d5ull ^ (uint64_t)(po.drop_phase_below * 1e12);
+    }
     if (po.relabel || h->permuted) {
         if (h->permuted) {
-            salt = 1469598103934665603ull;
-            for (int q = 0; q < h->n; ++q) salt = (salt ^ (uint64_t)h->perm[q]) * 1099511628211ull;
+            uint64_t ps = 1469598103934665603ull;
+            for (int q = 0; q < h->n; ++q) ps = (ps ^ (uint64_t)h->perm[q]) * 1099511628211ull;
+            salt ^= ps;
         }
         if (po.relabel) salt ^= 0x9e3779b97f4a7c15ull;
-        mapped.reserve(cg.size());
-        for (const CGate& g : cg) {
+        mapped.reserve(gl->size());
+        for (const CGate& g : *gl) {
             if (po.relabel && g.type == SV_SWAP) {
                 std::swap(h->perm[g.q[0]], h->perm[g.q[1]]);
                 continue;

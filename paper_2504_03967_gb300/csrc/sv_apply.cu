@@ -1027,6 +1027,12 @@ __device__ __forceinline__ void reg_gates(V* v, const GateRec* __restrict__ recs
             break;
         case GR_CX: reg_cx_any<V, RB>(v, g.a, g.b); break;
         case GR_H: reg_h_any<V, RB>(v, g.a); break;
+        case GR_HD:
+            reg_h_any<V, RB>(v, g.a);
+#pragma unroll
+            for (int j = 0; j < (1 << RB); ++j)
+                if ((g.b >> j) & 1) v[j] = cmul(sd[g.off + j], v[j]);
+            break;
         default: reg_swap_any<V, RB>(v, g.a, g.b); break;
         }
     }

@@ -56,7 +56,9 @@ constexpr int kStageCap = 48 * 1024;  // bytes of a pass region staged in shared
 
 // Gate-sequence block records (positions are block-local bits, data offsets
 // index the op's own complex values).
-enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4, GR_H = 5 };
+enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4, GR_H = 5, GR_HD = 6 };
+// GR_HD (register passes only): GR_H on position a followed by the phase table
+// at off with entry mask b (one dispatch for the pair).
 // GR_H (register passes only): the Hadamard without its 1/sqrt(2), a + b and
 // a - b; the pass multiplies its amplitudes by the product of the dropped
 // factors once, when it writes them back (PassDev::scale).
@@ -136,7 +138,10 @@ struct PlanOptions {
     int tensor = -1;  // 0: tensor cores for c64 blocks of k >= 3; -1: CUDA cores only
     int pass_kernel = 0;  // 1: shared-memory pass kernel only; 2: register passes fed by TMA
     int relabel = 0;      // SWAP gates relabel qubits
+    double drop_phase_below = 0.0;  // approximation: smaller P/RZ/CP angles are dropped
 };
+// The approximation for negligible rotations: the gates kept.
+void drop_small_phases(std::vector<CGate>* g, double eps);
 
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
 void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out);

@@ -292,6 +292,20 @@ int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out,
     return SV_OK;
 }
 
+void drop_small_phases(std::vector<CGate>* g, double eps) {
+    if (!(eps > 0.0)) return;
+    std::vector<CGate> kept;
+    kept.reserve(g->size());
+    for (const CGate& x : *g) {
+        if (x.type == SV_P || x.type == SV_RZ || x.type == SV_CP) {
+            double a = std::remainder(x.p[0], 2.0 * kPi);  // (-pi, pi]
+            if (std::fabs(a) < eps) continue;
+        }
+        kept.push_back(x);
+    }
+    g->swap(kept);
+}
+
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
     PlanOptions po;
     po.tile_m = dtype == SV_C64 ? 13 : 12;
@@ -302,6 +316,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         po.tensor = opt->tensor > 0 ? 0 : -1;
         po.pass_kernel = opt->pass_kernel == 1 || opt->pass_kernel == 2 ? opt->pass_kernel : 0;
         po.relabel = opt->relabel == 1 ? 1 : 0;
+        po.drop_phase_below = opt->drop_phase_below > 0.0 && std::isfinite(opt->drop_phase_below) ? opt->drop_phase_below : 0.0;
     }
     if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
@@ -937,6 +952,17 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
                 }
                 recs.push_back(t);
             }
+            // a butterfly followed by a phase table: one record
+            std::vector<GateRec> fused;
+            for (size_t r = 0; r < recs.size(); ++r) {
+                if (recs[r].kind == GR_H && r + 1 < recs.size() && recs[r + 1].kind == GR_DT) {
+                    fused.push_back(GateRec{GR_HD, recs[r].a, recs[r + 1].b, recs[r + 1].off});
+                    ++r;
+                } else {
+                    fused.push_back(recs[r]);
+                }
+            }
+            recs.swap(fused);
             O.mat_off = (int)pay.put_cplx(data, p.dtype);
             O.ndata = (int)data.size();
             O.nrec = (int)recs.size();

@@ -52,3 +52,17 @@ def test_plan_validation_errors():
     g = W.gates_from_list([(W.RX, (0,), (float("nan"),))])
     with pytest.raises(S.SVError):
         S.sv_plan_circuit(2, S.C64, g)
+
+
+def test_plan_drops_small_phases():
+    # QFT n=16 has CP angles pi/2^j, j = 1..15; eps = 1e-3 drops j >= 12
+    # (pi/2^12 = 7.7e-4), i.e. 4 + 3 + 2 + 1 = 10 gates; eps = 0 drops none.
+    g = W.qft(16)
+    assert S.sv_plan_circuit(16, S.C64, g)["gates"] == len(g)
+    assert S.sv_plan_circuit(16, S.C64, g, drop_phase_below=1e-3)["gates"] == len(g) - 10
+    # 2*pi wraps to zero and is dropped, -pi/2^14 has magnitude below 1e-3
+    h = W.gates_from_list([(W.P, (0,), (2 * np.pi,)), (W.RZ, (1,), (-np.pi / 2**14,)),
+                           (W.CP, (0, 1), (0.5,)), (W.H, (0,), ())])
+    assert S.sv_plan_circuit(2, S.C64, h, drop_phase_below=1e-3)["gates"] == 2
+    for off in (0.0, -1.0, float("nan")):  # no approximation
+        assert S.sv_plan_circuit(2, S.C64, h, drop_phase_below=off)["gates"] == 4
