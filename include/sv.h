@@ -106,7 +106,13 @@ typedef enum {
  * angle, reduced to (-pi, pi], is smaller in magnitude than this many radians
  * are left out; the result then differs from the exact circuit by at most
  * the sum of the dropped angles over 2 in norm (0, a negative value or NaN =
- * exact).  reserved: zero. */
+ * exact).  mux: multiplexor recognition (Sec. 2.3, QCrank's uniformly
+ * controlled rotations): a run of RY (or RZ / P / Z) and X gates on one
+ * target interleaved with CX gates into it, whose controls nothing else
+ * changes meanwhile, becomes one block-diagonal operator with per-control-value
+ * angles from a Walsh-Hadamard transform, and up to five such targets share
+ * one pass over the state; exact up to rounding.  0 = runs of at least 64
+ * gates, 1 = runs of at least 4 gates, -1 = off.  At most 16 controls. */
 typedef struct {
     int k_max;
     int tile_m;
@@ -115,7 +121,7 @@ typedef struct {
     int tensor;
     int pass_kernel;
     int relabel;
-    int reserved[1];
+    int mux;
     double drop_phase_below;
 } sv_options;
 
@@ -133,6 +139,8 @@ typedef struct {
     int64_t reg_passes;   /* passes run by the register-resident kernel */
     int64_t remaps;       /* register-layout exchanges over all such passes
                              (per tile) */
+    int64_t mux_ops;      /* recognised multiplexors (each one target) */
+    int64_t mux_passes;   /* passes that apply multiplexors */
 } sv_plan_info;
 
 /* ---- state lifetime (App. A, Eq. "hilbert") ---------------------------- */

@@ -39,13 +39,14 @@ class SVError(RuntimeError):
 class sv_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
                 ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("relabel", ctypes.c_int), ("reserved", ctypes.c_int * 1), ("drop_phase_below", ctypes.c_double)]
+                ("relabel", ctypes.c_int), ("mux", ctypes.c_int), ("drop_phase_below", ctypes.c_double)]
 
 
 class sv_plan_info(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_ops", ctypes.c_int64),
                 ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64),
-                ("gate_ops", ctypes.c_int64), ("reg_passes", ctypes.c_int64), ("remaps", ctypes.c_int64)]
+                ("gate_ops", ctypes.c_int64), ("reg_passes", ctypes.c_int64), ("remaps", ctypes.c_int64),
+                ("mux_ops", ctypes.c_int64), ("mux_passes", ctypes.c_int64)]
 
 
 _lib = None
@@ -121,10 +122,11 @@ def _check(rc):
     return rc
 
 
-def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0, drop_phase_below=0.0):
+def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0, drop_phase_below=0.0,
+          mux=0):
     o = sv_options()
     o.k_max, o.tile_m, o.planner, o.record, o.tensor = k_max, tile_m, planner, record, tensor
-    o.pass_kernel, o.relabel, o.drop_phase_below = pass_kernel, relabel, drop_phase_below
+    o.pass_kernel, o.relabel, o.drop_phase_below, o.mux = pass_kernel, relabel, drop_phase_below, mux
     return o
 
 
@@ -197,16 +199,16 @@ def sv_store_state(h):
 
 
 def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0,
-                     drop_phase_below=0.0):
+                     drop_phase_below=0.0, mux=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel, drop_phase_below)
+    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel, drop_phase_below, mux)
     _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
 
 
 def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, tensor=0, pass_kernel=0,
-                    drop_phase_below=0.0):
+                    drop_phase_below=0.0, mux=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, 0, tensor, pass_kernel, 0, drop_phase_below)
+    o = _opts(k_max, tile_m, planner, 0, tensor, pass_kernel, 0, drop_phase_below, mux)
     info = sv_plan_info()
     _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}
@@ -436,7 +438,7 @@ def sv_mlp_adam(params, grads, steps, lr):
 
 
 # ---- batches ----------------------------------------------------------------
-def sv_batch_run(circuits, dtype=C64, shots=0, seed=0, expz=True, k_max=0, tile_m=0, stream=None):
+def sv_batch_run(circuits, dtype=C64, shots=0, seed=0, expz=True, k_max=0, tile_m=0, stream=None, mux=0):
     """circuits: list of (n, gates).  Returns (samples C x shots uint64 or
     None, expz C x nmax float64 or None)."""
     L = lib()
@@ -457,7 +459,7 @@ def sv_batch_run(circuits, dtype=C64, shots=0, seed=0, expz=True, k_max=0, tile_
     nmax = int(ns.max())
     samp = np.empty((C, shots), dtype=np.uint64) if shots else None
     ez = np.empty((C, nmax), dtype=np.float64) if expz else None
-    o = _opts(k_max, tile_m)
+    o = _opts(k_max, tile_m, mux=mux)
     _check(L.sv_batch_run(C, _ptr(ns), _ptr(offs), _ptr(counts), _ptr(allg), dtype, int(shots), int(seed),
                           ctypes.byref(o), _ptr(samp) if samp is not None else None,
                           _ptr(ez) if ez is not None else None, nmax, stream))

@@ -275,8 +275,14 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
     const size_t before = cg.size();
     drop_small_phases(&cg, po.drop_phase_below);
     Plan plan;
-    if (po.planner == SV_PLAN_PLAIN) plan_plain(n, dt, cg, &plan);
-    else plan_greedy(n, dt, cg, po, &plan);
+    if (po.planner == SV_PLAN_PLAIN) {
+        plan_plain(n, dt, cg, &plan);
+    } else {
+        std::vector<CGate> muxed;
+        std::vector<Mux> muxes;
+        const bool rec = recognise_mux(n, cg, &muxed, &muxes, po.mux);
+        plan_greedy(n, dt, rec ? muxed : cg, po, &plan, &muxes);
+    }
     plan.gates = (int64_t)(count - (before - cg.size()));
     plan_summary(plan, info);
     if (!plan.plain) {  // which passes the register-resident kernel takes
@@ -284,7 +290,7 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
         serialise_plan(plan, &blob);
         const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off);
         for (int i = 0; i < blob.npasses; ++i) {
-            if (!pd[i].rmode) continue;
+            if (pd[i].rmode != 1 && pd[i].rmode != 2) continue;
             info->reg_passes++;
             const OpDev* od = (const OpDev*)(blob.bytes.data() + pd[i].region_off);
             for (int o = 0; o < pd[i].nops; ++o) info->remaps += od[o].kind == OP_REMAP;
@@ -348,9 +354,9 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
         gl = &mapped;
         if (mapped.empty()) return SV_OK;
     }
-    const std::vector<CGate>& cgm = *gl;
     Plan plan;
     if (po.planner == SV_PLAN_PLAIN) {
+        const std::vector<CGate>& cgm = *gl;
         plan_plain(h->n, h->dtype, cgm, &plan);
         for (const PlainOp& op : plan.plain_ops) {
             cudaError_t e = launch_plain_op(h, op);
@@ -358,15 +364,25 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
         }
         return SV_OK;
     }
+    std::vector<CGate> muxed;
+    std::vector<Mux> muxes;
+    if (recognise_mux(h->n, *gl, &muxed, &muxes, po.mux)) {
+        gl = &muxed;
+        salt ^= 0x2545f4914f6cdd1dull + (uint64_t)po.mux;
+    }
+    const std::vector<CGate>& cgm = *gl;
     cudaEvent_t judge0 = nullptr, judge1 = nullptr;
-    if (po.planner == SV_PLAN_MLP) po = mlp_plan_options(h, gates, count, cgm, po, salt, &judge0, &judge1);
-    plan_greedy(h->n, h->dtype, cgm, po, &plan);
+    if (po.planner == SV_PLAN_MLP)
+        po = mlp_plan_options(h, gates, count, cgm, &muxes, po, salt, &judge0, &judge1);
+    plan_greedy(h->n, h->dtype, cgm, po, &plan, &muxes);
     h->last_opts.k_max = po.k_max;
     h->last_opts.tile_m = po.tile_m;
     h->last_opts.planner = opt ? opt->planner : SV_PLAN_GREEDY;
     h->last_opts.tensor = po.tensor == 0 ? 1 : -1;
     h->last_opts.pass_kernel = po.pass_kernel;
     h->last_opts.relabel = po.relabel;
+    h->last_opts.mux = po.mux;
+    h->last_opts.drop_phase_below = po.drop_phase_below;
     PlanBlob blob;
     serialise_plan(plan, &blob);
     // Stage through pinned memory; only the previous upload from it has to
@@ -407,7 +423,7 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
         if (rec && e1) {
             cudaEventRecord(e1, h->stream);
             const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
-            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p], plan.tensor == 0, pd->rmode != 0));
+            h->rec_feat.push_back(pass_features(h->n, h->dtype, plan.passes[p], plan.tensor == 0, pd->rmode == 1 || pd->rmode == 2));
         }
     }
     if (judge1) cudaEventRecord(judge1, h->stream);

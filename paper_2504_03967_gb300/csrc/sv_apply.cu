@@ -1936,6 +1936,7 @@ static cudaError_t rpass_tma_any(sv_state* h, const void* blob_dev, const PlanBl
 
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, const HostPass& hp) {
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    if (pdh->rmode == kRmodeMux) return launch_mux(h, blob_dev, blob, pass);
     if (pdh->rmode) {
         bool used = false;
         cudaError_t e = cudaSuccess;

@@ -53,8 +53,8 @@ int64_t g_planned = 0, g_mispredicted = 0;
 }  // namespace
 
 // Candidates ranked by predicted time (best first); false without a model.
-bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& base,
-                  std::vector<PlanOptions>* ranked, std::vector<double>* ranked_ms) {
+bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const std::vector<Mux>* muxes,
+                  const PlanOptions& base, std::vector<PlanOptions>* ranked, std::vector<double>* ranked_ms) {
     std::vector<PlanOptions> cands;
     const int ms_c64[] = {12, 13, 14}, ms_c128[] = {11, 12, 13};
     for (int k = 2; k <= kMaxK; ++k)
@@ -80,7 +80,7 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanO
     std::vector<int> owner;
     for (size_t c = 0; c < cands.size(); ++c) {
         Plan p;
-        plan_greedy(n, dtype, gates, cands[c], &p);
+        plan_greedy(n, dtype, gates, cands[c], &p, muxes);
         for (HostPass& hp : p.passes) {
             const std::vector<float> f =
                 pass_features(n, dtype, hp, cands[c].tensor == 0, register_pass_eligible(p, hp));
@@ -105,7 +105,8 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const PlanO
 }
 
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
-                             const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0, cudaEvent_t* ev1) {
+                             const std::vector<Mux>* muxes, const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0,
+                             cudaEvent_t* ev1) {
     *ev0 = *ev1 = nullptr;
     uint64_t key = fnv1a(g, count * sizeof(sv_gate), 1469598103934665603ull);
     const int meta[3] = {h->n, h->dtype, base.tensor};
@@ -116,7 +117,7 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
     if (it == g_cache.end()) {
         std::vector<PlanOptions> ranked;
         std::vector<double> rms;
-        if (!rank_options(h->n, h->dtype, cg, base, &ranked, &rms)) return base;  // no model: greedy
+        if (!rank_options(h->n, h->dtype, cg, muxes, base, &ranked, &rms)) return base;  // no model: greedy
         Choice c;
         for (int i = 0; i < kExplore && i < (int)ranked.size(); ++i) c.trial.push_back(ranked[i]);
         c.trial.push_back(base);
@@ -169,7 +170,7 @@ extern "C" int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate* gates, si
     const PlanOptions base = resolve_options(n, dt, nullptr);
     std::vector<PlanOptions> ranked;
     std::vector<double> rms;
-    if (!rank_options(n, dt, cg, base, &ranked, &rms)) return set_error(SV_EINVAL, "no cost model loaded");
+    if (!rank_options(n, dt, cg, nullptr, base, &ranked, &rms)) return set_error(SV_EINVAL, "no cost model loaded");
     memset(chosen, 0, sizeof(*chosen));
     chosen->k_max = ranked[0].k_max;
     chosen->tile_m = ranked[0].tile_m;

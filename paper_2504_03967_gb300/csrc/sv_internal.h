@@ -25,7 +25,9 @@ constexpr int kPassThreads = 256;
 // local bit i <-> qubit q[i]) or diagonal (phase e^{i ph[j]} on local index
 // j, same bit convention).  MEASURE records are dropped.
 // ---------------------------------------------------------------------------
-enum GateKind { GK_DENSE = 0, GK_DIAG = 1 };
+// GK_MUX: a recognised multiplexor standing for a run of gates (q[0] = its
+// target, mux = index into the recognised set).
+enum GateKind { GK_DENSE = 0, GK_DIAG = 1, GK_MUX = 2 };
 
 struct CGate {
     int kind;
@@ -35,6 +37,7 @@ struct CGate {
     double ph[4];   // diag: phases (radians) per local index
     uint32_t type;  // original sv_gate_type
     double p[3];
+    int mux;        // GK_MUX: index of the multiplexor
 };
 
 // Validate and canonicalise; returns SV_OK or SV_EINVAL with *bad = index.
@@ -102,7 +105,43 @@ struct HostOp {
     int ngates = 0;           // logical gates folded into the op
 };
 
+// ---------------------------------------------------------------------------
+// Multiplexors (uniformly controlled rotations, the building block of the
+// QCrank encoder, Sec. 2.3, and of the Mottonen et al. decompositions the
+// paper cites).  A run of gates on one target t whose other qubits are only
+// CX controls collapses to: for each value j of the control bits,
+//     U_j = X^(popcount(j & flip) ^ flip_c)  R_j
+// with R_j = RY(phi[j]) (family Y: RY and X gates) or
+// R_j = diag(e^{i phi0[j]}, e^{i phi1[j]}) (family D: RZ, P, Z and X gates).
+// The angles are one Walsh-Hadamard transform of the run's angles indexed
+// by the CX-parity mask in force at each rotation.
+// ---------------------------------------------------------------------------
+enum MuxFamily { MUX_Y = 0, MUX_D = 1 };
+constexpr int kMuxMaxControls = 16;   // table of 2^16 entries per target at most
+constexpr int kMuxMaxTargets = 5;     // targets per multiplexor pass (2^5 amplitudes per thread)
+constexpr int kMuxMinGates = 64;      // shorter runs stay in the fused tile passes (mux = 0)
+
+struct Mux {
+    int target = -1;
+    std::vector<int> controls;  // ascending; bit b of j <-> controls[b]
+    int family = MUX_Y;
+    uint32_t flip = 0;          // X-parity mask over the j bits at the end of the run
+    int flip_c = 0;             // X gates on the target itself, mod 2
+    std::vector<double> phi0, phi1;  // Y: phi0 = RY angle; D: the two phases
+    int ngates = 0;
+    int type_count[14] = {0};
+};
+
+// Rewrite g into *rewritten, replacing each qualifying run with one GK_MUX
+// gate (placed where the run's last gate was; every gate in between commutes
+// with the run).  mode: 0 runs of at least kMuxMinGates gates, 1 runs of at
+// least 4 gates, -1 none.  Returns false (and leaves *rewritten alone) when
+// no run qualifies.
+bool recognise_mux(int n, const std::vector<CGate>& g, std::vector<CGate>* rewritten, std::vector<Mux>* muxes,
+                   int mode);
+
 struct HostPass {
+    std::vector<int> mux;   // multiplexor pass: indices into Plan::muxes (no tile ops)
     std::vector<int> tile;  // sorted ascending
     int L = 0;              // bits 0..L-1 are in the tile
     std::vector<HostOp> ops;
@@ -129,6 +168,7 @@ struct Plan {
     int tensor = -1;  // 0: dense blocks of k >= kMinTcK go to the tensor cores
     bool no_register_passes = false;
     bool use_tma = false;  // register passes move tiles with TMA tensor copies
+    std::vector<Mux> muxes;
 };
 
 struct PlanOptions {
@@ -139,12 +179,16 @@ struct PlanOptions {
     int pass_kernel = 0;  // 1: shared-memory pass kernel only; 2: register passes fed by TMA
     int relabel = 0;      // SWAP gates relabel qubits
     double drop_phase_below = 0.0;  // approximation: smaller P/RZ/CP angles are dropped
+    int mux = 0;          // multiplexor recognition: 0 long runs, 1 any run of 4+ gates, -1 off
 };
 // The approximation for negligible rotations: the gates kept.
 void drop_small_phases(std::vector<CGate>* g, double eps);
 
 PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
-void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out);
+// GK_MUX gates index muxes (may be null when there are none); the plan keeps
+// a copy of the multiplexors its passes use.
+void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out,
+                 const std::vector<Mux>* muxes = nullptr);
 void plan_plain(int n, int dtype, const std::vector<CGate>& gates, Plan* out);
 void plan_summary(const Plan& p, sv_plan_info* info);
 
@@ -161,7 +205,8 @@ bool register_pass_eligible(const Plan& p, const HostPass& hp);
 // Options for an apply under SV_PLAN_MLP; ev0/ev1 receive events to record
 // around the passes when the judge times this call (else nullptr).
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
-                             const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0, cudaEvent_t* ev1);
+                             const std::vector<Mux>* muxes, const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0,
+                             cudaEvent_t* ev1);
 
 // ---------------------------------------------------------------------------
 // Device-side plan blob: [PassDev x P][tensor-core B operands][pass regions].
@@ -205,7 +250,8 @@ struct PassDev {
     int m;
     int L;
     int rmode;           // register-resident pass (region in the register format): 1 fed by
-                         // cp.async copies, 2 by TMA tensor copies; 0: shared-memory kernel
+                         // cp.async copies, 2 by TMA tensor copies; 0: shared-memory kernel;
+                         // kRmodeMux: multiplexor pass
     int ndiag;           // register passes: diagonal runs (each folded once per tile)
     int nops;            // ops in the pass's region
     int region_off;      // byte offset of the region in the blob
@@ -218,6 +264,28 @@ struct PassDev {
     int nother;
     int oq[40];          // non-tile qubits ascending
 };
+
+// Multiplexor pass (PassDev::rmode == kRmodeMux): the region is MuxDev
+// followed by one angle table per target: 2^nc entries of the state's real
+// type (float for complex64, double for complex128), phi for family Y and
+// (phi0, phi1) pairs for family D, at byte offset tab_off[k] from the region.
+constexpr int kRmodeMux = 3;
+struct MuxDev {
+    int K;                          // targets
+    int nc;                         // control bits
+    int nruns;                      // runs of consecutive control qubits
+    int pad0;
+    int t[kMuxMaxTargets];          // target qubits, ascending
+    int family[kMuxMaxTargets];
+    int flip_c[kMuxMaxTargets];
+    uint32_t flip[kMuxMaxTargets];
+    int tab_off[kMuxMaxTargets];
+    int rs[kMuxMaxControls];        // run r: j bits [ro, ro + rw) = index bits [rs, rs + rw)
+    int rw[kMuxMaxControls];
+    int ro[kMuxMaxControls];
+    int pad1[3];
+};
+static_assert(sizeof(MuxDev) % 16 == 0, "tables after MuxDev stay 16-byte aligned");
 
 // Layout (in 8-byte words of fixed-point turns, 2^-64 turn units) of one
 // diagonal run inside a pass
@@ -277,6 +345,8 @@ struct PlanBlob {
 };
 
 void serialise_plan(const Plan& p, PlanBlob* blob);
+// Region of a multiplexor pass (MuxDev and its tables); sets P->rmode.
+void mux_region(const Plan& p, const HostPass& hp, PassDev* P, std::vector<unsigned char>* out);
 // Several plans (same dtype) in one blob, passes in order.
 void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob);
 
@@ -341,6 +411,7 @@ cudaError_t launch_init_basis(sv_state* h, uint64_t x);
 cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
                         const HostPass& hp);
+cudaError_t launch_mux(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass);
 // One persistent launch for circuits of at most mmax qubits (single-tile
 // plans, one pass each, in blob order); outputs per circuit c at
 // samples + c*shots and expz + c*nmax (either may be NULL).

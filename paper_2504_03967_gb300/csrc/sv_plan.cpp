@@ -317,6 +317,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         po.pass_kernel = opt->pass_kernel == 1 || opt->pass_kernel == 2 ? opt->pass_kernel : 0;
         po.relabel = opt->relabel == 1 ? 1 : 0;
         po.drop_phase_below = opt->drop_phase_below > 0.0 && std::isfinite(opt->drop_phase_below) ? opt->drop_phase_below : 0.0;
+        po.mux = opt->mux < 0 ? -1 : (opt->mux > 0 ? 1 : 0);
     }
     if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
@@ -326,7 +327,10 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
     return po;
 }
 
-void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out) {
+void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out,
+                 const std::vector<Mux>* muxes) {
+    out->muxes.clear();
+    if (muxes) out->muxes = *muxes;
     out->n = n;
     out->dtype = dtype;
     out->plain = false;
@@ -345,21 +349,70 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     std::vector<char> inT(n), blocked(n);
     std::vector<int> executed, deferred;
 
+    int nblocked = 0;
+    auto block = [&](const CGate& g) {
+        for (int i = 0; i < g.nq; ++i)
+            if (!blocked[g.q[i]]) blocked[g.q[i]] = 1, ++nblocked;
+        if (g.kind == GK_MUX)
+            for (int c : out->muxes[g.mux].controls)
+                if (!blocked[c]) blocked[c] = 1, ++nblocked;
+    };
+
     while (!remaining.empty()) {
+        // A multiplexor at the front opens a multiplexor pass: it takes every
+        // later multiplexor that the gates skipped over commute with (no
+        // shared qubit), up to kMuxMaxTargets targets whose controls stay off
+        // the targets and number at most kMuxMaxControls together.
+        if (gates[remaining[0]].kind == GK_MUX) {
+            HostPass pass;
+            std::fill(blocked.begin(), blocked.end(), 0);
+            nblocked = 0;
+            uint64_t tmask = 0, cunion = 0;
+            deferred.clear();
+            for (size_t r = 0; r < remaining.size(); ++r) {
+                const int gi = remaining[r];
+                const CGate& g = gates[gi];
+                bool take = false;
+                uint64_t tm = 0, cm = 0;
+                if (g.kind == GK_MUX && (int)pass.mux.size() < kMuxMaxTargets && nblocked < n) {
+                    const Mux& M = out->muxes[g.mux];
+                    tm = 1ull << M.target;
+                    bool fr = !blocked[M.target];
+                    for (int c : M.controls) {
+                        cm |= 1ull << c;
+                        fr &= !blocked[c];
+                    }
+                    const uint64_t nu = cunion | cm;
+                    take = fr && !(tmask & (tm | cm)) && !(nu & (tmask | tm)) &&
+                           __builtin_popcountll(nu) <= kMuxMaxControls;
+                    if (take) cunion = nu;
+                }
+                if (take) {
+                    const Mux& M = out->muxes[g.mux];
+                    pass.mux.push_back(g.mux);
+                    tmask |= tm;
+                    pass.ngates += M.ngates;
+                    for (int t = 0; t < 14; ++t) pass.type_count[t] += M.type_count[t];
+                } else {
+                    deferred.push_back(gi);
+                    block(g);
+                }
+            }
+            out->passes.push_back(std::move(pass));
+            remaining.swap(deferred);
+            continue;
+        }
         // Scan 1: grow the tile set T from the front of the remaining list.
         std::fill(inT.begin(), inT.end(), 0);
         std::fill(blocked.begin(), blocked.end(), 0);
-        int cnt = 0, nblocked = 0;
+        int cnt = 0;
+        nblocked = 0;
         for (int q = 0; q < L; ++q) inT[q] = 1, ++cnt;
-        auto block = [&](const CGate& g) {
-            for (int i = 0; i < g.nq; ++i)
-                if (!blocked[g.q[i]]) blocked[g.q[i]] = 1, ++nblocked;
-        };
         for (int gi : remaining) {
             const CGate& g = gates[gi];
             bool tb = false;
             for (int i = 0; i < g.nq; ++i) tb |= blocked[g.q[i]] != 0;
-            if (tb) { block(g); }
+            if (tb || g.kind == GK_MUX) { block(g); }
             else if (g.kind == GK_DENSE) {
                 int need = 0;
                 for (int i = 0; i < g.nq; ++i) need += !inT[g.q[i]];
@@ -390,7 +443,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                 tb |= blocked[g.q[i]] != 0;
                 fits &= inT[g.q[i]] != 0;
             }
-            if (!tb && (g.kind == GK_DIAG || fits)) executed.push_back(gi);
+            if (!tb && g.kind != GK_MUX && (g.kind == GK_DIAG || fits)) executed.push_back(gi);
             else { deferred.push_back(gi); block(g); }
         }
 
@@ -555,6 +608,8 @@ void plan_summary(const Plan& p, sv_plan_info* info) {
         info->passes = (int64_t)p.passes.size();
         for (const HostPass& hp : p.passes) {
             bytes += 2.0 * N * s;
+            info->mux_ops += (int64_t)hp.mux.size();
+            info->mux_passes += !hp.mux.empty();
             for (const HostOp& o : hp.ops) {
                 if (o.kind == OP_DENSE || o.kind == OP_GATES) {
                     info->dense_ops++;
@@ -1030,6 +1085,10 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
             P.nother = 0;
             for (int q = 0; q < n; ++q)
                 if (loc[q] < 0) P.oq[P.nother++] = q;
+            if (!hp.mux.empty()) {
+                mux_region(p, hp, &P, &regions[gpi]);
+                continue;
+            }
             if (!p.no_register_passes) {
                 PassDev R = P;
                 if (reg_region(p, hp, &R, loc, &regions[gpi])) {
@@ -1045,7 +1104,7 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
     for (size_t i = 0; i < npass; ++i) {
         pds[i].region_off = (int)roff;
         roff += regions[i].size();
-        blob->max_region = std::max(blob->max_region, pds[i].region_bytes);
+        if (pds[i].rmode != kRmodeMux) blob->max_region = std::max(blob->max_region, pds[i].region_bytes);
     }
     blob->bytes.assign(roff, 0);
     unsigned char* base = blob->bytes.data();

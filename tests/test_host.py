@@ -66,3 +66,24 @@ def test_plan_drops_small_phases():
     assert S.sv_plan_circuit(2, S.C64, h, drop_phase_below=1e-3)["gates"] == 2
     for off in (0.0, -1.0, float("nan")):  # no approximation
         assert S.sv_plan_circuit(2, S.C64, h, drop_phase_below=off)["gates"] == 4
+
+
+def test_plan_recognises_qcrank_multiplexors():
+    # a = 8, d = 7: every data qubit's ladder (2^9 gates) becomes one
+    # multiplexor; five share a pass.
+    a, d = 8, 7
+    g = W.qcrank(a, d, np.random.default_rng(0).uniform(0, 1, size=(1 << a, d)))
+    info = S.sv_plan_circuit(a + d, S.C64, g)
+    assert info["mux_ops"] == d and info["mux_passes"] == 2
+    assert info["gates"] == len(g)
+    assert info["passes"] == 1 + 2  # the Hadamards, then two multiplexor passes
+    off = S.sv_plan_circuit(a + d, S.C64, g, mux=-1)
+    # without it the ladders fill two tile passes with over a hundred fused blocks
+    assert off["mux_ops"] == 0 and off["dense_ops"] > 100 and info["dense_ops"] <= 2
+    # runs shorter than the default threshold stay gates; QFT and random
+    # U3 + CX circuits have no runs at all
+    small = W.qcrank(2, 2, np.full((4, 2), 0.5))
+    assert S.sv_plan_circuit(4, S.C64, small)["mux_ops"] == 0
+    assert S.sv_plan_circuit(4, S.C64, small, mux=1)["mux_ops"] == 2
+    assert S.sv_plan_circuit(20, S.C64, W.qft(20), mux=1)["mux_ops"] == 0
+    assert S.sv_plan_circuit(16, S.C64, W.random_u3_cx(16, 10, 3), mux=1)["mux_ops"] == 0
