@@ -385,6 +385,12 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     h->last_opts.drop_phase_below = po.drop_phase_below;
     PlanBlob blob;
     serialise_plan(plan, &blob);
+    return launch_plan(h, plan, blob, opt && opt->record, judge0, judge1);
+}
+
+int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, cudaEvent_t judge0,
+                cudaEvent_t judge1) {
+    int rc = SV_OK;
     // Stage through pinned memory; only the previous upload from it has to
     // be finished (the passes of earlier calls may still be running).
     cudaError_t e = cudaSuccess;
@@ -413,7 +419,6 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     e = cudaEventRecord(h->upload_ev, h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
     h->upload_pending = true;
-    const bool rec = opt && opt->record;
     if (judge0) cudaEventRecord(judge0, h->stream);
     for (int p = 0; p < blob.npasses; ++p) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <memory>
 #include <thread>
 
 #include "sv_internal.h"
@@ -34,6 +35,11 @@ void parallel_for(int n, F f) {
         });
     for (auto& x : th) x.join();
 }
+
+struct Prepared {
+    Plan plan;
+    PlanBlob blob;
+};
 
 struct Slot {
     cudaStream_t st = nullptr;
@@ -66,12 +72,34 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
     if (!host_expz) nmax = 1;
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
-    // 1. validate and canonicalise every circuit, on host threads
+    // 1. validate and canonicalise every circuit on host threads; circuits
+    //    for the tile-pass path are planned and serialised there too (their
+    //    canonical lists are dropped as soon as the plan exists)
     std::vector<std::vector<CGate>> cg(C);
     std::vector<int> bad(C, 0);
+    const PlanOptions probe = resolve_options(1, dt, opt);
+    const bool host_plans = probe.planner == SV_PLAN_GREEDY && !probe.relabel;
+    std::vector<std::unique_ptr<Prepared>> prep(C);
     parallel_for(C, [&](int c) {
         size_t b = 0;
-        bad[c] = canonicalise(n_qubits[c], gates + gate_offsets[c], (size_t)gate_counts[c], &cg[c], &b) != SV_OK;
+        const int n = n_qubits[c];
+        bad[c] = canonicalise(n, gates + gate_offsets[c], (size_t)gate_counts[c], &cg[c], &b) != SV_OK;
+        if (bad[c] || n <= small_limit(dt) || !host_plans) return;
+        const PlanOptions po = resolve_options(n, dt, opt);
+        std::vector<CGate>& g = cg[c];
+        drop_small_phases(&g, po.drop_phase_below);
+        std::vector<CGate> muxed;
+        std::vector<Mux> muxes;
+        const bool rec = recognise_mux(n, g, &muxed, &muxes, po.mux);
+        std::unique_ptr<Prepared> P(new Prepared);
+        plan_greedy(n, dt, rec ? muxed : g, po, &P->plan, &muxes);
+        serialise_plan(P->plan, &P->blob);
+        for (Mux& M : P->plan.muxes) {  // the blob holds the tables now
+            std::vector<double>().swap(M.phi0);
+            std::vector<double>().swap(M.phi1);
+        }
+        prep[c] = std::move(P);
+        std::vector<CGate>().swap(g);
     });
     for (int c = 0; c < C; ++c)
         if (bad[c]) return set_error(SV_EINVAL, "circuit " + std::to_string(c) + ": invalid gate record");
@@ -192,8 +220,14 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
             const int idx = Cs + (int)i;
             sv_state* h = &slots[i % slots.size()].h;
             h->n = n_qubits[c];
+            reset_perm(h);
             if (launch_init_basis(h, 0) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "init");
-            if (rc == SV_OK) rc = apply_canonical(h, gates + gate_offsets[c], (size_t)gate_counts[c], cg[c], opt);
+            if (rc == SV_OK && prep[c]) {
+                if (prep[c]->blob.npasses > 0) rc = launch_plan(h, prep[c]->plan, prep[c]->blob, false, nullptr, nullptr);
+                prep[c].reset();
+            } else if (rc == SV_OK) {
+                rc = apply_canonical(h, gates + gate_offsets[c], (size_t)gate_counts[c], cg[c], opt);
+            }
             if (rc == SV_OK && host_samples)
                 rc = measure_sample(h, shots, seed + (uint64_t)c, nullptr, d_samples + (size_t)idx * shots);
             if (rc == SV_OK && host_expz) rc = measure_expect_z(h, d_expz + (size_t)idx * nmax);
@@ -207,12 +241,12 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
     if (rc == SV_OK && e != cudaSuccess) rc = cuda_fail(e, "batch");
     std::vector<int> order(small);
     order.insert(order.end(), large.begin(), large.end());
-    if (rc == SV_OK && host_samples) {
-        std::vector<uint64_t> tmp((size_t)C * shots);
-        e = cudaMemcpy(tmp.data(), d_samples, sizeof(uint64_t) * tmp.size(), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = cuda_fail(e, "samples readback");
-        for (int i = 0; rc == SV_OK && i < C; ++i)
-            memcpy(host_samples + (size_t)order[i] * shots, tmp.data() + (size_t)i * shots, sizeof(uint64_t) * shots);
+    if (rc == SV_OK && host_samples) {  // straight into the caller's rows (no staging copy)
+        for (int i = 0; rc == SV_OK && i < C; ++i) {
+            e = cudaMemcpy(host_samples + (size_t)order[i] * shots, d_samples + (size_t)i * shots,
+                           sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) rc = cuda_fail(e, "samples readback");
+        }
     }
     if (rc == SV_OK && host_expz) {
         std::vector<double> tmp((size_t)C * nmax);

@@ -403,6 +403,11 @@ void count_launch(uint64_t k = 1);
 int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
                     const sv_options* opt);
 
+// Upload a serialised plan through h's pinned staging and launch its passes
+// on h's stream (rec: events around each pass; judge0/1: around all of them).
+int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, cudaEvent_t judge0,
+                cudaEvent_t judge1);
+
 int ensure_scratch(Scratch* s, size_t bytes, cudaStream_t st);
 int ensure_pinned(Scratch* s, size_t bytes);
 
@@ -421,7 +426,7 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
 size_t batch_small_smem_bytes(int dtype, int mmax);
 
 // Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
-int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks);
+int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks, int blog_cap = 10);
 cudaError_t launch_probs(sv_state* h, double* dev_out);
 // Amplitudes of logical indices x0 .. x0+cnt-1 into dev_out (the handle's dtype).
 cudaError_t launch_gather_logical(sv_state* h, uint64_t x0, uint64_t cnt, void* dev_out);

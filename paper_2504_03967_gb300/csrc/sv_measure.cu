@@ -333,18 +333,27 @@ int sms() {
 }
 
 // Scratch layout in h->red: [block sums/cdf: nblocks][chunk totals: nch][expz partials]
-size_t nblocks_of(int n, int* blog) {
-    *blog = n < kBlogMax ? n : kBlogMax;
+size_t nblocks_of(int n, int* blog, int cap = kBlogMax) {
+    *blog = n < cap ? n : cap;
     return (size_t)1 << (n - *blog);
+}
+
+// Block size for sampling: a shot scans one block, so with many shots
+// smaller blocks keep the shots' work (shots * 2^blog amplitudes) within
+// one read of the state; the block CDF then has more entries to search.
+int sample_blog(int n, uint64_t shots) {
+    int b = kBlogMax;
+    while (b > 5 && ldexp((double)shots, b) > ldexp(1.0, n)) --b;
+    return b;
 }
 }  // namespace
 
 // Block statistics in h->red: [raw block totals: nb][inclusive CDF: nb]
 // [chunk totals: nch][bit sums: 10 nb, when asked for].
 static int block_stats(sv_state* h, bool want_bits, double** tot_out, double** cdf_out, double** bits_out,
-                       int* blog_out, int64_t* nb_out) {
+                       int* blog_out, int64_t* nb_out, int blog_cap = kBlogMax) {
     int blog;
-    const size_t nb = nblocks_of(h->n, &blog);
+    const size_t nb = nblocks_of(h->n, &blog, blog_cap);
     const size_t nch = (nb + kScanCh - 1) / kScanCh;
     const size_t need = sizeof(double) * (2 * nb + nch + 64 + (want_bits ? 10 * nb : 0));
     int rc = ensure_scratch(&h->red, need, h->stream);
@@ -469,8 +478,8 @@ cudaError_t launch_gather_logical(sv_state* h, uint64_t x0, uint64_t cnt, void* 
     return cudaGetLastError();
 }
 
-int measure_block_sums(sv_state* h, double** cdf, int* blog_out, int64_t* nb_out) {
-    return block_stats(h, false, nullptr, cdf, nullptr, blog_out, nb_out);
+int measure_block_sums(sv_state* h, double** cdf, int* blog_out, int64_t* nb_out, int blog_cap) {
+    return block_stats(h, false, nullptr, cdf, nullptr, blog_out, nb_out, blog_cap);
 }
 
 cudaError_t launch_probs(sv_state* h, double* dev_out) {
@@ -556,7 +565,7 @@ int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev
     double* cdf;
     int blog;
     int64_t nb;
-    int rc = measure_block_sums(h, &cdf, &blog, &nb);
+    int rc = measure_block_sums(h, &cdf, &blog, &nb, sample_blog(h->n, shots));
     if (rc) return rc;
     cudaError_t e = launch_sample(h, blog, cdf, nb, shots, seed, dev_u, dev_out);
     if (e == cudaSuccess) e = to_logical_samples(h, dev_out, shots);
