@@ -232,6 +232,30 @@ int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_out);
 int sv_sample_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_out);
 int sv_sample_uniforms(sv_handle h, const double *host_u, uint64_t shots, uint64_t *host_out);
 
+/* QCrank read-out (Sec. 2.3, Table 2).  A QCrank state holds a uniform
+ * superposition over a address qubits (bits 0..a-1 of an outcome) with data
+ * qubit k (bit a+k) rotated by RY(pi * pixel[j][k]), so that
+ * P(bit a+k = 1 | address j) = sin^2(pi * pixel[j][k] / 2).  From shots:
+ *   counts[j]   = shots whose address bits equal j,
+ *   ones[j*d+k] = of those, the shots with bit a+k set,
+ *   pixels[j*d+k] = (2/pi) * asin(sqrt(ones[j*d+k] / counts[j])),
+ * NaN where counts[j] = 0.  Bits above a+d-1 are ignored.
+ * sv_qcrank_decode_device: every pointer is device memory (samples: shots
+ * uint64 outcomes; counts: 2^a uint64; ones: 2^a*d uint64; pixels: 2^a*d
+ * doubles, row-major [address][data qubit]), owned by the caller; the work
+ * is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * without synchronising and without allocating.
+ * sv_qcrank_reconstruct: draws `shots` outcomes of the state as sv_sample
+ * does (same seed, same shots), decodes them on the device (the shots never
+ * leave it) and copies pixels (2^a*d doubles) and, if host_counts is not
+ * NULL, counts (2^a) to the host.  Table 2 uses 3000 * 2^a shots.
+ * Errors: SV_EINVAL for NULL buffers, a < 1, d < 1, d > 32, a > 26, a + d > 63
+ * (sv_qcrank_reconstruct: a + d > n). */
+int sv_qcrank_decode_device(const uint64_t *samples, uint64_t shots, int a, int d, uint64_t *counts,
+                            uint64_t *ones, double *pixels, void *stream);
+int sv_qcrank_reconstruct(sv_handle h, int a, int d, uint64_t shots, uint64_t seed, double *host_pixels,
+                          uint64_t *host_counts);
+
 /* Shots (as sv_sample_device) and <Z_i> (as sv_expect_z_device) from ONE
  * pass over the state: the probability block statistics are computed once
  * and serve both.  Either output may be NULL (shots then ignored). */

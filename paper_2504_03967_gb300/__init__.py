@@ -85,6 +85,8 @@ def lib():
             "sv_sample_uniforms": [vp, vp, u64, vp],
             "sv_pass_times": [vp, vp, vp, i, P(i)],
             "sv_sample_uniforms_noalloc": [vp, i, i, vp, u64, vp, vp],
+            "sv_qcrank_decode_device": [vp, u64, i, i, vp, vp, vp, vp],
+            "sv_qcrank_reconstruct": [vp, i, i, u64, u64, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -265,6 +267,23 @@ def sv_sample(h, shots, seed):
     out = np.empty(int(shots), dtype=np.uint64)
     _check(lib().sv_sample(h, int(shots), int(seed), _ptr(out)))
     return out
+
+
+def sv_qcrank_reconstruct(h, a, d, shots, seed):
+    """QCrank read-out of the state (shots drawn as sv_sample draws them,
+    decoded on the device).  Returns (pixels [2^a, d], counts [2^a])."""
+    pix = np.empty((1 << a, d), dtype=np.float64)
+    counts = np.empty(1 << a, dtype=np.uint64)
+    _check(lib().sv_qcrank_reconstruct(h, int(a), int(d), int(shots), int(seed), _ptr(pix), _ptr(counts)))
+    return pix, counts
+
+
+def sv_qcrank_decode_device(samples_ptr, shots, a, d, counts_ptr, ones_ptr, pixels_ptr, stream=None):
+    """Device buffers (integer addresses): shots uint64 outcomes -> counts
+    [2^a] uint64, ones [2^a * d] uint64, pixels [2^a * d] float64."""
+    vp = ctypes.c_void_p
+    _check(lib().sv_qcrank_decode_device(vp(samples_ptr), int(shots), int(a), int(d), vp(counts_ptr), vp(ones_ptr),
+                                         vp(pixels_ptr), vp(stream) if stream else None))
 
 
 def sv_sample_device(h, shots, seed, dev_out_ptr):

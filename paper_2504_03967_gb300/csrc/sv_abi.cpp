@@ -191,6 +191,7 @@ int sv_free(sv_handle h) {
     if (h->out_dev.ptr) cudaFree(h->out_dev.ptr);
     if (h->err.ptr) cudaFree(h->err.ptr);
     if (h->perm_tmp.ptr) cudaFree(h->perm_tmp.ptr);
+    if (h->aux.ptr) cudaFree(h->aux.ptr);
     if (h->host_pin.ptr) cudaFreeHost(h->host_pin.ptr);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->upload_ev) cudaEventDestroy(h->upload_ev);
@@ -523,6 +524,40 @@ int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t* host_out) {
     rc = measure_sample(h, shots, seed, nullptr, (uint64_t*)h->out_dev.ptr);
     if (rc) return fail_state(h, rc);
     return sync_d2h(h, host_out, h->out_dev.ptr, sizeof(uint64_t) * shots, "sample readback");
+}
+
+int sv_qcrank_decode_device(const uint64_t* samples, uint64_t shots, int a, int d, uint64_t* counts, uint64_t* ones,
+                            double* pixels, void* stream) {
+    if (a < 1 || d < 1 || d > 32 || a > kQcrankMaxAddr || a + d > 63) return set_error(SV_EINVAL, "a or d out of range");
+    if ((shots && !samples) || !counts || !ones || !pixels) return set_error(SV_EINVAL, "NULL buffer");
+    cudaError_t e = launch_qcrank_decode(samples, shots, a, d, counts, ones, pixels, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "qcrank decode");
+    return SV_OK;
+}
+
+int sv_qcrank_reconstruct(sv_handle h, int a, int d, uint64_t shots, uint64_t seed, double* host_pixels,
+                          uint64_t* host_counts) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (a < 1 || d < 1 || d > 32 || a > kQcrankMaxAddr || a + d > h->n) return set_error(SV_EINVAL, "a or d out of range");
+    if (!host_pixels) return set_error(SV_EINVAL, "NULL output");
+    const size_t J = (size_t)1 << a;
+    const size_t bytes = sizeof(uint64_t) * (shots + J + J * d) + sizeof(double) * J * d;
+    rc = ensure_scratch(&h->aux, bytes, h->stream);
+    if (rc) return rc;
+    uint64_t* samples = (uint64_t*)h->aux.ptr;
+    uint64_t* counts = samples + shots;
+    uint64_t* ones = counts + J;
+    double* pixels = (double*)(ones + J * d);
+    rc = measure_sample(h, shots, seed, nullptr, samples);
+    if (rc) return fail_state(h, rc);
+    cudaError_t e = launch_qcrank_decode(samples, shots, a, d, counts, ones, pixels, h->stream);
+    if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "qcrank decode"));
+    if (host_counts) {
+        rc = sync_d2h(h, host_counts, counts, sizeof(uint64_t) * J, "qcrank counts");
+        if (rc) return rc;
+    }
+    return sync_d2h(h, host_pixels, pixels, sizeof(double) * J * d, "qcrank pixels");
 }
 
 int sv_sample_uniforms(sv_handle h, const double* host_u, uint64_t shots, uint64_t* host_out) {

@@ -16,6 +16,7 @@ using cd = std::complex<double>;
 
 constexpr int kMaxQubitsC64 = 34;
 constexpr int kMaxQubitsC128 = 33;
+constexpr int kQcrankMaxAddr = 26;  // address qubits of the QCrank read-out
 constexpr int kMaxK = 5;         // widest fused dense block
 constexpr int kMaxTileM = 14;    // qubits per shared-memory tile
 constexpr int kPassThreads = 256;
@@ -381,6 +382,7 @@ struct sv_state {
     int perm[64];            // logical qubit -> physical bit of the stored amplitudes
     bool permuted;           // perm is not the identity
     sv::Scratch perm_tmp;    // device scratch of the permuted read-outs
+    sv::Scratch aux;         // device scratch of the QCrank read-out (shots, counters, pixels)
     sv_options last_opts;    // options of the last planned apply
 };
 
@@ -434,6 +436,11 @@ int measure_norm(sv_state* h, double* host_out);
 int measure_expect_z(sv_state* h, double* dev_out);
 // Shots and <Z_i> from one pass over the state (either output may be NULL).
 int measure_readout(sv_state* h, uint64_t shots, uint64_t seed, uint64_t* dev_samples, double* dev_expz);
+
+// QCrank read-out (sv_qcrank.cu): counts[2^a], ones[2^a * d] and pixels
+// [2^a * d] from shots, all device memory, enqueued on st.
+cudaError_t launch_qcrank_decode(const uint64_t* samples, uint64_t shots, int a, int d, uint64_t* counts,
+                                 uint64_t* ones, double* pixels, cudaStream_t st);
 int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev_u, uint64_t* dev_out);
 
 }  // namespace sv
