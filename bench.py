@@ -41,6 +41,26 @@ METRIC = "amplitude updates/s and % HBM roofline, learned-fused vs plain, F≥1-
 UNIT = "amp_updates/s"
 
 
+# DRAM traffic of the tile pass per amplitude per launch, from the ncu capture
+# summarised in profiles/ (QFT n=26 complex64, k_max 5, tile 14, the 3 passes
+# of one step; dram__bytes_read.sum + dram__bytes_write.sum), valid only for
+# the kernel and planner sources it was taken with (SHA-256 over the files
+# below); a changed kernel reports traffic null until it is captured again.
+TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
+                   "paper_2504_03967_gb300/csrc/sv_internal.h"]
+TRAFFIC = {"sha256": None, "bytes_per_amp": None, "profile": None}
+
+
+def sources_sha():
+    import hashlib
+
+    hsh = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -187,6 +207,120 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _event_ms(torch, stream, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(reps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def report_approx(args):
+    """QFT n (default 28) complex64 with P/RZ/CP gates below eps dropped:
+    1 - F against the closed form QFT|x> = N^-1/2 sum_y e^{2 pi i x y / N}|y>
+    over the full state (on the device, in chunks), the bound
+    (sum of dropped |lambda| / 2)^2, and the fused apply time."""
+    import torch
+
+    import paper_2504_03967_gb300 as S
+
+    n = int(args.workload[3:]) if args.workload.startswith("qft") else 28
+    g = W.qft(n)
+    x = W.random_basis_index(n, W.SEED[2])
+    N = 1 << n
+    stream = torch.cuda.current_stream()
+    state = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    h = S.sv_attach(n, S.C64, state.data_ptr(), stream.cuda_stream)
+    lam = np.array([abs(np.remainder(r["p"][0] + np.pi, 2 * np.pi) - np.pi) for r in g if r["type"] == W.CP])
+    rows = []
+    for eps in [0.0, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 3e-2, 1e-1]:
+        def run(i):
+            S.sv_init_basis(h, x)
+            S.sv_apply_circuit(h, g, relabel=1, drop_phase_below=eps)
+        for i in range(3):
+            run(i)
+        ms = _event_ms(torch, stream, run, 5)
+        run(0)
+        S.sv_materialize(h)  # logical order, to compare index by index
+        st = state.view(torch.complex64)
+        ov = torch.zeros((), dtype=torch.complex128, device="cuda")
+        nrm = torch.zeros((), dtype=torch.float64, device="cuda")
+        C = 1 << 24
+        for off in range(0, N, C):
+            y = torch.arange(off, min(N, off + C), dtype=torch.int64, device="cuda")
+            ph = ((x * y) % N).to(torch.float64) * (2.0 * np.pi / N)
+            ref = torch.polar(torch.full_like(ph, N ** -0.5), ph)
+            got = st[off:off + len(y)].to(torch.complex128)
+            ov += (ref.conj() * got).sum()
+            nrm += (got.abs() ** 2).sum()
+        F = float(abs(ov.item()) ** 2 / nrm.item())
+        dropped = lam[lam < eps] if eps > 0 else lam[:0]
+        kept = S.sv_plan_circuit(n, S.C64, g[g["type"] != W.SWAP], drop_phase_below=eps)["gates"]
+        rows.append({"eps": eps, "gates_dropped": int(len(dropped)), "gates_applied": int(kept),
+                     "one_minus_F": max(0.0, 1.0 - F), "bound": float((dropped.sum() / 2) ** 2),
+                     "ms_per_apply": ms})
+    S.sv_free(h)
+    print(json.dumps({"report": "approximate QFT (drop P/RZ/CP below eps)", "n": n, "dtype": "c64",
+                      "reference": "closed form, full state", "rows": rows}), flush=True)
+
+
+def report_batch(args):
+    """Circuits/s end to end through sv_batch_run (host gate lists in,
+    planning included, outputs back): the QCrank batch (512 circuits,
+    a ~ U{8..14}, d ~ U{4..10}, 10^5 shots each) and the ansatz sweep
+    (4096 parameter sets, n = 20, 8 layers, <Z_i>); and the QCrank read-out
+    of Table 2's a = 14 row (3000 * 2^14 shots sampled and decoded on the
+    device)."""
+    import torch
+
+    import paper_2504_03967_gb300 as S
+
+    out = {"report": "batches and QCrank read-out"}
+    batch = W.qcrank_batch(512, W.SEED[3], a_range=(8, 14))
+    circuits = [(a + d, W.qcrank(a, d, pix)) for a, d, pix in batch]
+    gates = int(sum(len(gl) for _, gl in circuits))
+    S.sv_batch_run(circuits, dtype=S.C64, shots=100000, seed=31)
+    t0 = time.perf_counter()
+    S.sv_batch_run(circuits, dtype=S.C64, shots=100000, seed=31)
+    dt = time.perf_counter() - t0
+    out["qcrank_batch"] = {"circuits": 512, "gates": gates, "shots_per_circuit": 100000, "seconds": dt,
+                           "circuits_per_s": 512 / dt}
+    # the same first 32 circuits with and without multiplexor recognition
+    for mux, tag in ((0, "qcrank_first32"), (-1, "qcrank_first32_no_mux")):
+        t0 = time.perf_counter()
+        S.sv_batch_run(circuits[:32], dtype=S.C64, shots=100000, seed=31, mux=mux)
+        dt = time.perf_counter() - t0
+        out[tag] = {"circuits": 32, "seconds": dt, "circuits_per_s": 32 / dt}
+    params = W.hea_params(4096, 20, 8, W.SEED[5])
+    hc = [(20, W.hea(20, 8, params[s])) for s in range(4096)]
+    S.sv_batch_run(hc[:256], dtype=S.C64, shots=0)
+    t0 = time.perf_counter()
+    S.sv_batch_run(hc, dtype=S.C64, shots=0)
+    dt = time.perf_counter() - t0
+    out["ansatz_sweep"] = {"circuits": 4096, "n": 20, "seconds": dt, "circuits_per_s": 4096 / dt}
+    a, d = 14, 6
+    pix = np.random.default_rng(5).uniform(0, 1, size=(1 << a, d))
+    h = S.sv_alloc(a + d, S.C64)
+    S.sv_init_basis(h, 0)
+    S.sv_apply_circuit(h, W.qcrank(a, d, pix))
+    shots = 3000 << a
+    S.sv_qcrank_reconstruct(h, a, d, shots, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rec, counts = S.sv_qcrank_reconstruct(h, a, d, shots, 2)
+    dt = time.perf_counter() - t0
+    S.sv_free(h)
+    err = rec - pix
+    c = np.corrcoef(rec.ravel(), pix.ravel())[0, 1]
+    out["qcrank_readout"] = {"a": a, "d": d, "shots": shots, "seconds": dt, "shots_per_s": shots / dt,
+                             "rms_pixel_error": float(np.sqrt(np.mean(err ** 2))),
+                             "shot_noise_rms": float(1.0 / (np.pi * np.sqrt(3000))), "correlation": float(c)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,10 +340,18 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-gates", type=int, default=4)
     ap.add_argument("--no-relabel", action="store_true", help="SWAP gates move amplitudes instead of relabelling")
+    ap.add_argument("--report", default=None, choices=["approx", "batch"],
+                    help="secondary measurements instead of the bench line: approx = QFT fidelity loss and time "
+                         "against the rotation-dropping threshold; batch = circuits/s of the QCrank and "
+                         "ansatz batches and the QCrank read-out")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.report == "approx":
+        return report_approx(args)
+    if args.report == "batch":
+        return report_batch(args)
 
     import torch
 
@@ -315,7 +457,11 @@ def main():
         roof = {"bound": "hbm", "kernel": "tile pass (k_rpass register-resident / k_pass shared-memory)",
                 "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": src,
-                "frac_of_8tbs_nominal": achieved / 8000.0, "traffic": None,
+                "frac_of_8tbs_nominal": achieved / 8000.0,
+                "traffic": (TRAFFIC["bytes_per_amp"] * float(1 << n)
+                            if TRAFFIC["bytes_per_amp"] and TRAFFIC["sha256"] == sources_sha() and dt == S.C64
+                            else None),
+                "traffic_source": TRAFFIC["profile"],
                 "launches_timed": int(len(pass_ms)), "mean_launch_ms": float(np.mean(pass_ms)),
                 "step_frac": float(np.sum(pass_ms)) / args.steps / ms}
 
