@@ -48,7 +48,8 @@ UNIT = "amp_updates/s"
 # below); a changed kernel reports traffic null until it is captured again.
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h"]
-TRAFFIC = {"sha256": None, "bytes_per_amp": None, "profile": None}
+TRAFFIC = {"sha256": "26bfce770412e902ec20d5cde355e514f30f73972bb8ebcea47bd0fadd6f470a",
+           "bytes_per_amp": 15.3154, "profile": "profiles/k_rpass_qft26_c64_k5m14.md (n=26 capture, scaled to 2^n)"}
 
 
 def sources_sha():
