@@ -162,7 +162,7 @@ def train_cost_model(S, dt, n):
             hh = h if nq == n else S.sv_alloc(nq, dt)
             for k, m, t, pk in cands:
                 S.sv_init_basis(hh, 0)
-                S.sv_apply_circuit(hh, g, k_max=k, tile_m=m, tensor=t, pass_kernel=pk, record=1)
+                S.sv_apply_circuit(hh, g, k_max=k, tile_m=m, tensor=t, pass_kernel=pk, record=1, jit=-1)
                 ms, f = S.sv_pass_times(hh, features=True)
                 feats.append(f)
                 times.append(ms)
@@ -341,6 +341,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-gates", type=int, default=4)
     ap.add_argument("--no-relabel", action="store_true", help="SWAP gates move amplitudes instead of relabelling")
+    ap.add_argument("--no-jit", action="store_true", help="register passes on the interpreting kernel only")
     ap.add_argument("--report", default=None, choices=["approx", "batch"],
                     help="secondary measurements instead of the bench line: approx = QFT fidelity loss and time "
                          "against the rotation-dropping threshold; batch = circuits/s of the QCrank and "
@@ -381,11 +382,12 @@ def main():
     updates = float(len(g)) * float(1 << n)
 
     relabel = 0 if args.no_relabel else 1
+    jit = -1 if args.no_jit else 1
 
     def step(i, pl, record):
         S.sv_init_basis(h, x)
         S.sv_apply_circuit(h, g, planner=pl, k_max=args.k, tile_m=args.tile_m, record=record, tensor=args.tensor,
-                           relabel=relabel)
+                           relabel=relabel, jit=jit)
         S.sv_measure_device(h, args.shots, 1000 + i, shots_out.data_ptr(), ez_out.data_ptr())
 
     def barrier():
@@ -484,7 +486,7 @@ def main():
         for i in range(2):
             S.sv_init_basis(h2, x)
             S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
-                               relabel=relabel)
+                               relabel=relabel, jit=jit)
             S.sv_sample(h2, args.shots, i)
             S.sv_expect_z(h2)
         torch.cuda.synchronize()
@@ -493,7 +495,7 @@ def main():
         for i in range(K):
             S.sv_init_basis(h2, x)
             S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
-                               relabel=relabel)
+                               relabel=relabel, jit=jit)
             S.sv_sample(h2, args.shots, 1000 + i)
             S.sv_expect_z(h2)
         e2e_ms = 1e3 * (time.perf_counter() - t0) / K
@@ -507,7 +509,7 @@ def main():
         st = state.view(torch.complex64 if dt == S.C64 else torch.complex128)
         S.sv_init_basis(h, x)
         S.sv_apply_circuit(h, g, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
-                           relabel=relabel)
+                           relabel=relabel, jit=jit)
         torch.cuda.synchronize()
         rng = np.random.default_rng(0)
         ys = rng.integers(0, 1 << n, size=1 << 16)
@@ -534,6 +536,8 @@ def main():
                        "passes": plan["passes"], "plan_options": plan_opts,
                        "parallelism": "replicas" if world > 1 else "single",
                        "swap_gates": "qubit relabelling (read-outs honour the map)" if relabel else "data movement",
+                       "register_passes": "compiled at run time per pass structure (NVRTC)" if jit > 0
+                       else "interpreting kernel", "jit": S.sv_jit_stats(),
                        "l2": "inputs larger than L2 (state %d MiB)" % ((amp_b << n) >> 20)},
             "roofline": roof, "plain": plain, "greedy": greedy, "cost_model": cm, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clk.summary(), "check": fid}

@@ -112,7 +112,14 @@ typedef enum {
  * changes meanwhile, becomes one block-diagonal operator with per-control-value
  * angles from a Walsh-Hadamard transform, and up to five such targets share
  * one pass over the state; exact up to rounding.  0 = runs of at least 64
- * gates, 1 = runs of at least 4 gates, -1 = off.  At most 16 controls. */
+ * gates, 1 = runs of at least 4 gates, -1 = off.  At most 16 controls.
+ * jit: register-resident passes as kernels compiled at run time (NVRTC) for
+ * their structure -- op sequence, gate positions, table masks and register
+ * layouts fixed in the code, the data still read from the plan -- and cached
+ * for the process: 0 = compile a structure the second time it runs (the
+ * first run and one-off circuits stay on the library's interpreting kernel),
+ * 1 = compile on first use, -1 = never.  Results agree with the interpreting
+ * kernel to rounding; where NVRTC is missing the interpreting kernel runs. */
 typedef struct {
     int k_max;
     int tile_m;
@@ -123,6 +130,7 @@ typedef struct {
     int relabel;
     int mux;
     double drop_phase_below;
+    int jit;
 } sv_options;
 
 /* Plan summary returned by sv_plan_circuit (host only, no device work). */

@@ -39,7 +39,8 @@ class SVError(RuntimeError):
 class sv_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tile_m", ctypes.c_int), ("planner", ctypes.c_int),
                 ("record", ctypes.c_int), ("tensor", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("relabel", ctypes.c_int), ("mux", ctypes.c_int), ("drop_phase_below", ctypes.c_double)]
+                ("relabel", ctypes.c_int), ("mux", ctypes.c_int), ("drop_phase_below", ctypes.c_double),
+                ("jit", ctypes.c_int)]
 
 
 class sv_plan_info(ctypes.Structure):
@@ -125,10 +126,10 @@ def _check(rc):
 
 
 def _opts(k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0, drop_phase_below=0.0,
-          mux=0):
+          mux=0, jit=0):
     o = sv_options()
     o.k_max, o.tile_m, o.planner, o.record, o.tensor = k_max, tile_m, planner, record, tensor
-    o.pass_kernel, o.relabel, o.drop_phase_below, o.mux = pass_kernel, relabel, drop_phase_below, mux
+    o.pass_kernel, o.relabel, o.drop_phase_below, o.mux, o.jit = pass_kernel, relabel, drop_phase_below, mux, jit
     return o
 
 
@@ -201,9 +202,9 @@ def sv_store_state(h):
 
 
 def sv_apply_circuit(h, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, record=0, tensor=0, pass_kernel=0, relabel=0,
-                     drop_phase_below=0.0, mux=0):
+                     drop_phase_below=0.0, mux=0, jit=0):
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel, drop_phase_below, mux)
+    o = _opts(k_max, tile_m, planner, record, tensor, pass_kernel, relabel, drop_phase_below, mux, jit)
     _check(lib().sv_apply_circuit(h, _ptr(g), len(g), ctypes.byref(o)))
 
 
@@ -267,6 +268,42 @@ def sv_sample(h, shots, seed):
     out = np.empty(int(shots), dtype=np.uint64)
     _check(lib().sv_sample(h, int(shots), int(seed), _ptr(out)))
     return out
+
+
+def sv_jit_check(n, dtype, gates, arch=103, **opts):
+    """Host-only: write and compile (NVRTC, no GPU) the run-time kernel of
+    every register-resident pass of the circuit's plan.  Returns the number
+    of passes compiled; raises SVError with the compiler log on a failure."""
+    g = as_gates(gates)
+    o = _opts(**opts)
+    L = lib()
+    f = L.sv_jit_check
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(sv_options), ctypes.c_int,
+                  ctypes.POINTER(ctypes.c_int), ctypes.c_char_p, ctypes.c_size_t]
+    f.restype = ctypes.c_int
+    cnt = ctypes.c_int(0)
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = f(n, dtype, _ptr(g), len(g), ctypes.byref(o), arch, ctypes.byref(cnt), buf, len(buf))
+    if rc != 0:
+        raise SVError(rc, L.sv_last_error().decode() + "\n" + buf.value.decode(errors="replace"))
+    return cnt.value
+
+
+def sv_jit_stats():
+    """(kernels compiled, compiles failed, passes launched on them, compile ms)."""
+    L = lib()
+    f = L.sv_jit_stats
+    f.argtypes = [ctypes.c_void_p] * 4
+    f.restype = ctypes.c_int
+    c, fl, ln = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(f(ctypes.byref(c), ctypes.byref(fl), ctypes.byref(ln), ctypes.byref(ms)))
+    return {"compiled": c.value, "failed": fl.value, "launched": ln.value, "compile_ms": ms.value}
+
+
+def sv_jit_wait():
+    """Block until background pass compiles have finished."""
+    _check(lib().sv_jit_wait())
 
 
 def sv_qcrank_reconstruct(h, a, d, shots, seed):

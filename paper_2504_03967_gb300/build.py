@@ -34,7 +34,8 @@ def sources():
 
 
 def _deps_mtime():
-    files = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INC, "*.h"))
+    files = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+             glob.glob(os.path.join(INC, "*.h")))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 
@@ -62,7 +63,7 @@ def build(force=False, verbose=False, extra=()):
             if err.strip():
                 sys.stderr.write(err)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

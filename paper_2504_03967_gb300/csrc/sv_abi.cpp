@@ -383,6 +383,7 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     h->last_opts.pass_kernel = po.pass_kernel;
     h->last_opts.relabel = po.relabel;
     h->last_opts.mux = po.mux;
+    h->last_opts.jit = po.jit;
     h->last_opts.drop_phase_below = po.drop_phase_below;
     PlanBlob blob;
     serialise_plan(plan, &blob);
@@ -420,11 +421,15 @@ int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, c
     e = cudaEventRecord(h->upload_ev, h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
     h->upload_pending = true;
+    std::vector<void*> jit_fns;
+    jit_prepare(h, blob, plan.jit, &jit_fns);
     if (judge0) cudaEventRecord(judge0, h->stream);
     for (int p = 0; p < blob.npasses; ++p) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (rec && (e0 = next_event(h)) && (e1 = next_event(h))) cudaEventRecord(e0, h->stream);
-        e = launch_pass(h, h->plan_dev.ptr, blob, p, plan.passes[p]);
+        bool jitted = false;
+        e = jit_launch(h, jit_fns[p], h->plan_dev.ptr, blob, p, &jitted);
+        if (e == cudaSuccess && !jitted) e = launch_pass(h, h->plan_dev.ptr, blob, p, plan.passes[p]);
         if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "tile pass kernel"));
         if (rec && e1) {
             cudaEventRecord(e1, h->stream);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "sv.h"
+#include "sv_dev.h"
 
 namespace sv {
 
@@ -17,9 +18,6 @@ using cd = std::complex<double>;
 constexpr int kMaxQubitsC64 = 34;
 constexpr int kMaxQubitsC128 = 33;
 constexpr int kQcrankMaxAddr = 26;  // address qubits of the QCrank read-out
-constexpr int kMaxK = 5;         // widest fused dense block
-constexpr int kMaxTileM = 14;    // qubits per shared-memory tile
-constexpr int kPassThreads = 256;
 
 // ---------------------------------------------------------------------------
 // Canonical gates (host, FP64).  A gate is either dense (a 2^k x 2^k matrix,
@@ -50,27 +48,6 @@ int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out,
 // 2^L amplitudes is contiguous), applies its ops in shared memory and writes
 // the tile back: one HBM read and one write of the state per pass.
 // ---------------------------------------------------------------------------
-enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2, OP_REMAP = 3 };
-
-// Register-resident passes: each thread holds 2^kRegBits amplitudes of the
-// tile in registers; the other m - kRegBits tile bits index the thread.
-__host__ __device__ inline int reg_bits(int dtype) { return dtype == SV_C64 ? 5 : 4; }
-constexpr int kRegDenseMaxK = 3;  // dense blocks in registers (wider ones run as gate sequences)
-constexpr int kStageCap = 48 * 1024;  // bytes of a pass region staged in shared memory
-
-// Gate-sequence block records (positions are block-local bits, data offsets
-// index the op's own complex values).
-enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4, GR_H = 5, GR_HD = 6 };
-// GR_HD (register passes only): GR_H on position a followed by the phase table
-// at off with entry mask b (one dispatch for the pair).
-// GR_H (register passes only): the Hadamard without its 1/sqrt(2), a + b and
-// a - b; the pass multiplies its amplitudes by the product of the dropped
-// factors once, when it writes them back (PassDev::scale).
-struct GateRec {
-    int kind, a, b, off;
-};
-constexpr int kMaxGateRecs = 64;     // records per gate-sequence op
-constexpr int kMaxGateData = 768;    // complex values per gate-sequence op
 // Widest gate-sequence block: its 2^k amplitudes per thread stay in
 // registers (64 registers of data at the bound, for both dtypes).  The
 // shared-memory pass kernel, which holds more state per thread, takes one
@@ -169,6 +146,7 @@ struct Plan {
     int tensor = -1;  // 0: dense blocks of k >= kMinTcK go to the tensor cores
     bool no_register_passes = false;
     bool use_tma = false;  // register passes move tiles with TMA tensor copies
+    int jit = 0;           // PlanOptions::jit
     std::vector<Mux> muxes;
 };
 
@@ -181,6 +159,7 @@ struct PlanOptions {
     int relabel = 0;      // SWAP gates relabel qubits
     double drop_phase_below = 0.0;  // approximation: smaller P/RZ/CP angles are dropped
     int mux = 0;          // multiplexor recognition: 0 long runs, 1 any run of 4+ gates, -1 off
+    int jit = 0;          // run-time compiled register passes: 0 on repeat, 1 always, -1 never
 };
 // The approximation for negligible rotations: the gates kept.
 void drop_small_phases(std::vector<CGate>* g, double eps);
@@ -209,63 +188,6 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
                              const std::vector<Mux>* muxes, const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0,
                              cudaEvent_t* ev1);
 
-// ---------------------------------------------------------------------------
-// Device-side plan blob: [PassDev x P][tensor-core B operands][pass regions].
-// Each pass owns one contiguous region [OpDev x nops | payloads], every piece
-// 16-byte aligned, so a CTA can copy the whole region into shared memory once
-// and run all its tiles from there.  Payload offsets are bytes from the start
-// of the region.
-// ---------------------------------------------------------------------------
-struct OpDev {
-    int kind;
-    int k;
-    int mat_off;   // dense / gates: byte offset of the matrix / the records' complex data
-    int diag_off;  // diag: byte offset of the run's words (DiagLayout)
-    int lq[kMaxK]; // dense / gates: local tile positions, ascending
-    int ngates;
-    int tc;        // dense on the tensor cores (c64, k >= 3)
-    int tc_off;    // float offset of its B operands [hi | lo] in the tc section
-    int nrec;      // gates: number of records
-    int rec_off;   // gates: byte offset of the records
-    int ndata;     // gates: complex values at mat_off
-    int ord;       // register passes, diag: ordinal of the run within the pass
-};
-static_assert(sizeof(OpDev) % 16 == 0, "OpDev array must keep 16-byte alignment");
-
-// Tensor-core dense block of k qubits (D = 2^k): B operand = [Ur; Ui], N = 2D
-// rows x K = D columns, FP32 values laid out as the tcgen05 no-swizzle
-// K-major canonical layout (8-row x 4-element core matrices of 128 bytes;
-// 128 bytes between K-adjacent core matrices, (K/4)*128 between 8-row
-// groups), stored twice: hi = value with the low 13 mantissa bits cleared
-// (what the tensor core reads from an FP32 input) and lo = value - hi.
-constexpr int kMinTcK = 3;
-constexpr int kTcResidentFloats = 8192;  // 32 KiB of B operands kept per CTA
-__host__ __device__ inline int tc_floats(int k) { return 2 * (2 << k) * (1 << k); }  // hi + lo
-__host__ __device__ inline int tc_kmajor_index(int n, int kk, int K) {
-    return ((n >> 3) * (K >> 2) + (kk >> 2)) * 32 + (n & 7) * 4 + (kk & 3);
-}
-
-struct PassDev {
-    double scale;        // register passes: factor applied at write-back (1 unless GR_H records)
-    int n;               // qubits of the state the pass runs on
-    int m;
-    int L;
-    int rmode;           // register-resident pass (region in the register format): 1 fed by
-                         // cp.async copies, 2 by TMA tensor copies; 0: shared-memory kernel;
-                         // kRmodeMux: multiplexor pass
-    int ndiag;           // register passes: diagonal runs (each folded once per tile)
-    int nops;            // ops in the pass's region
-    int region_off;      // byte offset of the region in the blob
-    int region_bytes;    // its size (multiple of 16)
-    int ops_bytes;       // size of its OpDev array (multiple of 16)
-    int tc_k;            // widest tensor-core block in the pass (0: none)
-    int tc_base;         // float offset of the pass's first tensor-core B operands
-    int tc_res;          // floats of B operands kept resident in shared memory (0: loaded per op)
-    int tq[kMaxTileM];   // tile qubits ascending
-    int nother;
-    int oq[40];          // non-tile qubits ascending
-};
-
 // Multiplexor pass (PassDev::rmode == kRmodeMux): the region is MuxDev
 // followed by one angle table per target: 2^nc entries of the state's real
 // type (float for complex64, double for complex128), phi for family Y and
@@ -288,55 +210,7 @@ struct MuxDev {
 };
 static_assert(sizeof(MuxDev) % 16 == 0, "tables after MuxDev stay 16-byte aligned");
 
-// Layout (in 8-byte words of fixed-point turns, 2^-64 turn units) of one
-// diagonal run inside a pass
-// with m tile qubits and no = n - m other qubits:
-//   c | a_t[m] | a_o[no] | Bo[m][no] | Boo[no][no] | Qlo[2^h] | Qhi[2^(m-h)]
-//   | Rt[(m-h)][2^h]
-// with h = min(m, 7): the tile index splits into lo = bits 0..h-1 and hi.
-struct DiagLayout {
-    int h, mh, c, at, ao, bo, boo, qlo, qhi, rt, total;
-    __host__ __device__ DiagLayout(int m, int no) {
-        h = m < 7 ? m : 7;
-        mh = m - h;
-        c = 0;
-        at = 1;
-        ao = at + m;
-        bo = ao + no;
-        boo = bo + m * no;
-        qlo = boo + no * no;
-        qhi = qlo + (1 << h);
-        rt = qhi + (1 << mh);
-        total = rt + (mh << h);
-    }
-};
 __host__ __device__ inline size_t diag_doubles(int m, int no) { return (size_t)DiagLayout(m, no).total; }
-
-// Diagonal run of a register pass (8-byte words of fixed-point turns), for
-// the register layout in force: rpos[b] = tile position of register bit b,
-// tpos[t] = tile position of thread bit t (t < m - r; lo = thread bits 0..3,
-// hi = the rest, at most 5):
-//   c | a_t[m] | a_o[no] | Bo[m][no] | Boo[no][no]        (per-tile fold)
-//   | TQlo[16] | TQhi[32] | TR[5][16]                       (thread-thread couplings)
-//   | TAlo[5][16] | TAhi[5][32]                             (register-thread couplings)
-//   | beta[5][5]                                            (register-register couplings)
-struct RDiagLayout {
-    int c, at, ao, bo, boo, tqlo, tqhi, tr, talo, tahi, beta, total;
-    __host__ __device__ RDiagLayout(int m, int no) {
-        c = 0;
-        at = 1;
-        ao = at + m;
-        bo = ao + no;
-        boo = bo + m * no;
-        tqlo = boo + no * no;
-        tqhi = tqlo + 16;
-        tr = tqhi + 32;
-        talo = tr + 5 * 16;
-        tahi = talo + 5 * 16;
-        beta = tahi + 5 * 32;
-        total = beta + 25;
-    }
-};
 
 struct PlanBlob {
     std::vector<unsigned char> bytes;
@@ -419,6 +293,15 @@ cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
                         const HostPass& hp);
 cudaError_t launch_mux(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass);
+PassLayout rpass_layout(int dtype, const PassDev& P);
+int num_sms_pub();
+// Run-time compiled register passes (sv_jit.cpp).  jit_prepare: per pass of
+// the blob, the compiled kernel ready for it (else nullptr); policy 1
+// compiles missing ones now, 0 in the background once a structure is seen a
+// second time, -1 never.  jit_launch: run the pass on it (*used = false: the
+// caller runs the interpreting kernel).
+void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void*>* fns);
+cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const PlanBlob& blob, int pass, bool* used);
 // One persistent launch for circuits of at most mmax qubits (single-tile
 // plans, one pass each, in blob order); outputs per circuit c at
 // samples + c*shots and expz + c*nmax (either may be NULL).

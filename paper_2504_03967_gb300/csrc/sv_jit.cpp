@@ -1,0 +1,488 @@
+// Pass kernels compiled at run time (the paper's own route: Q-GEAR turns
+// circuits into GPU kernels, Sec. 2.2; here one kernel per pass structure).
+//
+// The library's register-pass kernel walks a pass's op list at run time: a
+// switch per op and per gate record, positions and masks read from shared
+// memory, register layouts computed per thread.  For a pass structure that
+// recurs (the same circuit again, or circuits of one shape with other
+// angles), this file writes the pass as straight-line code -- every op, gate
+// position, phase-table mask, data offset and register layout a compile-time
+// constant, the data (matrices, tables, phase words) still read from the
+// staged region -- compiles it with NVRTC for this GPU's architecture, and
+// launches it in place of the interpreting kernel.  The kernel body is the
+// same source (sv_rpass.cuh), so both produce the same arithmetic.
+//
+// NVRTC is loaded with dlopen; where it is missing or a compile fails, the
+// pass keeps running on the interpreting kernel (still on the GPU).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+// ---- NVRTC and driver entry points --------------------------------------
+struct Nvrtc {
+    bool ok = false;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+
+struct Driver {
+    bool ok = false;
+    CUresult (*module_load)(CUmodule*, const void*) = nullptr;
+    CUresult (*get_function)(CUfunction*, CUmodule, const char*) = nullptr;
+    CUresult (*set_attr)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                       void**, void**) = nullptr;
+};
+
+template <typename F> bool sym(void* lib, const char* name, F* out) {
+    *out = (F)dlsym(lib, name);
+    return *out != nullptr;
+}
+
+const Nvrtc& nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* lib = nullptr;
+        for (const char* nm : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"})
+            if ((lib = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!lib) return;
+        n.ok = sym(lib, "nvrtcCreateProgram", &n.create) && sym(lib, "nvrtcCompileProgram", &n.compile) &&
+               sym(lib, "nvrtcGetProgramLogSize", &n.log_size) && sym(lib, "nvrtcGetProgramLog", &n.log) &&
+               sym(lib, "nvrtcGetCUBINSize", &n.cubin_size) && sym(lib, "nvrtcGetCUBIN", &n.cubin) &&
+               sym(lib, "nvrtcDestroyProgram", &n.destroy);
+    });
+    return n;
+}
+
+template <typename F> bool entry(const char* name, F* out) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *out = (F)p;
+    return true;
+}
+
+const Driver& driver() {
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        d.ok = entry("cuModuleLoadData", &d.module_load) && entry("cuModuleGetFunction", &d.get_function) &&
+               entry("cuFuncSetAttribute", &d.set_attr) &&
+               entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy) &&
+               entry("cuLaunchKernel", &d.launch);
+    });
+    return d;
+}
+
+// Directory of the library's sources (csrc/ next to libsv.so): the include
+// path of the run-time compiler.
+std::string source_dir() {
+    Dl_info info;
+    if (!dladdr((void*)&source_dir, &info) || !info.dli_fname) return "";
+    std::string p(info.dli_fname);
+    const size_t s = p.rfind('/');
+    return (s == std::string::npos ? std::string(".") : p.substr(0, s)) + "/csrc";
+}
+
+int arch_of_device() {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaGetLastError();
+    return 10 * major + minor;
+}
+
+// ---- source of one pass ---------------------------------------------------
+void emit_layout(std::ostringstream& o, const char* name, const int* a, int cnt) {
+    o << "constexpr int " << name << "[" << (cnt ? cnt : 1) << "] = {";
+    for (int i = 0; i < cnt; ++i) o << (i ? ", " : "") << a[i];
+    if (!cnt) o << "0";
+    o << "};";
+}
+
+// The pass as straight-line code (mirrors InterpOps::tile op by op).
+// Returns false for a structure it does not take.
+bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int maxt, int minb, std::string* out) {
+    const int RB = reg_bits(dtype), tb = P.m - RB;
+    if (tb < 0 || tb > 9) return false;
+    const OpDev* ops = (const OpDev*)region;
+    std::ostringstream o;
+    o << "#include \"sv_rpass.cuh\"\nnamespace sv {\nstruct GenOps {\n"
+         "template <typename V, typename R, int RB>\n"
+         "static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,\n"
+         "                                            const uint64_t* fold, RegLayout<V, RB>& Lg) {\n";
+    const int m = P.m, no = P.nother;
+    int rpos[8] = {0}, tpos[16] = {0};
+    bool in_regs = false;
+    for (int oi = 0; oi < P.nops; ++oi) {
+        const OpDev& op = ops[oi];
+        o << "{\n";
+        switch (op.kind) {
+        case OP_REMAP: {
+            if (in_regs) o << "__syncthreads();\nreg_write<V, RB>(v, tile, Lg);\n";
+            o << "__syncthreads();\n";
+            for (int b = 0; b < RB; ++b) rpos[b] = op.lq[b];
+            const int* tp = (const int*)(region + op.mat_off);
+            for (int t = 0; t < tb; ++t) tpos[t] = tp[t];
+            emit_layout(o, "rp", rpos, RB);
+            emit_layout(o, "tp", tpos, tb);
+            o << "\nreg_layout<V, RB>(Lg, rp, tp, " << tb << ");\nreg_read<V, RB>(v, tile, Lg);\n";
+            in_regs = true;
+            break;
+        }
+        case OP_GATES: {
+            if (!in_regs) return false;
+            o << "const V* sd = (const V*)(stage + " << op.mat_off << ");\n";
+            const GateRec* recs = (const GateRec*)(region + op.rec_off);
+            for (int r = 0; r < op.nrec; ++r) {
+                const GateRec& g = recs[r];
+                const int f = g.off;
+                switch (g.kind) {
+                case GR_U:
+                    o << "reg_u<V, RB, " << g.a << ">(v, sd[" << f << "], sd[" << f + 1 << "], sd[" << f + 2
+                      << "], sd[" << f + 3 << "]);\n";
+                    break;
+                case GR_UR:
+                    o << "reg_ur<V, RB, " << g.a << ", R>(v, sd[" << f << "].x, sd[" << f + 1 << "].x, sd["
+                      << f + 2 << "].x, sd[" << f + 3 << "].x);\n";
+                    break;
+                case GR_DT:
+                    o << "reg_dt<V, RB, 0x" << std::hex << (unsigned)g.b << std::dec << "u>(v, sd + " << f << ");\n";
+                    break;
+                case GR_CX: o << "reg_cx<V, RB, " << g.a << ", " << g.b << ">(v);\n"; break;
+                case GR_H: o << "reg_h<V, RB, " << g.a << ">(v);\n"; break;
+                case GR_HD:
+                    o << "reg_h<V, RB, " << g.a << ">(v);\nreg_dt<V, RB, 0x" << std::hex << (unsigned)g.b << std::dec
+                      << "u>(v, sd + " << f << ");\n";
+                    break;
+                case GR_SWAP: o << "reg_swap<V, RB, " << g.a << ", " << g.b << ">(v);\n"; break;
+                default: return false;
+                }
+            }
+            break;
+        }
+        case OP_DENSE:
+            if (!in_regs || op.k < 1 || op.k > kRegDenseMaxK) return false;
+            o << "reg_dense<V, RB, " << op.k << ">(v, (const V*)(stage + " << op.mat_off << "));\n";
+            break;
+        case OP_DIAG:
+            if (!in_regs) return false;
+            emit_layout(o, "rp", rpos, RB);
+            emit_layout(o, "tp", tpos, tb);
+            o << "\nreg_diag<V, R, RB>(v, (const uint64_t*)(stage + " << op.diag_off << "), fold + " << op.ord * (m + 1)
+              << ", " << m << ", " << no << ", rp, tp, " << tb << ");\n";
+            break;
+        default:
+            return false;
+        }
+        o << "}\n";
+    }
+    if (!in_regs) return false;
+    const char* R = dtype == SV_C64 ? "float" : "double";
+    o << "}\n};\n}  // namespace sv\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
+      << "    sv::CT<" << R << ">::V* __restrict__ psi, int n, const sv::PassDev* __restrict__ pdp,\n"
+      << "    const unsigned char* __restrict__ blob, const sv::PassLayout lay) {\n"
+      << "    sv::rpass_body<" << R << ", " << RB << ", sv::GenOps>(psi, n, pdp, blob, lay);\n}\n";
+    *out = o.str();
+    return true;
+}
+
+// ---- cache ------------------------------------------------------------------
+// One entry per pass source.  A structure compiles once per process: on its
+// first use with jit = 1 (the calling thread waits for it, the passes of one
+// plan in parallel), or in the background once it has been seen twice with
+// jit = 0 (the interpreting kernel runs until the kernel is ready).
+enum { JIT_NEW = 0, JIT_COMPILING, JIT_READY, JIT_FAILED };
+struct Entry {
+    int seen = 0;
+    int state = JIT_NEW;
+    CUfunction fn = nullptr;
+    int attr_bytes = 0;
+};
+
+std::mutex g_mu;
+std::condition_variable g_cv;
+std::unordered_map<std::string, Entry> g_cache;
+uint64_t g_compiled = 0, g_failed = 0, g_launched = 0;
+double g_compile_ms = 0.0;
+std::string g_last_log;
+int g_pending = 0;
+
+CUfunction compile(const std::string& src, int dev) {
+    const Nvrtc& nv = nvrtc();
+    const Driver& dr = driver();
+    if (!nv.ok || !dr.ok) return nullptr;
+    if (cudaSetDevice(dev) != cudaSuccess) {  // the module goes into the device's primary context
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaFree(0);
+    cudaGetLastError();
+    const std::string inc = "--include-path=" + source_dir();
+    char arch[64];
+    snprintf(arch, sizeof(arch), "--gpu-architecture=sm_%da", arch_of_device());
+    const char* opts[] = {arch, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo"};
+    nvrtcProgram prog;
+    if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return nullptr;
+    const nvrtcResult rc = nv.compile(prog, 5, opts);
+    size_t ls = 0;
+    nv.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) nv.log(prog, &log[0]);
+    CUfunction fn = nullptr;
+    if (rc == NVRTC_SUCCESS) {
+        size_t cs = 0;
+        nv.cubin_size(prog, &cs);
+        std::vector<char> cubin(cs);
+        if (cs && nv.cubin(prog, cubin.data()) == NVRTC_SUCCESS) {
+            CUmodule mod = nullptr;  // kept for the life of the process
+            if (dr.module_load(&mod, cubin.data()) != CUDA_SUCCESS ||
+                dr.get_function(&fn, mod, "sv_jit_pass") != CUDA_SUCCESS)
+                fn = nullptr;
+        }
+    }
+    nv.destroy(&prog);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_last_log = log;
+    return fn;
+}
+
+// Compile the sources, the calling thread waiting (several in parallel), and
+// publish the results.
+void compile_all(const std::vector<std::string>& srcs, int dev) {
+    std::vector<CUfunction> fns(srcs.size(), nullptr);
+    std::vector<double> ms(srcs.size(), 0.0);
+    auto one = [&](size_t i) {
+        const auto c0 = std::chrono::steady_clock::now();
+        fns[i] = compile(srcs[i], dev);
+        ms[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count();
+    };
+    if (srcs.size() == 1) {
+        one(0);
+    } else {
+        std::vector<std::thread> th;
+        for (size_t i = 0; i < srcs.size(); ++i) th.emplace_back(one, i);
+        for (auto& t : th) t.join();
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = 0; i < srcs.size(); ++i) {
+        Entry& e = g_cache[srcs[i]];
+        e.fn = fns[i];
+        e.state = fns[i] ? JIT_READY : JIT_FAILED;
+        (fns[i] ? g_compiled : g_failed)++;
+        g_compile_ms += ms[i];
+    }
+}
+
+// Background compiles: joined at exit, counted for sv_jit_wait.
+struct Workers {
+    std::mutex mu;
+    std::vector<std::thread> th;
+    ~Workers() {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto& t : th)
+            if (t.joinable()) t.join();
+    }
+};
+Workers g_workers;
+
+}  // namespace
+
+void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void*>* fns) {
+    fns->assign(blob.npasses, nullptr);
+    if (policy < 0 || !nvrtc().ok || !driver().ok) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<std::string> srcs(blob.npasses);
+    std::vector<std::string> now, later;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (int p = 0; p < blob.npasses; ++p) {
+            const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
+            if (pd->rmode != 1) continue;
+            const int tb = pd->m - reg_bits(h->dtype);
+            if (!pass_source(*pd, blob.bytes.data() + pd->region_off, h->dtype, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
+                             tb <= 8 ? 2 : 1, &srcs[p]))
+                continue;
+            Entry& e = g_cache[srcs[p]];
+            e.seen++;
+            if (e.state == JIT_NEW && (policy == 1 || e.seen >= 2)) {
+                e.state = JIT_COMPILING;
+                (policy == 1 ? now : later).push_back(srcs[p]);
+            }
+        }
+        g_pending += (int)later.size();
+    }
+    if (!now.empty()) compile_all(now, dev);
+    if (!later.empty()) {
+        std::lock_guard<std::mutex> lk(g_workers.mu);
+        g_workers.th.emplace_back([later, dev]() {
+            compile_all(later, dev);
+            std::lock_guard<std::mutex> lk2(g_mu);
+            g_pending -= (int)later.size();
+            g_cv.notify_all();
+        });
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int p = 0; p < blob.npasses; ++p) {
+        if (srcs[p].empty()) continue;
+        auto it = g_cache.find(srcs[p]);
+        if (it != g_cache.end() && it->second.state == JIT_READY) (*fns)[p] = &it->second;
+    }
+}
+
+cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const PlanBlob& blob, int pass, bool* used) {
+    *used = false;
+    if (!entry) return cudaSuccess;
+    Entry& e = *(Entry*)entry;  // entries are never erased, so the pointer stays valid
+    const Driver& dr = driver();
+    const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    const int tb = pd->m - reg_bits(h->dtype);
+    const PassLayout lay = rpass_layout(h->dtype, *pd);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (lay.total > e.attr_bytes) {
+            if (dr.set_attr(e.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, lay.total) != CUDA_SUCCESS)
+                return cudaSuccess;  // stays on the interpreting kernel
+            e.attr_bytes = lay.total;
+        }
+    }
+    const int threads = 1 << tb;
+    int per_sm = 1;
+    if (dr.occupancy(&per_sm, e.fn, threads, (size_t)lay.total) != CUDA_SUCCESS || per_sm < 1) per_sm = 1;
+    const uint64_t ntiles = 1ull << (h->n - pd->m);
+    uint64_t grid = (uint64_t)num_sms_pub() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    const unsigned char* b = (const unsigned char*)blob_dev;
+    void* psi = h->amps;
+    int n = h->n;
+    const PassDev* pdp = (const PassDev*)(b + blob.pass_off) + pass;
+    PassLayout lay_arg = lay;
+    void* args[] = {&psi, &n, &pdp, &b, &lay_arg};
+    count_launch();
+    if (dr.launch(e.fn, (unsigned)grid, 1, 1, (unsigned)threads, 1, 1, (unsigned)lay.total, (CUstream)h->stream, args,
+                  nullptr) != CUDA_SUCCESS)
+        return cudaErrorLaunchFailure;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        ++g_launched;
+    }
+    *used = true;
+    return cudaSuccess;
+}
+
+}  // namespace sv
+
+using namespace sv;
+
+extern "C" int sv_jit_stats(uint64_t* compiled, uint64_t* failed, uint64_t* launched, double* compile_ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (compiled) *compiled = g_compiled;
+    if (failed) *failed = g_failed;
+    if (launched) *launched = g_launched;
+    if (compile_ms) *compile_ms = g_compile_ms;
+    return SV_OK;
+}
+
+extern "C" int sv_jit_wait(void) {
+    std::unique_lock<std::mutex> lk(g_mu);
+    g_cv.wait(lk, []() { return g_pending == 0; });
+    return SV_OK;
+}
+
+extern "C" int sv_jit_last_log(char* buf, size_t cap) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (buf && cap) {
+        const size_t k = std::min(cap - 1, g_last_log.size());
+        memcpy(buf, g_last_log.data(), k);
+        buf[k] = '\0';
+    }
+    return SV_OK;
+}
+
+// Host-only check of the pass compiler: plan the circuit, write the source
+// of every register-resident pass and compile it with NVRTC for sm_<arch>a
+// (no module is loaded, so no GPU is needed).  *compiled = passes compiled;
+// the last compiler log goes to log.
+extern "C" int sv_jit_check(int n, sv_dtype dt, const sv_gate* gates, size_t count, const sv_options* opt, int arch,
+                            int* compiled, char* log, size_t cap) {
+    if (!compiled || (count && !gates)) return set_error(SV_EINVAL, "bad arguments");
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (n < 1 || n > (dt == SV_C64 ? kMaxQubitsC64 : kMaxQubitsC128)) return set_error(SV_EINVAL, "n out of range");
+    const Nvrtc& nv = nvrtc();
+    if (!nv.ok) return set_error(SV_EUNSUPPORTED, "NVRTC not found");
+    std::vector<CGate> cg;
+    size_t bad = 0;
+    if (canonicalise(n, gates, count, &cg, &bad) != SV_OK)
+        return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
+    const PlanOptions po = resolve_options(n, dt, opt);
+    Plan plan;
+    plan_greedy(n, dt, cg, po, &plan);
+    PlanBlob blob;
+    serialise_plan(plan, &blob);
+    *compiled = 0;
+    const std::string inc = "--include-path=" + source_dir();
+    char archo[64];
+    snprintf(archo, sizeof(archo), "--gpu-architecture=sm_%da", arch);
+    const char* opts[] = {archo, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo"};
+    std::string lastlog;
+    for (int p = 0; p < blob.npasses; ++p) {
+        const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
+        if (pd->rmode != 1) continue;
+        const int tb = pd->m - reg_bits(dt);
+        std::string src;
+        if (!pass_source(*pd, blob.bytes.data() + pd->region_off, dt, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
+                         tb <= 8 ? 2 : 1, &src))
+            continue;
+        nvrtcProgram prog;
+        if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+            return set_error(SV_EUNSUPPORTED, "nvrtcCreateProgram failed");
+        const nvrtcResult rc = nv.compile(prog, 5, opts);
+        size_t ls = 0;
+        nv.log_size(prog, &ls);
+        lastlog.assign(ls, '\0');
+        if (ls) nv.log(prog, &lastlog[0]);
+        size_t cs = 0;
+        if (rc == NVRTC_SUCCESS) nv.cubin_size(prog, &cs);
+        nv.destroy(&prog);
+        if (rc != NVRTC_SUCCESS || cs == 0) {
+            if (log && cap) snprintf(log, cap, "%s\n--- source ---\n%s", lastlog.c_str(), src.c_str());
+            return set_error(SV_EINVAL, "pass compile failed");
+        }
+        ++*compiled;
+    }
+    if (log && cap) snprintf(log, cap, "%s", lastlog.c_str());
+    return SV_OK;
+}

@@ -318,6 +318,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         po.relabel = opt->relabel == 1 ? 1 : 0;
         po.drop_phase_below = opt->drop_phase_below > 0.0 && std::isfinite(opt->drop_phase_below) ? opt->drop_phase_below : 0.0;
         po.mux = opt->mux < 0 ? -1 : (opt->mux > 0 ? 1 : 0);
+        po.jit = opt->jit < 0 ? -1 : (opt->jit > 0 ? 1 : 0);
     }
     if (dtype != SV_C64) po.tensor = -1;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
@@ -339,6 +340,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     out->tensor = po.tensor;
     out->no_register_passes = po.pass_kernel == 1;
     out->use_tma = po.pass_kernel == 2;
+    out->jit = po.jit;
     const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
     // the tile holds the row bits plus room for any two-qubit gate
     const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));

@@ -87,3 +87,18 @@ def test_plan_recognises_qcrank_multiplexors():
     assert S.sv_plan_circuit(4, S.C64, small, mux=1)["mux_ops"] == 2
     assert S.sv_plan_circuit(20, S.C64, W.qft(20), mux=1)["mux_ops"] == 0
     assert S.sv_plan_circuit(16, S.C64, W.random_u3_cx(16, 10, 3), mux=1)["mux_ops"] == 0
+
+
+def test_jit_sources_compile_without_gpu():
+    # the run-time compiler writes and compiles (NVRTC, no GPU needed) the
+    # kernel of every register-resident pass: Hadamard/phase-table records and
+    # diagonal runs (QFT), complex 2x2 records (U3), dense blocks, both dtypes
+    try:
+        assert S.sv_jit_check(14, S.C64, W.qft(14)) >= 1
+    except S.SVError as e:
+        if "NVRTC not found" in str(e):
+            pytest.skip("NVRTC not installed")
+        raise
+    assert S.sv_jit_check(18, S.C128, W.qft(18)) >= 1
+    assert S.sv_jit_check(12, S.C64, W.random_u3_cx(12, 2, 4)) >= 1
+    assert S.sv_jit_check(12, S.C64, W.random_cx_blocks(12, 20, 5), k_max=3) >= 1

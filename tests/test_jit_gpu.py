@@ -1,0 +1,90 @@
+"""Run-time compiled register passes (jit) against the FP64 oracle, and
+against the interpreting kernel on the same plan: same bounds as every other
+plan (complex64 1-F <= 1e-6, max |d psi| <= 1e-5; complex128 1e-12)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2504_03967_gb300 as S
+import workloads as W
+from paper_2504_03967_gb300 import build as B
+from tests import gpu_util as U
+from tests.oracle_pins import random_mixed_circuit
+
+pytestmark = pytest.mark.gpu
+
+DT = [S.C64, S.C128]
+DTN = {S.C64: "c64", S.C128: "c128"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    oracle.set_threads(8)
+    yield
+
+
+def _circuits():
+    return [
+        ("qft16", 16, W.qft(16), {}),
+        ("qft18-relabel", 18, W.qft(18), {"relabel": 1}),
+        ("random-u3cx", 16, W.random_u3_cx(16, 6, 11), {}),
+        ("cx-blocks-k3", 15, W.random_cx_blocks(15, 60, 12), {"k_max": 3}),
+        ("hea", 14, W.hea(14, 3, W.hea_params(1, 14, 3, 13)[0]), {}),
+        ("mixed", 15, random_mixed_circuit(15, 200, np.random.default_rng(14)), {}),
+    ]
+
+
+@pytest.mark.parametrize("dtype", DT, ids=DTN.get)
+@pytest.mark.parametrize("case", range(6), ids=[c[0] for c in _circuits()])
+def test_jit_pass_vs_oracle(dtype, case):
+    name, n, g, opts = _circuits()[case]
+    psi0 = W.random_state(n, 300 + case)
+    ref = U.run_oracle(n, g, psi0)
+    before = S.sv_jit_stats()
+    got = U.run_gpu(n, g, dtype, psi0=psi0, jit=1, **opts)
+    after = S.sv_jit_stats()
+    assert after["failed"] == before["failed"]
+    info = S.sv_plan_circuit(n, dtype, g[g["type"] != W.SWAP] if opts.get("relabel") else g,
+                             k_max=opts.get("k_max", 0))
+    if info["reg_passes"]:
+        assert after["launched"] > before["launched"], name  # the compiled kernels ran
+    if opts.get("relabel"):
+        h = S.sv_alloc(n, dtype)
+        try:
+            S.sv_load_state(h, psi0)
+            S.sv_apply_circuit(h, g, jit=1, **opts)
+            S.sv_materialize(h)
+            got = S.sv_store_state(h).astype(np.complex128)
+        finally:
+            S.sv_free(h)
+    U.assert_close(got, ref, dtype, name)
+    interp = U.run_gpu(n, g, dtype, psi0=psi0, jit=-1, **opts) if not opts.get("relabel") else None
+    if interp is not None:
+        U.assert_close(got, interp, dtype, name + " vs interpreting kernel")
+
+
+def test_jit_auto_compiles_on_repeat():
+    """jit = 0: the first apply of a structure runs the interpreting kernel,
+    the second starts a background compile, later applies use the kernel."""
+    n = 17
+    g = W.random_u3_cx(n, 3, 21)  # a structure no other test uses
+    psi0 = W.random_state(n, 22)
+    ref = U.run_oracle(n, g, psi0)
+    s0 = S.sv_jit_stats()
+    U.assert_close(U.run_gpu(n, g, S.C64, psi0=psi0), ref, S.C64, "first")
+    s1 = S.sv_jit_stats()
+    assert s1["launched"] == s0["launched"] and s1["compiled"] == s0["compiled"]
+    U.assert_close(U.run_gpu(n, g, S.C64, psi0=psi0), ref, S.C64, "second")
+    S.sv_jit_wait()
+    s2 = S.sv_jit_stats()
+    assert s2["compiled"] > s1["compiled"]
+    U.assert_close(U.run_gpu(n, g, S.C64, psi0=psi0), ref, S.C64, "third")
+    s3 = S.sv_jit_stats()
+    assert s3["launched"] > s2["launched"]
+    # the same structure with other angles reuses the kernels
+    g2 = W.random_u3_cx(n, 3, 21)
+    g2["p"] = np.random.default_rng(5).uniform(0, 2 * np.pi, size=g2["p"].shape) * (g2["type"] == W.U3)[:, None]
+    U.assert_close(U.run_gpu(n, g2, S.C64, psi0=psi0), U.run_oracle(n, g2, psi0), S.C64, "other angles")
+    s4 = S.sv_jit_stats()
+    assert s4["compiled"] == s3["compiled"] and s4["launched"] > s3["launched"]
