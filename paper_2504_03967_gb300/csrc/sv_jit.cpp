@@ -124,46 +124,126 @@ int arch_of_device() {
 }
 
 // ---- source of one pass ---------------------------------------------------
-void emit_layout(std::ostringstream& o, const char* name, const int* a, int cnt) {
+int swz_host(int dtype, int i) {  // the tile swizzle (sv_rpass.cuh swz)
+    return dtype == SV_C64 ? i ^ (((i >> 4) & 7) << 1) : i ^ ((i >> 3) & 7);
+}
+
+void emit_ints(std::ostringstream& o, const char* name, const int* a, int cnt) {
     o << "constexpr int " << name << "[" << (cnt ? cnt : 1) << "] = {";
     for (int i = 0; i < cnt; ++i) o << (i ? ", " : "") << a[i];
     if (!cnt) o << "0";
-    o << "};";
+    o << "};\n";
 }
 
-// The pass as straight-line code (mirrors InterpOps::tile op by op).
-// Returns false for a structure it does not take.
+// Register layout rp/tp: the swizzled offsets C[k] of register combination
+// k, and whether no thread's base can share a bit with any C[k].
+struct CtLayout {
+    int rp[8], tp[16], C[64];
+    bool add;
+};
+CtLayout ct_layout(int dtype, int RB, int tb, const int* rp, const int* tp) {
+    CtLayout L;
+    int sbit[8], tmask = 0, cmask = 0;
+    for (int b = 0; b < RB; ++b) L.rp[b] = rp[b], sbit[b] = swz_host(dtype, 1 << rp[b]);
+    for (int t = 0; t < tb; ++t) L.tp[t] = tp[t], tmask |= swz_host(dtype, 1 << tp[t]);
+    for (int k = 0; k < (1 << RB); ++k) {
+        int c = 0;
+        for (int b = 0; b < RB; ++b)
+            if ((k >> b) & 1) c ^= sbit[b];
+        L.C[k] = c;
+        cmask |= c;
+    }
+    L.add = (tmask & cmask) == 0;
+    return L;
+}
+
+// The pass as straight-line code (mirrors InterpOps op by op).  Returns
+// false for a structure it does not take.
 bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int maxt, int minb, std::string* out) {
-    const int RB = reg_bits(dtype), tb = P.m - RB;
-    if (tb < 0 || tb > 9) return false;
+    const int RB = reg_bits(dtype), tb = P.m - RB, L = P.L, m = P.m, no = P.nother;
+    if (tb < 5 || tb > 9 || L < 1) return false;
     const OpDev* ops = (const OpDev*)region;
+    const int PER = dtype == SV_C64 ? 2 : 1;  // amplitudes per 16-byte chunk
+    const int T = 1 << tb, NCH = (1 << RB) / PER;
+    const int istep = PER * T;
+    if (istep % (1 << L)) return false;
     std::ostringstream o;
-    o << "#include \"sv_rpass.cuh\"\nnamespace sv {\nstruct GenOps {\n"
-         "template <typename V, typename R, int RB>\n"
+    o << "#include \"sv_rpass.cuh\"\nnamespace sv {\nstruct GenOps {\n";
+    // tile copies: thread part of the row index from i0 = PER * tid, chunk
+    // part from k * istep (disjoint bits, so the row offsets add)
+    {
+        uint64_t KO[64];
+        int SW[64];
+        int swmask = 0, s0mask = 0;
+        for (int k = 0; k < NCH; ++k) {
+            const int i = k * istep, r = i >> L;
+            uint64_t off = 0;
+            for (int b = 0; b < m - L; ++b)
+                if ((r >> b) & 1) off |= 1ull << P.tq[L + b];
+            KO[k] = off;
+            SW[k] = swz_host(dtype, i);
+            swmask |= SW[k];
+        }
+        for (int b = 0; (1 << b) < istep; ++b)
+            if ((1 << b) >= PER) s0mask |= swz_host(dtype, 1 << b);
+        const bool add = (swmask & s0mask) == 0;
+        o << "static constexpr unsigned long long KO[" << NCH << "] = {";
+        for (int k = 0; k < NCH; ++k) o << (k ? ", " : "") << KO[k] << "ull";
+        o << "};\n";
+        o << "static constexpr int SW[" << NCH << "] = {";
+        for (int k = 0; k < NCH; ++k) o << (k ? ", " : "") << SW[k];
+        o << "};\n";
+        // per-thread global offset: in-row part and the row bits of i0
+        o << "static __device__ __forceinline__ uint64_t thread_goff() {\n"
+          << "const int i0 = " << PER << " * (int)threadIdx.x;\n"
+          << "uint64_t g = (uint64_t)(i0 & " << ((1 << L) - 1) << ");\n";
+        for (int b = 0; (1 << (L + b)) < istep && L + b < m; ++b)
+            o << "g |= (uint64_t)((i0 >> " << L + b << ") & 1) << " << P.tq[L + b] << ";\n";
+        o << "return g;\n}\n";
+        o << "template <typename V>\nstatic __device__ __forceinline__ void issue(V* tile, const V* __restrict__ psi, "
+             "uint64_t base, const uint32_t*, int) {\n"
+          << "issue_ct<V, " << NCH << ", " << (add ? "true" : "false")
+          << ">(tile, psi, base + thread_goff(), swz<V>(" << PER << " * (int)threadIdx.x), KO, SW);\n}\n";
+        o << "template <typename V>\nstatic __device__ __forceinline__ void store(const V* tile, V* __restrict__ psi, "
+             "uint64_t base, const uint32_t*, int) {\n"
+          << "store_ct<V, " << NCH << ", " << (add ? "true" : "false")
+          << ">(tile, psi, base + thread_goff(), swz<V>(" << PER << " * (int)threadIdx.x), KO, SW);\n}\n";
+    }
+    o << "template <typename V, typename R, int RB>\n"
          "static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,\n"
          "                                            const uint64_t* fold, RegLayout<V, RB>& Lg) {\n";
-    const int m = P.m, no = P.nother;
     int rpos[8] = {0}, tpos[16] = {0};
     bool in_regs = false;
+    CtLayout cur;
+    int nl = 0;
+    auto emit_rw = [&](const char* fn, const CtLayout& Lc, int id) {
+        o << "{\n";
+        emit_ints(o, "tp", Lc.tp, tb);
+        emit_ints(o, "C", Lc.C, 1 << RB);
+        o << fn << "<V, RB, " << (Lc.add ? "true" : "false") << ">(v, tile, thread_sbase<V, " << tb
+          << ">(tp), C);\n}\n";
+        (void)id;
+    };
     for (int oi = 0; oi < P.nops; ++oi) {
         const OpDev& op = ops[oi];
-        o << "{\n";
         switch (op.kind) {
         case OP_REMAP: {
-            if (in_regs) o << "__syncthreads();\nreg_write<V, RB>(v, tile, Lg);\n";
+            if (in_regs) {
+                o << "__syncthreads();\n";
+                emit_rw("reg_write_ct", cur, nl);
+            }
             o << "__syncthreads();\n";
             for (int b = 0; b < RB; ++b) rpos[b] = op.lq[b];
             const int* tp = (const int*)(region + op.mat_off);
             for (int t = 0; t < tb; ++t) tpos[t] = tp[t];
-            emit_layout(o, "rp", rpos, RB);
-            emit_layout(o, "tp", tpos, tb);
-            o << "\nreg_layout<V, RB>(Lg, rp, tp, " << tb << ");\nreg_read<V, RB>(v, tile, Lg);\n";
+            cur = ct_layout(dtype, RB, tb, rpos, tpos);
+            emit_rw("reg_read_ct", cur, ++nl);
             in_regs = true;
             break;
         }
         case OP_GATES: {
             if (!in_regs) return false;
-            o << "const V* sd = (const V*)(stage + " << op.mat_off << ");\n";
+            o << "{\nconst V* sd = (const V*)(stage + " << op.mat_off << ");\n";
             const GateRec* recs = (const GateRec*)(region + op.rec_off);
             for (int r = 0; r < op.nrec; ++r) {
                 const GateRec& g = recs[r];
@@ -190,6 +270,7 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
                 default: return false;
                 }
             }
+            o << "}\n";
             break;
         }
         case OP_DENSE:
@@ -198,20 +279,31 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
             break;
         case OP_DIAG:
             if (!in_regs) return false;
-            emit_layout(o, "rp", rpos, RB);
-            emit_layout(o, "tp", tpos, tb);
-            o << "\nreg_diag<V, R, RB>(v, (const uint64_t*)(stage + " << op.diag_off << "), fold + " << op.ord * (m + 1)
-              << ", " << m << ", " << no << ", rp, tp, " << tb << ");\n";
+            o << "{\n";
+            emit_ints(o, "rp", rpos, RB);
+            emit_ints(o, "tp", tpos, tb);
+            o << "reg_diag<V, R, RB>(v, (const uint64_t*)(stage + " << op.diag_off << "), fold + " << op.ord * (m + 1)
+              << ", " << m << ", " << no << ", rp, tp, " << tb << ");\n}\n";
             break;
         default:
             return false;
         }
-        o << "}\n";
     }
     if (!in_regs) return false;
+    o << "}\n";
+    // write-back: the pass's scale (a constant here), then the last layout
+    o << "template <typename V, typename R, int RB>\n"
+         "static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev&, const RegLayout<V, RB>&) {\n";
+    if (P.scale != 1.0) {
+        char buf[64];
+        snprintf(buf, sizeof(buf), "%.17g", P.scale);
+        o << "scale_regs<V, RB>(v, (R)" << buf << ");\n";
+    }
+    o << "__syncthreads();\n";
+    emit_rw("reg_write_ct", cur, nl);
+    o << "}\n};\n}  // namespace sv\n";
     const char* R = dtype == SV_C64 ? "float" : "double";
-    o << "}\n};\n}  // namespace sv\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
+    o << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
       << "    sv::CT<" << R << ">::V* __restrict__ psi, int n, const sv::PassDev* __restrict__ pdp,\n"
       << "    const unsigned char* __restrict__ blob, const sv::PassLayout lay) {\n"
       << "    sv::rpass_body<" << R << ", " << RB << ", sv::GenOps>(psi, n, pdp, blob, lay);\n}\n";

@@ -467,6 +467,52 @@ __device__ __forceinline__ void reg_diag(V* v, const uint64_t* __restrict__ dw, 
     }
 }
 
+// ---- helpers for the run-time compiled kernels (compile-time geometry) ----
+// Swizzled tile offset of this thread's register 0 for thread-bit positions
+// tp[0..TB-1].
+template <typename V, int TB>
+__device__ __forceinline__ int thread_sbase(const int* tp) {
+    int base = 0;
+#pragma unroll
+    for (int t = 0; t < TB; ++t) base |= ((int)(threadIdx.x >> t) & 1) << tp[t];
+    return swz<V>(base);
+}
+// Registers from / to the tile: register k sits at sb ^ C[k] (sb + C[k]
+// when no bit of sb can meet a bit of C, so the offset is an immediate).
+template <typename V, int RB, bool ADD>
+__device__ __forceinline__ void reg_read_ct(V* v, const V* tile, int sb, const int* C) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); ++k) v[k] = tile[ADD ? sb + C[k] : sb ^ C[k]];
+}
+template <typename V, int RB, bool ADD>
+__device__ __forceinline__ void reg_write_ct(const V* v, V* tile, int sb, const int* C) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); ++k) tile[ADD ? sb + C[k] : sb ^ C[k]] = v[k];
+}
+// Tile copies: chunk k of this thread is 16 bytes at psi[g + KO[k]] and at
+// tile[s0 ^ SW[k]] (s0 + SW[k] under ADD).
+template <typename V, int NCH, bool ADD>
+__device__ __forceinline__ void issue_ct(V* tile, const V* __restrict__ psi, uint64_t g, int s0, const uint64_t* KO,
+                                         const int* SW) {
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) cp_async16(tile + (ADD ? s0 + SW[k] : s0 ^ SW[k]), psi + g + KO[k]);
+}
+template <typename V, int NCH, bool ADD>
+__device__ __forceinline__ void store_ct(const V* tile, V* __restrict__ psi, uint64_t g, int s0, const uint64_t* KO,
+                                         const int* SW) {
+#pragma unroll
+    for (int k = 0; k < NCH; ++k)
+        *(float4*)(psi + g + KO[k]) = *(const float4*)(tile + (ADD ? s0 + SW[k] : s0 ^ SW[k]));
+}
+template <typename V, int RB>
+__device__ __forceinline__ void scale_regs(V* v, decltype(V().x) sc) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); ++k) {
+        v[k].x *= sc;
+        v[k].y *= sc;
+    }
+}
+
 // Per-tile fold of every diagonal run of the pass for tile t.
 template <typename R>
 __device__ __forceinline__ void fold_diags(const PassDev& P, const unsigned char* stage, uint64_t* fold,
@@ -504,8 +550,33 @@ __device__ __forceinline__ void fold_diags(const PassDev& P, const unsigned char
 }
 
 // The op list of a pass, walked at run time (the library's kernel).  On
-// return the amplitudes are in registers in the last layout (Lg).
+// return the amplitudes are in registers in the last layout (Lg).  issue /
+// store move a tile between the state and shared memory; finish applies the
+// pass's write-back scale and puts the registers back into the tile.
 struct InterpOps {
+    template <typename V>
+    static __device__ __forceinline__ void issue(V* tile, const V* __restrict__ psi, uint64_t base,
+                                                 const uint32_t* rowoff, int L) {
+        rissue_tile(tile, psi, base, rowoff, L);
+    }
+    template <typename V>
+    static __device__ __forceinline__ void store(const V* tile, V* __restrict__ psi, uint64_t base,
+                                                 const uint32_t* rowoff, int L) {
+        rstore_tile(tile, psi, base, rowoff, L);
+    }
+    template <typename V, typename R, int RB>
+    static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>& Lg) {
+        if (P.scale != 1.0) {
+            const R sc = (R)P.scale;
+#pragma unroll
+            for (int k = 0; k < (1 << RB); ++k) {
+                v[k].x *= sc;
+                v[k].y *= sc;
+            }
+        }
+        __syncthreads();
+        reg_write<V, RB>(v, tile, Lg);
+    }
     template <typename V, typename R, int RB>
     static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,
                                                 const uint64_t* fold, RegLayout<V, RB>& Lg) {
@@ -594,7 +665,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     auto tile_base = [&](uint64_t t) { return table_base(tbase, t, L); };
     int cur = 0;
     if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
-        rissue_tile(tiles[0], psi, tile_base(blockIdx.x), rowoff, L);
+        Ops::template issue<V>(tiles[0], psi, tile_base(blockIdx.x), rowoff, L);
         cp_async_commit();
     }
     V v[1 << RB];
@@ -604,14 +675,14 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         const uint64_t tn = t + gridDim.x;
         if (lay.nbuf == 2) {
             if (tn < ntiles) {
-                rissue_tile(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L);
+                Ops::template issue<V>(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L);
                 cp_async_commit();
                 cp_async_wait_group<1>();
             } else {
                 cp_async_wait_group<0>();
             }
         } else {
-            rissue_tile(tiles[0], psi, base, rowoff, L);
+            Ops::template issue<V>(tiles[0], psi, base, rowoff, L);
             cp_async_commit();
             cp_async_wait_group<0>();
         }
@@ -619,18 +690,9 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         V* tile = tiles[cur];
         if (nd) fold_diags<R>(P, stage, fold, dofs, t);
         Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg);
-        if (P.scale != 1.0) {
-            const R sc = (R)P.scale;
-#pragma unroll
-            for (int k = 0; k < (1 << RB); ++k) {
-                v[k].x *= sc;
-                v[k].y *= sc;
-            }
-        }
+        Ops::template finish<V, R, RB>(v, tile, P, Lg);
         __syncthreads();
-        reg_write<V, RB>(v, tile, Lg);
-        __syncthreads();
-        rstore_tile(tile, psi, base, rowoff, L);
+        Ops::template store<V>(tile, psi, base, rowoff, L);
         __syncthreads();
         if (lay.nbuf == 2) cur ^= 1;
     }
