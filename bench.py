@@ -42,14 +42,15 @@ UNIT = "amp_updates/s"
 
 
 # DRAM traffic of the tile pass per amplitude per launch, from the ncu capture
-# summarised in profiles/ (QFT n=26 complex64, k_max 5, tile 14, the 3 passes
-# of one step; dram__bytes_read.sum + dram__bytes_write.sum), valid only for
-# the kernel and planner sources it was taken with (SHA-256 over the files
-# below); a changed kernel reports traffic null until it is captured again.
+# summarised in profiles/ (QFT n=26 complex64, k_max 5, tile 13, the 3 passes
+# of one step on the run-time compiled kernel; dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel, compiler and planner
+# sources it was taken with (SHA-256 over the files below); a changed kernel
+# reports traffic null until it is captured again.
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
-                   "paper_2504_03967_gb300/csrc/sv_internal.h"]
-TRAFFIC = {"sha256": "26bfce770412e902ec20d5cde355e514f30f73972bb8ebcea47bd0fadd6f470a",
-           "bytes_per_amp": 15.3154, "profile": "profiles/k_rpass_qft26_c64_k5m14.md (n=26 capture, scaled to 2^n)"}
+                   "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
+                   "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
+TRAFFIC = {"sha256": None, "bytes_per_amp": None, "profile": None}
 
 
 def sources_sha():
@@ -457,7 +458,8 @@ def main():
     if len(pass_ms):
         per_launch_bytes = 2.0 * amp_b * float(1 << n)
         achieved = per_launch_bytes / (float(np.mean(pass_ms)) / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "tile pass (k_rpass register-resident / k_pass shared-memory)",
+        roof = {"bound": "hbm", "kernel": "tile pass (sv_jit_pass compiled per pass structure; k_rpass / k_pass "
+                "interpreting kernels)",
                 "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": src,
                 "frac_of_8tbs_nominal": achieved / 8000.0,

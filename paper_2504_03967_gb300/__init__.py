@@ -286,6 +286,7 @@ def sv_jit_check(n, dtype, gates, arch=103, **opts):
     rc = f(n, dtype, _ptr(g), len(g), ctypes.byref(o), arch, ctypes.byref(cnt), buf, len(buf))
     if rc != 0:
         raise SVError(rc, L.sv_last_error().decode() + "\n" + buf.value.decode(errors="replace"))
+    sv_jit_check.last_log = buf.value.decode(errors="replace")  # ptxas register / spill report
     return cnt.value
 
 

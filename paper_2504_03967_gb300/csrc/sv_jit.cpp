@@ -548,8 +548,9 @@ extern "C" int sv_jit_check(int n, sv_dtype dt, const sv_gate* gates, size_t cou
     const std::string inc = "--include-path=" + source_dir();
     char archo[64];
     snprintf(archo, sizeof(archo), "--gpu-architecture=sm_%da", arch);
-    const char* opts[] = {archo, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo"};
-    std::string lastlog;
+    // the check also asks ptxas for its register and spill report
+    const char* opts[] = {archo, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo", "--ptxas-options=-v"};
+    std::string lastlog, alllogs;
     for (int p = 0; p < blob.npasses; ++p) {
         const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
         if (pd->rmode != 1) continue;
@@ -561,11 +562,12 @@ extern "C" int sv_jit_check(int n, sv_dtype dt, const sv_gate* gates, size_t cou
         nvrtcProgram prog;
         if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
             return set_error(SV_EUNSUPPORTED, "nvrtcCreateProgram failed");
-        const nvrtcResult rc = nv.compile(prog, 5, opts);
+        const nvrtcResult rc = nv.compile(prog, 6, opts);
         size_t ls = 0;
         nv.log_size(prog, &ls);
         lastlog.assign(ls, '\0');
         if (ls) nv.log(prog, &lastlog[0]);
+        alllogs += lastlog;
         size_t cs = 0;
         if (rc == NVRTC_SUCCESS) nv.cubin_size(prog, &cs);
         nv.destroy(&prog);
@@ -575,6 +577,6 @@ extern "C" int sv_jit_check(int n, sv_dtype dt, const sv_gate* gates, size_t cou
         }
         ++*compiled;
     }
-    if (log && cap) snprintf(log, cap, "%s", lastlog.c_str());
+    if (log && cap) snprintf(log, cap, "%s", alllogs.c_str());
     return SV_OK;
 }
