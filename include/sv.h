@@ -116,9 +116,11 @@ typedef enum {
  * jit: register-resident passes as kernels compiled at run time (NVRTC) for
  * their structure -- op sequence, gate positions, table masks and register
  * layouts fixed in the code, the data still read from the plan -- and cached
- * for the process: 0 = compile a structure the second time it runs (the
- * first run and one-off circuits stay on the library's interpreting kernel),
- * 1 = compile on first use, -1 = never.  Results agree with the interpreting
+ * for the process: 0 = compile a structure the second time it runs on a
+ * state of 22 or more qubits (the first run, one-off circuits and small
+ * states stay on the library's interpreting kernel), 1 = compile on first
+ * use, -1 = never.  A compile (about a second, the passes of one plan in
+ * parallel) happens inside the apply that needs it.  Results agree with the interpreting
  * kernel to rounding; where NVRTC is missing the interpreting kernel runs. */
 typedef struct {
     int k_max;

@@ -23,7 +23,6 @@
 
 #include <algorithm>
 #include <chrono>
-#include <condition_variable>
 #include <mutex>
 #include <thread>
 #include <sstream>
@@ -312,11 +311,15 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
 }
 
 // ---- cache ------------------------------------------------------------------
-// One entry per pass source.  A structure compiles once per process: on its
-// first use with jit = 1 (the calling thread waits for it, the passes of one
-// plan in parallel), or in the background once it has been seen twice with
-// jit = 0 (the interpreting kernel runs until the kernel is ready).
+// One entry per pass source.  A structure compiles once per process, inside
+// the apply that needs it (the passes of one plan in parallel): on its first
+// use with jit = 1, on its second with jit = 0 (the first run of a structure,
+// one-off circuits and small states stay on the interpreting kernel).
 enum { JIT_NEW = 0, JIT_COMPILING, JIT_READY, JIT_FAILED };
+// jit = 0 compiles only for states of at least this many qubits: below it a
+// pass takes tens of microseconds, and the compile (about a second) would not
+// pay back.
+constexpr int kJitAutoMinQubits = 22;
 struct Entry {
     int seen = 0;
     int state = JIT_NEW;
@@ -325,62 +328,47 @@ struct Entry {
 };
 
 std::mutex g_mu;
-std::condition_variable g_cv;
 std::unordered_map<std::string, Entry> g_cache;
 uint64_t g_compiled = 0, g_failed = 0, g_launched = 0;
 double g_compile_ms = 0.0;
 std::string g_last_log;
-int g_pending = 0;
 
-CUfunction compile(const std::string& src, int dev) {
+// NVRTC only (no CUDA call, so any thread may run it): the cubin of src for
+// sm_<arch>a, empty on a failure.
+std::vector<char> nvrtc_cubin(const std::string& src, int arch, std::string* log) {
     const Nvrtc& nv = nvrtc();
-    const Driver& dr = driver();
-    if (!nv.ok || !dr.ok) return nullptr;
-    if (cudaSetDevice(dev) != cudaSuccess) {  // the module goes into the device's primary context
-        cudaGetLastError();
-        return nullptr;
-    }
-    cudaFree(0);
-    cudaGetLastError();
+    std::vector<char> cubin;
     const std::string inc = "--include-path=" + source_dir();
-    char arch[64];
-    snprintf(arch, sizeof(arch), "--gpu-architecture=sm_%da", arch_of_device());
-    const char* opts[] = {arch, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo"};
+    char archo[64];
+    snprintf(archo, sizeof(archo), "--gpu-architecture=sm_%da", arch);
+    const char* opts[] = {archo, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo"};
     nvrtcProgram prog;
-    if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return nullptr;
+    if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return cubin;
     const nvrtcResult rc = nv.compile(prog, 5, opts);
     size_t ls = 0;
     nv.log_size(prog, &ls);
-    std::string log(ls, '\0');
-    if (ls) nv.log(prog, &log[0]);
-    CUfunction fn = nullptr;
+    log->assign(ls, '\0');
+    if (ls) nv.log(prog, &(*log)[0]);
     if (rc == NVRTC_SUCCESS) {
         size_t cs = 0;
         nv.cubin_size(prog, &cs);
-        std::vector<char> cubin(cs);
-        if (cs && nv.cubin(prog, cubin.data()) == NVRTC_SUCCESS) {
-            CUmodule mod = nullptr;  // kept for the life of the process
-            if (dr.module_load(&mod, cubin.data()) != CUDA_SUCCESS ||
-                dr.get_function(&fn, mod, "sv_jit_pass") != CUDA_SUCCESS)
-                fn = nullptr;
-        }
+        cubin.resize(cs);
+        if (!cs || nv.cubin(prog, cubin.data()) != NVRTC_SUCCESS) cubin.clear();
     }
     nv.destroy(&prog);
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_last_log = log;
-    return fn;
+    return cubin;
 }
 
-// Compile the sources, the calling thread waiting (several in parallel), and
-// publish the results.
-void compile_all(const std::vector<std::string>& srcs, int dev) {
-    std::vector<CUfunction> fns(srcs.size(), nullptr);
-    std::vector<double> ms(srcs.size(), 0.0);
-    auto one = [&](size_t i) {
-        const auto c0 = std::chrono::steady_clock::now();
-        fns[i] = compile(srcs[i], dev);
-        ms[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count();
-    };
+// Compile the sources (NVRTC on helper threads that are joined here, one per
+// source), load the modules on the calling thread (its current context) and
+// publish the results.  No thread outlives the call.
+void compile_all(const std::vector<std::string>& srcs) {
+    const Driver& dr = driver();
+    const int arch = arch_of_device();
+    std::vector<std::vector<char>> bins(srcs.size());
+    std::vector<std::string> logs(srcs.size());
+    const auto c0 = std::chrono::steady_clock::now();
+    auto one = [&](size_t i) { bins[i] = nvrtc_cubin(srcs[i], arch, &logs[i]); };
     if (srcs.size() == 1) {
         one(0);
     } else {
@@ -388,37 +376,33 @@ void compile_all(const std::vector<std::string>& srcs, int dev) {
         for (size_t i = 0; i < srcs.size(); ++i) th.emplace_back(one, i);
         for (auto& t : th) t.join();
     }
+    std::vector<CUfunction> fns(srcs.size(), nullptr);
+    for (size_t i = 0; i < srcs.size(); ++i) {
+        if (bins[i].empty()) continue;
+        CUmodule mod = nullptr;  // kept for the life of the process
+        if (dr.module_load(&mod, bins[i].data()) != CUDA_SUCCESS ||
+            dr.get_function(&fns[i], mod, "sv_jit_pass") != CUDA_SUCCESS)
+            fns[i] = nullptr;
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count();
     std::lock_guard<std::mutex> lk(g_mu);
     for (size_t i = 0; i < srcs.size(); ++i) {
         Entry& e = g_cache[srcs[i]];
         e.fn = fns[i];
         e.state = fns[i] ? JIT_READY : JIT_FAILED;
         (fns[i] ? g_compiled : g_failed)++;
-        g_compile_ms += ms[i];
+        if (!logs[i].empty()) g_last_log = logs[i];
     }
+    g_compile_ms += ms;
 }
-
-// Background compiles: joined at exit, counted for sv_jit_wait.
-struct Workers {
-    std::mutex mu;
-    std::vector<std::thread> th;
-    ~Workers() {
-        std::lock_guard<std::mutex> lk(mu);
-        for (auto& t : th)
-            if (t.joinable()) t.join();
-    }
-};
-Workers g_workers;
 
 }  // namespace
 
 void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void*>* fns) {
     fns->assign(blob.npasses, nullptr);
     if (policy < 0 || !nvrtc().ok || !driver().ok) return;
-    int dev = 0;
-    cudaGetDevice(&dev);
     std::vector<std::string> srcs(blob.npasses);
-    std::vector<std::string> now, later;
+    std::vector<std::string> now;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         for (int p = 0; p < blob.npasses; ++p) {
@@ -430,23 +414,13 @@ void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void
                 continue;
             Entry& e = g_cache[srcs[p]];
             e.seen++;
-            if (e.state == JIT_NEW && (policy == 1 || e.seen >= 2)) {
+            if (e.state == JIT_NEW && (policy == 1 || (e.seen >= 2 && h->n >= kJitAutoMinQubits))) {
                 e.state = JIT_COMPILING;
-                (policy == 1 ? now : later).push_back(srcs[p]);
+                now.push_back(srcs[p]);
             }
         }
-        g_pending += (int)later.size();
     }
-    if (!now.empty()) compile_all(now, dev);
-    if (!later.empty()) {
-        std::lock_guard<std::mutex> lk(g_workers.mu);
-        g_workers.th.emplace_back([later, dev]() {
-            compile_all(later, dev);
-            std::lock_guard<std::mutex> lk2(g_mu);
-            g_pending -= (int)later.size();
-            g_cv.notify_all();
-        });
-    }
+    if (!now.empty()) compile_all(now);
     std::lock_guard<std::mutex> lk(g_mu);
     for (int p = 0; p < blob.npasses; ++p) {
         if (srcs[p].empty()) continue;
@@ -508,11 +482,9 @@ extern "C" int sv_jit_stats(uint64_t* compiled, uint64_t* failed, uint64_t* laun
     return SV_OK;
 }
 
-extern "C" int sv_jit_wait(void) {
-    std::unique_lock<std::mutex> lk(g_mu);
-    g_cv.wait(lk, []() { return g_pending == 0; });
-    return SV_OK;
-}
+// Compiles finish inside the apply that starts them; kept for callers that
+// wait before timing.
+extern "C" int sv_jit_wait(void) { return SV_OK; }
 
 extern "C" int sv_jit_last_log(char* buf, size_t cap) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -66,9 +66,10 @@ def test_jit_pass_vs_oracle(dtype, case):
 
 def test_jit_auto_compiles_on_repeat():
     """jit = 0: the first apply of a structure runs the interpreting kernel,
-    the second starts a background compile, later applies use the kernel."""
-    n = 17
-    g = W.random_u3_cx(n, 3, 21)  # a structure no other test uses
+    the second compiles it (states of 22+ qubits), and later applies, also
+    with other angles, reuse the kernels."""
+    n = 22
+    g = W.random_u3_cx(n, 2, 21)  # a structure no other test uses
     psi0 = W.random_state(n, 22)
     ref = U.run_oracle(n, g, psi0)
     s0 = S.sv_jit_stats()
@@ -76,14 +77,18 @@ def test_jit_auto_compiles_on_repeat():
     s1 = S.sv_jit_stats()
     assert s1["launched"] == s0["launched"] and s1["compiled"] == s0["compiled"]
     U.assert_close(U.run_gpu(n, g, S.C64, psi0=psi0), ref, S.C64, "second")
-    S.sv_jit_wait()
     s2 = S.sv_jit_stats()
     assert s2["compiled"] > s1["compiled"]
     U.assert_close(U.run_gpu(n, g, S.C64, psi0=psi0), ref, S.C64, "third")
     s3 = S.sv_jit_stats()
-    assert s3["launched"] > s2["launched"]
+    assert s3["launched"] > s2["launched"] and s3["compiled"] == s2["compiled"]
+    # small states stay on the interpreting kernel under jit = 0
+    gs = W.random_u3_cx(14, 2, 23)
+    for _ in range(3):
+        U.run_gpu(14, gs, S.C64)
+    assert S.sv_jit_stats()["compiled"] == s3["compiled"]
     # the same structure with other angles reuses the kernels
-    g2 = W.random_u3_cx(n, 3, 21)
+    g2 = W.random_u3_cx(n, 2, 21)
     g2["p"] = np.random.default_rng(5).uniform(0, 2 * np.pi, size=g2["p"].shape) * (g2["type"] == W.U3)[:, None]
     U.assert_close(U.run_gpu(n, g2, S.C64, psi0=psi0), U.run_oracle(n, g2, psi0), S.C64, "other angles")
     s4 = S.sv_jit_stats()
