@@ -60,6 +60,69 @@ __device__ __forceinline__ FF ff_allreduce(FF a) {
     return a;
 }
 
+// Full 1024-amplitude blocks of complex64 with bit sums.  Lane l holds
+// p_j = |a|^2 of amplitudes l + 32 j as float pairs; a pairwise tree over j
+// gives the lane's total and its sums over j with bit b set (57 double-float
+// additions for 32 amplitudes), and one reduce-scatter across the warp sums
+// the 11 per-lane values (total, total where lane bit b is set, the 5 j-bit
+// sums): each of the first four exchange steps halves the values a lane
+// keeps, so lane 2e (e < 11) ends with value e summed over all 32 lanes.
+__device__ __forceinline__ void block_stats_c64_full(const float2* __restrict__ psi, uint64_t wid, int lane,
+                                                     double* __restrict__ tot, double* __restrict__ bits) {
+    const uint64_t b0 = wid << 10;
+    FF p[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const float2 v = psi[b0 + lane + 32 * j];
+        const float r2 = v.x * v.x, r2e = fmaf(v.x, v.x, -r2);
+        const float i2 = v.y * v.y, i2e = fmaf(v.y, v.y, -i2);
+        const float sum = r2 + i2, bb = sum - r2;
+        p[j].hi = sum;
+        p[j].lo = ((r2 - (sum - bb)) + (i2 - bb)) + r2e + i2e;
+    }
+    FF e[16];
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+        const int half = 16 >> lev;
+        FF odd = p[1];
+#pragma unroll
+        for (int i = 1; i < half; ++i) ff_add(odd, p[2 * i + 1].hi, p[2 * i + 1].lo);
+        e[6 + lev] = odd;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            FF t = p[2 * i];
+            ff_add(t, p[2 * i + 1].hi, p[2 * i + 1].lo);
+            p[i] = t;
+        }
+    }
+    e[0] = p[0];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) e[1 + b] = ((lane >> b) & 1) ? p[0] : FF{0.f, 0.f};
+#pragma unroll
+    for (int k = 11; k < 16; ++k) e[k] = FF{0.f, 0.f};
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {  // lane bits 4, 3, 2, 1
+        const int h = 8 >> st, mask = 16 >> st;
+        const bool up = (lane & mask) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const FF send = up ? e[k] : e[k + h];
+            FF keep = up ? e[k + h] : e[k];
+            const float rh = __shfl_xor_sync(0xffffffffu, send.hi, mask);
+            const float rl = __shfl_xor_sync(0xffffffffu, send.lo, mask);
+            ff_add(keep, rh, rl);
+            e[k] = keep;
+        }
+    }
+    ff_add(e[0], __shfl_xor_sync(0xffffffffu, e[0].hi, 1), __shfl_xor_sync(0xffffffffu, e[0].lo, 1));
+    const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    if (!(lane & 1) && idx < 11) {
+        const double val = ff_val(e[0]);
+        if (idx == 0) tot[wid] = val;
+        else bits[wid * 10 + (idx - 1)] = val;  // 1..5: lane bits 0..4; 6..10: j bits = index bits 5..9
+    }
+}
+
 template <typename V>
 __global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, int blog, uint64_t nblocks,
                                                      double* __restrict__ tot, double* __restrict__ bits) {
@@ -70,6 +133,10 @@ __global__ void __launch_bounds__(256) k_block_stats(const V* __restrict__ psi, 
     const int len = 1 << blog;
     const int jn = len >= 32 ? len / 32 : 1;
     if constexpr (sizeof(V) == 8) {
+        if (bits && blog == 10) {
+            block_stats_c64_full((const float2*)psi, wid, lane, tot, bits);
+            return;
+        }
         FF acc = {0.f, 0.f}, ab[5];
 #pragma unroll
         for (int b = 0; b < 5; ++b) ab[b] = FF{0.f, 0.f};
