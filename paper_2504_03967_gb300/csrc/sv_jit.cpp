@@ -400,7 +400,9 @@ void compile_all(const std::vector<std::string>& srcs) {
 
 void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void*>* fns) {
     fns->assign(blob.npasses, nullptr);
-    if (policy < 0 || !nvrtc().ok || !driver().ok) return;
+    // jit = 0 on a small state: nothing to compile or look up (writing the
+    // pass sources would cost more than the passes)
+    if (policy < 0 || (policy == 0 && h->n < kJitAutoMinQubits) || !nvrtc().ok || !driver().ok) return;
     std::vector<std::string> srcs(blob.npasses);
     std::vector<std::string> now;
     {
