@@ -196,7 +196,14 @@ int sv_materialize(sv_handle h);
  * candidate the cost model and its judge picked for that call). */
 int sv_last_plan(sv_handle h, sv_options *out);
 
-/* |x>: all amplitudes 0 except a_x = 1.  SV_EINVAL if x >= 2^n. */
+/* |x>: all amplitudes 0 except a_x = 1.  SV_EINVAL if x >= 2^n.  The write
+ * is deferred: the next sv_apply_circuit whose first pass runs on a compiled
+ * register kernel (see sv_options.jit) builds that pass's tiles from x
+ * instead of reading the state, and every other call that uses the state
+ * (read-outs, sv_store_state, other applies, sv_info asking for the device
+ * pointer, sv_set_stream) writes |x> first.  Code that reads attached memory
+ * directly must therefore take the pointer from sv_info after the init, or
+ * call a read-out, before reading it. */
 int sv_init_basis(sv_handle h, uint64_t x);
 
 /* Copy 2^n amplitudes (interleaved, the handle's dtype) from host memory to

@@ -178,9 +178,17 @@ def sv_set_stream(h, stream):
 
 
 def sv_info(h):
+    """(n, dtype, device pointer).  Handing out the pointer writes a deferred
+    sv_init_basis first, so the memory holds the state."""
     n, dt, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
     _check(lib().sv_info(h, ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p)))
     return n.value, dt.value, p.value
+
+
+def _n_dtype(h):
+    n, dt = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sv_info(h, ctypes.byref(n), ctypes.byref(dt), None))
+    return n.value, dt.value
 
 
 def sv_init_basis(h, x=0):
@@ -188,14 +196,14 @@ def sv_init_basis(h, x=0):
 
 
 def sv_load_state(h, amps):
-    n, dt, _ = sv_info(h)
+    n, dt = _n_dtype(h)
     a = np.ascontiguousarray(amps, dtype=np.complex64 if dt == C64 else np.complex128)
     assert a.shape == (1 << n,)
     _check(lib().sv_load_state(h, _ptr(a)))
 
 
 def sv_store_state(h):
-    n, dt, _ = sv_info(h)
+    n, dt = _n_dtype(h)
     a = np.empty(1 << n, dtype=np.complex64 if dt == C64 else np.complex128)
     _check(lib().sv_store_state(h, _ptr(a)))
     return a
@@ -219,7 +227,7 @@ def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, ten
 
 def sv_qubit_map(h):
     """Physical bit of each logical qubit (identity unless relabelled)."""
-    n, _, _ = sv_info(h)
+    n, _ = _n_dtype(h)
     m = (ctypes.c_int * max(1, n))()
     _check(lib().sv_qubit_map(h, m))
     return [m[i] for i in range(n)]
@@ -237,7 +245,7 @@ def sv_last_plan(h):
 
 
 def sv_probs(h):
-    n, _, _ = sv_info(h)
+    n, _ = _n_dtype(h)
     out = np.empty(1 << n, dtype=np.float64)
     _check(lib().sv_probs(h, _ptr(out)))
     return out
@@ -254,7 +262,7 @@ def sv_norm(h):
 
 
 def sv_expect_z(h):
-    n, _, _ = sv_info(h)
+    n, _ = _n_dtype(h)
     out = np.empty(n, dtype=np.float64)
     _check(lib().sv_expect_z(h, _ptr(out)))
     return out

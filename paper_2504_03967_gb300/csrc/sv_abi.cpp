@@ -73,16 +73,35 @@ int ensure_pinned(Scratch* s, size_t bytes) {
     return SV_OK;
 }
 
+int flush_init(sv_state* h) {
+    if (h->pending_basis < 0) return SV_OK;
+    const uint64_t x = (uint64_t)h->pending_basis;
+    h->pending_basis = -1;
+    cudaError_t e = launch_init_basis(h, x);
+    if (e != cudaSuccess) {
+        h->bad = true;
+        return cuda_fail(e, "init_basis");
+    }
+    return SV_OK;
+}
+
 }  // namespace sv
 
 using namespace sv;
 
 namespace {
 
-int check_handle(sv_handle h) {
+int check_handle_noflush(sv_handle h) {
     if (!h) return set_error(SV_EINVAL, "NULL handle");
     if (h->bad) return set_error(SV_ESTATE, "state flagged by an earlier CUDA failure; re-initialise it");
     return SV_OK;
+}
+
+// Entry points that use the amplitudes first write a deferred basis state.
+int check_handle(sv_handle h) {
+    int rc = check_handle_noflush(h);
+    if (rc == SV_OK) rc = flush_init(h);
+    return rc;
 }
 
 int max_qubits(int dt) { return dt == SV_C64 ? kMaxQubitsC64 : kMaxQubitsC128; }
@@ -101,6 +120,7 @@ int make_handle(int n, sv_dtype dt, void* amps, bool owned, void* stream, sv_han
     h->ev_used = 0;
     h->upload_ev = nullptr;
     h->upload_pending = false;
+    h->pending_basis = -1;
     reset_perm(h);
     memset(&h->last_opts, 0, sizeof(h->last_opts));
     *out = h;
@@ -202,6 +222,7 @@ int sv_free(sv_handle h) {
 
 int sv_set_stream(sv_handle h, void* cuda_stream) {
     if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (!h->bad) flush_init(h);
     cudaStreamSynchronize(h->stream);
     h->stream = (cudaStream_t)cuda_stream;
     return SV_OK;
@@ -209,6 +230,10 @@ int sv_set_stream(sv_handle h, void* cuda_stream) {
 
 int sv_info(sv_handle h, int* n, int* dtype, void** dev_amps) {
     if (!h) return set_error(SV_EINVAL, "NULL handle");
+    if (dev_amps && !h->bad) {  // the caller may read the amplitudes through the pointer
+        const int rc = flush_init(h);
+        if (rc) return rc;
+    }
     if (n) *n = h->n;
     if (dtype) *dtype = h->dtype;
     if (dev_amps) *dev_amps = h->amps;
@@ -218,11 +243,9 @@ int sv_info(sv_handle h, int* n, int* dtype, void** dev_amps) {
 int sv_init_basis(sv_handle h, uint64_t x) {
     if (!h) return set_error(SV_EINVAL, "NULL handle");
     if (x >> h->n) return set_error(SV_EINVAL, "basis index out of range");
-    cudaError_t e = launch_init_basis(h, x);
-    if (e != cudaSuccess) {
-        h->bad = true;
-        return cuda_fail(e, "init_basis");
-    }
+    // Deferred: the next apply's first compiled pass builds its tiles from x
+    // (no write and read of the state); anything else writes it first.
+    h->pending_basis = (long long)x;
     h->bad = false;
     reset_perm(h);
     return SV_OK;
@@ -231,6 +254,7 @@ int sv_init_basis(sv_handle h, uint64_t x) {
 int sv_load_state(sv_handle h, const void* host_amps) {
     if (!h) return set_error(SV_EINVAL, "NULL handle");
     if (!host_amps) return set_error(SV_EINVAL, "NULL host buffer");
+    h->pending_basis = -1;
     cudaError_t e = cudaMemcpyAsync(h->amps, host_amps, amp_bytes(h->dtype) << h->n, cudaMemcpyHostToDevice,
                                     h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -301,7 +325,7 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
 }
 
 int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_options* opt) {
-    int rc = check_handle(h);
+    int rc = check_handle_noflush(h);
     if (rc) return rc;
     if (count && !gates) return set_error(SV_EINVAL, "NULL gate list");
     std::vector<CGate> cg;
@@ -357,6 +381,8 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     }
     Plan plan;
     if (po.planner == SV_PLAN_PLAIN) {
+        rc = flush_init(h);
+        if (rc) return rc;
         const std::vector<CGate>& cgm = *gl;
         plan_plain(h->n, h->dtype, cgm, &plan);
         for (const PlainOp& op : plan.plain_ops) {
@@ -393,6 +419,23 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
 int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, cudaEvent_t judge0,
                 cudaEvent_t judge1) {
     int rc = SV_OK;
+    // Compiled kernels (compiles happen here, before any timing event).  A
+    // deferred |x> is built by pass 0's tile loads when that pass has a
+    // compiled kernel for it; otherwise it is written now.
+    std::vector<void*> jit_fns;
+    void* fill0 = nullptr;
+    jit_prepare(h, blob, plan.jit, h->pending_basis, &jit_fns, &fill0);
+    long long basis = -1;
+    if (h->pending_basis >= 0) {
+        if (fill0) {
+            basis = h->pending_basis;
+            jit_fns[0] = fill0;
+            h->pending_basis = -1;
+        } else {
+            rc = flush_init(h);
+            if (rc) return rc;
+        }
+    }
     // Stage through pinned memory; only the previous upload from it has to
     // be finished (the passes of earlier calls may still be running).
     cudaError_t e = cudaSuccess;
@@ -416,13 +459,12 @@ int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, c
         if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "error word"));
     }
     memcpy(h->host_pin.ptr, blob.bytes.data(), blob.bytes.size());
+    if (basis >= 0) ((PassDev*)((char*)h->host_pin.ptr + blob.pass_off))[0].basis = basis;
     e = cudaMemcpyAsync(h->plan_dev.ptr, h->host_pin.ptr, blob.bytes.size(), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "plan upload"));
     e = cudaEventRecord(h->upload_ev, h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
     h->upload_pending = true;
-    std::vector<void*> jit_fns;
-    jit_prepare(h, blob, plan.jit, &jit_fns);
     if (judge0) cudaEventRecord(judge0, h->stream);
     for (int p = 0; p < blob.npasses; ++p) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -87,6 +87,8 @@ struct PassDev {
     int tq[kMaxTileM];   // tile qubits ascending
     int nother;
     int oq[40];          // non-tile qubits ascending
+    long long basis;     // >= 0: the state is |basis> and this pass's compiled kernel builds its tiles from it
+                         // instead of reading them (the deferred sv_init_basis); -1 otherwise
 };
 
 

@@ -257,6 +257,8 @@ struct sv_state {
     bool permuted;           // perm is not the identity
     sv::Scratch perm_tmp;    // device scratch of the permuted read-outs
     sv::Scratch aux;         // device scratch of the QCrank read-out (shots, counters, pixels)
+    long long pending_basis; // >= 0: sv_init_basis(x) not written yet (the next apply's first pass or any other
+                             // use of the state writes it)
     sv_options last_opts;    // options of the last planned apply
 };
 
@@ -274,6 +276,9 @@ QubitMap qubit_map(const sv_state* h);
 int set_error(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 void count_launch(uint64_t k = 1);
+
+// Write a deferred sv_init_basis to the state (no-op when none is pending).
+int flush_init(sv_state* h);
 
 // The body of sv_apply_circuit after validation: plan and launch on h's stream.
 int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
@@ -300,7 +305,10 @@ int num_sms_pub();
 // compiles missing ones now, 0 in the background once a structure is seen a
 // second time, -1 never.  jit_launch: run the pass on it (*used = false: the
 // caller runs the interpreting kernel).
-void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void*>* fns);
+// basis >= 0: *fill0 = a kernel for pass 0 that builds its tiles from |basis>
+// instead of reading them (nullptr when not ready).
+void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis, std::vector<void*>* fns,
+                 void** fill0);
 cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const PlanBlob& blob, int pass, bool* used);
 // One persistent launch for circuits of at most mmax qubits (single-tile
 // plans, one pass each, in blob order); outputs per circuit c at

@@ -158,7 +158,8 @@ CtLayout ct_layout(int dtype, int RB, int tb, const int* rp, const int* tp) {
 
 // The pass as straight-line code (mirrors InterpOps op by op).  Returns
 // false for a structure it does not take.
-bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int maxt, int minb, std::string* out) {
+bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int maxt, int minb, std::string* out,
+                 bool fill = false) {
     const int RB = reg_bits(dtype), tb = P.m - RB, L = P.L, m = P.m, no = P.nother;
     if (tb < 5 || tb > 9 || L < 1) return false;
     const OpDev* ops = (const OpDev*)region;
@@ -200,9 +201,20 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
             o << "g |= (uint64_t)((i0 >> " << L + b << ") & 1) << " << P.tq[L + b] << ";\n";
         o << "return g;\n}\n";
         o << "template <typename V>\nstatic __device__ __forceinline__ void issue(V* tile, const V* __restrict__ psi, "
-             "uint64_t base, const uint32_t*, int) {\n"
-          << "issue_ct<V, " << NCH << ", " << (add ? "true" : "false")
-          << ">(tile, psi, base + thread_goff(), swz<V>(" << PER << " * (int)threadIdx.x), KO, SW);\n}\n";
+             "uint64_t base, const uint32_t*, int, const PassDev& P) {\n";
+        if (fill) {
+            // |basis>: is it in this tile, and at which tile position?
+            uint64_t tmask = 0;
+            for (int p = 0; p < m; ++p) tmask |= 1ull << P.tq[p];
+            o << "const unsigned long long x = (unsigned long long)P.basis;\nint ix = -1;\n"
+              << "if ((x & ~" << tmask << "ull) == base) {\nix = 0;\n";
+            for (int p = 0; p < m; ++p) o << "ix |= (int)((x >> " << P.tq[p] << ") & 1) << " << p << ";\n";
+            o << "}\nfill_basis_ct<V, " << NCH << ", " << (add ? "true" : "false") << ">(tile, ix, " << PER
+              << " * (int)threadIdx.x, " << istep << ", swz<V>(" << PER << " * (int)threadIdx.x), SW);\n}\n";
+        } else {
+            o << "issue_ct<V, " << NCH << ", " << (add ? "true" : "false")
+              << ">(tile, psi, base + thread_goff(), swz<V>(" << PER << " * (int)threadIdx.x), KO, SW);\n}\n";
+        }
         o << "template <typename V>\nstatic __device__ __forceinline__ void store(const V* tile, V* __restrict__ psi, "
              "uint64_t base, const uint32_t*, int) {\n"
           << "store_ct<V, " << NCH << ", " << (add ? "true" : "false")
@@ -398,25 +410,31 @@ void compile_all(const std::vector<std::string>& srcs) {
 
 }  // namespace
 
-void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void*>* fns) {
+void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis, std::vector<void*>* fns,
+                 void** fill0) {
     fns->assign(blob.npasses, nullptr);
+    *fill0 = nullptr;
     // jit = 0 on a small state: nothing to compile or look up (writing the
     // pass sources would cost more than the passes)
     if (policy < 0 || (policy == 0 && h->n < kJitAutoMinQubits) || !nvrtc().ok || !driver().ok) return;
-    std::vector<std::string> srcs(blob.npasses);
+    // sources: one per register pass, plus pass 0 building |basis>
+    std::vector<std::string> srcs(blob.npasses + 1);
     std::vector<std::string> now;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        for (int p = 0; p < blob.npasses; ++p) {
-            const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
+        for (int p = 0; p <= blob.npasses; ++p) {
+            const bool fill = p == blob.npasses;
+            const int q = fill ? 0 : p;
+            if (fill && (basis < 0 || blob.npasses == 0)) continue;
+            const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + q;
             if (pd->rmode != 1) continue;
             const int tb = pd->m - reg_bits(h->dtype);
             if (!pass_source(*pd, blob.bytes.data() + pd->region_off, h->dtype, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
-                             tb <= 8 ? 2 : 1, &srcs[p]))
+                             tb <= 8 ? 2 : 1, &srcs[p], fill))
                 continue;
             Entry& e = g_cache[srcs[p]];
             e.seen++;
-            if (e.state == JIT_NEW && (policy == 1 || (e.seen >= 2 && h->n >= kJitAutoMinQubits))) {
+            if (e.state == JIT_NEW && (policy == 1 || e.seen >= 2)) {
                 e.state = JIT_COMPILING;
                 now.push_back(srcs[p]);
             }
@@ -424,10 +442,12 @@ void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, std::vector<void
     }
     if (!now.empty()) compile_all(now);
     std::lock_guard<std::mutex> lk(g_mu);
-    for (int p = 0; p < blob.npasses; ++p) {
+    for (int p = 0; p <= blob.npasses; ++p) {
         if (srcs[p].empty()) continue;
         auto it = g_cache.find(srcs[p]);
-        if (it != g_cache.end() && it->second.state == JIT_READY) (*fns)[p] = &it->second;
+        if (it == g_cache.end() || it->second.state != JIT_READY) continue;
+        if (p == blob.npasses) *fill0 = &it->second;
+        else (*fns)[p] = &it->second;
     }
 }
 
@@ -525,13 +545,15 @@ extern "C" int sv_jit_check(int n, sv_dtype dt, const sv_gate* gates, size_t cou
     // the check also asks ptxas for its register and spill report
     const char* opts[] = {archo, "-std=c++17", inc.c_str(), "-DSV_JIT=1", "-lineinfo", "--ptxas-options=-v"};
     std::string lastlog, alllogs;
-    for (int p = 0; p < blob.npasses; ++p) {
-        const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + p;
+    for (int p = 0; p <= blob.npasses; ++p) {  // the last round: pass 0 building its tiles from |x>
+        const bool fill = p == blob.npasses;
+        if (fill && blob.npasses == 0) break;
+        const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + (fill ? 0 : p);
         if (pd->rmode != 1) continue;
         const int tb = pd->m - reg_bits(dt);
         std::string src;
         if (!pass_source(*pd, blob.bytes.data() + pd->region_off, dt, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
-                         tb <= 8 ? 2 : 1, &src))
+                         tb <= 8 ? 2 : 1, &src, fill))
             continue;
         nvrtcProgram prog;
         if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)

@@ -1075,6 +1075,7 @@ void serialise_plans(const std::vector<const Plan*>& plans, PlanBlob* blob) {
             PassDev& P = pds[gpi];
             memset(&P, 0, sizeof(P));
             P.scale = 1.0;
+            P.basis = -1;
             P.n = n;
             P.m = (int)hp.tile.size();
             P.L = hp.L;

@@ -504,6 +504,26 @@ __device__ __forceinline__ void store_ct(const V* tile, V* __restrict__ psi, uin
     for (int k = 0; k < NCH; ++k)
         *(float4*)(psi + g + KO[k]) = *(const float4*)(tile + (ADD ? s0 + SW[k] : s0 ^ SW[k]));
 }
+// Tile of |x> (the deferred basis state) instead of loading it: this
+// thread's chunks are written with zeros, and the one holding tile position
+// ix (-1: x is not in this tile) gets the 1.
+template <typename V, int NCH, bool ADD>
+__device__ __forceinline__ void fill_basis_ct(V* tile, int ix, int i0, int istep, int s0, const int* SW) {
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int i = i0 + k * istep;
+        V* dst = tile + (ADD ? s0 + SW[k] : s0 ^ SW[k]);
+        if constexpr (sizeof(V) == 8) {  // two amplitudes per 16-byte chunk
+            *(float4*)dst = make_float4(ix == i ? 1.f : 0.f, 0.f, ix == i + 1 ? 1.f : 0.f, 0.f);
+        } else {
+            V a;
+            a.x = ix == i ? 1.0 : 0.0;
+            a.y = 0.0;
+            *dst = a;
+        }
+    }
+}
+
 template <typename V, int RB>
 __device__ __forceinline__ void scale_regs(V* v, decltype(V().x) sc) {
 #pragma unroll
@@ -556,7 +576,7 @@ __device__ __forceinline__ void fold_diags(const PassDev& P, const unsigned char
 struct InterpOps {
     template <typename V>
     static __device__ __forceinline__ void issue(V* tile, const V* __restrict__ psi, uint64_t base,
-                                                 const uint32_t* rowoff, int L) {
+                                                 const uint32_t* rowoff, int L, const PassDev&) {
         rissue_tile(tile, psi, base, rowoff, L);
     }
     template <typename V>
@@ -665,7 +685,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     auto tile_base = [&](uint64_t t) { return table_base(tbase, t, L); };
     int cur = 0;
     if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
-        Ops::template issue<V>(tiles[0], psi, tile_base(blockIdx.x), rowoff, L);
+        Ops::template issue<V>(tiles[0], psi, tile_base(blockIdx.x), rowoff, L, P);
         cp_async_commit();
     }
     V v[1 << RB];
@@ -675,14 +695,14 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         const uint64_t tn = t + gridDim.x;
         if (lay.nbuf == 2) {
             if (tn < ntiles) {
-                Ops::template issue<V>(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L);
+                Ops::template issue<V>(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L, P);
                 cp_async_commit();
                 cp_async_wait_group<1>();
             } else {
                 cp_async_wait_group<0>();
             }
         } else {
-            Ops::template issue<V>(tiles[0], psi, base, rowoff, L);
+            Ops::template issue<V>(tiles[0], psi, base, rowoff, L, P);
             cp_async_commit();
             cp_async_wait_group<0>();
         }
