@@ -490,8 +490,7 @@ def main():
             S.sv_init_basis(h2, x)
             S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
                                relabel=relabel, jit=jit)
-            S.sv_sample(h2, args.shots, i)
-            S.sv_expect_z(h2)
+            S.sv_measure(h2, args.shots, i)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         K = max(3, args.steps // 2)
@@ -499,8 +498,7 @@ def main():
             S.sv_init_basis(h2, x)
             S.sv_apply_circuit(h2, gh, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
                                relabel=relabel, jit=jit)
-            S.sv_sample(h2, args.shots, 1000 + i)
-            S.sv_expect_z(h2)
+            S.sv_measure(h2, args.shots, 1000 + i)  # shots and <Z> from one read, to host memory
         e2e_ms = 1e3 * (time.perf_counter() - t0) / K
         S.sv_free(h2)
         e2e = {"value": world * updates / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,

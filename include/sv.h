@@ -277,6 +277,9 @@ int sv_qcrank_reconstruct(sv_handle h, int a, int d, uint64_t shots, uint64_t se
  * pass over the state: the probability block statistics are computed once
  * and serve both.  Either output may be NULL (shots then ignored). */
 int sv_measure_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_samples, double *dev_expz);
+/* The same with host outputs (shots uint64 values, n doubles); returns when
+ * both are in host memory. */
+int sv_measure(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_samples, double *host_expz);
 
 /* Sampling that allocates nothing.  The paper has no counterpart; this entry
  * point exists for callers of this library that cannot allocate device

@@ -336,6 +336,19 @@ def sv_sample_device(h, shots, seed, dev_out_ptr):
     _check(lib().sv_sample_device(h, int(shots), int(seed), ctypes.c_void_p(dev_out_ptr)))
 
 
+def sv_measure(h, shots, seed, expz=True):
+    """Shots and <Z_i> from one read of the state, to host arrays."""
+    n, _ = _n_dtype(h)
+    L = lib()
+    f = L.sv_measure
+    f.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    samp = np.empty(int(shots), dtype=np.uint64)
+    ez = np.empty(n, dtype=np.float64) if expz else None
+    _check(f(h, int(shots), int(seed), _ptr(samp) if shots else None, _ptr(ez) if expz else None))
+    return samp, ez
+
+
 def sv_measure_device(h, shots, seed, dev_samples_ptr, dev_expz_ptr):
     L = lib()
     f = L.sv_measure_device

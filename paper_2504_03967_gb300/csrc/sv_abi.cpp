@@ -73,6 +73,27 @@ int ensure_pinned(Scratch* s, size_t bytes) {
     return SV_OK;
 }
 
+// Key of a plan: FNV-1a over the gate records, the options that shape the
+// plan, the state's size and type, and the qubit map it starts from.
+uint64_t plan_key(const sv_state* h, const sv_gate* gates, size_t count, const sv_options* opt) {
+    uint64_t k = 1469598103934665603ull;
+    auto mix = [&k](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) k = (k ^ b[i]) * 1099511628211ull;
+    };
+    mix(gates, count * sizeof(sv_gate));
+    const int hdr[3] = {h->n, h->dtype, h->permuted ? 1 : 0};
+    mix(hdr, sizeof(hdr));
+    if (opt) {
+        const int f[9] = {opt->k_max, opt->tile_m, opt->planner, opt->tensor, opt->pass_kernel, opt->relabel, opt->mux,
+                          opt->jit, 1};
+        mix(f, sizeof(f));
+        mix(&opt->drop_phase_below, sizeof(double));
+    }
+    if (h->permuted) mix(h->perm, sizeof(int) * h->n);
+    return k ? k : 1;
+}
+
 int flush_init(sv_state* h) {
     if (h->pending_basis < 0) return SV_OK;
     const uint64_t x = (uint64_t)h->pending_basis;
@@ -121,6 +142,7 @@ int make_handle(int n, sv_dtype dt, void* amps, bool owned, void* stream, sv_han
     h->upload_ev = nullptr;
     h->upload_pending = false;
     h->pending_basis = -1;
+    h->plans = nullptr;
     reset_perm(h);
     memset(&h->last_opts, 0, sizeof(h->last_opts));
     *out = h;
@@ -212,6 +234,7 @@ int sv_free(sv_handle h) {
     if (h->err.ptr) cudaFree(h->err.ptr);
     if (h->perm_tmp.ptr) cudaFree(h->perm_tmp.ptr);
     if (h->aux.ptr) cudaFree(h->aux.ptr);
+    delete h->plans;
     if (h->host_pin.ptr) cudaFreeHost(h->host_pin.ptr);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->upload_ev) cudaEventDestroy(h->upload_ev);
@@ -328,11 +351,29 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     int rc = check_handle_noflush(h);
     if (rc) return rc;
     if (count && !gates) return set_error(SV_EINVAL, "NULL gate list");
+    // the plain planner has no plan; the cost-model planner's plans are kept
+    // once its judge has settled on a candidate for the circuit
+    const bool cacheable = count && (!opt || opt->planner != SV_PLAN_PLAIN);
+    uint64_t key = 0;
+    if (cacheable) {
+        key = plan_key(h, gates, count, opt);
+        if (h->plans) {
+            for (auto& kv : h->plans->entries) {
+                if (kv.first != key) continue;
+                CachedPlan& c = kv.second;
+                c.stamp = ++h->plans->clock;
+                memcpy(h->perm, c.perm_after, sizeof(h->perm));
+                h->permuted = c.permuted_after;
+                h->last_opts = c.last_opts;
+                return launch_plan(h, c.plan, c.blob, opt && opt->record, nullptr, nullptr, &c.jit_srcs);
+            }
+        }
+    }
     std::vector<CGate> cg;
     size_t bad = 0;
     if (canonicalise(h->n, gates, count, &cg, &bad) != SV_OK)
         return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
-    return sv::apply_canonical(h, gates, count, cg, opt);
+    return sv::apply_canonical(h, gates, count, cg, opt, key);
 }
 
 }  // extern "C"
@@ -340,7 +381,7 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
 namespace sv {
 
 int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
-                    const sv_options* opt) {
+                    const sv_options* opt, uint64_t cache_key) {
     int rc = SV_OK;
     if (cg.empty()) return SV_OK;
     PlanOptions po = resolve_options(h->n, h->dtype, opt);
@@ -413,18 +454,38 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     h->last_opts.drop_phase_below = po.drop_phase_below;
     PlanBlob blob;
     serialise_plan(plan, &blob);
+    if (cache_key && !judge0) {  // keep it for the next apply of the same circuit (not while the judge times)
+        if (!h->plans) h->plans = new (std::nothrow) PlanCache();
+        if (h->plans) {
+            auto& es = h->plans->entries;
+            if ((int)es.size() >= kPlanCacheEntries) {
+                size_t old = 0;
+                for (size_t i = 1; i < es.size(); ++i)
+                    if (es[i].second.stamp < es[old].second.stamp) old = i;
+                es.erase(es.begin() + old);
+            }
+            es.emplace_back(cache_key, CachedPlan());
+            CachedPlan& c = es.back().second;
+            c.plan = plan;
+            c.blob = blob;
+            memcpy(c.perm_after, h->perm, sizeof(h->perm));
+            c.permuted_after = h->permuted;
+            c.last_opts = h->last_opts;
+            c.stamp = ++h->plans->clock;
+        }
+    }
     return launch_plan(h, plan, blob, opt && opt->record, judge0, judge1);
 }
 
 int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, cudaEvent_t judge0,
-                cudaEvent_t judge1) {
+                cudaEvent_t judge1, std::vector<std::string>* jit_srcs) {
     int rc = SV_OK;
     // Compiled kernels (compiles happen here, before any timing event).  A
     // deferred |x> is built by pass 0's tile loads when that pass has a
     // compiled kernel for it; otherwise it is written now.
     std::vector<void*> jit_fns;
     void* fill0 = nullptr;
-    jit_prepare(h, blob, plan.jit, h->pending_basis, &jit_fns, &fill0);
+    jit_prepare(h, blob, plan.jit, h->pending_basis, &jit_fns, &fill0, jit_srcs);
     long long basis = -1;
     if (h->pending_basis >= 0) {
         if (fill0) {
@@ -679,4 +740,26 @@ extern "C" int sv_measure_device(sv_handle h, uint64_t shots, uint64_t seed, uin
     if (rc) return rc;
     if (shots && !dev_samples) return set_error(SV_EINVAL, "NULL samples output");
     return fail_state(h, measure_readout(h, dev_samples ? shots : 0, seed, dev_samples, dev_expz));
+}
+
+// Host outputs of sv_measure_device: one read of the state for both.
+extern "C" int sv_measure(sv_handle h, uint64_t shots, uint64_t seed, uint64_t* host_samples, double* host_expz) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (shots && !host_samples) return set_error(SV_EINVAL, "NULL samples output");
+    if (!host_samples) shots = 0;
+    const size_t sb = sizeof(uint64_t) * shots, eb = host_expz ? sizeof(double) * h->n : 0;
+    if (!sb && !eb) return SV_OK;
+    rc = ensure_scratch(&h->out_dev, sb + eb, h->stream);
+    if (rc) return rc;
+    uint64_t* ds = sb ? (uint64_t*)h->out_dev.ptr : nullptr;
+    double* de = eb ? (double*)((char*)h->out_dev.ptr + sb) : nullptr;
+    rc = measure_readout(h, shots, seed, ds, de);
+    if (rc) return fail_state(h, rc);
+    if (eb && sb) {
+        cudaError_t e = cudaMemcpyAsync(host_samples, ds, sb, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "samples readback"));
+        return sync_d2h(h, host_expz, de, eb, "expz readback");
+    }
+    return sb ? sync_d2h(h, host_samples, ds, sb, "samples readback") : sync_d2h(h, host_expz, de, eb, "expz readback");
 }

@@ -232,6 +232,7 @@ struct Scratch {
     void* ptr = nullptr;
     size_t cap = 0;
 };
+struct PlanCache;
 
 }  // namespace sv
 
@@ -259,6 +260,7 @@ struct sv_state {
     sv::Scratch aux;         // device scratch of the QCrank read-out (shots, counters, pixels)
     long long pending_basis; // >= 0: sv_init_basis(x) not written yet (the next apply's first pass or any other
                              // use of the state writes it)
+    sv::PlanCache* plans;    // recent plans of this handle (sv_apply_circuit)
     sv_options last_opts;    // options of the last planned apply
 };
 
@@ -279,15 +281,35 @@ void count_launch(uint64_t k = 1);
 
 // Write a deferred sv_init_basis to the state (no-op when none is pending).
 int flush_init(sv_state* h);
+uint64_t plan_key(const sv_state* h, const sv_gate* gates, size_t count, const sv_options* opt);
 
 // The body of sv_apply_circuit after validation: plan and launch on h's stream.
+// cache_key != 0: keep the plan under that key (see PlanCache).
 int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
-                    const sv_options* opt);
+                    const sv_options* opt, uint64_t cache_key = 0);
+
+// Recent plans of a handle: the same gate records, options and qubit map
+// give the same plan, so a repeated apply skips validation, planning and
+// serialisation (and the compiled-kernel lookup reuses its sources).
+struct CachedPlan {
+    Plan plan;
+    PlanBlob blob;
+    int perm_after[64];
+    bool permuted_after;
+    sv_options last_opts;
+    uint64_t stamp;
+    std::vector<std::string> jit_srcs;  // compiled-kernel sources of its passes (filled on first launch)
+};
+struct PlanCache {
+    std::vector<std::pair<uint64_t, CachedPlan>> entries;  // small: linear search, least recently used evicted
+    uint64_t clock = 0;
+};
+constexpr int kPlanCacheEntries = 8;
 
 // Upload a serialised plan through h's pinned staging and launch its passes
 // on h's stream (rec: events around each pass; judge0/1: around all of them).
 int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, cudaEvent_t judge0,
-                cudaEvent_t judge1);
+                cudaEvent_t judge1, std::vector<std::string>* jit_srcs = nullptr);
 
 int ensure_scratch(Scratch* s, size_t bytes, cudaStream_t st);
 int ensure_pinned(Scratch* s, size_t bytes);
@@ -307,8 +329,10 @@ int num_sms_pub();
 // caller runs the interpreting kernel).
 // basis >= 0: *fill0 = a kernel for pass 0 that builds its tiles from |basis>
 // instead of reading them (nullptr when not ready).
+// srcs (optional): the pass sources of this blob, written on first use and
+// reused after (a cached plan keeps them).
 void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis, std::vector<void*>* fns,
-                 void** fill0);
+                 void** fill0, std::vector<std::string>* srcs = nullptr);
 cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const PlanBlob& blob, int pass, bool* used);
 // One persistent launch for circuits of at most mmax qubits (single-tile
 // plans, one pass each, in blob order); outputs per circuit c at

@@ -411,27 +411,34 @@ void compile_all(const std::vector<std::string>& srcs) {
 }  // namespace
 
 void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis, std::vector<void*>* fns,
-                 void** fill0) {
+                 void** fill0, std::vector<std::string>* memo) {
     fns->assign(blob.npasses, nullptr);
     *fill0 = nullptr;
     // jit = 0 on a small state: nothing to compile or look up (writing the
     // pass sources would cost more than the passes)
     if (policy < 0 || (policy == 0 && h->n < kJitAutoMinQubits) || !nvrtc().ok || !driver().ok) return;
-    // sources: one per register pass, plus pass 0 building |basis>
-    std::vector<std::string> srcs(blob.npasses + 1);
+    // sources: one per register pass, plus pass 0 building |basis> (a
+    // cached plan keeps them: writing them is most of this function's time)
+    std::vector<std::string> local;
+    std::vector<std::string>& srcs = memo ? *memo : local;
+    const bool fresh = (int)srcs.size() != blob.npasses + 1;
+    if (fresh) {
+        srcs.assign(blob.npasses + 1, std::string());
+        for (int p = 0; p <= blob.npasses; ++p) {
+            const bool fill = p == blob.npasses;
+            const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + (fill ? 0 : p);
+            if ((fill && blob.npasses == 0) || pd->rmode != 1) continue;
+            const int tb = pd->m - reg_bits(h->dtype);
+            if (!pass_source(*pd, blob.bytes.data() + pd->region_off, h->dtype, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
+                             tb <= 8 ? 2 : 1, &srcs[p], fill))
+                srcs[p].clear();
+        }
+    }
     std::vector<std::string> now;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         for (int p = 0; p <= blob.npasses; ++p) {
-            const bool fill = p == blob.npasses;
-            const int q = fill ? 0 : p;
-            if (fill && (basis < 0 || blob.npasses == 0)) continue;
-            const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + q;
-            if (pd->rmode != 1) continue;
-            const int tb = pd->m - reg_bits(h->dtype);
-            if (!pass_source(*pd, blob.bytes.data() + pd->region_off, h->dtype, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
-                             tb <= 8 ? 2 : 1, &srcs[p], fill))
-                continue;
+            if (srcs[p].empty() || (p == blob.npasses && basis < 0)) continue;
             Entry& e = g_cache[srcs[p]];
             e.seen++;
             if (e.state == JIT_NEW && (policy == 1 || e.seen >= 2)) {
@@ -443,7 +450,7 @@ void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis,
     if (!now.empty()) compile_all(now);
     std::lock_guard<std::mutex> lk(g_mu);
     for (int p = 0; p <= blob.npasses; ++p) {
-        if (srcs[p].empty()) continue;
+        if (srcs[p].empty() || (p == blob.npasses && basis < 0)) continue;
         auto it = g_cache.find(srcs[p]);
         if (it == g_cache.end() || it->second.state != JIT_READY) continue;
         if (p == blob.npasses) *fill0 = &it->second;

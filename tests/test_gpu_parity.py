@@ -239,6 +239,8 @@ def test_measure_device_one_pass(dtype, n):
         assert np.array_equal(ds.cpu().numpy().view(np.uint64), S.sv_sample(h, 3000, 42))
         ez = S.sv_expect_z(h)
         assert np.array_equal(dz.cpu().numpy(), ez)
+        hs, hz = S.sv_measure(h, 3000, 42)  # host outputs, one read
+        assert np.array_equal(hs, ds.cpu().numpy().view(np.uint64)) and np.array_equal(hz, ez)
         ref = U.run_oracle(n, g)
         assert np.abs(ez - oracle.expect_z(ref)).max() <= (1e-5 if dtype == S.C64 else 1e-12)
     finally:
