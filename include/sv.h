@@ -223,6 +223,24 @@ int sv_apply_circuit(sv_handle h, const sv_gate *gates, size_t count, const sv_o
 
 /* Plan without running: fills *info for a circuit on n qubits of dtype dt.
  * Host only; usable without a GPU. */
+/* Run-time compiled passes: kernels compiled, compiles that failed, passes
+ * launched on them and host milliseconds spent compiling (process totals);
+ * sv_jit_fills: passes that built their tiles from a deferred basis state
+ * instead of reading the state.  sv_jit_wait returns at once (compiles finish
+ * inside the apply that starts them). */
+int sv_jit_stats(uint64_t *compiled, uint64_t *failed, uint64_t *launched, double *compile_ms);
+int sv_jit_fills(uint64_t *filled);
+int sv_jit_wait(void);
+/* Host-only check of the pass compiler (no GPU needed): plan the circuit,
+ * write the run-time kernel source of every register-resident pass (and of
+ * pass 0 building its tiles from a basis state) and compile it with NVRTC for
+ * sm_<arch>a.  *compiled = kernels compiled; log (cap bytes) receives the
+ * compiler's output (with the source when a compile fails).  SV_EUNSUPPORTED
+ * without NVRTC.  sv_jit_last_log: the last run-time compile's log. */
+int sv_jit_check(int n, sv_dtype dt, const sv_gate *gates, size_t count, const sv_options *opt, int arch,
+                 int *compiled, char *log, size_t cap);
+int sv_jit_last_log(char *buf, size_t cap);
+
 int sv_plan_circuit(int n, sv_dtype dt, const sv_gate *gates, size_t count,
                     const sv_options *opt, sv_plan_info *info);
 

@@ -307,7 +307,13 @@ def sv_jit_stats():
     c, fl, ln = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     ms = ctypes.c_double()
     _check(f(ctypes.byref(c), ctypes.byref(fl), ctypes.byref(ln), ctypes.byref(ms)))
-    return {"compiled": c.value, "failed": fl.value, "launched": ln.value, "compile_ms": ms.value}
+    fi = ctypes.c_uint64()
+    g = L.sv_jit_fills
+    g.argtypes = [ctypes.c_void_p]
+    g.restype = ctypes.c_int
+    _check(g(ctypes.byref(fi)))
+    return {"compiled": c.value, "failed": fl.value, "launched": ln.value, "compile_ms": ms.value,
+            "filled": fi.value}
 
 
 def sv_jit_wait():

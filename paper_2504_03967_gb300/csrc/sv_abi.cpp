@@ -532,6 +532,7 @@ int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, c
         if (rec && (e0 = next_event(h)) && (e1 = next_event(h))) cudaEventRecord(e0, h->stream);
         bool jitted = false;
         e = jit_launch(h, jit_fns[p], h->plan_dev.ptr, blob, p, &jitted);
+        if (e == cudaSuccess && jitted && p == 0 && basis >= 0) jit_count_fill();
         if (e == cudaSuccess && !jitted) e = launch_pass(h, h->plan_dev.ptr, blob, p, plan.passes[p]);
         if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "tile pass kernel"));
         if (rec && e1) {

@@ -79,6 +79,13 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
     std::vector<int> bad(C, 0);
     const PlanOptions probe = resolve_options(1, dt, opt);
     const bool host_plans = probe.planner == SV_PLAN_GREEDY && !probe.relabel;
+    // Run-time compiled passes only when asked for (jit = 1): a batch of
+    // mostly different circuits would spend its time compiling.
+    sv_options bopt;
+    memset(&bopt, 0, sizeof(bopt));
+    if (opt) bopt = *opt;
+    if (bopt.jit != 1) bopt.jit = -1;
+    opt = &bopt;
     std::vector<std::unique_ptr<Prepared>> prep(C);
     parallel_for(C, [&](int c) {
         size_t b = 0;
@@ -210,6 +217,8 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
             slots[s].h.ev_used = 0;
             slots[s].h.upload_ev = nullptr;
             slots[s].h.upload_pending = false;
+            slots[s].h.pending_basis = -1;
+            slots[s].h.plans = nullptr;
         }
         if (e != cudaSuccess) {
             cudaGetLastError();

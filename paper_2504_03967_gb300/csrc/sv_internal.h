@@ -334,6 +334,7 @@ int num_sms_pub();
 void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis, std::vector<void*>* fns,
                  void** fill0, std::vector<std::string>* srcs = nullptr);
 cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const PlanBlob& blob, int pass, bool* used);
+void jit_count_fill();
 // One persistent launch for circuits of at most mmax qubits (single-tile
 // plans, one pass each, in blob order); outputs per circuit c at
 // samples + c*shots and expz + c*nmax (either may be NULL).

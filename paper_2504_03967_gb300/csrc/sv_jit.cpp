@@ -341,7 +341,7 @@ struct Entry {
 
 std::mutex g_mu;
 std::unordered_map<std::string, Entry> g_cache;
-uint64_t g_compiled = 0, g_failed = 0, g_launched = 0;
+uint64_t g_compiled = 0, g_failed = 0, g_launched = 0, g_filled = 0;
 double g_compile_ms = 0.0;
 std::string g_last_log;
 
@@ -501,6 +501,20 @@ cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const Pla
 }  // namespace sv
 
 using namespace sv;
+
+namespace sv {
+void jit_count_fill() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    ++g_filled;
+}
+}  // namespace sv
+
+// Passes that built their tiles from a deferred basis state (no state read).
+extern "C" int sv_jit_fills(uint64_t* filled) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (filled) *filled = g_filled;
+    return SV_OK;
+}
 
 extern "C" int sv_jit_stats(uint64_t* compiled, uint64_t* failed, uint64_t* launched, double* compile_ms) {
     std::lock_guard<std::mutex> lk(g_mu);
