@@ -50,8 +50,8 @@ UNIT = "amp_updates/s"
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
                    "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
-TRAFFIC = {"sha256": "5d6038a2b5b2d5815b7dc36688c5b228910ef69a3cd7bb628f85c9da405c3204",
-           "bytes_per_amp": 15.7528, "profile": "profiles/sv_jit_pass_qft26_c64_k5m13.md (n=26 capture, scaled to 2^n)"}
+TRAFFIC = {"sha256": "68c77dc7a770022fc93405e841e761ef78ba3737d11c18158cf43f8c4b084234",
+           "bytes_per_amp": 13.0828, "profile": "profiles/sv_jit_pass_qft26_c64_k5m13.md (n=26 capture, scaled to 2^n)"}
 
 
 def sources_sha():
