@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
         const uint64_t t = tile_of(j);
         V* tile = (V*)(smem + (size_t)s * lay.tile_bytes);
         if (P.ndiag) fold_diags<R>(P, stage, fold, dofs, t);
-        InterpOps::tile<V, R, RB>(v, tile, P, stage, fold, Lg);
+        InterpOps::tile<V, R, RB>(v, tile, P, stage, fold, Lg, nullptr);
         if (P.scale != 1.0) {
             const R sc = (R)P.scale;
 #pragma unroll

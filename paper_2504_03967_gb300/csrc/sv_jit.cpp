@@ -222,7 +222,7 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     }
     o << "template <typename V, typename R, int RB>\n"
          "static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,\n"
-         "                                            const uint64_t* fold, RegLayout<V, RB>& Lg) {\n";
+         "                                            const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab) {\n";
     int rpos[8] = {0}, tpos[16] = {0};
     bool in_regs = false;
     CtLayout cur;
@@ -294,7 +294,7 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
             emit_ints(o, "rp", rpos, RB);
             emit_ints(o, "tp", tpos, tb);
             o << "reg_diag<V, R, RB>(v, (const uint64_t*)(stage + " << op.diag_off << "), fold + " << op.ord * (m + 1)
-              << ", " << m << ", " << no << ", rp, tp, " << tb << ");\n}\n";
+              << ", " << m << ", " << no << ", rp, tp, " << tb << ", ttab);\n}\n";
             break;
         default:
             return false;

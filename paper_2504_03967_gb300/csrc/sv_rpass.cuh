@@ -241,6 +241,7 @@ template <> struct Turns<float> {
     static __device__ __forceinline__ void sincos(U ph, float* s, float* c) {
         __sincosf((float)(int32_t)ph * 1.46291807926715968e-09f, s, c);  // 2 pi / 2^32
     }
+    static __device__ __forceinline__ void sincos_t(U ph, const double2*, float* s, float* c) { sincos(ph, s, c); }
 };
 template <> struct Turns<double> {
     using U = uint64_t;
@@ -248,7 +249,35 @@ template <> struct Turns<double> {
     static __device__ __forceinline__ void sincos(U ph, double* s, double* c) {
         sincospi((double)(int64_t)ph * 1.08420217248550443e-19, s, c);  // 2 / 2^64
     }
+    // Table-driven (Tang's method): the top 8 bits of the phase pick
+    // (cos, sin)(2 pi k / 256) from tab, the remaining fraction of a turn
+    // (an angle below 2 pi / 256) goes through its Taylor series to the
+    // x^9 / x^8 terms (truncation below 1e-18), and the angle-sum formulas
+    // combine the two: about half the FP64 work of a general sincos.
+    static __device__ __forceinline__ void sincos_t(U ph, const double2* tab, double* s, double* c) {
+        if (!tab) {
+            sincos(ph, s, c);
+            return;
+        }
+        const double2 e = tab[ph >> 56];
+        const double th = (double)(ph & 0x00ffffffffffffffull) * 3.4061215800865545e-19;  // 2 pi / 2^64
+        const double t = th * th;
+        const double sn = th * fma(t, fma(t, fma(t, fma(t, 2.7557319223985893e-06, -1.984126984126984e-04),
+                                                  8.333333333333333e-03), -1.6666666666666666e-01), 1.0);
+        const double cs = fma(t, fma(t, fma(t, fma(t, 2.48015873015873e-05, -1.388888888888889e-03),
+                                             4.1666666666666664e-02), -0.5), 1.0);
+        *c = fma(e.x, cs, -e.y * sn);
+        *s = fma(e.y, cs, e.x * sn);
+    }
 };
+// (cos, sin)(2 pi k / 256), k < 256, into a CTA's table (complex128 phases).
+__device__ __forceinline__ void build_turn_table(double2* tab) {
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        double sn, cs;
+        sincospi((double)k / 128.0, &sn, &cs);
+        tab[k] = make_double2(cs, sn);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Register-resident tile pass.  Thread t of a CTA of 2^(m-RB) threads holds
@@ -398,7 +427,7 @@ __device__ __forceinline__ uint64_t table_base(const uint32_t (*tb)[256], uint64
 // run's RDiagLayout words for the current layout.
 template <typename V, typename R, int RB>
 __device__ __forceinline__ void reg_diag(V* v, const uint64_t* __restrict__ dw, const uint64_t* fold, int m, int no,
-                                         const int* rpos, const int* tpos, int tb) {
+                                         const int* rpos, const int* tpos, int tb, const double2* ttab = nullptr) {
     using T = Turns<R>;
     using U = typename T::U;
     const RDiagLayout Lr(m, no);
@@ -457,7 +486,7 @@ __device__ __forceinline__ void reg_diag(V* v, const uint64_t* __restrict__ dw, 
             for (int b = 0; b < LB; ++b)
                 if ((u >> b) & 1) ph += cb[b];
             R sn, cs;
-            T::sincos(ph, &sn, &cs);
+            T::sincos_t(ph, ttab, &sn, &cs);
             V f;
             f.x = cs;
             f.y = sn;
@@ -599,7 +628,7 @@ struct InterpOps {
     }
     template <typename V, typename R, int RB>
     static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,
-                                                const uint64_t* fold, RegLayout<V, RB>& Lg) {
+                                                const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab) {
     const int m = P.m, tb = m - RB, no = P.nother;
     const OpDev* ops = (const OpDev*)stage;
     const int* rpos = nullptr;
@@ -634,7 +663,7 @@ struct InterpOps {
         }
         default:
             reg_diag<V, R, RB>(v, (const uint64_t*)(stage + op.diag_off), fold + (size_t)op.ord * (m + 1), m, no,
-                               rpos, tpos, tb);
+                               rpos, tpos, tb, ttab);
             break;
         }
     }
@@ -652,6 +681,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
     __shared__ uint32_t tbase[3][256];
+    __shared__ double2 ttab[sizeof(R) == 8 ? 256 : 1];  // complex128: the phase table of Turns::sincos_t
     {
         const int* src = (const int*)pdp;
         int* dst = (int*)&P;
@@ -675,6 +705,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         rowoff[r] = o;
     }
     build_base_tables(tbase, P);
+    if constexpr (sizeof(R) == 8) build_turn_table(ttab);
     cp_async_wait_group<0>();
     __syncthreads();
     const OpDev* ops = (const OpDev*)stage;
@@ -709,7 +740,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         __syncthreads();
         V* tile = tiles[cur];
         if (nd) fold_diags<R>(P, stage, fold, dofs, t);
-        Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg);
+        Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg, sizeof(R) == 8 ? ttab : nullptr);
         Ops::template finish<V, R, RB>(v, tile, P, Lg);
         __syncthreads();
         Ops::template store<V>(tile, psi, base, rowoff, L);
