@@ -210,6 +210,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (every rank gets it); x itself without a
+    process group.  Replicas: each rank runs the whole workload on its GPU, so
+    the job's time is the slowest rank's and its value is
+    world_size * work / that time (weak scaling)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def _event_ms(torch, stream, fn, reps):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -417,11 +436,7 @@ def main():
         launches = S.sv_launch_count() - l0
         timed.fills = S.sv_jit_stats()["filled"] - f0
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, "cuda")
         return ms, launches
 
     cm = None
@@ -455,7 +470,7 @@ def main():
                      "source": args.planner}
     plan_opts.update({"dense_ops": plan["dense_ops"], "gate_ops": plan["gate_ops"], "diag_ops": plan["diag_ops"],
                       "register_passes": plan["reg_passes"], "remaps": plan["remaps"]})
-    value = world * updates / (ms / 1e3)
+    value = job_value(world, updates, ms)
     hbm, src = peaks()
     # dominant kernel: the tile pass (one read + one write of 2^n amplitudes)
     roof = None
