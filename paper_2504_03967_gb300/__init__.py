@@ -317,7 +317,7 @@ def sv_jit_stats():
 
 
 def sv_jit_wait():
-    """Block until background pass compiles have finished."""
+    """Returns at once: pass compiles finish inside the apply that starts them."""
     _check(lib().sv_jit_wait())
 
 

@@ -324,9 +324,10 @@ PassLayout rpass_layout(int dtype, const PassDev& P);
 int num_sms_pub();
 // Run-time compiled register passes (sv_jit.cpp).  jit_prepare: per pass of
 // the blob, the compiled kernel ready for it (else nullptr); policy 1
-// compiles missing ones now, 0 in the background once a structure is seen a
-// second time, -1 never.  jit_launch: run the pass on it (*used = false: the
-// caller runs the interpreting kernel).
+// compiles missing ones now, 0 once a structure is seen a second time on a
+// state of 22 or more qubits (compiles finish inside the call), -1 never.
+// jit_launch: run the pass on it (*used = false: the caller runs the
+// interpreting kernel).
 // basis >= 0: *fill0 = a kernel for pass 0 that builds its tiles from |basis>
 // instead of reading them (nullptr when not ready).
 // srcs (optional): the pass sources of this blob, written on first use and
