@@ -85,15 +85,11 @@ def test_batch_variational_sweep():
     _check_expz(ez, circuits, S.C64)
 
 
-@pytest.mark.parametrize("count,a_max", [
-    (64, 10),
-    pytest.param(512, 14, marks=pytest.mark.skipif(
-        not os.environ.get("SV_FULL_SIZE"), reason="full config-3 batch (~4 min): set SV_FULL_SIZE=1")),
-], ids=["64x-a10", "512x-a14"])
+@pytest.mark.parametrize("count,a_max", [(64, 10), (512, 14)], ids=["64x-a10", "512x-a14"])
 def test_batch_qcrank_full_size(count, a_max):
     """Config-3 shape: QCrank circuits with a ~ U{8..a_max}, d ~ U{4..10},
-    10^5 shots each, complex64, one call (512 circuits up to 24 qubits with
-    SV_FULL_SIZE=1).  Pinned: every circuit's <Z> of the data qubits against
+    10^5 shots each, complex64, one call (the full batch: 512 circuits up to
+    24 qubits, 37.5 M gates, seconds with the multiplexor passes).  Pinned: every circuit's <Z> of the data qubits against
     the closed form mean_j cos(pi pixel_jk) and of the address qubits against
     0 (uniform addresses), the data marginals from the shots of sampled
     circuits, and exact <Z> against the oracle on the smallest circuits."""
