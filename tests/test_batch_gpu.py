@@ -2,7 +2,6 @@
 uneven sizes spanning the shared-memory path (n <= 13 / 12) and the tile-pass
 path, QCrank image-encoding circuits (config-3 shape at reduced size) and
 variational-ansatz parameter sets (config-5 shape)."""
-import os
 
 import numpy as np
 import pytest
