@@ -210,57 +210,274 @@ bool is_real(const cd* m, int cnt) {
 }
 
 // The block as a sequence on block-local positions: consecutive one-qubit
-// gates on one position multiplied together, runs of diagonal gates folded
-// into one 2^k-entry phase table, CX and SWAP kept as permutations.  False
-// when the block holds a gate this form does not cover or exceeds the
-// record limits.
-bool gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<cd>* data) {
+// gates on one position multiplied together, diagonal gates gathered into
+// one 2^k-entry phase table, CX and SWAP kept as permutations.  The pending
+// table is applied only before a one-qubit gate on a position it depends on:
+// it commutes with one-qubit gates elsewhere, and it moves past a
+// permutation P as D'[j] = D[P(j)] (CX and SWAP are involutions).  Before
+// such a flush, later diagonal gates that commute with every gate between
+// join the table.  With split_u3, U3(t, f, l) enters as P(l) RY(t) P(f), an
+// exact factorisation whose phases join the tables and whose RY is a real
+// 2x2 (half the arithmetic of a complex one).  False when the block holds a
+// gate this form does not cover or exceeds the record limits.
+bool gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<cd>* data, bool split_u3 = false) {
     recs->clear();
     data->clear();
     const int k = (int)B.qubits.size(), D = 1 << k;
+    std::vector<CGate> seq;
+    seq.reserve(B.seq.size() * 3);
+    for (const CGate& g : B.seq) {
+        if (split_u3 && g.type == SV_U3) {
+            sv_gate e;
+            memset(&e, 0, sizeof(e));
+            e.nq = 1;
+            e.q[0] = (uint32_t)g.q[0];
+            CGate c;
+            e.type = SV_P;
+            e.p[0] = g.p[2];
+            make_canonical(e, &c);
+            seq.push_back(c);
+            e.type = SV_RY;
+            e.p[0] = g.p[0];
+            make_canonical(e, &c);
+            seq.push_back(c);
+            e.type = SV_P;
+            e.p[0] = g.p[1];
+            make_canonical(e, &c);
+            seq.push_back(c);
+        } else {
+            seq.push_back(g);
+        }
+    }
+    auto posmask = [&](const CGate& g) {
+        int m = 1 << B.pos(g.q[0]);
+        if (g.nq > 1) m |= 1 << B.pos(g.q[1]);
+        return m;
+    };
     std::vector<double> ph(D, 0.0);
     bool dpend = false;
+    int dep = 0;  // positions the pending table depends on
+    auto add_diag = [&](const CGate& g) {
+        const int p0 = B.pos(g.q[0]), p1 = g.nq > 1 ? B.pos(g.q[1]) : 0;
+        for (int j = 0; j < D; ++j) {
+            int li = (j >> p0) & 1;
+            if (g.nq > 1) li |= ((j >> p1) & 1) << 1;
+            ph[j] += g.ph[li];
+        }
+        dpend = true;
+        dep |= posmask(g);
+    };
     auto flush_diag = [&]() {
         if (!dpend) return;
         recs->push_back(GateRec{GR_DT, 0, 0, (int)data->size()});
         for (int j = 0; j < D; ++j) data->push_back(std::polar(1.0, ph[j]));
         std::fill(ph.begin(), ph.end(), 0.0);
         dpend = false;
+        dep = 0;
     };
-    for (const CGate& g : B.seq) {
+    const int N = (int)seq.size();
+    std::vector<char> used(N, 0);
+    for (int i = 0; i < N; ++i) {
+        if (used[i]) continue;
+        const CGate& g = seq[i];
         if (g.kind == GK_DIAG) {
-            const int p0 = B.pos(g.q[0]), p1 = g.nq > 1 ? B.pos(g.q[1]) : 0;
-            for (int j = 0; j < D; ++j) {
-                int li = (j >> p0) & 1;
-                if (g.nq > 1) li |= ((j >> p1) & 1) << 1;
-                ph[j] += g.ph[li];
-            }
-            dpend = true;
+            add_diag(g);
             continue;
         }
-        flush_diag();
-        if (g.nq == 1) {
-            const int p = B.pos(g.q[0]);
-            if (!recs->empty() && (recs->back().kind == GR_U || recs->back().kind == GR_UR) && recs->back().a == p) {
-                cd* Mp = data->data() + recs->back().off;  // merge: M = G * M_prev
-                const cd M[4] = {g.m[0] * Mp[0] + g.m[1] * Mp[2], g.m[0] * Mp[1] + g.m[1] * Mp[3],
-                                 g.m[2] * Mp[0] + g.m[3] * Mp[2], g.m[2] * Mp[1] + g.m[3] * Mp[3]};
-                for (int i = 0; i < 4; ++i) Mp[i] = M[i];
-                recs->back().kind = is_real(Mp, 4) ? GR_UR : GR_U;
-            } else {
-                recs->push_back(GateRec{is_real(g.m, 4) ? GR_UR : GR_U, p, 0, (int)data->size()});
-                for (int i = 0; i < 4; ++i) data->push_back(g.m[i]);
+        if (g.type == SV_CX || g.type == SV_SWAP) {
+            const int pa = B.pos(g.q[0]), pb = B.pos(g.q[1]);
+            if (dpend) {
+                std::vector<double> moved(D);
+                for (int j = 0; j < D; ++j) {
+                    const int ba = (j >> pa) & 1, bb = (j >> pb) & 1;
+                    const int pj = g.type == SV_CX ? j ^ (ba << pb)
+                                                   : (j & ~((1 << pa) | (1 << pb))) | (bb << pa) | (ba << pb);
+                    moved[j] = ph[pj];
+                }
+                ph.swap(moved);
+                const int da = (dep >> pa) & 1, db = (dep >> pb) & 1;
+                if (g.type == SV_CX) dep |= db << pa;  // the target's phase now reads the control too
+                else dep = (dep & ~((1 << pa) | (1 << pb))) | (db << pa) | (da << pb);
             }
-        } else if (g.type == SV_CX) {
-            recs->push_back(GateRec{GR_CX, B.pos(g.q[0]), B.pos(g.q[1]), 0});
-        } else if (g.type == SV_SWAP) {
-            recs->push_back(GateRec{GR_SWAP, B.pos(g.q[0]), B.pos(g.q[1]), 0});
+            recs->push_back(GateRec{g.type == SV_CX ? GR_CX : GR_SWAP, pa, pb, 0});
+            continue;
+        }
+        if (g.nq != 1) return false;
+        const int p = B.pos(g.q[0]);
+        if (dpend && ((dep >> p) & 1)) {
+            // take in later diagonal gates that commute with everything
+            // between, then apply the table
+            int blocked = 1 << p;
+            for (int j = i + 1; j < N && blocked != D - 1; ++j) {
+                if (used[j]) continue;
+                const int pm = posmask(seq[j]);
+                if (seq[j].kind == GK_DIAG) {
+                    if (!(pm & blocked)) {
+                        add_diag(seq[j]);
+                        used[j] = 1;
+                    }
+                } else {
+                    blocked |= pm;
+                }
+            }
+            flush_diag();
+        }
+        // merge with the previous record when it is a one-qubit gate on the
+        // same position (a pending table here does not depend on p)
+        if (!recs->empty() && (recs->back().kind == GR_U || recs->back().kind == GR_UR) && recs->back().a == p) {
+            cd* Mp = data->data() + recs->back().off;  // merge: M = G * M_prev
+            const cd M[4] = {g.m[0] * Mp[0] + g.m[1] * Mp[2], g.m[0] * Mp[1] + g.m[1] * Mp[3],
+                             g.m[2] * Mp[0] + g.m[3] * Mp[2], g.m[2] * Mp[1] + g.m[3] * Mp[3]};
+            for (int t = 0; t < 4; ++t) Mp[t] = M[t];
+            recs->back().kind = is_real(Mp, 4) ? GR_UR : GR_U;
         } else {
-            return false;
+            recs->push_back(GateRec{is_real(g.m, 4) ? GR_UR : GR_U, p, 0, (int)data->size()});
+            for (int t = 0; t < 4; ++t) data->push_back(g.m[t]);
         }
     }
     flush_diag();
     return (int)recs->size() <= kMaxGateRecs && (int)data->size() <= kMaxGateData;
+}
+
+// A block's gate sequence: the cheaper of the plain form and, when the block
+// holds U3 gates, the form with each U3 split into P RY P.
+bool best_gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<cd>* data) {
+    const bool ok = gate_sequence(B, recs, data, false);
+    bool u3 = false;
+    for (const CGate& g : B.seq) u3 |= g.type == SV_U3;
+    if (!u3) return ok;
+    std::vector<GateRec> r2;
+    std::vector<cd> d2;
+    if (gate_sequence(B, &r2, &d2, true) && (!ok || gate_sequence_cost(r2) < gate_sequence_cost(*recs))) {
+        recs->swap(r2);
+        data->swap(d2);
+        return true;
+    }
+    return ok;
+}
+
+constexpr int kMaxBlockGates = 40;  // 20 one-qubit gates and 20 phase tables fit kMaxGateData
+
+// Estimated instructions per amplitude of a pass's ops: each block pays its
+// own cost plus a register remap (a shared-memory round trip of the tile),
+// each diagonal run one table product.
+double ops_cost(const std::vector<HostOp>& ops) {
+    constexpr double kRemap = 16.0, kDiagRun = 6.0;
+    double c = 0.0;
+    for (const HostOp& o : ops) {
+        if (o.kind == OP_DIAG) c += kDiagRun;
+        else if (o.kind == OP_GATES) c += gate_sequence_cost(o.recs) + kRemap;
+        else c += dense_cost((int)o.qubits.size()) + kRemap;
+    }
+    return c;
+}
+
+// Reorder a pass's gates so that they come in groups of at most kmax qubits:
+// each group starts from the earliest gate that can run next and grows its
+// qubit set S one gate at a time, taking the gate whose qubits let the most
+// further gates join, and every gate that can run next with qubits inside S
+// joins.  A gate can run next once all earlier gates on its qubits have; so
+// each qubit sees its gates in the original order and the product of the
+// reordered list is the same operator.
+std::vector<int> cluster_order(const std::vector<CGate>& gates, const std::vector<int>& order, int kmax) {
+    const int G = (int)order.size();
+    int nq = 0;
+    for (int gi : order)
+        for (int i = 0; i < gates[gi].nq; ++i) nq = std::max(nq, gates[gi].q[i] + 1);
+    if (nq > 64) return order;
+    std::vector<std::vector<int>> seq(nq);  // positions in `order` per qubit
+    for (int i = 0; i < G; ++i)
+        for (int j = 0; j < gates[order[i]].nq; ++j) seq[gates[order[i]].q[j]].push_back(i);
+    auto qmask = [&](int i) {
+        uint64_t m = 0;
+        for (int j = 0; j < gates[order[i]].nq; ++j) m |= 1ull << gates[order[i]].q[j];
+        return m;
+    };
+    std::vector<uint64_t> masks(G);
+    for (int i = 0; i < G; ++i) masks[i] = qmask(i);
+    auto is_ready = [&](const std::vector<int>& head, int i) {
+        for (int j = 0; j < gates[order[i]].nq; ++j) {
+            const int q = gates[order[i]].q[j];
+            if (head[q] >= (int)seq[q].size() || seq[q][head[q]] != i) return false;
+        }
+        return true;
+    };
+    // take every gate that can run next with qubits inside S; returns the count
+    auto closure = [&](uint64_t S, std::vector<int>& head, std::vector<int>* emit) {
+        int cnt = 0;
+        for (bool progress = true; progress;) {
+            progress = false;
+            for (uint64_t r = S; r; r &= r - 1) {
+                const int q = __builtin_ctzll(r);
+                while (head[q] < (int)seq[q].size()) {
+                    const int i = seq[q][head[q]];
+                    if ((masks[i] & ~S) || !is_ready(head, i)) break;
+                    for (int j = 0; j < gates[order[i]].nq; ++j) ++head[gates[order[i]].q[j]];
+                    if (emit) emit->push_back(i);
+                    ++cnt;
+                    progress = true;
+                }
+            }
+        }
+        return cnt;
+    };
+    std::vector<int> head(nq, 0), out;  // out: positions in `order`
+    std::vector<char> taken(G, 0);
+    out.reserve(G);
+    auto take = [&](uint64_t S) {
+        const size_t b = out.size();
+        closure(S, head, &out);
+        for (size_t t = b; t < out.size(); ++t) taken[out[t]] = 1;
+    };
+    while ((int)out.size() < G) {
+        // seed: the earliest gate that can run next, dense before diagonal
+        int seed = -1;
+        for (int pass = 0; pass < 2 && seed < 0; ++pass)
+            for (int i = 0; i < G && seed < 0; ++i)
+                if (!taken[i] && (pass == 0) == (gates[order[i]].kind == GK_DENSE) && is_ready(head, i)) seed = i;
+        if (seed < 0) return order;  // cannot happen for a valid order
+        uint64_t S = masks[seed];
+        take(S);
+        for (;;) {
+            int best = -1, best_gain = 0, best_pop = 0;
+            for (uint64_t r = S; r; r &= r - 1) {
+                const int q = __builtin_ctzll(r);
+                if (head[q] >= (int)seq[q].size()) continue;
+                const int i = seq[q][head[q]];
+                const uint64_t S2 = S | masks[i];
+                if (S2 == S || __builtin_popcountll(S2) > kmax || !is_ready(head, i)) continue;
+                std::vector<int> h2 = head;
+                const int gain = closure(S2, h2, nullptr);
+                const int pop = __builtin_popcountll(S2);
+                if (gain > best_gain || (gain == best_gain && best >= 0 && (pop < best_pop || (pop == best_pop && i < best)))) {
+                    best = i;
+                    best_gain = gain;
+                    best_pop = pop;
+                }
+            }
+            // also grow into a qubit outside S through any gate that can run next
+            if (best < 0) {
+                for (int i = 0; i < G; ++i) {
+                    if (taken[i] || !is_ready(head, i)) continue;
+                    const uint64_t S2 = S | masks[i];
+                    if (S2 == S || __builtin_popcountll(S2) > kmax) continue;
+                    std::vector<int> h2 = head;
+                    const int gain = closure(S2, h2, nullptr);
+                    const int pop = __builtin_popcountll(S2);
+                    if (gain > best_gain || (gain == best_gain && best >= 0 && pop < best_pop)) {
+                        best = i;
+                        best_gain = gain;
+                        best_pop = pop;
+                    }
+                }
+            }
+            if (best < 0) break;
+            S |= masks[best];
+            take(S);
+        }
+    }
+    for (int& i : out) i = order[i];
+    return out;
 }
 
 }  // namespace
@@ -460,97 +677,117 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
         pass.ngates = (int)executed.size();
         for (int gi : executed) pass.type_count[gates[gi].type < 14 ? gates[gi].type : 13]++;
 
-        // Fuse the executed gates into dense blocks and diagonal runs.
-        Block B;
-        DiagForm D;
-        D.init(n);
-        bool dpend = false;
-        auto flushB = [&]() {
-            if (!B.active()) return;
-            HostOp op;
-            op.qubits = B.qubits;
-            op.ngates = B.ngates;
-            // the cheaper representation: the dense 2^k matrix, or the gate
-            // sequence applied in registers (tensor-core blocks stay dense)
-            const bool tc_block = po.tensor == 0 && dtype == SV_C64 && (int)B.qubits.size() >= kMinTcK;
-            op.mat = B.mat;
-            if (!tc_block && (int)B.qubits.size() <= max_gates_k(dtype) && gate_sequence(B, &op.recs, &op.gdata) &&
-                gate_sequence_cost(op.recs) <= dense_cost((int)B.qubits.size())) {
-                op.kind = OP_GATES;
-            } else {
-                op.kind = OP_DENSE;
-                op.recs.clear();
-                op.gdata.clear();
-            }
-            pass.ops.push_back(std::move(op));
-            B = Block();
-        };
-        int dgates = 0;
-        auto flushD = [&]() {
-            if (!dpend) return;
-            HostOp op;
-            op.kind = OP_DIAG;
-            op.diag = D;
-            op.ngates = dgates;
-            pass.ops.push_back(std::move(op));
+        // Fuse the executed gates into dense blocks and diagonal runs, in the
+        // given order (any order that keeps each qubit's gates in sequence).
+        auto fuse = [&](const std::vector<int>& order, std::vector<HostOp>* ops_out) {
+            Block B;
+            DiagForm D;
             D.init(n);
-            dpend = false;
-            dgates = 0;
-        };
-        for (int gi : executed) {
-            const CGate& g = gates[gi];
-            if (g.kind == GK_DIAG) {
-                bool inB = B.active();
-                for (int i = 0; inB && i < g.nq; ++i) inB = B.pos(g.q[i]) >= 0;
-                // A diagonal gate on tile qubits may also widen the current
-                // block (diagonals commute with the pending run D, so moving
-                // it into the block is exact).
-                bool widen = false;
-                std::vector<int> u;
-                if (!inB && B.active()) {
-                    bool inT_all = true;
-                    u = B.qubits;
-                    for (int i = 0; i < g.nq; ++i) {
-                        inT_all &= inT[g.q[i]] != 0;
-                        if (B.pos(g.q[i]) < 0) u.push_back(g.q[i]);
-                    }
-                    widen = inT_all && (int)u.size() <= kmax;
-                }
-                if (widen) {
-                    std::sort(u.begin(), u.end());
-                    expand_block(&B, u);
-                }
-                if (inB || widen) {
-                    block_apply_diag(&B, g);
-                    B.seq.push_back(g);
-                    B.ngates++;
+            bool dpend = false;
+            auto flushB = [&]() {
+                if (!B.active()) return;
+                HostOp op;
+                op.qubits = B.qubits;
+                op.ngates = B.ngates;
+                // the cheaper representation: the dense 2^k matrix, or the gate
+                // sequence applied in registers (tensor-core blocks stay dense)
+                const bool tc_block = po.tensor == 0 && dtype == SV_C64 && (int)B.qubits.size() >= kMinTcK;
+                op.mat = B.mat;
+                // (blocks wider than the register kernel's dense limit stay
+                // gate sequences, which keeps the pass on the register kernel)
+                const int kb = (int)B.qubits.size();
+                if (!tc_block && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata) &&
+                    (gate_sequence_cost(op.recs) <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
+                    op.kind = OP_GATES;
                 } else {
-                    diag_add(&D, n, g);
-                    dpend = true;
-                    dgates++;
+                    op.kind = OP_DENSE;
+                    op.recs.clear();
+                    op.gdata.clear();
                 }
-                continue;
-            }
-            if (dpend && touches(D, g)) {
-                flushB();
-                flushD();
-            }
-            std::vector<int> u = B.qubits;
-            for (int i = 0; i < g.nq; ++i)
-                if (std::find(u.begin(), u.end(), g.q[i]) == u.end()) u.push_back(g.q[i]);
-            std::sort(u.begin(), u.end());
-            if (B.active() && (int)u.size() > kmax) {
-                flushB();
-                u.assign(g.q, g.q + g.nq);
+                ops_out->push_back(std::move(op));
+                B = Block();
+            };
+            int dgates = 0;
+            auto flushD = [&]() {
+                if (!dpend) return;
+                HostOp op;
+                op.kind = OP_DIAG;
+                op.diag = D;
+                op.ngates = dgates;
+                ops_out->push_back(std::move(op));
+                D.init(n);
+                dpend = false;
+                dgates = 0;
+            };
+            for (int gi : order) {
+                const CGate& g = gates[gi];
+                if (g.kind == GK_DIAG) {
+                    bool inB = B.active();
+                    for (int i = 0; inB && i < g.nq; ++i) inB = B.pos(g.q[i]) >= 0;
+                    // A diagonal gate on tile qubits may also widen the current
+                    // block (diagonals commute with the pending run D, so moving
+                    // it into the block is exact).
+                    bool widen = false;
+                    std::vector<int> u;
+                    if (!inB && B.active()) {
+                        bool inT_all = true;
+                        u = B.qubits;
+                        for (int i = 0; i < g.nq; ++i) {
+                            inT_all &= inT[g.q[i]] != 0;
+                            if (B.pos(g.q[i]) < 0) u.push_back(g.q[i]);
+                        }
+                        widen = inT_all && (int)u.size() <= kmax;
+                    }
+                    if (widen) {
+                        std::sort(u.begin(), u.end());
+                        expand_block(&B, u);
+                    }
+                    if (inB || widen) {
+                        block_apply_diag(&B, g);
+                        B.seq.push_back(g);
+                        B.ngates++;
+                    } else {
+                        diag_add(&D, n, g);
+                        dpend = true;
+                        dgates++;
+                    }
+                    continue;
+                }
+                if (dpend && touches(D, g)) {
+                    flushB();
+                    flushD();
+                }
+                std::vector<int> u = B.qubits;
+                for (int i = 0; i < g.nq; ++i)
+                    if (std::find(u.begin(), u.end(), g.q[i]) == u.end()) u.push_back(g.q[i]);
                 std::sort(u.begin(), u.end());
+                // a block holds at most kMaxBlockGates gates, so that its gate
+                // sequence stays within the record and data limits
+                if (B.active() && ((int)u.size() > kmax || B.ngates >= kMaxBlockGates)) {
+                    flushB();
+                    u.assign(g.q, g.q + g.nq);
+                    std::sort(u.begin(), u.end());
+                }
+                expand_block(&B, u);
+                block_apply_dense(&B, g);
+                B.seq.push_back(g);
+                B.ngates++;
             }
-            expand_block(&B, u);
-            block_apply_dense(&B, g);
-            B.seq.push_back(g);
-            B.ngates++;
+            flushB();
+            flushD();
+        };
+        fuse(executed, &pass.ops);
+        // A reordering that groups gates by qubit set (each qubit's gates
+        // kept in sequence, so the circuit is the same) often needs fewer
+        // blocks; keep it when its estimated cost is lower.
+        if (kmax >= 2) {
+            std::vector<int> reord = cluster_order(gates, executed, kmax);
+            if (reord != executed) {
+                std::vector<HostOp> alt;
+                fuse(reord, &alt);
+                if (ops_cost(alt) < ops_cost(pass.ops)) pass.ops.swap(alt);
+            }
         }
-        flushB();
-        flushD();
         out->passes.push_back(std::move(pass));
         remaining.swap(deferred);
     }
