@@ -20,9 +20,15 @@ constexpr int kStageCap = 48 * 1024;  // bytes of a pass region staged in shared
 
 // Gate-sequence block records (positions are block-local bits, data offsets
 // index the op's own complex values).
-enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4, GR_H = 5, GR_HD = 6 };
+enum GateRecKind { GR_U = 0, GR_UR = 1, GR_DT = 2, GR_CX = 3, GR_SWAP = 4, GR_H = 5, GR_HD = 6, GR_URS = 7 };
+// GR_DT: a = mask of the positions its entries depend on (entry j equals
+// entry j & a), b = mask of the entries that differ from 1 (register passes).
 // GR_HD (register passes only): GR_H on position a followed by the phase table
 // at off with entry mask b (one dispatch for the pair).
+// GR_URS (register passes only): a rotation [[c, -s], [s, c]] on position a
+// without its larger factor: [[1, -t], [t, 1]] with t = s / c (b = 0) or
+// [[t, -1], [1, t]] with t = c / s (b = 1), t at off; the factor joins
+// PassDev::scale like GR_H's.
 // GR_H (register passes only): the Hadamard without its 1/sqrt(2), a + b and
 // a - b; the pass multiplies its amplitudes by the product of the dropped
 // factors once, when it writes them back (PassDev::scale).

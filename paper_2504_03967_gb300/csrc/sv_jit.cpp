@@ -235,6 +235,7 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
           << ">(tp), C);\n}\n";
         (void)id;
     };
+    bool scaled = false;  // the pass holds rotations whose factor joins the scale
     for (int oi = 0; oi < P.nops; ++oi) {
         const OpDev& op = ops[oi];
         switch (op.kind) {
@@ -269,10 +270,20 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
                       << f + 2 << "].x, sd[" << f + 3 << "].x);\n";
                     break;
                 case GR_DT:
-                    o << "reg_dt<V, RB, 0x" << std::hex << (unsigned)g.b << std::dec << "u>(v, sd + " << f << ");\n";
+                    // a table on at most three register bits: its (at most 8)
+                    // distinct entries are read once
+                    if (__builtin_popcount((unsigned)g.a) <= 3)
+                        o << "reg_dt_dep<V, RB, 0x" << std::hex << (unsigned)g.b << "u, 0x" << (unsigned)g.a
+                          << std::dec << "u>(v, sd + " << f << ");\n";
+                    else
+                        o << "reg_dt<V, RB, 0x" << std::hex << (unsigned)g.b << std::dec << "u>(v, sd + " << f << ");\n";
                     break;
                 case GR_CX: o << "reg_cx<V, RB, " << g.a << ", " << g.b << ">(v);\n"; break;
                 case GR_H: o << "reg_h<V, RB, " << g.a << ">(v);\n"; break;
+                case GR_URS:
+                    o << "reg_urs<V, RB, " << g.a << ", " << g.b << ", R>(v, sd[" << f << "].x);\n";
+                    scaled = true;
+                    break;
                 case GR_HD:
                     o << "reg_h<V, RB, " << g.a << ">(v);\nreg_dt<V, RB, 0x" << std::hex << (unsigned)g.b << std::dec
                       << "u>(v, sd + " << f << ");\n";
@@ -302,10 +313,14 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     }
     if (!in_regs) return false;
     o << "}\n";
-    // write-back: the pass's scale (a constant here), then the last layout
+    // write-back: the pass's scale, then the last layout.  A scale made of
+    // Hadamard factors alone is a constant of the structure; one with rotation
+    // factors depends on the angles and is read from the pass record.
     o << "template <typename V, typename R, int RB>\n"
-         "static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev&, const RegLayout<V, RB>&) {\n";
-    if (P.scale != 1.0) {
+         "static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>&) {\n";
+    if (scaled) {
+        o << "scale_regs<V, RB>(v, (R)P.scale);\n";
+    } else if (P.scale != 1.0) {
         char buf[64];
         snprintf(buf, sizeof(buf), "%.17g", P.scale);
         o << "scale_regs<V, RB>(v, (R)" << buf << ");\n";

@@ -197,9 +197,18 @@ bool touches(const DiagForm& D, const CGate& g) {
 // Estimated CUDA-core instructions per amplitude of a block of k qubits as a
 // dense 2^k x 2^k product, and as a gate sequence applied in registers.
 double dense_cost(int k) { return 4.0 * (double)(1 << k) + 2.0; }
-double gate_sequence_cost(const std::vector<GateRec>& recs) {
+// A real rotation [[c, -s], [s, c]] costs 2 in a register pass (its factor is
+// deferred to the write-back), another real 2x2 4.
+double gate_sequence_cost(const std::vector<GateRec>& recs, const std::vector<cd>* data = nullptr) {
     double c = 2.0;
-    for (const GateRec& r : recs) c += r.kind == GR_U ? 8.0 : r.kind == GR_UR ? 4.0 : r.kind == GR_DT ? 5.0 : 1.0;
+    for (const GateRec& r : recs) {
+        if (r.kind == GR_UR && data) {
+            const cd* m = data->data() + r.off;
+            c += m[0] == m[3] && m[1] == -m[2] ? 2.0 : 4.0;
+        } else {
+            c += r.kind == GR_U ? 8.0 : r.kind == GR_UR ? 4.0 : r.kind == GR_DT ? 5.0 : 1.0;
+        }
+    }
     return c;
 }
 
@@ -269,7 +278,8 @@ bool gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<cd>* 
     };
     auto flush_diag = [&]() {
         if (!dpend) return;
-        recs->push_back(GateRec{GR_DT, 0, 0, (int)data->size()});
+        // a = the positions the table depends on: entry j equals entry j & a
+        recs->push_back(GateRec{GR_DT, dep, 0, (int)data->size()});
         for (int j = 0; j < D; ++j) data->push_back(std::polar(1.0, ph[j]));
         std::fill(ph.begin(), ph.end(), 0.0);
         dpend = false;
@@ -348,7 +358,7 @@ bool best_gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<
     if (!u3) return ok;
     std::vector<GateRec> r2;
     std::vector<cd> d2;
-    if (gate_sequence(B, &r2, &d2, true) && (!ok || gate_sequence_cost(r2) < gate_sequence_cost(*recs))) {
+    if (gate_sequence(B, &r2, &d2, true) && (!ok || gate_sequence_cost(r2, &d2) < gate_sequence_cost(*recs, data))) {
         recs->swap(r2);
         data->swap(d2);
         return true;
@@ -366,7 +376,7 @@ double ops_cost(const std::vector<HostOp>& ops) {
     double c = 0.0;
     for (const HostOp& o : ops) {
         if (o.kind == OP_DIAG) c += kDiagRun;
-        else if (o.kind == OP_GATES) c += gate_sequence_cost(o.recs) + kRemap;
+        else if (o.kind == OP_GATES) c += gate_sequence_cost(o.recs, &o.gdata) + kRemap;
         else c += dense_cost((int)o.qubits.size()) + kRemap;
     }
     return c;
@@ -697,7 +707,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                 // gate sequences, which keeps the pass on the register kernel)
                 const int kb = (int)B.qubits.size();
                 if (!tc_block && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata) &&
-                    (gate_sequence_cost(op.recs) <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
+                    (gate_sequence_cost(op.recs, &op.gdata) <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
                     op.kind = OP_GATES;
                 } else {
                     op.kind = OP_DENSE;
@@ -880,7 +890,7 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tenso
         if (o.kind == OP_DENSE || o.kind == OP_GATES) {
             const int k = (int)o.qubits.size();
             f[3 + k] += 1.0f / 8.0f;  // f[4..8]: dense blocks of width 1..5
-            flops += (o.kind == OP_GATES ? gate_sequence_cost(o.recs) : dense_cost(k)) / 4.0;
+            flops += (o.kind == OP_GATES ? gate_sequence_cost(o.recs, &o.gdata) : dense_cost(k)) / 4.0;
             msize += ldexp(1.0, 2 * k);
         } else {
             ++ndiag;
@@ -1223,9 +1233,13 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
                 GateRec t = g;
                 if (g.kind == GR_DT) {
                     // the table over all 2^r register values; b = mask of the
-                    // entries that are not exactly 1 (the others are skipped)
+                    // entries that are not exactly 1 (the others are skipped),
+                    // a = the register bits the entries depend on
                     t.off = (int)data.size();
                     t.b = 0;
+                    t.a = 0;
+                    for (int j = 0; j < O.k; ++j)
+                        if ((g.a >> j) & 1) t.a |= 1 << O.lq[j];
                     for (int v = 0; v < (1 << r); ++v) {
                         int idx = 0;
                         for (int j = 0; j < O.k; ++j) idx |= ((v >> O.lq[j]) & 1) << j;
@@ -1243,6 +1257,17 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
                         t.kind = GR_H;  // butterfly; the factor goes to the pass's write-back scale
                         t.off = 0;
                         P->scale *= hs;
+                    } else if (g.kind == GR_UR && gm[0] == gm[3] && gm[1] == -gm[2] && std::fabs(P->scale) > 0x1p-40) {
+                        // rotation [[c, -s], [s, c]]: the larger of c, s goes to the
+                        // write-back scale (each factor is at least 1/sqrt(2) in
+                        // magnitude, so the deferred growth stays below 2^40)
+                        const double c = gm[0].real(), sn = gm[2].real();
+                        const bool cform = std::fabs(c) >= std::fabs(sn);
+                        t.kind = GR_URS;
+                        t.b = cform ? 0 : 1;
+                        t.off = (int)data.size();
+                        data.push_back(cd(cform ? sn / c : c / sn, 0.0));
+                        P->scale *= cform ? c : sn;
                     } else if (gm) {
                         t.off = (int)data.size();
                         for (int e = 0; e < 4; ++e) data.push_back(gm[e]);

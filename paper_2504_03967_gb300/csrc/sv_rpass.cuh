@@ -85,6 +85,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait_group() {
 // code unrolled for its (compile-time) position inside the block:
 //   GR_U   2x2 complex matrix on position a        8 FMA per amplitude
 //   GR_UR  2x2 real matrix on position a           4
+//   GR_URS rotation with its factor deferred       2
 //   GR_DT  2^K-entry diagonal (phase) table        one complex product
 //   GR_CX  controlled-NOT (control a, target b)    register moves
 //   GR_SWAP                                        register moves
@@ -110,6 +111,29 @@ __device__ __forceinline__ void reg_ur(V* v, R u00, R u01, R u10, R u11) {
             x.y = fma(u00, a.y, u01 * b.y);
             y.x = fma(u10, a.x, u11 * b.x);
             y.y = fma(u10, a.y, u11 * b.y);
+            v[j] = x;
+            v[j | (1 << P)] = y;
+        }
+}
+// Rotation without its factor: FORM 0 [[1, -t], [t, 1]], FORM 1 [[t, -1], [1, t]].
+template <typename V, int K, int P, int FORM, typename R>
+__device__ __forceinline__ void reg_urs(V* v, R t) {
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if (!((j >> P) & 1)) {
+            const V a = v[j], b = v[j | (1 << P)];
+            V x, y;
+            if (FORM == 0) {
+                x.x = fma(-t, b.x, a.x);
+                x.y = fma(-t, b.y, a.y);
+                y.x = fma(t, a.x, b.x);
+                y.y = fma(t, a.y, b.y);
+            } else {
+                x.x = fma(t, a.x, -b.x);
+                x.y = fma(t, a.y, -b.y);
+                y.x = fma(t, b.x, a.x);
+                y.y = fma(t, b.y, a.y);
+            }
             v[j] = x;
             v[j | (1 << P)] = y;
         }
@@ -159,6 +183,19 @@ __device__ __forceinline__ void reg_dt(V* v, const V* __restrict__ t) {
         if ((MASK >> j) & 1u) v[j] = cmul(t[j], v[j]);
 }
 
+// The same when the table depends only on the register bits in DEP (entry j
+// equals entry j & DEP): each distinct entry is read once.
+template <typename V, int K, unsigned MASK, unsigned DEP>
+__device__ __forceinline__ void reg_dt_dep(V* v, const V* __restrict__ t) {
+    V e[1 << K];
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if ((j & ~DEP) == 0 && ((MASK >> j) & 1u)) e[j] = t[j];
+#pragma unroll
+    for (int j = 0; j < (1 << K); ++j)
+        if ((MASK >> j) & 1u) v[j] = cmul(e[j & DEP], v[j]);
+}
+
 template <typename V, int K>
 __device__ __forceinline__ void reg_u_any(V* v, int p, V u00, V u01, V u10, V u11) {
     switch (p) {
@@ -178,6 +215,21 @@ __device__ __forceinline__ void reg_ur_any(V* v, int p, R u00, R u01, R u10, R u
     case 3: if constexpr (K > 3) reg_ur<V, K, 3>(v, u00, u01, u10, u11); break;
     default: if constexpr (K > 4) reg_ur<V, K, 4>(v, u00, u01, u10, u11); break;
     }
+}
+template <typename V, int K, int FORM, typename R>
+__device__ __forceinline__ void reg_urs_p(V* v, int p, R t) {
+    switch (p) {
+    case 0: reg_urs<V, K, 0, FORM, R>(v, t); break;
+    case 1: if constexpr (K > 1) reg_urs<V, K, 1, FORM, R>(v, t); break;
+    case 2: if constexpr (K > 2) reg_urs<V, K, 2, FORM, R>(v, t); break;
+    case 3: if constexpr (K > 3) reg_urs<V, K, 3, FORM, R>(v, t); break;
+    default: if constexpr (K > 4) reg_urs<V, K, 4, FORM, R>(v, t); break;
+    }
+}
+template <typename V, int K, typename R>
+__device__ __forceinline__ void reg_urs_any(V* v, int p, int form, R t) {
+    if (form == 0) reg_urs_p<V, K, 0, R>(v, p, t);
+    else reg_urs_p<V, K, 1, R>(v, p, t);
 }
 template <typename V, int K>
 __device__ __forceinline__ void reg_h_any(V* v, int p) {
@@ -361,6 +413,7 @@ __device__ __forceinline__ void reg_gates(V* v, const GateRec* __restrict__ recs
             for (int j = 0; j < (1 << RB); ++j)
                 if ((g.b >> j) & 1) v[j] = cmul(sd[g.off + j], v[j]);
             break;
+        case GR_URS: reg_urs_any<V, RB, R>(v, g.a, g.b, sd[g.off].x); break;
         case GR_CX: reg_cx_any<V, RB>(v, g.a, g.b); break;
         case GR_H: reg_h_any<V, RB>(v, g.a); break;
         case GR_HD:
