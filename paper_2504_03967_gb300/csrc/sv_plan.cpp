@@ -440,11 +440,21 @@ std::vector<int> cluster_order(const std::vector<CGate>& gates, const std::vecto
         for (size_t t = b; t < out.size(); ++t) taken[out[t]] = 1;
     };
     while ((int)out.size() < G) {
-        // seed: the earliest gate that can run next, dense before diagonal
+        // a gate that can run next is at the head of each of its qubits'
+        // queues: the candidates, in list order
+        std::vector<int> cand;
+        for (int q = 0; q < nq; ++q)
+            if (head[q] < (int)seq[q].size() && is_ready(head, seq[q][head[q]])) cand.push_back(seq[q][head[q]]);
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        // seed: the earliest of them, dense before diagonal
         int seed = -1;
         for (int pass = 0; pass < 2 && seed < 0; ++pass)
-            for (int i = 0; i < G && seed < 0; ++i)
-                if (!taken[i] && (pass == 0) == (gates[order[i]].kind == GK_DENSE) && is_ready(head, i)) seed = i;
+            for (int i : cand)
+                if ((pass == 0) == (gates[order[i]].kind == GK_DENSE)) {
+                    seed = i;
+                    break;
+                }
         if (seed < 0) return order;  // cannot happen for a valid order
         uint64_t S = masks[seed];
         take(S);
@@ -467,8 +477,12 @@ std::vector<int> cluster_order(const std::vector<CGate>& gates, const std::vecto
             }
             // also grow into a qubit outside S through any gate that can run next
             if (best < 0) {
-                for (int i = 0; i < G; ++i) {
-                    if (taken[i] || !is_ready(head, i)) continue;
+                cand.clear();
+                for (int q = 0; q < nq; ++q)
+                    if (head[q] < (int)seq[q].size() && is_ready(head, seq[q][head[q]])) cand.push_back(seq[q][head[q]]);
+                std::sort(cand.begin(), cand.end());
+                cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+                for (int i : cand) {
                     const uint64_t S2 = S | masks[i];
                     if (S2 == S || __builtin_popcountll(S2) > kmax) continue;
                     std::vector<int> h2 = head;
