@@ -231,7 +231,8 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
         o << "{\n";
         emit_ints(o, "tp", Lc.tp, tb);
         emit_ints(o, "C", Lc.C, 1 << RB);
-        o << fn << "<V, RB, " << (Lc.add ? "true" : "false") << ">(v, tile, thread_sbase<V, " << tb
+        // complex64 with tile position 0 at register bit 0: 16-byte accesses
+        o << fn << (dtype == SV_C64 && Lc.rp[0] == 0 ? "2" : "") << "<V, RB, " << (Lc.add ? "true" : "false") << ">(v, tile, thread_sbase<V, " << tb
           << ">(tp), C);\n}\n";
         (void)id;
     };

@@ -1143,6 +1143,13 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
         std::vector<int> slots = PQ;
         for (size_t c = 0; c < cand.size() && (int)slots.size() < r; ++c) slots.push_back(cand[c]);
         std::sort(slots.begin() + PQ.size(), slots.end());
+        // before a gate sequence (any register order serves it), tile position
+        // 0 goes to register bit 0: compiled complex64 passes then move
+        // register pairs with 16-byte shared-memory accesses
+        if (hp.ops[i].kind == OP_GATES) {
+            const auto z = std::find(slots.begin(), slots.end(), 0);
+            if (z != slots.end()) std::iter_swap(slots.begin(), z);
+        }
         rpos = slots;
         tpos.clear();
         for (int q = 0; q < m; ++q)

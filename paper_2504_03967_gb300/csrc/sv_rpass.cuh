@@ -571,6 +571,27 @@ __device__ __forceinline__ void reg_write_ct(const V* v, V* tile, int sb, const 
 #pragma unroll
     for (int k = 0; k < (1 << RB); ++k) tile[ADD ? sb + C[k] : sb ^ C[k]] = v[k];
 }
+// The same for complex64 when register bit 0 is tile position 0: registers
+// 2j and 2j + 1 share one 16-byte chunk (sb and C[2j] are even), moved with
+// one 16-byte access.
+template <typename V, int RB, bool ADD>
+__device__ __forceinline__ void reg_read_ct2(V* v, const V* tile, int sb, const int* C) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); k += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(tile + (ADD ? sb + C[k] : sb ^ C[k]));
+        v[k].x = q.x;
+        v[k].y = q.y;
+        v[k + 1].x = q.z;
+        v[k + 1].y = q.w;
+    }
+}
+template <typename V, int RB, bool ADD>
+__device__ __forceinline__ void reg_write_ct2(const V* v, V* tile, int sb, const int* C) {
+#pragma unroll
+    for (int k = 0; k < (1 << RB); k += 2)
+        *reinterpret_cast<float4*>(tile + (ADD ? sb + C[k] : sb ^ C[k])) =
+            make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+}
 // Tile copies: chunk k of this thread is 16 bytes at psi[g + KO[k]] and at
 // tile[s0 ^ SW[k]] (s0 + SW[k] under ADD).
 template <typename V, int NCH, bool ADD>
