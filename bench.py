@@ -50,8 +50,8 @@ UNIT = "amp_updates/s"
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
                    "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
-TRAFFIC = {"sha256": "628717577bc930cfbfe5b9f0a3c03a0b64fc82dd6ca5926744e7d6e1eaaa91bb",
-           "bytes_per_amp": 13.0894, "profile": "profiles/sv_jit_pass_qft26_c64_k5m13.md (n=26 capture, scaled to 2^n)"}
+TRAFFIC = {"sha256": "ee2fdf564ed6b3a970b567c5bd48063ed58d508fb4c750271f1f3c0e5c3f55cf",
+           "bytes_per_amp": 12.9808, "profile": "profiles/sv_jit_pass_qft26_c64_k5m13.md (n=26 capture, scaled to 2^n)"}
 
 
 def sources_sha():
