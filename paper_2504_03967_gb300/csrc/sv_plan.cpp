@@ -1273,8 +1273,10 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
                     if (g.kind == GR_CX || g.kind == GR_SWAP) t.b = O.lq[g.b];
                     const cd* gm = g.kind == GR_U || g.kind == GR_UR ? &o.gdata[(size_t)g.off] : nullptr;
                     const double hs = 1.0 / std::sqrt(2.0);
+                    // (factors deferred only while the growth they leave in the
+                    // registers stays below 2^40)
                     if (g.kind == GR_UR && gm[0] == cd(hs, 0.0) && gm[1] == cd(hs, 0.0) && gm[2] == cd(hs, 0.0) &&
-                        gm[3] == cd(-hs, 0.0)) {
+                        gm[3] == cd(-hs, 0.0) && std::fabs(P->scale) > 0x1p-40) {
                         t.kind = GR_H;  // butterfly; the factor goes to the pass's write-back scale
                         t.off = 0;
                         P->scale *= hs;

@@ -40,3 +40,25 @@ def test_full_depth_vs_oracle(ref, dtype, opts):
     got = U.run_gpu(N, g, dtype, **opts)
     U.assert_close(got, want, dtype, "random n=%d, %d layers %s" % (N, LAYERS, opts))
 
+
+
+@pytest.mark.parametrize("dtype,opts", [(S.C64, {}), (S.C64, {"jit": 1}), (S.C128, {})], ids=["c64", "c64-jit", "c128"])
+def test_many_rotations_in_one_pass(dtype, opts):
+    """250 RY rotations and 50 Hadamards kept apart by CX gates on five
+    qubits of a 12-qubit state: one pass whose rotations and Hadamards defer
+    more factors than the write-back scale takes (each at least 1/sqrt(2), at
+    most 2^40 of growth), so the later ones run with their factor in the
+    matrix.  Against the oracle."""
+    import numpy as np
+
+    rng = np.random.default_rng(77)
+    items = [(W.H, (q,), ()) for q in range(12)]
+    for r in range(50):
+        for q in range(5):
+            items.append((W.RY, (q,), (rng.uniform(np.pi / 4, 3 * np.pi / 4),)))
+        items.append((W.H, (r % 5,), ()))
+        for q in range(4):
+            items.append((W.CX, (q, q + 1), ()))
+    g = W.gates_from_list(items)
+    got = U.run_gpu(12, g, dtype, **opts)
+    U.assert_close(got, U.run_oracle(12, g), dtype, "250 rotations in one pass %s" % opts)
