@@ -221,8 +221,6 @@ int sv_store_state(sv_handle h, void *host_amps);
  * records are validated before any device work. */
 int sv_apply_circuit(sv_handle h, const sv_gate *gates, size_t count, const sv_options *opt);
 
-/* Plan without running: fills *info for a circuit on n qubits of dtype dt.
- * Host only; usable without a GPU. */
 /* Run-time compiled passes: kernels compiled, compiles that failed, passes
  * launched on them and host milliseconds spent compiling (process totals);
  * sv_jit_fills: passes that built their tiles from a deferred basis state
@@ -241,8 +239,45 @@ int sv_jit_check(int n, sv_dtype dt, const sv_gate *gates, size_t count, const s
                  int *compiled, char *log, size_t cap);
 int sv_jit_last_log(char *buf, size_t cap);
 
+/* Plan without running: fills *info for a circuit on n qubits of dtype dt.
+ * Host only; usable without a GPU. */
 int sv_plan_circuit(int n, sv_dtype dt, const sv_gate *gates, size_t count,
                     const sv_options *opt, sv_plan_info *info);
+
+/* One op of a fused plan as the planner built it, in FP64, before the device
+ * encoding (register layouts, deferred factors, single precision), so that a
+ * plan can be checked against the circuit without a GPU.  The ops of each
+ * pass apply in order, passes in order; their product is the circuit's
+ * operator (App. D.2 "gate fusion"; Eq. "cr1" for the phase runs).
+ *   kind 0, dense block: the 2^k x 2^k matrix on qubits q[0..k-1] (block bit
+ *     i <-> q[i]), row-major, 2 * 4^k doubles (re, im) at data_off.
+ *   kind 1, phase run: phase(x) = c + sum_q a_q x_q + sum_{p<q} b_pq x_p x_q
+ *     radians on every amplitude x; 1 + n + n*n doubles at data_off: c, a[n],
+ *     b[n*n] (row p, column q; only p < q is used).  k = 0.
+ *   kind 2, gate sequence on the block positions of q[0..k-1]: nrec records
+ *     of 4 ints (rkind, a, b, off) from recs[rec_off]; complex values (re, im)
+ *     at data + data_off + 2 * off.  rkind 0: 2x2 complex matrix on position
+ *     a (4 values, row-major); 1: the same with real entries; 2: a 2^k-entry
+ *     diagonal table over the block index (a = mask of the positions it
+ *     depends on); 3: CX, control a, target b; 4: SWAP a, b.
+ *   kind 3, multiplexor (not described further): q[0] = its target.
+ * pass: the pass the op runs in.  Planner SV_PLAN_GREEDY only
+ * (SV_EUNSUPPORTED otherwise).  The counts are always written; ops, recs and
+ * data are filled where they fit, and SV_EINVAL reports buffers too small
+ * (call with zero capacities to size them).  Host only. */
+typedef struct {
+    int pass;
+    int kind;
+    int k;
+    int q[5];
+    int nrec;
+    int rec_off;
+    int64_t data_off;
+} sv_plan_op;
+
+int sv_plan_ops(int n, sv_dtype dt, const sv_gate *gates, size_t count, const sv_options *opt,
+                sv_plan_op *ops, size_t ops_cap, size_t *nops, int *recs, size_t recs_cap, size_t *nrecs,
+                double *data, size_t data_cap, size_t *ndata);
 
 /* ---- read-out (Sec. 3 shots; App. A Eq. "hilbert") --------------------- */
 

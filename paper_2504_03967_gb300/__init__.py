@@ -50,6 +50,11 @@ class sv_plan_info(ctypes.Structure):
                 ("mux_ops", ctypes.c_int64), ("mux_passes", ctypes.c_int64)]
 
 
+class sv_plan_op(ctypes.Structure):
+    _fields_ = [("pass_", ctypes.c_int), ("kind", ctypes.c_int), ("k", ctypes.c_int), ("q", ctypes.c_int * 5),
+                ("nrec", ctypes.c_int), ("rec_off", ctypes.c_int), ("data_off", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -76,6 +81,7 @@ def lib():
             "sv_store_state": [vp, vp],
             "sv_apply_circuit": [vp, vp, sz, P(sv_options)],
             "sv_plan_circuit": [i, i, vp, sz, P(sv_options), P(sv_plan_info)],
+            "sv_plan_ops": [i, i, vp, sz, P(sv_options), vp, sz, P(sz), vp, sz, P(sz), vp, sz, P(sz)],
             "sv_probs": [vp, vp],
             "sv_probs_device": [vp, vp],
             "sv_norm": [vp, P(ctypes.c_double)],
@@ -223,6 +229,51 @@ def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, ten
     info = sv_plan_info()
     _check(lib().sv_plan_circuit(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}
+
+
+def sv_plan_ops(n, dtype, gates, k_max=0, tile_m=0, mux=-1, drop_phase_below=0.0):
+    """Host only: the greedy plan's ops in FP64 (see sv_plan_op in sv.h), as a
+    list of dicts: pass, kind ("dense", "diag", "gates", "mux"), qubits, and
+    per kind: mat (2^k x 2^k complex), c / a / b (phase run), recs (rkind, a,
+    b, off rows) with vals (complex values), target (multiplexor)."""
+    g = as_gates(gates)
+    o = _opts(k_max, tile_m, PLAN_GREEDY, 0, 0, 0, 0, drop_phase_below, mux)
+    L = lib()
+    cnt = [ctypes.c_size_t(0) for _ in range(3)]
+    rc = L.sv_plan_ops(n, dtype, _ptr(g), len(g), ctypes.byref(o), None, 0, ctypes.byref(cnt[0]), None, 0,
+                       ctypes.byref(cnt[1]), None, 0, ctypes.byref(cnt[2]))
+    if rc not in (0, -1) or (rc == -1 and cnt[0].value == 0 and len(g)):
+        _check(rc)
+    ops = (sv_plan_op * max(1, cnt[0].value))()
+    recs = np.zeros(max(1, cnt[1].value), dtype=np.int32)
+    data = np.zeros(max(1, cnt[2].value), dtype=np.float64)
+    _check(L.sv_plan_ops(n, dtype, _ptr(g), len(g), ctypes.byref(o), ctypes.cast(ops, ctypes.c_void_p), len(ops),
+                         ctypes.byref(cnt[0]), _ptr(recs), len(recs), ctypes.byref(cnt[1]), _ptr(data), len(data),
+                         ctypes.byref(cnt[2])))
+    out = []
+    for r in ops[: cnt[0].value]:
+        k = r.k
+        d = {"pass": r.pass_, "kind": ("dense", "diag", "gates", "mux")[r.kind], "qubits": list(r.q[:k])}
+        off = r.data_off
+        if r.kind == 0:
+            v = data[off: off + 2 * 4 ** k]
+            d["mat"] = (v[0::2] + 1j * v[1::2]).reshape(1 << k, 1 << k)
+        elif r.kind == 1:
+            d["c"] = float(data[off])
+            d["a"] = data[off + 1: off + 1 + n].copy()
+            d["b"] = data[off + 1 + n: off + 1 + n + n * n].reshape(n, n).copy()
+        elif r.kind == 2:
+            rr = recs[r.rec_off: r.rec_off + 4 * r.nrec].reshape(-1, 4).copy()
+            d["recs"] = rr
+            nv = 0
+            for rk, _, _, ro in rr:
+                nv = max(nv, ro + (4 if rk in (0, 1) else (1 << k) if rk == 2 else 0))
+            v = data[off: off + 2 * nv]
+            d["vals"] = v[0::2] + 1j * v[1::2]
+        else:
+            d["target"] = r.q[0]
+        out.append(d)
+    return out
 
 
 def sv_qubit_map(h):

@@ -347,6 +347,89 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
     return SV_OK;
 }
 
+int sv_plan_ops(int n, sv_dtype dt, const sv_gate* gates, size_t count, const sv_options* opt, sv_plan_op* ops,
+                size_t ops_cap, size_t* nops, int* recs, size_t recs_cap, size_t* nrecs, double* data,
+                size_t data_cap, size_t* ndata) {
+    if (!nops || !nrecs || !ndata) return set_error(SV_EINVAL, "NULL count");
+    if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+    if (n < 1 || n > max_qubits(dt)) return set_error(SV_EINVAL, "n out of range");
+    if (count && !gates) return set_error(SV_EINVAL, "NULL gate list");
+    std::vector<CGate> cg;
+    size_t bad = 0;
+    if (canonicalise(n, gates, count, &cg, &bad) != SV_OK)
+        return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
+    const PlanOptions po = resolve_options(n, dt, opt);
+    if (po.planner != SV_PLAN_GREEDY) return set_error(SV_EUNSUPPORTED, "sv_plan_ops describes greedy plans");
+    drop_small_phases(&cg, po.drop_phase_below);
+    std::vector<CGate> muxed;
+    std::vector<Mux> muxes;
+    const bool rec = recognise_mux(n, cg, &muxed, &muxes, po.mux);
+    Plan plan;
+    plan_greedy(n, dt, rec ? muxed : cg, po, &plan, &muxes);
+    size_t no = 0, nr = 0, nd = 0;
+    auto put_d = [&](double v) {
+        if (data && nd < data_cap) data[nd] = v;
+        ++nd;
+    };
+    for (size_t pi = 0; pi < plan.passes.size(); ++pi) {
+        const HostPass& hp = plan.passes[pi];
+        std::vector<sv_plan_op> out;
+        for (int mi : hp.mux) {
+            sv_plan_op r;
+            memset(&r, 0, sizeof(r));
+            r.pass = (int)pi;
+            r.kind = 3;
+            r.k = 1;
+            r.q[0] = plan.muxes[(size_t)mi].target;
+            r.rec_off = (int)nr;
+            r.data_off = (int64_t)nd;
+            out.push_back(r);
+        }
+        for (const HostOp& o : hp.ops) {
+            sv_plan_op r;
+            memset(&r, 0, sizeof(r));
+            r.pass = (int)pi;
+            r.rec_off = (int)nr;
+            r.data_off = (int64_t)nd;
+            if (o.kind == OP_DIAG) {
+                r.kind = 1;
+                put_d(o.diag.c);
+                for (int q = 0; q < n; ++q) put_d(o.diag.a[(size_t)q]);
+                for (size_t i = 0; i < (size_t)n * n; ++i) put_d(o.diag.b[i]);
+            } else {
+                r.k = (int)o.qubits.size();
+                for (int i = 0; i < r.k && i < 5; ++i) r.q[i] = o.qubits[(size_t)i];
+                if (o.kind == OP_GATES) {
+                    r.kind = 2;
+                    r.nrec = (int)o.recs.size();
+                    for (const GateRec& g : o.recs) {
+                        const int w[4] = {g.kind, g.a, g.b, g.off};
+                        for (int j = 0; j < 4; ++j) {
+                            if (recs && nr < recs_cap) recs[nr] = w[j];
+                            ++nr;
+                        }
+                    }
+                    for (const cd& v : o.gdata) put_d(v.real()), put_d(v.imag());
+                } else {
+                    r.kind = 0;
+                    for (const cd& v : o.mat) put_d(v.real()), put_d(v.imag());
+                }
+            }
+            out.push_back(r);
+        }
+        for (const sv_plan_op& r : out) {
+            if (ops && no < ops_cap) ops[no] = r;
+            ++no;
+        }
+    }
+    *nops = no;
+    *nrecs = nr;
+    *ndata = nd;
+    if (no > ops_cap || nr > recs_cap || nd > data_cap)
+        return set_error(SV_EINVAL, "buffers too small (the counts are returned)");
+    return SV_OK;
+}
+
 int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_options* opt) {
     int rc = check_handle_noflush(h);
     if (rc) return rc;

@@ -1,0 +1,136 @@
+"""The fused plan itself, checked on the CPU: the ops the greedy planner
+builds (dense blocks, gate sequences with their phase tables, phase runs;
+sv_plan_ops, FP64, before the device encoding) are applied here in numpy,
+op by op, and the result must equal the oracle's gate-by-gate state to FP64
+rounding.  This pins the planner's exact rewrites without a GPU: grouping a
+pass's gates by qubit set, phase tables kept pending past gates they commute
+with and moved through CX / SWAP, U3 = P(phi) RY(theta) P(lambda), diagonal
+gates folded into blocks or runs (App. D.2 "gate fusion", Eq. "cr1")."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2504_03967_gb300 as S
+import workloads as W
+from paper_2504_03967_gb300 import build as B
+from tests.oracle_pins import random_mixed_circuit
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    yield
+
+
+def _block(psi, n, qubits, mat):
+    """Apply a 2^k x 2^k matrix (block bit i <-> qubits[i]) to psi."""
+    k = len(qubits)
+    offs = np.zeros(1 << k, dtype=np.int64)
+    for j in range(1 << k):
+        for i, q in enumerate(qubits):
+            if (j >> i) & 1:
+                offs[j] |= 1 << q
+    idx = np.arange(1 << n)
+    mask = 0
+    for q in qubits:
+        mask |= 1 << q
+    bases = idx[(idx & mask) == 0]
+    sel = bases[:, None] + offs[None, :]
+    psi[sel] = psi[sel] @ np.asarray(mat).T
+    return psi
+
+
+def _apply_ops(n, ops, psi):
+    psi = psi.astype(np.complex128).copy()
+    idx = np.arange(1 << n)
+    bits = (idx[:, None] >> np.arange(n)[None, :]) & 1
+    for op in ops:
+        qs = op["qubits"]
+        if op["kind"] == "dense":
+            psi = _block(psi, n, qs, op["mat"])
+        elif op["kind"] == "diag":
+            ph = op["c"] + bits @ op["a"] + np.einsum("ip,pq,iq->i", bits, np.triu(op["b"], 1), bits)
+            psi *= np.exp(1j * ph)
+        elif op["kind"] == "gates":
+            vals = op["vals"]
+            jblk = np.zeros(1 << n, dtype=np.int64)
+            for i, q in enumerate(qs):
+                jblk |= ((idx >> q) & 1) << i
+            for rk, a, b, off in op["recs"]:
+                if rk in (0, 1):
+                    psi = _block(psi, n, [qs[a]], vals[off:off + 4].reshape(2, 2))
+                elif rk == 2:
+                    psi *= vals[off + jblk]
+                elif rk == 3:
+                    c, t = qs[a], qs[b]
+                    src = np.where((idx >> c) & 1, idx ^ (1 << t), idx)
+                    psi = psi[src]
+                elif rk == 4:
+                    p, q = qs[a], qs[b]
+                    diff = ((idx >> p) ^ (idx >> q)) & 1
+                    psi = psi[np.where(diff == 1, idx ^ (1 << p) ^ (1 << q), idx)]
+                else:
+                    raise AssertionError("unknown record kind %d" % rk)
+        else:
+            raise AssertionError("multiplexors are not described")
+    return psi
+
+
+CASES = {
+    "random-u3cx": lambda: (11, W.random_u3_cx(11, 12, 3)),
+    "qft": lambda: (10, W.qft(10)),
+    "cx-blocks": lambda: (10, W.random_cx_blocks(10, 120, 5)),
+    "ansatz": lambda: (10, W.hea(10, 4, W.hea_params(1, 10, 4, 9)[0])),
+    "mixed": lambda: (9, random_mixed_circuit(9, 160, np.random.default_rng(4))),
+}
+
+
+@pytest.mark.parametrize("k,tile_m", [(5, 7), (3, 7), (5, 9), (2, 6)])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_plan_ops_reproduce_the_circuit(case, k, tile_m):
+    n, g = CASES[case]()
+    ops = S.sv_plan_ops(n, S.C64, g, k_max=k, tile_m=tile_m)
+    assert ops and (tile_m >= n or max(op["pass"] for op in ops) >= 1)  # several passes
+    rng = np.random.default_rng(n + k)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    got = _apply_ops(n, ops, psi0)
+    want = oracle.apply_circuit(n, g, psi0)
+    assert np.abs(got - want).max() < 1e-12, (case, np.abs(got - want).max())
+
+
+def test_phase_tables_depend_only_on_their_mask():
+    """Compiled passes read entry j of a phase table as entry j & a: every
+    table must satisfy that exactly."""
+    n, g = CASES["random-u3cx"]()
+    seen = 0
+    for op in S.sv_plan_ops(n, S.C64, g, k_max=5, tile_m=9):
+        if op["kind"] != "gates":
+            continue
+        for rk, a, _, off in op["recs"]:
+            if rk != 2:
+                continue
+            t = op["vals"][off: off + (1 << len(op["qubits"]))]
+            j = np.arange(len(t))
+            assert np.array_equal(t, t[j & a])
+            seen += 1
+    assert seen > 0
+
+
+def test_u3_blocks_take_the_p_ry_p_form():
+    """Random U3+CX blocks come out as real rotations and phase tables, with
+    fewer tables than rotations (phases wait past gates they commute with)."""
+    n, g = CASES["random-u3cx"]()
+    kinds = np.concatenate([op["recs"][:, 0] for op in S.sv_plan_ops(n, S.C64, g, k_max=5, tile_m=9)
+                            if op["kind"] == "gates"])
+    ur, dt, u = (kinds == 1).sum(), (kinds == 2).sum(), (kinds == 0).sum()
+    assert ur >= 0.9 * (g["type"] == W.U3).sum() and u == 0
+    assert 0 < dt < ur
+
+
+def test_plan_ops_arguments():
+    with pytest.raises(S.SVError):
+        S.sv_plan_ops(0, S.C64, W.qft(3))
+    with pytest.raises(S.SVError):
+        S.sv_plan_ops(4, S.C64, W.gates_from_list([(W.H, (4,), ())]))
+    assert S.sv_plan_ops(4, S.C64, W.gates_from_list([])) == []
