@@ -99,6 +99,22 @@ def test_plan_ops_reproduce_the_circuit(case, k, tile_m):
     assert np.abs(got - want).max() < 1e-12, (case, np.abs(got - want).max())
 
 
+@pytest.mark.parametrize("case", ["random-u3cx", "mixed", "qft"])
+@pytest.mark.parametrize("dtype,pass_kernel", [(S.C128, 0), (S.C64, 1)], ids=["c128", "c64-smem-kernel"])
+def test_plan_ops_other_dtype_and_kernel(case, dtype, pass_kernel):
+    """complex128 plans (4-qubit blocks by default) and plans for the
+    shared-memory kernel (wide blocks may stay dense) reproduce the circuit."""
+    n, g = CASES[case]()
+    ops = S.sv_plan_ops(n, dtype, g, tile_m=7, pass_kernel=pass_kernel)
+    if dtype == S.C128:
+        assert max(len(op["qubits"]) for op in ops) <= 4
+    rng = np.random.default_rng(3)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    got = _apply_ops(n, ops, psi0)
+    assert np.abs(got - oracle.apply_circuit(n, g, psi0)).max() < 1e-12
+
+
 def test_phase_tables_depend_only_on_their_mask():
     """Compiled passes read entry j of a phase table as entry j & a: every
     table must satisfy that exactly."""
