@@ -150,3 +150,14 @@ def test_plan_ops_arguments():
     with pytest.raises(S.SVError):
         S.sv_plan_ops(4, S.C64, W.gates_from_list([(W.H, (4,), ())]))
     assert S.sv_plan_ops(4, S.C64, W.gates_from_list([])) == []
+
+
+def test_plan_ops_name_the_multiplexor_targets():
+    """A QCrank circuit (a address qubits in superposition, d data qubits
+    under uniformly controlled RY) plans as Hadamard blocks plus one
+    multiplexor per data qubit."""
+    a, d = 8, 6
+    pix = np.random.default_rng(1).uniform(0, 1, size=(1 << a, d))
+    ops = S.sv_plan_ops(a + d, S.C64, W.qcrank(a, d, pix), mux=1)
+    assert sorted(op["target"] for op in ops if op["kind"] == "mux") == list(range(a, a + d))
+    assert all(op["kind"] in ("mux", "gates", "dense") for op in ops)
