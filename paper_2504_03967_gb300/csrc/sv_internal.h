@@ -76,7 +76,9 @@ struct DiagForm {
 struct HostOp {
     int kind;
     std::vector<int> qubits;  // dense / gates: sorted ascending, block bit i <-> qubits[i]
-    std::vector<cd> mat;      // dense and gates: the block's 2^k x 2^k matrix, row-major
+    std::vector<cd> mat;      // dense: the block's 2^k x 2^k matrix, row-major (gates: formed on demand
+                              // from seq, see op_matrix)
+    std::vector<CGate> seq;   // gates: the block's gates in order
     std::vector<cd> gdata;    // gates: the records' complex data
     DiagForm diag;            // diag
     std::vector<GateRec> recs;  // gates

@@ -169,6 +169,17 @@ void block_apply_diag(Block* b, const CGate& g) {
     }
 }
 
+// The 2^k x 2^k matrix of gates on the sorted qubit set qubits.
+std::vector<cd> block_matrix(const std::vector<int>& qubits, const std::vector<CGate>& seq) {
+    Block b;
+    expand_block(&b, qubits);
+    for (const CGate& g : seq) {
+        if (g.kind == GK_DIAG) block_apply_diag(&b, g);
+        else block_apply_dense(&b, g);
+    }
+    return b.mat;
+}
+
 void diag_add(DiagForm* D, int n, const CGate& g) {
     if (g.nq == 1) {
         const int q = g.q[0];
@@ -703,6 +714,8 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
 
         // Fuse the executed gates into dense blocks and diagonal runs, in the
         // given order (any order that keeps each qubit's gates in sequence).
+        // Blocks keep their qubits and gates; a dense op's matrix is formed
+        // when it is emitted, a gate sequence's only if a kernel needs it.
         auto fuse = [&](const std::vector<int>& order, std::vector<HostOp>* ops_out) {
             Block B;
             DiagForm D;
@@ -716,15 +729,16 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                 // the cheaper representation: the dense 2^k matrix, or the gate
                 // sequence applied in registers (tensor-core blocks stay dense)
                 const bool tc_block = po.tensor == 0 && dtype == SV_C64 && (int)B.qubits.size() >= kMinTcK;
-                op.mat = B.mat;
                 // (blocks wider than the register kernel's dense limit stay
                 // gate sequences, which keeps the pass on the register kernel)
                 const int kb = (int)B.qubits.size();
                 if (!tc_block && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata) &&
                     (gate_sequence_cost(op.recs, &op.gdata) <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
                     op.kind = OP_GATES;
+                    op.seq = B.seq;
                 } else {
                     op.kind = OP_DENSE;
+                    op.mat = block_matrix(B.qubits, B.seq);
                     op.recs.clear();
                     op.gdata.clear();
                 }
@@ -764,10 +778,9 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                     }
                     if (widen) {
                         std::sort(u.begin(), u.end());
-                        expand_block(&B, u);
+                        B.qubits = u;
                     }
                     if (inB || widen) {
-                        block_apply_diag(&B, g);
                         B.seq.push_back(g);
                         B.ngates++;
                     } else {
@@ -792,8 +805,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                     u.assign(g.q, g.q + g.nq);
                     std::sort(u.begin(), u.end());
                 }
-                expand_block(&B, u);
-                block_apply_dense(&B, g);
+                B.qubits = u;
                 B.seq.push_back(g);
                 B.ngates++;
             }
@@ -805,7 +817,7 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
         // kept in sequence, so the circuit is the same) often needs fewer
         // blocks; keep it when its estimated cost is lower.
         if (kmax >= 2) {
-            std::vector<int> reord = cluster_order(gates, executed, kmax);
+            const std::vector<int> reord = cluster_order(gates, executed, kmax);
             if (reord != executed) {
                 std::vector<HostOp> alt;
                 fuse(reord, &alt);
@@ -1067,7 +1079,7 @@ void smem_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, 
                 O.nrec = (int)o.recs.size();
                 O.rec_off = (int)pay.put(o.recs.data(), sizeof(GateRec) * o.recs.size());
             } else {
-                O.mat_off = (int)pay.put_cplx(o.mat, p.dtype);
+                O.mat_off = (int)pay.put_cplx(o.kind == OP_DENSE ? o.mat : block_matrix(o.qubits, o.seq), p.dtype);
             }
             if (use_tc(p, o)) {
                 // B = [Ur; Ui]: row n < D holds Re U[n][j], row D + n holds Im U[n][j]
