@@ -42,7 +42,9 @@ void make_canonical(const sv_gate& g, CGate* c) {
     for (int i = 0; i < 3; ++i) c->p[i] = g.p[i];
     const cd I(0.0, 1.0);
     const double h = 0.5 * g.p[0];
-    const double cs = cos(h), sn = sin(h);
+    // the half-angle cosine and sine only for the gates that use them
+    const bool rot = g.type == SV_RX || g.type == SV_RY || g.type == SV_U3;
+    const double cs = rot ? cos(h) : 0.0, sn = rot ? sin(h) : 0.0;
     cd* m = c->m;
     c->kind = GK_DENSE;
     switch (g.type) {
@@ -537,9 +539,8 @@ int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out,
             return SV_EINVAL;
         }
         if (g[i].type == SV_MEASURE) continue;
-        CGate c;
-        make_canonical(g[i], &c);
-        out->push_back(c);
+        out->emplace_back();
+        make_canonical(g[i], &out->back());
     }
     return SV_OK;
 }
