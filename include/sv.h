@@ -260,7 +260,13 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate *gates, size_t count,
  *     a (4 values, row-major); 1: the same with real entries; 2: a 2^k-entry
  *     diagonal table over the block index (a = mask of the positions it
  *     depends on); 3: CX, control a, target b; 4: SWAP a, b.
- *   kind 3, multiplexor (not described further): q[0] = its target.
+ *   kind 3, multiplexor (a uniformly controlled rotation, recognised from a
+ *     run of the circuit): q[0] = its target t, k = 1; at data_off: family
+ *     (0: RY, 1: diagonal), flip, flip_c, nc, the nc control qubits
+ *     (ascending), then phi0[2^nc] and, for the diagonal family, phi1[2^nc].
+ *     With j the value of the control bits (bit b <-> control b) it applies
+ *     U_j = X^(popcount(j & flip) ^ flip_c) R_j on t, R_j = RY(phi0[j]) or
+ *     diag(e^{i phi0[j]}, e^{i phi1[j]}).
  * pass: the pass the op runs in.  Planner SV_PLAN_GREEDY only
  * (SV_EUNSUPPORTED otherwise).  The counts are always written; ops, recs and
  * data are filled where they fit, and SV_EINVAL reports buffers too small

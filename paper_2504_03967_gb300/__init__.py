@@ -235,7 +235,8 @@ def sv_plan_ops(n, dtype, gates, k_max=0, tile_m=0, mux=-1, drop_phase_below=0.0
     """Host only: the greedy plan's ops in FP64 (see sv_plan_op in sv.h), as a
     list of dicts: pass, kind ("dense", "diag", "gates", "mux"), qubits, and
     per kind: mat (2^k x 2^k complex), c / a / b (phase run), recs (rkind, a,
-    b, off rows) with vals (complex values), target (multiplexor)."""
+    b, off rows) with vals (complex values), target / family / flip / flip_c /
+    controls / phi0 / phi1 (multiplexor)."""
     g = as_gates(gates)
     o = _opts(k_max, tile_m, PLAN_GREEDY, 0, 0, pass_kernel, 0, drop_phase_below, mux)
     L = lib()
@@ -272,6 +273,14 @@ def sv_plan_ops(n, dtype, gates, k_max=0, tile_m=0, mux=-1, drop_phase_below=0.0
             d["vals"] = v[0::2] + 1j * v[1::2]
         else:
             d["target"] = r.q[0]
+            fam, flip, flip_c, nc = (int(v) for v in data[off: off + 4])
+            J = 1 << nc
+            d["family"] = ("ry", "diag")[fam]
+            d["flip"], d["flip_c"] = flip, flip_c
+            d["controls"] = [int(v) for v in data[off + 4: off + 4 + nc]]
+            d["phi0"] = data[off + 4 + nc: off + 4 + nc + J].copy()
+            if fam:
+                d["phi1"] = data[off + 4 + nc + J: off + 4 + nc + 2 * J].copy()
         out.append(d)
     return out
 

@@ -375,14 +375,23 @@ int sv_plan_ops(int n, sv_dtype dt, const sv_gate* gates, size_t count, const sv
         const HostPass& hp = plan.passes[pi];
         std::vector<sv_plan_op> out;
         for (int mi : hp.mux) {
+            const Mux& M = plan.muxes[(size_t)mi];
             sv_plan_op r;
             memset(&r, 0, sizeof(r));
             r.pass = (int)pi;
             r.kind = 3;
             r.k = 1;
-            r.q[0] = plan.muxes[(size_t)mi].target;
+            r.q[0] = M.target;
             r.rec_off = (int)nr;
             r.data_off = (int64_t)nd;
+            put_d(M.family);
+            put_d((double)M.flip);
+            put_d(M.flip_c);
+            put_d((double)M.controls.size());
+            for (int c : M.controls) put_d(c);
+            for (double v : M.phi0) put_d(v);
+            if (M.family != MUX_Y)
+                for (double v : M.phi1) put_d(v);
             out.push_back(r);
         }
         for (const HostOp& o : hp.ops) {

@@ -5,7 +5,8 @@ op by op, and the result must equal the oracle's gate-by-gate state to FP64
 rounding.  This pins the planner's exact rewrites without a GPU: grouping a
 pass's gates by qubit set, phase tables kept pending past gates they commute
 with and moved through CX / SWAP, U3 = P(phi) RY(theta) P(lambda), diagonal
-gates folded into blocks or runs (App. D.2 "gate fusion", Eq. "cr1")."""
+gates folded into blocks or runs (App. D.2 "gate fusion", Eq. "cr1"), and
+runs recognised as multiplexors (Sec. 2.3)."""
 import numpy as np
 import pytest
 
@@ -71,8 +72,22 @@ def _apply_ops(n, ops, psi):
                     psi = psi[np.where(diff == 1, idx ^ (1 << p) ^ (1 << q), idx)]
                 else:
                     raise AssertionError("unknown record kind %d" % rk)
-        else:
-            raise AssertionError("multiplexors are not described")
+        else:  # multiplexor: U_j = X^(popcount(j & flip) ^ flip_c) R_j on the target
+            t = op["target"]
+            i0 = idx[((idx >> t) & 1) == 0]
+            i1 = i0 | (1 << t)
+            j = np.zeros(len(i0), dtype=np.int64)
+            for b, c in enumerate(op["controls"]):
+                j |= ((i0 >> c) & 1) << b
+            a0, a1 = psi[i0].copy(), psi[i1].copy()
+            if op["family"] == "ry":
+                cs, sn = np.cos(op["phi0"][j] / 2), np.sin(op["phi0"][j] / 2)
+                y0, y1 = cs * a0 - sn * a1, sn * a0 + cs * a1
+            else:
+                y0, y1 = np.exp(1j * op["phi0"][j]) * a0, np.exp(1j * op["phi1"][j]) * a1
+            par = np.array([bin(v).count("1") & 1 for v in (j & op["flip"])]) ^ op["flip_c"]
+            psi[i0] = np.where(par == 1, y1, y0)
+            psi[i1] = np.where(par == 1, y0, y1)
     return psi
 
 
@@ -152,6 +167,26 @@ def test_plan_ops_arguments():
     assert S.sv_plan_ops(4, S.C64, W.gates_from_list([])) == []
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_multiplexors_reproduce_the_circuit(seed):
+    """Runs of both recognised families (RY with X and CX from scattered
+    controls; RZ, P, Z, X and CX), interleaved with gates that commute with
+    them, become multiplexors whose angles (one Walsh-Hadamard transform of
+    the run's angles, Sec. 2.3's uniformly controlled rotations) reproduce the
+    oracle's gate-by-gate state."""
+    from tests.test_mux_gpu import _ladder_mix
+
+    g = _ladder_mix(seed)
+    ops = S.sv_plan_ops(10, S.C64, g, mux=1)
+    fams = sorted(op["family"] for op in ops if op["kind"] == "mux")
+    assert "ry" in fams and "diag" in fams
+    rng = np.random.default_rng(seed)
+    psi0 = rng.normal(size=1 << 10) + 1j * rng.normal(size=1 << 10)
+    psi0 /= np.linalg.norm(psi0)
+    got = _apply_ops(10, ops, psi0)
+    assert np.abs(got - oracle.apply_circuit(10, g, psi0)).max() < 1e-12
+
+
 def test_plan_ops_name_the_multiplexor_targets():
     """A QCrank circuit (a address qubits in superposition, d data qubits
     under uniformly controlled RY) plans as Hadamard blocks plus one
@@ -161,3 +196,7 @@ def test_plan_ops_name_the_multiplexor_targets():
     ops = S.sv_plan_ops(a + d, S.C64, W.qcrank(a, d, pix), mux=1)
     assert sorted(op["target"] for op in ops if op["kind"] == "mux") == list(range(a, a + d))
     assert all(op["kind"] in ("mux", "gates", "dense") for op in ops)
+    psi0 = np.zeros(1 << (a + d), dtype=complex)
+    psi0[0] = 1.0
+    got = _apply_ops(a + d, ops, psi0)
+    assert np.abs(got - oracle.apply_circuit(a + d, W.qcrank(a, d, pix), psi0)).max() < 1e-12
