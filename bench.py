@@ -50,7 +50,7 @@ UNIT = "amp_updates/s"
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
                    "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
-TRAFFIC = {"sha256": "9fd9fbe82dd739e6be55b40c547669fa2e5c7d20349a711e2d5a414bfc189dfc",
+TRAFFIC = {"sha256": "bb21599293b90f469fcf304fe7c2c9a206f3ea793dcbb915c067ae8695d4594f",
            "bytes_per_amp": 12.9808, "profile": "profiles/sv_jit_pass_qft26_c64_k5m13.md (n=26 capture, scaled to 2^n)"}
 
 

@@ -103,8 +103,8 @@ typedef enum {
  * become a relabelling of the state's qubits instead of data movement (see
  * sv_qubit_map); 0 = SWAPs move amplitudes.  drop_phase_below: the
  * approximation for negligible rotations (App. D.2): P, RZ and CP gates whose
- * angle, reduced to (-pi, pi], is smaller in magnitude than this many radians
- * are left out; the result then differs from the exact circuit by at most
+ * angle, reduced modulo the gate's period (2 pi; 4 pi for RZ, as RZ(2 pi) =
+ * -I), is smaller in magnitude than this many radians are left out; the result then differs from the exact circuit by at most
  * the sum of the dropped angles over 2 in norm (0, a negative value or NaN =
  * exact).  mux: multiplexor recognition (Sec. 2.3, QCrank's uniformly
  * controlled rotations): a run of RY (or RZ / P / Z) and X gates on one

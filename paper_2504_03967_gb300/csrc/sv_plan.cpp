@@ -551,7 +551,9 @@ void drop_small_phases(std::vector<CGate>* g, double eps) {
     kept.reserve(g->size());
     for (const CGate& x : *g) {
         if (x.type == SV_P || x.type == SV_RZ || x.type == SV_CP) {
-            double a = std::remainder(x.p[0], 2.0 * kPi);  // (-pi, pi]
+            // reduced modulo the gate's period: 2 pi for P and CP, 4 pi for RZ
+            // (RZ(2 pi) = -I is not the identity)
+            const double a = std::remainder(x.p[0], (x.type == SV_RZ ? 4.0 : 2.0) * kPi);
             if (std::fabs(a) < eps) continue;
         }
         kept.push_back(x);

@@ -159,6 +159,24 @@ def test_u3_blocks_take_the_p_ry_p_form():
     assert 0 < dt < ur
 
 
+def test_dropped_rotations_are_the_near_identity_ones():
+    """drop_phase_below leaves out P, RZ and CP gates within eps of the
+    identity: angles near 0 or 2 pi for P and CP, near 0 or 4 pi for RZ
+    (RZ(2 pi) = -I stays).  The plan equals the oracle run of the kept gates."""
+    eps = 1e-6
+    items = [(W.H, (q,), ()) for q in range(4)]
+    items += [(W.P, (0,), (5e-7,)), (W.P, (1,), (2 * np.pi - 5e-7,)), (W.CP, (0, 1), (-3e-7,)),
+              (W.RZ, (2,), (4 * np.pi - 2e-7,)), (W.RZ, (3,), (2 * np.pi - 2e-7,)), (W.RZ, (1,), (0.3,)),
+              (W.CP, (2, 3), (2e-6,))]
+    g = W.gates_from_list(items)
+    kept = W.gates_from_list([items[i] for i in (0, 1, 2, 3, 8, 9, 10)])
+    ops = S.sv_plan_ops(4, S.C64, g, drop_phase_below=eps)
+    psi0 = oracle.basis_state(4, 0)
+    got = _apply_ops(4, ops, psi0)
+    assert np.abs(got - oracle.apply_circuit(4, kept, psi0)).max() < 1e-12
+    assert np.abs(got - oracle.apply_circuit(4, g, psi0)).max() < 1e-6  # within the dropped angles
+
+
 def test_plan_ops_arguments():
     with pytest.raises(S.SVError):
         S.sv_plan_ops(0, S.C64, W.qft(3))
