@@ -184,9 +184,9 @@ int sv_info(sv_handle h, int *n, int *dtype, void **dev_amps);
  * buffer directly (sv_info, sv_attach memory, sv_sample_uniforms_noalloc)
  * sees the physical order.  sv_init_basis and sv_load_state reset the map to
  * the identity.  Shots under a non-identity map follow the sampling rule
- * over the stored order and are reported in logical labels: the distribution
- * is exactly |a_x|^2, but the outcome drawn for a given uniform is the one of
- * the stored order (sv_materialize first to reproduce identity-map draws).
+ * over the LOGICAL index, exactly as for the materialised state: the block
+ * CDF is formed in logical order from one more read of the state and the
+ * chosen block is rescanned in logical order through the map.
  * sv_qubit_map writes map[0..n-1]; sv_materialize moves the amplitudes into
  * logical order (fused SWAP passes) and resets the map. */
 int sv_qubit_map(sv_handle h, int *map);
@@ -347,11 +347,16 @@ int sv_measure(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_sample
  * overrun its budget) or a caller that cannot accept the device-wide
  * synchronisation that cudaFree implies.
  *
- * Same outcomes as sv_sample_uniforms for the same state and uniforms, but
- * the state (dev_amps: 2^n amplitudes of dtype dt, 16-byte aligned), the
+ * The same rule as sv_sample_uniforms, outcome = min{x : C_x > u C_{N-1}}
+ * over the stored index order, with its own block size (1024 amplitudes),
+ * so a draw within rounding of a CDF boundary may differ from that call's.
+ * The state (dev_amps: 2^n amplitudes of dtype dt, 16-byte aligned), the
  * uniforms (dev_u: shots doubles in [0,1)) and the outcomes (dev_out: shots
  * uint64) all live in caller-owned device memory, and the call runs
- * asynchronously on cuda_stream (NULL = legacy default stream).
+ * asynchronously on cuda_stream (NULL = legacy default stream).  The call
+ * reads dev_amps on cuda_stream only: when the state belongs to a handle,
+ * order cuda_stream after that handle's stream (or synchronise it) first,
+ * including after an sv_info call that wrote a deferred sv_init_basis.
  *
  * Its only scratch (the FP64 block CDF) is a fixed array of 128.5 KiB
  * inside this library, which every GPU that loads the library holds until

@@ -26,6 +26,26 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// SM count of the current device, looked up once per device ordinal.
+int device_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    if (dev < 0 || dev >= 64) dev = 0;
+    int s = cache[dev].load(std::memory_order_relaxed);
+    if (s <= 0) {
+        if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) {
+            cudaGetLastError();
+            s = 148;
+        }
+        cache[dev].store(s, std::memory_order_relaxed);
+    }
+    return s;
+}
+
 void reset_perm(sv_state* h) {
     for (int q = 0; q < 64; ++q) h->perm[q] = q;
     h->permuted = false;
@@ -73,15 +93,37 @@ int ensure_pinned(Scratch* s, size_t bytes) {
     return SV_OK;
 }
 
-// Key of a plan: FNV-1a over the gate records, the options that shape the
-// plan, the state's size and type, and the qubit map it starts from.
-uint64_t plan_key(const sv_state* h, const sv_gate* gates, size_t count, const sv_options* opt) {
+// The fields of each gate record the library reads: type, nq, the first nq
+// qubits and the type's parameters (three for U3, one for RX, RY, RZ, P and
+// CP, none otherwise); every other entry is zeroed, so records that differ
+// only in ignored entries share a plan.
+void used_fields(const sv_gate* gates, size_t count, std::vector<sv_gate>* out) {
+    out->assign(count, sv_gate{});
+    for (size_t i = 0; i < count; ++i) {
+        const sv_gate& g = gates[i];
+        sv_gate& r = (*out)[i];
+        r.type = g.type;
+        r.nq = g.nq;
+        for (uint32_t a = 0; a < g.nq && a < 3; ++a) r.q[a] = g.q[a];
+        const uint32_t t = g.type;
+        const int np = t == SV_U3 ? 3 : ((t == SV_RX || t == SV_RY || t == SV_RZ || t == SV_P || t == SV_CP) ? 1 : 0);
+        for (int a = 0; a < np; ++a) r.p[a] = g.p[a];
+    }
+}
+
+// Key of a plan: FNV-1a over the used fields of the gate records, the
+// options that shape the plan, the state's size and type, and the qubit map
+// it starts from.  A cache hit also compares the records themselves.
+uint64_t plan_key(const sv_state* h, const std::vector<sv_gate>& recs, const sv_options* opt) {
     uint64_t k = 1469598103934665603ull;
     auto mix = [&k](const void* p, size_t n) {
         const unsigned char* b = (const unsigned char*)p;
         for (size_t i = 0; i < n; ++i) k = (k ^ b[i]) * 1099511628211ull;
     };
-    mix(gates, count * sizeof(sv_gate));
+    for (const sv_gate& r : recs) {
+        mix(&r.type, sizeof(uint32_t) * 5);  // type, nq, q[3]
+        mix(r.p, sizeof(double) * 3);
+    }
     const int hdr[3] = {h->n, h->dtype, h->permuted ? 1 : 0};
     mix(hdr, sizeof(hdr));
     if (opt) {
@@ -92,6 +134,14 @@ uint64_t plan_key(const sv_state* h, const sv_gate* gates, size_t count, const s
     }
     if (h->permuted) mix(h->perm, sizeof(int) * h->n);
     return k ? k : 1;
+}
+
+bool same_records(const std::vector<sv_gate>& a, const std::vector<sv_gate>& b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (memcmp(&a[i].type, &b[i].type, sizeof(uint32_t) * 5) || memcmp(a[i].p, b[i].p, sizeof(double) * 3))
+            return false;
+    return true;
 }
 
 int flush_init(sv_state* h) {
@@ -234,6 +284,7 @@ int sv_free(sv_handle h) {
     if (h->err.ptr) cudaFree(h->err.ptr);
     if (h->perm_tmp.ptr) cudaFree(h->perm_tmp.ptr);
     if (h->aux.ptr) cudaFree(h->aux.ptr);
+    if (h->lcdf.ptr) cudaFree(h->lcdf.ptr);
     delete h->plans;
     if (h->host_pin.ptr) cudaFreeHost(h->host_pin.ptr);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -447,12 +498,15 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     // once its judge has settled on a candidate for the circuit
     const bool cacheable = count && (!opt || opt->planner != SV_PLAN_PLAIN);
     uint64_t key = 0;
+    std::vector<sv_gate> recs;
     if (cacheable) {
-        key = plan_key(h, gates, count, opt);
+        used_fields(gates, count, &recs);
+        key = plan_key(h, recs, opt);
         if (h->plans) {
             for (auto& kv : h->plans->entries) {
                 if (kv.first != key) continue;
                 CachedPlan& c = kv.second;
+                if (!same_records(c.recs, recs)) continue;  // a hash collision: not this circuit
                 c.stamp = ++h->plans->clock;
                 memcpy(h->perm, c.perm_after, sizeof(h->perm));
                 h->permuted = c.permuted_after;
@@ -465,7 +519,7 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
     size_t bad = 0;
     if (canonicalise(h->n, gates, count, &cg, &bad) != SV_OK)
         return set_error(SV_EINVAL, "invalid gate record at index " + std::to_string(bad));
-    return sv::apply_canonical(h, gates, count, cg, opt, key);
+    return sv::apply_canonical(h, gates, count, cg, opt, key, &recs);
 }
 
 }  // extern "C"
@@ -473,7 +527,7 @@ int sv_apply_circuit(sv_handle h, const sv_gate* gates, size_t count, const sv_o
 namespace sv {
 
 int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
-                    const sv_options* opt, uint64_t cache_key) {
+                    const sv_options* opt, uint64_t cache_key, const std::vector<sv_gate>* recs) {
     int rc = SV_OK;
     if (cg.empty()) return SV_OK;
     PlanOptions po = resolve_options(h->n, h->dtype, opt);
@@ -546,7 +600,7 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     h->last_opts.drop_phase_below = po.drop_phase_below;
     PlanBlob blob;
     serialise_plan(plan, &blob);
-    if (cache_key && !judge0) {  // keep it for the next apply of the same circuit (not while the judge times)
+    if (cache_key && recs && !judge0) {  // keep it for the next apply of the same circuit (not while the judge times)
         if (!h->plans) h->plans = new (std::nothrow) PlanCache();
         if (h->plans) {
             auto& es = h->plans->entries;
@@ -560,6 +614,7 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
             CachedPlan& c = es.back().second;
             c.plan = plan;
             c.blob = blob;
+            if (recs) c.recs = *recs;
             memcpy(c.perm_after, h->perm, sizeof(h->perm));
             c.permuted_after = h->permuted;
             c.last_opts = h->last_opts;

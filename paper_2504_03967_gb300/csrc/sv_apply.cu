@@ -1068,9 +1068,7 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_small<double>, kPassThreads, smem);
     }
     if (per_sm < 1) per_sm = 1;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     int grid = sms * per_sm;
     if (grid > C) grid = C;
     count_launch();
@@ -1089,16 +1087,7 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
 // Launchers.
 // ---------------------------------------------------------------------------
 namespace {
-int g_sms = 0;
-int num_sms() {
-    if (!g_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sms <= 0) g_sms = 148;
-    }
-    return g_sms;
-}
+int num_sms() { return device_sms(); }
 unsigned grid_for(uint64_t items, int per_thread = UNR) {
     const uint64_t want = (items + (uint64_t)256 * per_thread - 1) / ((uint64_t)256 * per_thread);
     const uint64_t cap = (uint64_t)num_sms() * 16;

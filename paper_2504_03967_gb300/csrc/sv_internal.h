@@ -260,6 +260,7 @@ struct sv_state {
     bool permuted;           // perm is not the identity
     sv::Scratch perm_tmp;    // device scratch of the permuted read-outs
     sv::Scratch aux;         // device scratch of the QCrank read-out (shots, counters, pixels)
+    sv::Scratch lcdf;        // device scratch of the logical-order block CDF of a relabelled state
     long long pending_basis; // >= 0: sv_init_basis(x) not written yet (the next apply's first pass or any other
                              // use of the state writes it)
     sv::PlanCache* plans;    // recent plans of this handle (sv_apply_circuit)
@@ -280,15 +281,20 @@ QubitMap qubit_map(const sv_state* h);
 int set_error(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 void count_launch(uint64_t k = 1);
+// SM count of the current device (cached per device ordinal).
+int device_sms();
 
 // Write a deferred sv_init_basis to the state (no-op when none is pending).
 int flush_init(sv_state* h);
-uint64_t plan_key(const sv_state* h, const sv_gate* gates, size_t count, const sv_options* opt);
+void used_fields(const sv_gate* gates, size_t count, std::vector<sv_gate>* out);
+uint64_t plan_key(const sv_state* h, const std::vector<sv_gate>& recs, const sv_options* opt);
+bool same_records(const std::vector<sv_gate>& a, const std::vector<sv_gate>& b);
 
 // The body of sv_apply_circuit after validation: plan and launch on h's stream.
 // cache_key != 0: keep the plan under that key (see PlanCache).
+// recs: the used fields of the records (see used_fields), kept with a cached plan.
 int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::vector<CGate>& cg,
-                    const sv_options* opt, uint64_t cache_key = 0);
+                    const sv_options* opt, uint64_t cache_key = 0, const std::vector<sv_gate>* recs = nullptr);
 
 // Recent plans of a handle: the same gate records, options and qubit map
 // give the same plan, so a repeated apply skips validation, planning and
@@ -301,6 +307,7 @@ struct CachedPlan {
     sv_options last_opts;
     uint64_t stamp;
     std::vector<std::string> jit_srcs;  // compiled-kernel sources of its passes (filled on first launch)
+    std::vector<sv_gate> recs;          // the used fields of the circuit's gate records (compared on a hit)
 };
 struct PlanCache {
     std::vector<std::pair<uint64_t, CachedPlan>> entries;  // small: linear search, least recently used evicted

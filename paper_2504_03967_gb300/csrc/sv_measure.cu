@@ -324,12 +324,137 @@ __global__ void __launch_bounds__(kScanT) k_scan_totals(double* __restrict__ tot
         }
 }
 
-// ---- sampler: one warp per shot ------------------------------------------
+// ---------------------------------------------------------------------------
+// Relabelled qubits: logical qubit q is stored at bit map.phys[q].  The
+// logical index x lives at P(x) = sum_q x_q 2^phys[q]; P is evaluated with
+// per-byte tables of x in shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void build_byte_tables(uint64_t (*T)[256], const QubitMap& map) {
+    for (int e = threadIdx.x; e < 5 * 256; e += blockDim.x) {
+        const int b = e >> 8, v = e & 255;
+        uint64_t o = 0;
+        for (int i = 0; i < 8; ++i) {
+            const int q = 8 * b + i;
+            if (q < map.n && ((v >> i) & 1)) o |= 1ull << map.phys[q];
+        }
+        T[b][v] = o;
+    }
+}
+__device__ __forceinline__ uint64_t phys_index(const uint64_t (*T)[256], uint64_t x) {
+    return T[0][x & 255] | T[1][(x >> 8) & 255] | T[2][(x >> 16) & 255] | T[3][(x >> 24) & 255] |
+           T[4][(x >> 32) & 255];
+}
+
+// ---- logical-order block totals of a relabelled state ----------------------
+// The sampler's rule min{x : C_x > u S} runs over the LOGICAL index x.  Logical
+// block j holds x = j 2^B .. (j + 1) 2^B - 1; its amplitudes are the physical
+// ones whose bits phys[0..B-1] (the set S) vary while the other physical bits
+// spell j.  The state is read once in physical order, in chunks of 2^c
+// contiguous amplitudes: a chunk's bits outside S (K_low) select different
+// blocks and its bits in S (S_low) are summed; the physical bits above the
+// chunk outside S (K_high) number the units the CTAs take, and those in S
+// (S_high) are summed by a loop over all chunks of a unit.  Every sum has a
+// fixed order, so the totals are bitwise reproducible.
+struct LogicalBlocks {
+    int c;          // chunk bits (physical bits 0..c-1)
+    int nkh;        // physical bits >= c outside S
+    int kh[40];     // their positions, ascending
+    int khb[40];    // the block-index bit each one spells
+    uint64_t shmask;  // physical bits >= c inside S
+    int nkl, nsl;   // chunk bits outside / inside S
+    int kl[10], klb[10], sl[10];
+};
+
+// Probability accumulator of one chunk position: complex64 forms |a|^2
+// exactly as a float pair and adds in double-float; complex128 adds in FP64.
+template <typename V> struct PAcc;
+template <> struct PAcc<float2> {
+    FF a{0.f, 0.f};
+    __device__ __forceinline__ void add(float2 v) {
+        const float r2 = v.x * v.x, r2e = fmaf(v.x, v.x, -r2);
+        const float i2 = v.y * v.y, i2e = fmaf(v.y, v.y, -i2);
+        const float sum = r2 + i2, bb = sum - r2;
+        ff_add(a, sum, ((r2 - (sum - bb)) + (i2 - bb)) + r2e + i2e);
+    }
+    __device__ __forceinline__ double val() const { return ff_val(a); }
+};
+template <> struct PAcc<double2> {
+    double a = 0.0;
+    __device__ __forceinline__ void add(double2 v) { a += prob(v); }
+    __device__ __forceinline__ double val() const { return a; }
+};
+
 template <typename V>
+__global__ void __launch_bounds__(256) k_block_tot_logical(const V* __restrict__ psi, const LogicalBlocks lb,
+                                                           uint64_t nunits, double* __restrict__ tot) {
+    __shared__ double sacc[1 << kBlogMax];
+    const int P = 1 << lb.c, tid = threadIdx.x;
+    for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        uint64_t base = 0, jb = 0;
+        for (int k = 0; k < lb.nkh; ++k)
+            if ((u >> k) & 1) {
+                base |= 1ull << lb.kh[k];
+                jb |= 1ull << lb.khb[k];
+            }
+        PAcc<V> a[4];
+        uint64_t sub = 0;  // the S_high bits, every subset of shmask in increasing order
+        do {
+            const V* src = psi + (base | sub);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int pos = tid + 256 * r;
+                if (pos < P) a[r].add(src[pos]);
+            }
+            sub = (sub - lb.shmask) & lb.shmask;
+        } while (sub);
+        // chunk position -> (K_low pattern t, S_low pattern v) at t 2^nsl + v,
+        // then a halving tree over v inside each segment
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int pos = tid + 256 * r;
+            if (pos < P) {
+                int t = 0, v = 0;
+                for (int k = 0; k < lb.nkl; ++k) t |= ((pos >> lb.kl[k]) & 1) << k;
+                for (int k = 0; k < lb.nsl; ++k) v |= ((pos >> lb.sl[k]) & 1) << k;
+                sacc[(t << lb.nsl) | v] = a[r].val();
+            }
+        }
+        __syncthreads();
+        for (int w = (1 << lb.nsl) >> 1; w >= 1; w >>= 1) {
+            for (int q = tid; q < P / 2; q += blockDim.x) {
+                const int seg = q / w, o = q - seg * w;
+                sacc[seg * 2 * w + o] += sacc[seg * 2 * w + o + w];
+            }
+            __syncthreads();
+        }
+        for (int t = tid; t < (1 << lb.nkl); t += blockDim.x) {
+            uint64_t j = jb;
+            for (int k = 0; k < lb.nkl; ++k)
+                if ((t >> k) & 1) j |= 1ull << lb.klb[k];
+            tot[j] = sacc[t << lb.nsl];
+        }
+        __syncthreads();
+    }
+}
+
+// ---- sampler: one warp per shot ------------------------------------------
+// PERM (a relabelled state): cdf is the block CDF in LOGICAL order (from
+// k_block_tot_logical) and the chosen block is rescanned in logical order,
+// amplitude x read at its physical index; the outcome is the logical x.
+template <typename V, bool PERM>
 __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n, int blog,
                                                 const double* __restrict__ cdf, uint64_t nblocks,
                                                 uint64_t shots, uint64_t seed, const double* __restrict__ u_in,
-                                                uint64_t* __restrict__ out) {
+                                                uint64_t* __restrict__ out, const QubitMap map) {
+    __shared__ uint64_t qt[PERM ? 5 : 1][256];
+    if constexpr (PERM) {
+        build_byte_tables(qt, map);
+        __syncthreads();
+    }
+    auto amp = [&](uint64_t x) -> V {
+        if constexpr (PERM) return psi[phys_index(qt, x)];
+        else return psi[x];
+    };
     const int lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const double S = cdf[nblocks - 1];
@@ -352,7 +477,7 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
         const uint64_t c0 = b0 + (uint64_t)lane * per;
         double ls = 0.0;
         if ((uint64_t)lane * per < len)
-            for (int i = 0; i < per; ++i) ls += prob(psi[c0 + i]);
+            for (int i = 0; i < per; ++i) ls += prob(amp(c0 + i));
         double inc = ls;
 #pragma unroll
         for (int sh = 1; sh < 32; sh <<= 1) {
@@ -369,7 +494,7 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
             const uint64_t cb = b0 + (uint64_t)L * per;
             uint64_t pick = UINT64_MAX, last_nz = cb;
             for (int i = 0; i < per && (uint64_t)L * per + i < len; ++i) {
-                const double p = prob(psi[cb + i]);
+                const double p = prob(amp(cb + i));
                 if (p > 0.0) last_nz = cb + i;
                 acc += p;
                 if (acc > t && p > 0.0) {
@@ -388,16 +513,7 @@ __global__ void __launch_bounds__(256) k_probs(const V* __restrict__ psi, uint64
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) out[i] = prob(psi[i]);
 }
 
-int sms() {
-    static int s = 0;
-    if (!s) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-        if (s <= 0) s = 148;
-    }
-    return s;
-}
+int sms() { return device_sms(); }
 
 // Scratch layout in h->red: [block sums/cdf: nblocks][chunk totals: nch][expz partials]
 size_t nblocks_of(int n, int* blog, int cap = kBlogMax) {
@@ -414,6 +530,75 @@ int sample_blog(int n, uint64_t shots) {
     return b;
 }
 }  // namespace
+
+// Inclusive FP64 scan of a[0..len) in place; chunks: (len + kScanCh - 1) / kScanCh doubles of scratch.
+static void scan_in_place(double* a, size_t len, double* chunks, cudaStream_t st) {
+    const size_t nch = (len + kScanCh - 1) / kScanCh;
+    if (nch <= 1) {
+        count_launch();
+        k_scan_chunks<<<1, kScanT, 0, st>>>(a, len, nullptr);
+    } else {
+        count_launch(3);
+        k_chunk_totals<<<(unsigned)nch, kScanT, 0, st>>>(a, len, chunks);
+        k_scan_totals<<<1, kScanT, 0, st>>>(chunks, (int)nch);
+        k_scan_chunks<<<(unsigned)nch, kScanT, 0, st>>>(a, len, chunks);
+    }
+}
+
+// Block CDF in LOGICAL order of a relabelled state (blocks of 2^blog
+// consecutive logical indices), in h->lcdf: [cdf: nb][chunk totals: nch].
+static int logical_block_cdf(sv_state* h, int blog, double** cdf_out, int64_t* nb_out) {
+    const int n = h->n;
+    const size_t nb = (size_t)1 << (n - blog);
+    const size_t nch = (nb + kScanCh - 1) / kScanCh;
+    int rc = ensure_scratch(&h->lcdf, sizeof(double) * (nb + nch), h->stream);
+    if (rc) return rc;
+    double* cdf = (double*)h->lcdf.ptr;
+    const QubitMap map = qubit_map(h);
+    int inv[64];  // physical bit -> logical qubit
+    for (int q = 0; q < n; ++q) inv[map.phys[q]] = q;
+    uint64_t smask = 0;  // physical bits of the in-block logical qubits
+    for (int q = 0; q < blog; ++q) smask |= 1ull << map.phys[q];
+    auto unit_bits = [&](int c) {
+        int k = 0;
+        for (int b = c; b < n; ++b) k += !((smask >> b) & 1);
+        return k;
+    };
+    // chunk bits: up to 10; fewer (down to 8) when the units would not fill the GPU
+    int c = n < kBlogMax ? n : kBlogMax;
+    while (c > 8 && ((uint64_t)1 << unit_bits(c)) < (uint64_t)4 * sms()) --c;
+    LogicalBlocks lb{};
+    lb.c = c;
+    for (int b = 0; b < n; ++b) {
+        const bool in_s = (smask >> b) & 1;
+        if (b < c) {
+            if (in_s) lb.sl[lb.nsl++] = b;
+            else {
+                lb.kl[lb.nkl] = b;
+                lb.klb[lb.nkl++] = inv[b] - blog;
+            }
+        } else if (in_s) {
+            lb.shmask |= 1ull << b;
+        } else {
+            lb.kh[lb.nkh] = b;
+            lb.khb[lb.nkh++] = inv[b] - blog;
+        }
+    }
+    const uint64_t nunits = 1ull << lb.nkh;
+    const uint64_t cap = (uint64_t)sms() * 8;
+    const unsigned g = (unsigned)(nunits < cap ? nunits : cap);
+    count_launch();
+    if (h->dtype == SV_C64)
+        k_block_tot_logical<float2><<<g, 256, 0, h->stream>>>((const float2*)h->amps, lb, nunits, cdf);
+    else
+        k_block_tot_logical<double2><<<g, 256, 0, h->stream>>>((const double2*)h->amps, lb, nunits, cdf);
+    scan_in_place(cdf, nb, cdf + nb, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "logical block statistics");
+    *cdf_out = cdf;
+    *nb_out = (int64_t)nb;
+    return SV_OK;
+}
 
 // Block statistics in h->red: [raw block totals: nb][inclusive CDF: nb]
 // [chunk totals: nch][bit sums: 10 nb, when asked for].
@@ -437,15 +622,7 @@ static int block_stats(sv_state* h, bool want_bits, double** tot_out, double** c
         k_block_stats<double2><<<g, 256, 0, h->stream>>>((const double2*)h->amps, blog, nb, tot, bits);
     cudaError_t e = cudaMemcpyAsync(cdf, tot, sizeof(double) * nb, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "block totals copy");
-    if (nch <= 1) {
-        count_launch();
-        k_scan_chunks<<<1, kScanT, 0, h->stream>>>(cdf, nb, nullptr);
-    } else {
-        count_launch(3);
-        k_chunk_totals<<<(unsigned)nch, kScanT, 0, h->stream>>>(cdf, nb, chunks);
-        k_scan_totals<<<1, kScanT, 0, h->stream>>>(chunks, (int)nch);
-        k_scan_chunks<<<(unsigned)nch, kScanT, 0, h->stream>>>(cdf, nb, chunks);
-    }
+    scan_in_place(cdf, nb, chunks, h->stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "block statistics");
     if (tot_out) *tot_out = tot;
@@ -456,28 +633,7 @@ static int block_stats(sv_state* h, bool want_bits, double** tot_out, double** c
     return SV_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Relabelled qubits: logical qubit q is stored at bit map.phys[q].  The
-// logical index x lives at P(x) = sum_q x_q 2^phys[q]; P is evaluated with
-// per-byte tables of x in shared memory.
-// ---------------------------------------------------------------------------
 namespace {
-__device__ __forceinline__ void build_byte_tables(uint64_t (*T)[256], const QubitMap& map) {
-    for (int e = threadIdx.x; e < 5 * 256; e += blockDim.x) {
-        const int b = e >> 8, v = e & 255;
-        uint64_t o = 0;
-        for (int i = 0; i < 8; ++i) {
-            const int q = 8 * b + i;
-            if (q < map.n && ((v >> i) & 1)) o |= 1ull << map.phys[q];
-        }
-        T[b][v] = o;
-    }
-}
-__device__ __forceinline__ uint64_t phys_index(const uint64_t (*T)[256], uint64_t x) {
-    return T[0][x & 255] | T[1][(x >> 8) & 255] | T[2][(x >> 16) & 255] | T[3][(x >> 24) & 255] |
-           T[4][(x >> 32) & 255];
-}
-
 template <typename V>
 __global__ void __launch_bounds__(256) k_probs_logical(const V* __restrict__ psi, uint64_t N, double* __restrict__ out,
                                                        const QubitMap map) {
@@ -503,17 +659,6 @@ __global__ void __launch_bounds__(256) k_gather_logical(const V* __restrict__ ps
         out[i] = psi[phys_index(T, x0 + i)];
 }
 
-// physical outcome y -> logical x (bit q of x = bit phys[q] of y), in place
-__global__ void k_logical_samples(uint64_t* __restrict__ s, uint64_t shots, const QubitMap map) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < shots; i += stride) {
-        const uint64_t y = s[i];
-        uint64_t x = 0;
-        for (int q = 0; q < map.n; ++q) x |= ((y >> map.phys[q]) & 1ull) << q;
-        s[i] = x;
-    }
-}
-
 __global__ void k_logical_expz(const double* __restrict__ phys, double* __restrict__ out, const QubitMap map) {
     const int q = threadIdx.x;
     if (q < map.n) out[q] = phys[map.phys[q]];
@@ -526,12 +671,6 @@ unsigned grid_n(uint64_t n, int cap_per_sm) {
     return (unsigned)(g ? g : 1);
 }
 
-cudaError_t to_logical_samples(sv_state* h, uint64_t* dev_samples, uint64_t shots) {
-    if (!h->permuted || !shots) return cudaSuccess;
-    count_launch();
-    k_logical_samples<<<grid_n(shots, 4), 256, 0, h->stream>>>(dev_samples, shots, qubit_map(h));
-    return cudaGetLastError();
-}
 }  // namespace
 
 cudaError_t launch_gather_logical(sv_state* h, uint64_t x0, uint64_t cnt, void* dev_out) {
@@ -580,19 +719,38 @@ int measure_norm(sv_state* h, double* host_out) {
     return SV_OK;
 }
 
+// Shots from a block CDF; logical = the CDF is in logical order (relabelled
+// state) and the outcomes come out as logical indices.
 static cudaError_t launch_sample(sv_state* h, int blog, const double* cdf, int64_t nb, uint64_t shots,
-                                 uint64_t seed, const double* dev_u, uint64_t* dev_out) {
+                                 uint64_t seed, const double* dev_u, uint64_t* dev_out, bool logical = false) {
     uint64_t g = (shots * 32 + 255) / 256;
     const uint64_t cap = (uint64_t)sms() * 16;
     if (g > cap) g = cap;
     count_launch();
-    if (h->dtype == SV_C64)
-        k_sample<float2><<<(unsigned)g, 256, 0, h->stream>>>((const float2*)h->amps, h->n, blog, cdf, (uint64_t)nb,
-                                                            shots, seed, dev_u, dev_out);
-    else
-        k_sample<double2><<<(unsigned)g, 256, 0, h->stream>>>((const double2*)h->amps, h->n, blog, cdf,
-                                                             (uint64_t)nb, shots, seed, dev_u, dev_out);
+    const QubitMap map = qubit_map(h);
+    const unsigned gg = (unsigned)g;
+    if (h->dtype == SV_C64) {
+        const float2* a = (const float2*)h->amps;
+        if (logical) k_sample<float2, true><<<gg, 256, 0, h->stream>>>(a, h->n, blog, cdf, nb, shots, seed, dev_u, dev_out, map);
+        else k_sample<float2, false><<<gg, 256, 0, h->stream>>>(a, h->n, blog, cdf, nb, shots, seed, dev_u, dev_out, map);
+    } else {
+        const double2* a = (const double2*)h->amps;
+        if (logical) k_sample<double2, true><<<gg, 256, 0, h->stream>>>(a, h->n, blog, cdf, nb, shots, seed, dev_u, dev_out, map);
+        else k_sample<double2, false><<<gg, 256, 0, h->stream>>>(a, h->n, blog, cdf, nb, shots, seed, dev_u, dev_out, map);
+    }
     return cudaGetLastError();
+}
+
+// Shots of a relabelled state: logical-order block CDF, logical rescan.
+static int sample_logical(sv_state* h, int blog, uint64_t shots, uint64_t seed, const double* dev_u,
+                          uint64_t* dev_out) {
+    double* cdf;
+    int64_t nb;
+    int rc = logical_block_cdf(h, blog, &cdf, &nb);
+    if (rc) return rc;
+    cudaError_t e = launch_sample(h, blog, cdf, nb, shots, seed, dev_u, dev_out, true);
+    if (e != cudaSuccess) return cuda_fail(e, "sample (relabelled state)");
+    return SV_OK;
 }
 
 // Shots and <Z_i> from ONE pass over the state (either output may be NULL).
@@ -617,11 +775,14 @@ int measure_readout(sv_state* h, uint64_t shots, uint64_t seed, uint64_t* dev_sa
         }
     }
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && dev_samples && shots) {
-        e = launch_sample(h, blog, cdf, nb, shots, seed, nullptr, dev_samples);
-        if (e == cudaSuccess) e = to_logical_samples(h, dev_samples, shots);
-    }
     if (e != cudaSuccess) return cuda_fail(e, "read-out");
+    if (dev_samples && shots) {
+        // a relabelled state samples from its logical-order CDF (a second
+        // read of the state; <Z> above used the physical block statistics)
+        if (h->permuted) return sample_logical(h, blog, shots, seed, nullptr, dev_samples);
+        e = launch_sample(h, blog, cdf, nb, shots, seed, nullptr, dev_samples);
+        if (e != cudaSuccess) return cuda_fail(e, "read-out");
+    }
     return SV_OK;
 }
 
@@ -629,13 +790,14 @@ int measure_expect_z(sv_state* h, double* dev_out) { return measure_readout(h, 0
 
 int measure_sample(sv_state* h, uint64_t shots, uint64_t seed, const double* dev_u, uint64_t* dev_out) {
     if (shots == 0) return SV_OK;
+    const int sb = sample_blog(h->n, shots);
+    if (h->permuted) return sample_logical(h, h->n < sb ? h->n : sb, shots, seed, dev_u, dev_out);
     double* cdf;
     int blog;
     int64_t nb;
-    int rc = measure_block_sums(h, &cdf, &blog, &nb, sample_blog(h->n, shots));
+    int rc = measure_block_sums(h, &cdf, &blog, &nb, sb);
     if (rc) return rc;
     cudaError_t e = launch_sample(h, blog, cdf, nb, shots, seed, dev_u, dev_out);
-    if (e == cudaSuccess) e = to_logical_samples(h, dev_out, shots);
     if (e != cudaSuccess) return cuda_fail(e, "sample");
     return SV_OK;
 }
@@ -731,11 +893,11 @@ extern "C" int sv_sample_uniforms_noalloc(const void* dev_amps, int n, sv_dtype 
     if (gs > cap) gs = cap;
     count_launch();
     if (dt == SV_C64)
-        k_sample<float2><<<(unsigned)gs, 256, 0, st>>>((const float2*)dev_amps, n, blog, bs, (uint64_t)nb, shots,
-                                                      0, dev_u, dev_out);
+        k_sample<float2, false><<<(unsigned)gs, 256, 0, st>>>((const float2*)dev_amps, n, blog, bs, (uint64_t)nb,
+                                                             shots, 0, dev_u, dev_out, QubitMap{});
     else
-        k_sample<double2><<<(unsigned)gs, 256, 0, st>>>((const double2*)dev_amps, n, blog, bs, (uint64_t)nb,
-                                                       shots, 0, dev_u, dev_out);
+        k_sample<double2, false><<<(unsigned)gs, 256, 0, st>>>((const double2*)dev_amps, n, blog, bs,
+                                                              (uint64_t)nb, shots, 0, dev_u, dev_out, QubitMap{});
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sv_sample_uniforms_noalloc");
     return SV_OK;

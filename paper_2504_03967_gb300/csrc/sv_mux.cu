@@ -97,16 +97,7 @@ __global__ void __launch_bounds__(256) k_mux(const MuxDev D, const unsigned char
     }
 }
 
-int mux_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
+int mux_sms() { return device_sms(); }
 
 template <typename T, typename C>
 cudaError_t mux_t(sv_state* h, const unsigned char* region, const MuxDev& D) {

@@ -75,16 +75,7 @@ __global__ void __launch_bounds__(256) k_qc_pixels(const unsigned long long* __r
     }
 }
 
-int qc_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
+int qc_sms() { return device_sms(); }
 
 }  // namespace
 

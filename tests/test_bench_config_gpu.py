@@ -4,13 +4,17 @@ first one building its tiles from the deferred basis state), k_max 5, tile
 13.  QFT|x> = 2^(-n/2) sum_y e^{2 pi i x y / N}|y> is known amplitude by
 amplitude, so 2^16 sampled amplitudes are compared with it (complex64 bound
 1e-5 relative), and the norm and <Z_i> = 0 (uniform magnitudes) hold for the
-whole state."""
+whole state.  Its probabilities are all 1/N, so the oracle's shot rule
+min{x : C_x > u C_{N-1}} over the logical index gives x = floor(u N): the
+relabelled state's shots must equal it except within 1e-9 of a boundary."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2504_03967_gb300 as S
 import workloads as W
 from paper_2504_03967_gb300 import build as B
+from tests import gpu_util as U
 
 pytestmark = pytest.mark.gpu
 
@@ -42,5 +46,14 @@ def test_qft28_bench_configuration():
         got = state.view(torch.complex64)[torch.from_numpy(phys).cuda()].cpu().numpy().astype(np.complex128)
         ref = np.exp(2j * np.pi * ((x * ys) % N) / N) / np.sqrt(N)
         assert np.abs(got - ref).max() * np.sqrt(N) < 1e-5
+        # shots of the relabelled state under the logical-order rule
+        shots = 4096
+        samp, _ = S.sv_measure(h, shots, 1234)
+        t = oracle.uniforms(1234, shots) * N
+        x0 = np.floor(t).astype(np.int64)
+        near = np.minimum(t - x0, x0 + 1 - t) / N < U.BAND
+        bad = np.nonzero((samp.astype(np.int64) != x0) & ~near)[0]
+        assert len(bad) == 0, "shots %s: got %s want %s" % (bad[:5], samp[bad[:5]], x0[bad[:5]])
+        assert (~near).sum() > shots // 4
     finally:
         S.sv_free(h)

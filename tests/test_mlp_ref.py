@@ -1,8 +1,12 @@
 """Pins for the FP64 cost-model reference (CPU only): central finite
 differences of the loss, the closed-form gradient of a network reduced to a
-linear model, and Adam's first step (which moves each parameter by lr in the
-direction of -sign(g))."""
+linear model, Adam's first step (which moves each parameter by lr in the
+direction of -sign(g)), and Adam under a constant gradient, where bias
+correction makes the corrected moments exactly g and g^2 at every step, so
+every step moves each parameter by lr g / (|g| + eps) (Kingma & Ba 2015,
+Sec. 3): a missing, constant or mis-indexed correction fails from step 2."""
 import numpy as np
+import pytest
 
 from oracle import mlp_ref as M
 
@@ -61,3 +65,43 @@ def test_adam_first_step():
     assert big.sum() > 100
     assert np.allclose((p1 - p)[big], -1e-3 * np.sign(g[big]), rtol=1e-5, atol=0)
     assert np.all(np.abs(p1 - p) <= 1e-3 * (1 + 1e-12))
+
+
+def _adam_constant_gradient(adam, steps=12, lr=1e-3):
+    rng = np.random.default_rng(4)
+    p0 = _params(rng)
+    g = rng.standard_normal(M.NPARAMS)
+    m = np.zeros(M.NPARAMS)
+    v = np.zeros(M.NPARAMS)
+    p = p0
+    for k in range(1, steps + 1):
+        p, m, v = adam(p, g, m, v, k, lr=lr)
+        # the moments themselves: m_k = (1 - b1^k) g, v_k = (1 - b2^k) g^2
+        assert np.allclose(m, (1 - 0.9 ** k) * g, rtol=1e-12, atol=0), k
+        assert np.allclose(v, (1 - 0.999 ** k) * g * g, rtol=1e-12, atol=0), k
+        # every step moves by lr g / (|g| + eps)
+        assert np.allclose(p, p0 - k * lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15), k
+
+
+def test_adam_constant_gradient():
+    _adam_constant_gradient(M.adam)
+
+
+def _adam_variant(replace_from, replace_to):
+    import inspect
+    src = inspect.getsource(M.adam)
+    assert src.count(replace_from) == 1
+    ns = {"np": np}
+    exec(src.replace(replace_from, replace_to), ns)
+    return ns["adam"]
+
+
+@pytest.mark.parametrize("mutant", [
+    ("mh = m / (1.0 - b1 ** step)", "mh = m / (1.0 - b1)"),          # constant correction
+    ("vh = v / (1.0 - b2 ** step)", "vh = v / (1.0 - b2)"),
+    ("mh = m / (1.0 - b1 ** step)", "mh = m"),                       # no correction
+    ("mh = m / (1.0 - b1 ** step)", "mh = m / (1.0 - b1 ** (step + 1))"),  # off by one step
+])
+def test_adam_constant_gradient_catches_planted_mistakes(mutant):
+    with pytest.raises(AssertionError):
+        _adam_constant_gradient(_adam_variant(*mutant))

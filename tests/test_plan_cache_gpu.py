@@ -77,3 +77,30 @@ def test_options_are_part_of_the_key():
         assert oracle.fidelity(approx, exact) < 1 - 1e-4
     finally:
         S.sv_free(h)
+
+
+def test_cache_ignores_unused_fields_and_compares_records():
+    """Records that differ only in entries the library ignores (unused qubits
+    and parameters) share a cached plan; records that differ in a used
+    parameter do not, even right after the first circuit's plan was cached."""
+    n = 12
+    g = W.random_u3_cx(n, 3, 21)
+    noisy = g.copy()
+    rng = np.random.default_rng(4)
+    one_q = noisy["nq"] == 1
+    noisy["q"][one_q, 1] = rng.integers(0, 1 << 30, size=int(one_q.sum()))
+    noisy["q"][:, 2] = rng.integers(0, 1 << 30, size=len(noisy))
+    cx = noisy["type"] == W.CX
+    noisy["p"][cx] = rng.standard_normal((int(cx.sum()), 3))
+    other = g.copy()
+    u3 = np.nonzero(g["type"] == W.U3)[0]
+    other["p"][u3[5], 1] += 0.25  # one used parameter changed
+    psi0 = W.random_state(n, 3)
+    h = S.sv_alloc(n, S.C64)
+    try:
+        for circ in (g, noisy, other, g):
+            S.sv_load_state(h, psi0)
+            S.sv_apply_circuit(h, circ)
+            U.assert_close(S.sv_store_state(h).astype(np.complex128), U.run_oracle(n, circ, psi0), S.C64)
+    finally:
+        S.sv_free(h)

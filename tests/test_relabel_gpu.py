@@ -60,18 +60,20 @@ def test_relabelled_readouts(dtype, planner, kind):
         ez = S.sv_expect_z(h)
         ez_ref = oracle.expect_z(ref)
         assert np.abs(ez - ez_ref).max() < (1e-5 if dtype == S.C64 else 1e-11)
-        # shots: the sampling rule runs over the stored (physical) order and the
-        # outcomes come back in logical labels
-        qmap = S.sv_qubit_map(h)
-        xs = np.arange(1 << n, dtype=np.int64)
-        ys = np.zeros_like(xs)
-        for q in range(n):
-            ys |= ((xs >> q) & 1) << qmap[q]
-        p_phys = np.empty_like(p)
-        p_phys[ys] = p
+        # shots follow the oracle's rule over the LOGICAL index: outcome =
+        # min{x : C_x > u C_{N-1}}.  complex128 end to end against the
+        # oracle's own probabilities; complex64 against the oracle's CDF of
+        # the GPU's probabilities (its amplitudes differ in the 7th digit)
+        c_ref = oracle.cdf(np.abs(ref) ** 2 if dtype == S.C128 else p)
         u = np.random.default_rng(5).random(2000)
         shots = S.sv_sample_uniforms(h, u).astype(np.int64)
-        U.compare_samples(ys[shots], u, oracle.cdf(p_phys), U.BAND)
+        U.compare_samples(shots, u, c_ref, U.BAND)
+        # Philox shots (sv_sample and the one-read sv_measure) follow the same rule
+        us = oracle.uniforms(77, 3000)
+        U.compare_samples(S.sv_sample(h, 3000, 77).astype(np.int64), us, c_ref, U.BAND)
+        sm, ezm = S.sv_measure(h, 3000, 77)
+        U.compare_samples(sm.astype(np.int64), us, c_ref, U.BAND)
+        assert np.abs(ezm - ez_ref).max() < (1e-5 if dtype == S.C64 else 1e-11)
         # a second circuit acts on the logical qubits
         g2 = W.random_u3_cx(n, 2, 44)
         S.sv_apply_circuit(h, g2, planner=planner, relabel=1)
