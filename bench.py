@@ -1,22 +1,30 @@
 """Benchmark: amplitude updates/s of the fused state-vector path on GB300.
 
-Workload (default): QFT on n=28 qubits with the textbook H + controlled-phase
-ladder and final swaps (420 gates) applied to a seeded random basis state,
-complex64, then 100 shots and <Z_i> for all qubits.  One step = state init,
-plan + fused apply, probability block sums, block CDF scan, sampling and
-<Z>: every stage of the hot path.  The state (2 GiB) is larger than L2
-(129 MB), so no flush is needed between steps.
+Workload (default, --workload random32): 60 layers of seeded U3 on every
+qubit plus CX on a random disjoint pairing (2880 gates) applied to |0...0>
+on n=32 qubits, complex64 (32 GiB state), then 100 shots and <Z_i> for all
+qubits.  One step = state init, plan + fused apply (cost-model planner),
+probability block sums, block CDF scan, sampling and <Z>: every stage of the
+hot path.  The state is larger than L2 (129 MB), so no flush is needed
+between steps.  --workload qft28 runs QFT n=28 (420 gates) on a seeded basis
+state instead.
 
-value      = whole-job amplitude updates/s (420 * 2^28 per step per GPU),
+value      = whole-job amplitude updates/s (gates * 2^n per step per GPU),
              device-timed with CUDA events on the library's stream.
 e2e        = the same metric through the C ABI with host buffers: gate list
              from host memory in, samples and <Z> copied back every step.
 roofline   = the tile-pass kernel: algorithmic bytes per launch (one read and
              one write of the state, 16 B per amplitude) / mean launch time
              from CUDA events recorded by the library around each pass.
+greedy     = the same step with the greedy fixed-k planner (the cost model's
+             fallback and judge).
 plain      = the same step with one kernel per gate (no fusion).
+check      = after the timed steps: QFT, sampled amplitudes against the closed
+             form; random circuits, the circuit then its inverse from |0>,
+             which must give <Z_i> = 1 for every qubit.
 cpu_baseline = the FP64 oracle on the host cores over a bounded prefix of
-             the same gate list (rank 0, N=1 only).
+             the same gate list at the same n (rank 0, N=1 only), all cores
+             and one thread, extrapolated to the step by gate count.
 
 --impl reference runs the oracle as the reference arm (host cores).
 """
@@ -130,22 +138,50 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(n, gates, x, budget_s=12.0):
-    """FP64 oracle on all host cores over a bounded prefix of the gate list."""
+    """FP64 oracle on the host cores over a bounded prefix of the gate list at
+    the same n: one thread for the first gate, all cores for the next ones
+    (about budget_s), each extrapolated to the whole list by gate count."""
     import oracle
 
     cores = len(os.sched_getaffinity(0))
-    oracle.set_threads(cores)
-    psi = oracle.basis_state(n, x)
+    psi = oracle.basis_state(n, x)  # complex128: 16 B per amplitude
+    oracle.set_threads(1)
     t0 = time.perf_counter()
-    psi = oracle.apply_circuit(n, gates[:1], psi)
+    oracle.apply_inplace(n, gates[:1], psi)
     t1 = time.perf_counter() - t0
-    G = int(max(1, min(len(gates) - 1, budget_s / max(t1, 1e-3))))
+    oracle.set_threads(cores)
     t0 = time.perf_counter()
-    oracle.apply_circuit(n, gates[1:1 + G], psi)
+    oracle.apply_inplace(n, gates[1:2], psi)
+    tg = time.perf_counter() - t0
+    G = int(max(1, min(len(gates) - 2, budget_s / max(tg, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.apply_inplace(n, gates[2:2 + G], psi)
     dt = time.perf_counter() - t0
-    return {"value": G * float(1 << n) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "gates 2..%d of the %d-gate list at n=%d, FP64 complex128, %.1f s" % (G + 1, len(gates), n, dt)}
+    del psi
+    N = float(1 << n)
+    return {"value": G * N / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": "gates 3..%d of the %d-gate list at n=%d, FP64 complex128, %d threads, %.1f s; extrapolated "
+                      "to the whole list by gate count" % (G + 2, len(gates), n, cores, dt),
+            "single_thread": {"value": N / t1, "unit": UNIT, "cores": 1,
+                              "sample": "gate 1 of the list at n=%d, one thread, %.1f s; extrapolated" % (n, t1)}}
 
 
 def train_cost_model(S, dt, n):
@@ -179,7 +215,8 @@ def train_cost_model(S, dt, n):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only), each
+    step a bounded slice of the same gate list at the same n."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -191,12 +228,12 @@ def run_reference(args):
     psi = oracle.basis_state(n, x)
     per = max(1, args.ref_gates)
     for s in range(args.warmup):
-        oracle.apply_circuit(n, g[:per], psi)
+        oracle.apply_inplace(n, g[:per], psi)
     times = []
     for s in range(args.steps):
         lo = (s * per) % len(g)
         t0 = time.perf_counter()
-        psi = oracle.apply_circuit(n, g[lo:lo + per], psi)
+        oracle.apply_inplace(n, g[lo:lo + per], psi)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     val = per * float(1 << n) / (ms / 1e3)
@@ -204,7 +241,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates_per_step": per, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": "%d gates of the list per step at n=%d, FP64" % (per, n)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -349,7 +386,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qft28")
+    ap.add_argument("--workload", default="random32")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--planner", default="mlp", choices=["greedy", "mlp", "plain"])
     ap.add_argument("--cm-n", type=int, default=26, help="qubits of the cost-model training circuits")
@@ -495,7 +532,8 @@ def main():
 
     plain = None
     if not args.no_plain and planner != S.PLAN_PLAIN:
-        pms, _ = timed(S.PLAN_PLAIN, max(2, args.steps // 3), 1, 0, "plain_steps")
+        # one kernel per gate: about 25 s per step at n=32, so one timed step there
+        pms, _ = timed(S.PLAN_PLAIN, 1 if n >= 30 else max(2, args.steps // 3), 1, 0, "plain_steps")
         plain = {"value": world * updates / (pms / 1e3), "ms_per_step": pms,
                  "fused_over_plain": pms / ms}
     greedy = None
@@ -526,7 +564,9 @@ def main():
         e2e = {"value": world * updates / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": int(gh.nbytes + 8), "d2h_bytes_per_step": int(8 * args.shots + 8 * n)}
 
-    # fidelity check on sampled amplitudes (QFT of a basis state has a closed form)
+    # correctness after the timed steps.  QFT of a basis state: sampled
+    # amplitudes against the closed form.  Random circuits: the circuit and
+    # then its inverse from |x> give back |x>, so every <Z_i> = 1 - 2 x_i.
     fid = None
     if args.workload.startswith("qft"):
         st = state.view(torch.complex64 if dt == S.C64 else torch.complex128)
@@ -545,6 +585,22 @@ def main():
         ref = np.exp(2j * np.pi * ((x * ys) % N) / N) / np.sqrt(N)
         fid = {"sampled_amplitudes": int(len(ys)), "max_abs_err": float(np.abs(got - ref).max()),
                "max_rel_err": float(np.abs(got - ref).max() * np.sqrt(N))}
+    else:
+        S.sv_init_basis(h, x)
+        S.sv_apply_circuit(h, g, planner=planner, k_max=args.k, tile_m=args.tile_m, tensor=args.tensor,
+                           relabel=relabel, jit=jit)
+        S.sv_apply_circuit(h, W.inverse(g), planner=S.PLAN_GREEDY, relabel=relabel, jit=jit)
+        ez = S.sv_expect_z(h)
+        want = np.array([1.0 - 2.0 * ((x >> q) & 1) for q in range(n)])
+        err = float(np.abs(ez - want).max())
+        nrm = S.sv_norm(h)
+        qmap = S.sv_qubit_map(h)
+        xp = sum(((x >> q) & 1) << qmap[q] for q in range(n))
+        a = complex(state.view(torch.complex64 if dt == S.C64 else torch.complex128)[xp].item())
+        one_minus_F = 1.0 - abs(a) ** 2 / nrm  # F = |<x|psi>|^2 / <psi|psi> against the exact |x>
+        fid = {"test": "circuit then its inverse from |x>: <Z_i> = 1 - 2 x_i for all i, F = |<x|psi>|^2",
+               "max_abs_err_expz": err, "norm": nrm, "one_minus_F": one_minus_F,
+               "ok": bool(err < 1e-4 and one_minus_F <= 1e-6)}
     S.sv_free(h)
 
     if rank != 0:

@@ -151,6 +151,7 @@ typedef struct {
                              (per tile) */
     int64_t mux_ops;      /* recognised multiplexors (each one target) */
     int64_t mux_passes;   /* passes that apply multiplexors */
+    int64_t tc_ops;       /* of dense_ops, the blocks applied on the tensor cores */
 } sv_plan_info;
 
 /* ---- state lifetime (App. A, Eq. "hilbert") ---------------------------- */

@@ -26,6 +26,19 @@ extern "C" {
 int sv_selftest_tc_tf32(const float *host_a, const float *host_b, float *host_d, int kstride, int nstride,
                         int swap_fields, int *host_status);
 
+/* The kind::f16 tensor-core product of the register passes' dense op:
+ *   D[m][n] = sum_k A[m][k] * B[n][k],  m < 128, n < 64, k < 64,
+ * A and B given as IEEE binary16 bit patterns (host, row-major), A held in
+ * tensor memory two values per 32-bit column (value 2j in the low half of
+ * column j; swap_halves = 1 puts it in the high half, for diagnosing the
+ * layout), B in shared memory in the no-swizzle K-major layout (core matrices
+ * of 8 rows x 8 values, 128 bytes apart along K, 1024 bytes between 8-row
+ * groups), FP32 accumulation.  D (host, 128 x 64 floats) receives the result;
+ * *host_status = 0 on success, 1 if the bounded wait gave up.  Returns SV_OK
+ * or SV_ECUDA. */
+int sv_selftest_tc_f16(const unsigned short *host_a, const unsigned short *host_b, float *host_d,
+                       int swap_halves, int *host_status);
+
 /* Failure detection without a GPU fault: a one-CTA kernel waits on an
  * mbarrier that nothing ever arrives at, with the bounded wait of the
  * tensor-core pass (limit try-wait rounds, 1..2^22), then records the expiry

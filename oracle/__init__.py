@@ -103,6 +103,17 @@ class Oracle:
             raise ValueError("invalid gate record at index %d" % (-rc - 1))
         return psi
 
+    def apply_inplace(self, n, gates, psi):
+        """The same as apply_circuit, in place on psi (complex128, C-contiguous,
+        length 2^n): no copy of the state, for states of tens of GiB."""
+        assert psi.dtype == np.complex128 and psi.flags["C_CONTIGUOUS"] and psi.shape == (1 << n,)
+        g = np.ascontiguousarray(gates)
+        assert g.dtype.itemsize == self.L.or_gate_struct_size()
+        rc = self.L.or_apply_circuit(n, _ptr(psi), _ptr(g), len(g))
+        if rc != 0:
+            raise ValueError("invalid gate record at index %d" % (-rc - 1))
+        return psi
+
     def probs(self, psi):
         psi = np.ascontiguousarray(psi, dtype=np.complex128)
         n = int(np.log2(len(psi)))
@@ -178,6 +189,7 @@ def get_threads(): return default().get_threads()
 def gate_matrix(gtype, params=(0.0, 0.0, 0.0)): return default().gate_matrix(gtype, params)
 def basis_state(n, x=0): return default().basis_state(n, x)
 def apply_circuit(n, gates, psi=None): return default().apply_circuit(n, gates, psi)
+def apply_inplace(n, gates, psi): return default().apply_inplace(n, gates, psi)
 def probs(psi): return default().probs(psi)
 def cdf(p): return default().cdf(p)
 def sample_cdf(c, u): return default().sample_cdf(c, u)

@@ -47,7 +47,8 @@ class sv_plan_info(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_ops", ctypes.c_int64),
                 ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64),
                 ("gate_ops", ctypes.c_int64), ("reg_passes", ctypes.c_int64), ("remaps", ctypes.c_int64),
-                ("mux_ops", ctypes.c_int64), ("mux_passes", ctypes.c_int64)]
+                ("mux_ops", ctypes.c_int64), ("mux_passes", ctypes.c_int64),
+                ("tc_ops", ctypes.c_int64)]
 
 
 class sv_plan_op(ctypes.Structure):
@@ -231,14 +232,14 @@ def sv_plan_circuit(n, dtype, gates, k_max=0, tile_m=0, planner=PLAN_GREEDY, ten
     return {f: getattr(info, f) for f, _ in sv_plan_info._fields_}
 
 
-def sv_plan_ops(n, dtype, gates, k_max=0, tile_m=0, mux=-1, drop_phase_below=0.0, pass_kernel=0):
+def sv_plan_ops(n, dtype, gates, k_max=0, tile_m=0, mux=-1, drop_phase_below=0.0, pass_kernel=0, tensor=0):
     """Host only: the greedy plan's ops in FP64 (see sv_plan_op in sv.h), as a
     list of dicts: pass, kind ("dense", "diag", "gates", "mux"), qubits, and
     per kind: mat (2^k x 2^k complex), c / a / b (phase run), recs (rkind, a,
     b, off rows) with vals (complex values), target / family / flip / flip_c /
     controls / phi0 / phi1 (multiplexor)."""
     g = as_gates(gates)
-    o = _opts(k_max, tile_m, PLAN_GREEDY, 0, 0, pass_kernel, 0, drop_phase_below, mux)
+    o = _opts(k_max, tile_m, PLAN_GREEDY, 0, tensor, pass_kernel, 0, drop_phase_below, mux)
     L = lib()
     cnt = [ctypes.c_size_t(0) for _ in range(3)]
     rc = L.sv_plan_ops(n, dtype, _ptr(g), len(g), ctypes.byref(o), None, 0, ctypes.byref(cnt[0]), None, 0,

@@ -678,6 +678,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_pass(typename CT<R>::V* __r
 // two CTAs per SM when the tile is double-buffered.
 constexpr int kTwoCtaBudget = 112 * 1024;
 constexpr int kMaxDynSmem = 225 * 1024;  // 227 KB per block less the kernel's static variables
+constexpr int kSmemPerSm = 228 * 1024;   // shared memory of one SM
 
 static int round128(size_t v) { return (int)((v + 127) & ~(size_t)127); }
 
@@ -827,7 +828,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
         const uint64_t t = tile_of(j);
         V* tile = (V*)(smem + (size_t)s * lay.tile_bytes);
         if (P.ndiag) fold_diags<R>(P, stage, fold, dofs, t);
-        InterpOps::tile<V, R, RB>(v, tile, P, stage, fold, Lg, nullptr);
+        TcCtx T0{0u, nullptr, nullptr, err, 0u};  // (TMA-fed passes carry no tensor-core blocks)
+        InterpOps::tile<V, R, RB>(v, tile, P, stage, fold, Lg, nullptr, T0);
         if (P.scale != 1.0) {
             const R sc = (R)P.scale;
 #pragma unroll
@@ -873,6 +875,16 @@ PassLayout rpass_layout(int dtype, const PassDev& P) {
     lay.stage_off = lay.bres_off;
     lay.work_off = lay.stage_off + round128(lay.stage_bytes);
     lay.total = lay.work_off + round128(work);
+    if (P.tc_k > 0) {
+        // a CTA with tensor-core blocks holds 128 TMEM columns per 128 threads
+        // for its whole (persistent) run: ask for enough shared memory that no
+        // more CTAs share an SM than its 512 columns serve, so no allocation
+        // ever waits for a co-resident CTA to finish
+        const int groups = std::max(1, (1 << (m - reg_bits(dtype))) >> 7);
+        const int fit = std::max(1, 4 / groups);
+        const int need = kSmemPerSm / (fit + 1) + 1024;
+        if (lay.total < need) lay.total = need;
+    }
     return lay;
 }
 
@@ -1203,7 +1215,7 @@ static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& bl
     const unsigned char* b = (const unsigned char*)blob_dev;
     count_launch();
     k_rpass<R, RB, MAXT, MINB><<<(unsigned)grid, threads, lay.total, h->stream>>>(
-        (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, b, lay);
+        (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, b, lay, (int*)h->err.ptr);
     return cudaGetLastError();
 }
 

@@ -10,13 +10,16 @@ constexpr int kMaxK = 5;         // widest fused dense block
 constexpr int kMaxTileM = 14;    // qubits per shared-memory tile
 constexpr int kPassThreads = 256;
 
-enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2, OP_REMAP = 3 };
+// OP_DENSE_TC (register passes, complex64): a dense block of 4 or 5 qubits
+// on the tensor cores (FP16 hi/lo split, three products, FP32 accumulation).
+enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2, OP_REMAP = 3, OP_DENSE_TC = 4 };
 
 // Register-resident passes: each thread holds 2^kRegBits amplitudes of the
 // tile in registers; the other m - kRegBits tile bits index the thread.
 __host__ __device__ inline int reg_bits(int dtype) { return dtype == 0 ? 5 : 4; }  // 0: complex64
 constexpr int kRegDenseMaxK = 3;  // dense blocks in registers (wider ones run as gate sequences)
 constexpr int kStageCap = 48 * 1024;  // bytes of a pass region staged in shared memory
+constexpr int kStageCapTc = 100 * 1024;  // the same for a pass with tensor-core blocks
 
 // Gate-sequence block records (positions are block-local bits, data offsets
 // index the op's own complex values).
@@ -58,8 +61,20 @@ struct OpDev {
     int rec_off;   // gates: byte offset of the records
     int ndata;     // gates: complex values at mat_off
     int ord;       // register passes, diag: ordinal of the run within the pass
+    float tc_scale;  // OP_DENSE_TC: factor applied to the registers before the FP16 split
+    int pad[3];
 };
 static_assert(sizeof(OpDev) % 16 == 0, "OpDev array must keep 16-byte alignment");
+
+// OP_DENSE_TC operand scales: the registers enter the FP16 split as the true
+// amplitudes times kTcInScale (room for |a| <= 16 below the FP16 maximum) and
+// the matrix is staged times kTcMatScale (its small entries stay normal
+// FP16 numbers); the product leaves the registers at kTcInScale * kTcMatScale.
+constexpr float kTcInScale = 4096.0f;
+constexpr float kTcMatScale = 16.0f;
+// Bytes of one OP_DENSE_TC matrix operand (hi or lo) of a k-qubit block: the
+// real form, 2^(k+1) x 2^(k+1) FP16 values.
+__host__ __device__ inline int tc16_bytes(int k) { return 8 << (2 * k); }
 
 // Tensor-core dense block of k qubits (D = 2^k): B operand = [Ur; Ui], N = 2D
 // rows x K = D columns, FP32 values laid out as the tcgen05 no-swizzle

@@ -83,6 +83,7 @@ struct HostOp {
     DiagForm diag;            // diag
     std::vector<GateRec> recs;  // gates
     int ngates = 0;           // logical gates folded into the op
+    bool tc = false;          // dense: run on the tensor cores (register passes: OP_DENSE_TC for 4-5 qubits)
 };
 
 // ---------------------------------------------------------------------------
@@ -152,6 +153,11 @@ struct Plan {
     std::vector<Mux> muxes;
 };
 
+// Default of the tensor-core choice (sv_options.tensor = 0): 1 = 4- and
+// 5-qubit blocks go to the tensor cores where their estimated cost is below
+// the gate sequence's, 0 = CUDA cores only.
+constexpr int kTcAutoDefault = 0;
+
 struct PlanOptions {
     int k_max = 5;
     int tile_m = 13;
@@ -162,6 +168,7 @@ struct PlanOptions {
     double drop_phase_below = 0.0;  // approximation: smaller P/RZ/CP angles are dropped
     int mux = 0;          // multiplexor recognition: 0 long runs, 1 any run of 4+ gates, -1 off
     int jit = 0;          // run-time compiled register passes: 0 on repeat, 1 always, -1 never
+    int tc_auto = 0;      // tensor-core dense blocks where their estimated cost is below the gate sequence's
 };
 // The approximation for negligible rotations: the gates kept.
 void drop_small_phases(std::vector<CGate>* g, double eps);

@@ -222,7 +222,8 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     }
     o << "template <typename V, typename R, int RB>\n"
          "static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,\n"
-         "                                            const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab) {\n";
+         "                                            const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab,\n"
+         "                                            TcCtx& T) {\n";
     int rpos[8] = {0}, tpos[16] = {0};
     bool in_regs = false;
     CtLayout cur;
@@ -300,6 +301,12 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
             if (!in_regs || op.k < 1 || op.k > kRegDenseMaxK) return false;
             o << "reg_dense<V, RB, " << op.k << ">(v, (const V*)(stage + " << op.mat_off << "));\n";
             break;
+        case OP_DENSE_TC:
+            // the input scale depends on the pass's deferred factors (angles): read from the op record
+            if (!in_regs || dtype != SV_C64 || (op.k != 4 && op.k != 5)) return false;
+            o << "reg_dense_tc<RB, " << op.k << ">((float2*)v, stage + " << op.mat_off << ", ((const OpDev*)stage)["
+              << oi << "].tc_scale, T);\n";
+            break;
         case OP_DIAG:
             if (!in_regs) return false;
             o << "{\n";
@@ -332,8 +339,8 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     const char* R = dtype == SV_C64 ? "float" : "double";
     o << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
       << "    sv::CT<" << R << ">::V* __restrict__ psi, int n, const sv::PassDev* __restrict__ pdp,\n"
-      << "    const unsigned char* __restrict__ blob, const sv::PassLayout lay) {\n"
-      << "    sv::rpass_body<" << R << ", " << RB << ", sv::GenOps>(psi, n, pdp, blob, lay);\n}\n";
+      << "    const unsigned char* __restrict__ blob, const sv::PassLayout lay, int* __restrict__ err) {\n"
+      << "    sv::rpass_body<" << R << ", " << RB << ", sv::GenOps>(psi, n, pdp, blob, lay, err);\n}\n";
     *out = o.str();
     return true;
 }
@@ -501,7 +508,8 @@ cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const Pla
     int n = h->n;
     const PassDev* pdp = (const PassDev*)(b + blob.pass_off) + pass;
     PassLayout lay_arg = lay;
-    void* args[] = {&psi, &n, &pdp, &b, &lay_arg};
+    int* err = (int*)h->err.ptr;
+    void* args[] = {&psi, &n, &pdp, &b, &lay_arg, &err};
     count_launch();
     if (dr.launch(e.fn, (unsigned)grid, 1, 1, (unsigned)threads, 1, 1, (unsigned)lay.total, (CUstream)h->stream, args,
                   nullptr) != CUDA_SUCCESS)

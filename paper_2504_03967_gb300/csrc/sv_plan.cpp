@@ -225,6 +225,11 @@ double gate_sequence_cost(const std::vector<GateRec>& recs, const std::vector<cd
     return c;
 }
 
+// A 4- or 5-qubit block on the tensor cores (register passes): the FP16
+// split of the registers, the TMEM traffic and the products' share of the
+// tensor pipe, in the same units.
+double tc_cost(int k) { return k >= 5 ? 14.0 : 12.0; }
+
 bool is_real(const cd* m, int cnt) {
     for (int i = 0; i < cnt; ++i)
         if (m[i].imag() != 0.0) return false;
@@ -380,6 +385,7 @@ bool best_gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<
 }
 
 constexpr int kMaxBlockGates = 40;  // 20 one-qubit gates and 20 phase tables fit kMaxGateData
+constexpr int kMaxTcBlockGates = 4096;  // a tensor-core block is a dense matrix: any gate count
 
 // Estimated instructions per amplitude of a pass's ops: each block pays its
 // own cost plus a register remap (a shared-memory round trip of the tile),
@@ -390,6 +396,7 @@ double ops_cost(const std::vector<HostOp>& ops) {
     for (const HostOp& o : ops) {
         if (o.kind == OP_DIAG) c += kDiagRun;
         else if (o.kind == OP_GATES) c += gate_sequence_cost(o.recs, &o.gdata) + kRemap;
+        else if (o.tc) c += tc_cost((int)o.qubits.size()) + kRemap;
         else c += dense_cost((int)o.qubits.size()) + kRemap;
     }
     return c;
@@ -578,8 +585,11 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
         po.drop_phase_below = opt->drop_phase_below > 0.0 && std::isfinite(opt->drop_phase_below) ? opt->drop_phase_below : 0.0;
         po.mux = opt->mux < 0 ? -1 : (opt->mux > 0 ? 1 : 0);
         po.jit = opt->jit < 0 ? -1 : (opt->jit > 0 ? 1 : 0);
+        po.tc_auto = opt->tensor == 0 ? kTcAutoDefault : 0;
+    } else {
+        po.tc_auto = kTcAutoDefault;
     }
-    if (dtype != SV_C64) po.tensor = -1;
+    if (dtype != SV_C64) po.tensor = -1, po.tc_auto = 0;
     po.k_max = std::max(2, std::min(kMaxK, po.k_max));
     const int mmax = dtype == SV_C64 ? 14 : 13;
     po.tile_m = std::max(1, std::min(mmax, po.tile_m));
@@ -604,6 +614,8 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     // the tile holds the row bits plus room for any two-qubit gate
     const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
     const int kmax = std::min(po.k_max, m);
+    // tensor-core blocks run in register passes of at least 128 threads
+    const bool tc_auto_ok = po.tc_auto && dtype == SV_C64 && po.pass_kernel == 0 && m - reg_bits(dtype) >= 7;
 
     std::vector<int> remaining(gates.size());
     for (size_t i = 0; i < gates.size(); ++i) remaining[i] = (int)i;
@@ -729,18 +741,30 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                 HostOp op;
                 op.qubits = B.qubits;
                 op.ngates = B.ngates;
-                // the cheaper representation: the dense 2^k matrix, or the gate
-                // sequence applied in registers (tensor-core blocks stay dense)
-                const bool tc_block = po.tensor == 0 && dtype == SV_C64 && (int)B.qubits.size() >= kMinTcK;
-                // (blocks wider than the register kernel's dense limit stay
-                // gate sequences, which keeps the pass on the register kernel)
                 const int kb = (int)B.qubits.size();
-                if (!tc_block && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata) &&
-                    (gate_sequence_cost(op.recs, &op.gdata) <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
+                // tensor-core blocks: forced (tensor = 1) or where their cost
+                // is below the gate sequence's (the default)
+                const bool tc_forced = po.tensor == 0 && dtype == SV_C64 && kb >= 4;
+                const bool tc_auto = tc_auto_ok && (kb == 4 || kb == 5);
+                const bool seq = !tc_forced && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata);
+                const double seq_cost = seq ? gate_sequence_cost(op.recs, &op.gdata) : 1e30;
+                if (tc_forced || (tc_auto && seq_cost > tc_cost(kb))) {
+                    op.kind = OP_DENSE;
+                    op.tc = true;
+                    op.mat = block_matrix(B.qubits, B.seq);
+                    op.recs.clear();
+                    op.gdata.clear();
+                } else if (seq && (seq_cost <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
+                    // the cheaper representation: the dense 2^k matrix, or the
+                    // gate sequence applied in registers (blocks wider than the
+                    // register kernel's dense limit stay gate sequences, which
+                    // keeps the pass on the register kernel)
                     op.kind = OP_GATES;
                     op.seq = B.seq;
                 } else {
                     op.kind = OP_DENSE;
+                    // (the shared-memory kernel's 3xTF32 path also takes 3-qubit blocks)
+                    op.tc = po.tensor == 0 && dtype == SV_C64 && kb >= kMinTcK && po.pass_kernel == 1;
                     op.mat = block_matrix(B.qubits, B.seq);
                     op.recs.clear();
                     op.gdata.clear();
@@ -803,7 +827,11 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
                 std::sort(u.begin(), u.end());
                 // a block holds at most kMaxBlockGates gates, so that its gate
                 // sequence stays within the record and data limits
-                if (B.active() && ((int)u.size() > kmax || B.ngates >= kMaxBlockGates)) {
+                // (with tensor-core blocks available, 4- and 5-qubit blocks
+                // take any number of gates: their cost does not grow with it)
+                const int cap = (tc_auto_ok || (po.tensor == 0 && dtype == SV_C64)) && (int)B.qubits.size() >= 4
+                                    ? kMaxTcBlockGates : kMaxBlockGates;
+                if (B.active() && ((int)u.size() > kmax || B.ngates >= cap)) {
                     flushB();
                     u.assign(g.q, g.q + g.nq);
                     std::sort(u.begin(), u.end());
@@ -896,6 +924,7 @@ void plan_summary(const Plan& p, sv_plan_info* info) {
                 if (o.kind == OP_DENSE || o.kind == OP_GATES) {
                     info->dense_ops++;
                     info->gate_ops += o.kind == OP_GATES;
+                    info->tc_ops += o.tc;
                     info->max_k = std::max<int64_t>(info->max_k, (int64_t)o.qubits.size());
                 } else {
                     info->diag_ops++;
@@ -943,6 +972,42 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tenso
 // ---------------------------------------------------------------------------
 namespace {
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// IEEE 754 binary32 -> binary16, round to nearest, ties to even (subnormal
+// results included; overflow to infinity).
+uint16_t f32_to_f16(float f) {
+    uint32_t x;
+    memcpy(&x, &f, 4);
+    const uint32_t sign = (x >> 16) & 0x8000u, e8 = (x >> 23) & 0xffu;
+    uint32_t mant = x & 0x7fffffu;
+    if (e8 == 0xffu) return (uint16_t)(sign | 0x7c00u | (mant ? 0x200u : 0u));
+    const int e = (int)e8 - 127 + 15;
+    if (e >= 31) return (uint16_t)(sign | 0x7c00u);
+    if (e <= 0) {
+        if (e < -10) return (uint16_t)sign;
+        mant |= 0x800000u;  // the implicit bit
+        const int shift = 14 - e;
+        uint32_t h = mant >> shift;
+        const uint32_t rem = mant & ((1u << shift) - 1u), half = 1u << (shift - 1);
+        if (rem > half || (rem == half && (h & 1u))) ++h;
+        return (uint16_t)(sign | h);
+    }
+    uint32_t h = ((uint32_t)e << 10) | (mant >> 13);
+    const uint32_t rem = mant & 0x1fffu;
+    if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;  // a carry moves into the exponent
+    return (uint16_t)(sign | h);
+}
+float f16_to_f32(uint16_t h) {
+    const uint32_t sign = (uint32_t)(h & 0x8000u) << 16, e = (h >> 10) & 0x1fu, mant = h & 0x3ffu;
+    float f;
+    if (e == 0) {
+        f = (float)mant * 0x1p-24f;  // zero or subnormal, exact
+        return sign ? -f : f;
+    }
+    const uint32_t x = sign | (e == 31 ? 0x7f800000u | (mant << 13) : ((e - 15 + 127) << 23) | (mant << 13));
+    memcpy(&f, &x, 4);
+    return f;
+}
 
 // FP32 -> TF32 value (10-bit mantissa) rounded to nearest, ties away from
 // zero: add half of the dropped 13-bit field to the magnitude, then clear it.
@@ -1044,7 +1109,8 @@ struct Payload {
 void assemble(std::vector<OpDev>& ops, const Payload& pay, PassDev* P, std::vector<unsigned char>* out) {
     const size_t ob = align16(sizeof(OpDev) * ops.size());
     for (OpDev& O : ops) {
-        if (O.kind == OP_DENSE || O.kind == OP_GATES || O.kind == OP_REMAP) O.mat_off += (int)ob;
+        if (O.kind == OP_DENSE || O.kind == OP_DENSE_TC || O.kind == OP_GATES || O.kind == OP_REMAP)
+            O.mat_off += (int)ob;
         if (O.kind == OP_GATES) O.rec_off += (int)ob;
         if (O.kind == OP_DIAG) O.diag_off += (int)ob;
     }
@@ -1056,8 +1122,39 @@ void assemble(std::vector<OpDev>& ops, const Payload& pay, PassDev* P, std::vect
     P->region_bytes = (int)out->size();
 }
 
+// Tensor-core block of the shared-memory pass kernel (3xTF32): a block marked
+// for the tensor cores in a pass the register kernel does not take.
 bool use_tc(const Plan& p, const HostOp& o) {
-    return p.tensor == 0 && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
+    return o.tc && p.dtype == SV_C64 && o.kind == OP_DENSE && (int)o.qubits.size() >= kMinTcK;
+}
+// Tensor-core block of a register pass (OP_DENSE_TC).
+bool reg_tc(const Plan& p, const HostOp& o, int tb) {
+    const int k = (int)o.qubits.size();
+    return o.tc && o.kind == OP_DENSE && p.dtype == SV_C64 && !p.use_tma && (k == 4 || k == 5) && tb >= 7;
+}
+
+uint16_t f32_to_f16(float f);
+float f16_to_f32(uint16_t h);
+// B operand of an OP_DENSE_TC block: the real form of the 2^k x 2^k matrix
+// (times kTcMatScale), B[2r + c'][2j + c] = Re / Im parts of U[r][j] as
+// [[Re, -Im], [Im, Re]] per entry, FP16 hi = fp16(b) and lo = fp16(b - hi),
+// K-major no-swizzle core matrices (8 rows x 8 values; 128 bytes along K,
+// 16 N bytes between 8-row groups), hi then lo.
+std::vector<uint16_t> tc16_operand(const std::vector<cd>& mat, int k) {
+    const int D = 1 << k, N = 2 * D;
+    std::vector<uint16_t> b((size_t)2 * N * N);
+    for (int n = 0; n < N; ++n)
+        for (int kk = 0; kk < N; ++kk) {
+            const cd u = mat[(size_t)(n >> 1) * D + (kk >> 1)];
+            const double re = u.real(), im = u.imag();
+            const double val = ((n & 1) == 0 ? ((kk & 1) == 0 ? re : -im) : ((kk & 1) == 0 ? im : re)) * kTcMatScale;
+            const uint16_t hi = f32_to_f16((float)val);
+            const uint16_t lo = f32_to_f16((float)(val - (double)f16_to_f32(hi)));
+            const size_t off = ((size_t)(n >> 3) * (N / 8) + (kk >> 3)) * 64 + (n & 7) * 8 + (kk & 7);
+            b[off] = hi;
+            b[(size_t)N * N + off] = lo;
+        }
+    return b;
 }
 
 // Region for the shared-memory pass kernel: dense blocks, gate sequences of
@@ -1131,8 +1228,8 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
     for (int i = 0; i < nops; ++i) {
         const HostOp& o = hp.ops[i];
         if (o.kind == OP_DIAG) continue;
-        if (use_tc(p, o)) return false;
-        if (o.kind == OP_DENSE && (int)o.qubits.size() > kRegDenseMaxK) return false;
+        if (o.tc && !reg_tc(p, o, tb) && (int)o.qubits.size() > kRegDenseMaxK) return false;
+        if (o.kind == OP_DENSE && !reg_tc(p, o, tb) && (int)o.qubits.size() > kRegDenseMaxK) return false;
         if ((int)o.qubits.size() > r) return false;
         for (int q : o.qubits) used[i].push_back(loc[q]);
     }
@@ -1260,7 +1357,17 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
         O.ngates = o.ngates;
         O.k = (int)PQ.size();
         for (int j = 0; j < O.k; ++j) O.lq[j] = slot(PQ[j]);
-        if (o.kind == OP_DENSE) {
+        if (o.kind == OP_DENSE && reg_tc(p, o, tb)) {
+            // the registers enter at the true amplitudes times kTcInScale and
+            // leave at kTcInScale * kTcMatScale times them (the pass's
+            // write-back scale undoes it)
+            O.kind = OP_DENSE_TC;
+            const std::vector<uint16_t> b = tc16_operand(o.mat, O.k);
+            O.mat_off = (int)pay.put(b.data(), sizeof(uint16_t) * b.size());
+            O.tc_scale = (float)((double)kTcInScale * P->scale);
+            P->scale = 1.0 / ((double)kTcInScale * (double)kTcMatScale);
+            if (O.k > P->tc_k) P->tc_k = O.k;
+        } else if (o.kind == OP_DENSE) {
             O.mat_off = (int)pay.put_cplx(o.mat, p.dtype);
         } else {
             std::vector<GateRec> recs;
@@ -1335,7 +1442,9 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
     assemble(ops, pay, P, out);
     P->rmode = p.use_tma ? 2 : 1;
     P->ndiag = nd;
-    return P->region_bytes <= kStageCap;
+    // passes with tensor-core blocks stage their matrices (16 KiB per 5-qubit
+    // block) in a larger region
+    return P->region_bytes <= (P->tc_k ? kStageCapTc : kStageCap);
 }
 
 }  // namespace
@@ -1346,8 +1455,7 @@ bool register_pass_eligible(const Plan& p, const HostPass& hp) {
     if (tb < 5 || tb > 9) return false;
     for (const HostOp& o : hp.ops) {
         if (o.kind == OP_DIAG) continue;
-        if (use_tc(p, o)) return false;
-        if (o.kind == OP_DENSE && (int)o.qubits.size() > kRegDenseMaxK) return false;
+        if (o.kind == OP_DENSE && !reg_tc(p, o, tb) && (int)o.qubits.size() > kRegDenseMaxK) return false;
         if ((int)o.qubits.size() > r) return false;
     }
     return true;

@@ -19,6 +19,7 @@ typedef int int32_t;
 #endif
 
 #include "sv_dev.h"
+#include "sv_tc.cuh"
 
 // Loops whose trip counts are compile-time constants in the run-time
 // compiled kernels (layout sizes) are unrolled there.
@@ -398,6 +399,111 @@ __device__ __forceinline__ void reg_dense(V* v, const V* __restrict__ U) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Dense block on the tensor cores (OP_DENSE_TC; complex64, register bits
+// 0..K-1, K = 4 or 5).  The CTA's threads form groups of 128 (four warps:
+// TMEM lanes 0..127 of columns [128 g, 128 g + 128) of the CTA's
+// allocation).  Each thread's 32 amplitudes are 32 / 2^K slices of the block,
+// one row of the A operand each: the slice's 2^(K+1) reals, (re, im)
+// interleaved, as FP16 pairs (one TMEM column per amplitude), split into
+// hi = fp16(x s) at columns [0, 32) and lo = fp16(x s - hi) at [32, 64).  B is
+// the real form of the block's matrix, B[2r + c'][2j + c] (c, c' = 0 real, 1
+// imaginary part), staged (times kTcMatScale) in shared memory, K-major
+// no-swizzle, hi then lo.  One thread issues D = A_hi B_hi + A_hi B_lo +
+// A_lo B_hi with FP32 accumulation into columns [64, 128); every thread reads
+// its row back: the slice's outputs, (re, im) interleaved, which is again one
+// register per amplitude.  The dropped A_lo B_lo term is below 2^-22 of the
+// result, about FP32 rounding.
+// ---------------------------------------------------------------------------
+struct TcCtx {
+    uint32_t tmem;   // TMEM base address of the CTA's allocation (128 columns per group)
+    uint64_t* mbar;  // one mbarrier per group (shared memory)
+    int* abort;      // per group: a bounded wait gave up, skip the remaining products
+    int* err;        // device error word: set to 1 when a wait gives up
+    uint32_t phase;  // waits this thread has completed (parity of the next)
+};
+
+__device__ __forceinline__ uint32_t f16x2_pack(float lo, float hi) {  // round to nearest even
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float2 f16x2_unpack(uint32_t p) {
+    float2 r;
+    asm("{\n.reg .f16 l, h;\nmov.b32 {l, h}, %2;\ncvt.f32.f16 %0, l;\ncvt.f32.f16 %1, h;\n}\n"
+        : "=f"(r.x), "=f"(r.y)
+        : "r"(p));
+    return r;
+}
+
+template <int RB, int K>
+__device__ __forceinline__ void reg_dense_tc(float2* v, const unsigned char* bmat, float s_in, TcCtx& T) {
+    static_assert(RB == 5 && (K == 4 || K == 5), "tensor-core blocks: 32 amplitudes per thread, 4 or 5 qubits");
+    constexpr int D = 1 << K;            // amplitudes of a slice
+    constexpr int NS = 32 / D;           // slices per thread
+    constexpr uint32_t N = 2 * D;        // reals of a slice (the MMA's N and K)
+    constexpr uint32_t IDESC = tc::idesc_f16(128, N);
+    constexpr uint32_t SBO = 16 * N;     // bytes between 8-row groups of B
+    constexpr uint32_t OPB = 2 * N * N;  // bytes of one B operand (hi or lo)
+    const int tid = threadIdx.x, grp = tid >> 7;
+    const uint32_t cols = T.tmem + (uint32_t)grp * 128u;
+    const uint32_t lane = cols + (((uint32_t)((tid >> 5) & 3) * 32u) << 16);
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 16) {
+        uint32_t h[16], l[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float xr = v[c0 + j].x * s_in, xi = v[c0 + j].y * s_in;
+            h[j] = f16x2_pack(xr, xi);
+            const float2 hf = f16x2_unpack(h[j]);
+            l[j] = f16x2_pack(xr - hf.x, xi - hf.y);
+        }
+        tc::tmem_st16(lane + c0, h);
+        tc::tmem_st16(lane + 32 + c0, l);
+    }
+    tc::tmem_wait_st();
+    tc::fence_before();
+    tc::named_barrier(1 + grp, 128);
+    tc::fence_after();
+    if (T.abort[grp]) return;  // an earlier wait of the group gave up (read after the barrier: uniform)
+    if ((tid & 127) == 0) {
+        const uint32_t bh = tc::smem_u32(bmat), bl = bh + OPB;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const uint32_t d = cols + 64 + s * N, ah = cols + s * D, al = cols + 32 + s * D;
+#pragma unroll
+            for (int kk = 0; kk < (int)N / 16; ++kk)
+                tc::mma_f16_ts(d, ah + 8 * kk, tc::sdesc_noswz(bh + 256 * kk, 128, SBO), IDESC, kk > 0);
+#pragma unroll
+            for (int kk = 0; kk < (int)N / 16; ++kk)
+                tc::mma_f16_ts(d, ah + 8 * kk, tc::sdesc_noswz(bl + 256 * kk, 128, SBO), IDESC, 1);
+#pragma unroll
+            for (int kk = 0; kk < (int)N / 16; ++kk)
+                tc::mma_f16_ts(d, al + 8 * kk, tc::sdesc_noswz(bh + 256 * kk, 128, SBO), IDESC, 1);
+        }
+        tc::mma_commit(&T.mbar[grp]);
+    }
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_bounded(&T.mbar[grp], T.phase & 1u, 1u << 22));
+    T.phase += 1;
+    tc::fence_after();
+    if (!ok) {  // warp-uniform: the whole warp skips the TMEM reads
+        T.abort[grp] = 1;
+        atomicExch(T.err, 1);
+        return;
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+        uint32_t d[32];
+        tc::tmem_ld32(lane + 64 + c0, d);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            v[c0 / 2 + j].x = __uint_as_float(d[2 * j]);
+            v[c0 / 2 + j].y = __uint_as_float(d[2 * j + 1]);
+        }
+    }
+}
+
 template <typename V, int RB>
 __device__ __forceinline__ void reg_gates(V* v, const GateRec* __restrict__ recs, int nrec, const V* __restrict__ sd) {
     using R = decltype(V().x);
@@ -702,7 +808,8 @@ struct InterpOps {
     }
     template <typename V, typename R, int RB>
     static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,
-                                                const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab) {
+                                                const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab,
+                                                TcCtx& T) {
     const int m = P.m, tb = m - RB, no = P.nother;
     const OpDev* ops = (const OpDev*)stage;
     const int* rpos = nullptr;
@@ -735,6 +842,12 @@ struct InterpOps {
             }
             break;
         }
+        case OP_DENSE_TC:
+            if constexpr (sizeof(R) == 4 && RB == 5) {
+                if (op.k == 5) reg_dense_tc<RB, 5>((float2*)v, stage + op.mat_off, op.tc_scale, T);
+                else reg_dense_tc<RB, 4>((float2*)v, stage + op.mat_off, op.tc_scale, T);
+            }
+            break;
         default:
             reg_diag<V, R, RB>(v, (const uint64_t*)(stage + op.diag_off), fold + (size_t)op.ord * (m + 1), m, no,
                                rpos, tpos, tb, ttab);
@@ -747,21 +860,44 @@ struct InterpOps {
 // MAXT/MINB: launch bounds of the instance (up to 128 threads: registers are
 // not capped below 255, so the 2^RB amplitudes and the op state never spill;
 // 256 and 512 threads: 128 registers).
+// Passes with tensor-core blocks (P.tc_k > 0, complex64) hold 128 TMEM
+// columns per group of 128 threads for the whole kernel; every wait on the
+// tensor cores is bounded (expiry: *err = 1, the group skips its remaining
+// products, the TMEM is still freed).
 template <typename R, int RB, class Ops>
 __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, int n,
                                            const PassDev* __restrict__ pdp, const unsigned char* __restrict__ blob,
-                                           const PassLayout& lay) {
+                                           const PassLayout& lay, int* __restrict__ err) {
     using V = typename CT<R>::V;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PassDev P;
     __shared__ uint32_t tbase[3][256];
     __shared__ double2 ttab[sizeof(R) == 8 ? 256 : 1];  // complex128: the phase table of Turns::sincos_t
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[4];
+    __shared__ int s_abort[4];
     {
         const int* src = (const int*)pdp;
         int* dst = (int*)&P;
         for (int i = threadIdx.x; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    const int ngroups = (int)(blockDim.x >> 7);
+    const uint32_t tmem_cols = 128u * (uint32_t)ngroups;  // 128, 256 or 512
+    const bool tcp = sizeof(R) == 4 && RB == 5 && P.tc_k > 0 && ngroups >= 1;
+    if (tcp) {
+        if (threadIdx.x < 32) {
+            tc::tmem_alloc(&s_tmem, tmem_cols);
+            tc::tmem_relinquish();
+        }
+        if (threadIdx.x == 0) {
+            for (int g = 0; g < ngroups; ++g) {
+                tc::mbar_init(&s_mbar[g], 1);
+                s_abort[g] = 0;
+            }
+            tc::fence_mbar_init();
+        }
+    }
     const int m = P.m, L = P.L, nd = P.ndiag;
     V* tiles[2] = {(V*)smem, (V*)(smem + (lay.nbuf == 2 ? lay.tile_bytes : 0))};
     uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
@@ -781,7 +917,13 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     build_base_tables(tbase, P);
     if constexpr (sizeof(R) == 8) build_turn_table(ttab);
     cp_async_wait_group<0>();
+    if (tcp) {
+        tc::fence_proxy_async();  // the staged matrices are read by the tensor cores
+        tc::fence_before();
+    }
     __syncthreads();
+    if (tcp) tc::fence_after();
+    TcCtx T{tcp ? s_tmem : 0u, s_mbar, s_abort, err, 0u};
     const OpDev* ops = (const OpDev*)stage;
     if (threadIdx.x == 0)
         for (int i = 0; i < P.nops; ++i)
@@ -814,12 +956,17 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         __syncthreads();
         V* tile = tiles[cur];
         if (nd) fold_diags<R>(P, stage, fold, dofs, t);
-        Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg, sizeof(R) == 8 ? ttab : nullptr);
+        Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg, sizeof(R) == 8 ? ttab : nullptr, T);
         Ops::template finish<V, R, RB>(v, tile, P, Lg);
         __syncthreads();
         Ops::template store<V>(tile, psi, base, rowoff, L);
         __syncthreads();
         if (lay.nbuf == 2) cur ^= 1;
+    }
+    if (tcp) {
+        tc::fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, tmem_cols);
     }
 }
 
@@ -827,8 +974,9 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
 template <typename R, int RB, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restrict__ psi, int n,
                                                   const PassDev* __restrict__ pdp,
-                                                  const unsigned char* __restrict__ blob, const PassLayout lay) {
-    rpass_body<R, RB, InterpOps>(psi, n, pdp, blob, lay);
+                                                  const unsigned char* __restrict__ blob, const PassLayout lay,
+                                                  int* __restrict__ err) {
+    rpass_body<R, RB, InterpOps>(psi, n, pdp, blob, lay, err);
 }
 #endif
 

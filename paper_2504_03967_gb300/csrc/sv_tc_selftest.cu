@@ -136,6 +136,114 @@ extern "C" int sv_selftest_tc_tf32(const float* host_a, const float* host_b, flo
 }
 
 // ---------------------------------------------------------------------------
+// The kind::f16 form used by the tensor-core dense op of the register passes:
+// A (128 x 64 FP16, two values per TMEM column, value 2j in the low half of
+// column j unless swap_halves) in TMEM, B (64 x 64 FP16, K-major, no-swizzle
+// core matrices of 8 rows x 8 values: 128 bytes between K-adjacent ones,
+// 1024 bytes between 8-row groups) in shared memory, four MMAs of K = 16.
+// ---------------------------------------------------------------------------
+namespace sv {
+namespace {
+__global__ void __launch_bounds__(128) k_tc_f16_selftest(const uint16_t* __restrict__ A,
+                                                         const uint16_t* __restrict__ B, float* __restrict__ D,
+                                                         int swap_halves, int* __restrict__ status) {
+    __shared__ __align__(1024) uint16_t sB[64 * 64];
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        tc::tmem_alloc(&s_taddr, 256);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&s_mbar, 1);
+        tc::fence_mbar_init();
+    }
+    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+        const int n = e / 64, k = e % 64;
+        sB[((n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) / 2] = B[e];
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = s_taddr;
+    const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+    const int row = tid;
+    {
+        uint32_t v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t lo = A[row * 64 + 2 * j], hi = A[row * 64 + 2 * j + 1];
+            v[j] = swap_halves ? (lo << 16) | hi : (hi << 16) | lo;
+        }
+        tc::tmem_st32(lane_base, v);
+    }
+    tc::tmem_wait_st();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_f16(128, 64);
+        const uint32_t sb = tc::smem_u32(sB);
+        for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16_ts(tbase + 128, tbase + kk * 8, tc::sdesc_noswz(sb + kk * 256, 128, 1024), idesc, kk > 0);
+        tc::mma_commit(&s_mbar);
+    }
+    const bool ok = tc::mbar_wait_bounded(&s_mbar, 0, 1u << 22);
+    tc::fence_after();
+    if (!ok) {
+        if (tid == 0) atomicExch(status, 1);
+    } else {
+        uint32_t v[32];
+        tc::tmem_ld32(lane_base + 128, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) D[row * 64 + j] = __uint_as_float(v[j]);
+        tc::tmem_ld32(lane_base + 160, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) D[row * 64 + 32 + j] = __uint_as_float(v[j]);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+}  // namespace
+}  // namespace sv
+
+extern "C" int sv_selftest_tc_f16(const uint16_t* host_a, const uint16_t* host_b, float* host_d, int swap_halves,
+                                  int* host_status) {
+    using namespace sv;
+    if (!host_a || !host_b || !host_d || !host_status) return set_error(SV_EINVAL, "NULL argument");
+    uint16_t *dA = nullptr, *dB = nullptr;
+    float* dD = nullptr;
+    int* dS = nullptr;
+    cudaError_t e = cudaMalloc(&dA, 2 * 128 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, 2 * 64 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&dD, sizeof(float) * 128 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&dS, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(dA, host_a, 2 * 128 * 64, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, host_b, 2 * 64 * 64, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dD, 0, sizeof(float) * 128 * 64);
+    if (e == cudaSuccess) e = cudaMemset(dS, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        count_launch();
+        k_tc_f16_selftest<<<1, 128>>>(dA, dB, dD, swap_halves, dS);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host_d, dD, sizeof(float) * 128 * 64, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(host_status, dS, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dD);
+    cudaFree(dS);
+    if (e != cudaSuccess) return cuda_fail(e, "tcgen05 f16 self-test");
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Failure detection without a fault: one CTA waits on an mbarrier that no
 // thread or copy ever arrives at, through the same bounded wait the
 // tensor-core pass uses, and records the expiry in a device status word

@@ -4,9 +4,11 @@ first one building its tiles from the deferred basis state), k_max 5, tile
 13.  QFT|x> = 2^(-n/2) sum_y e^{2 pi i x y / N}|y> is known amplitude by
 amplitude, so 2^16 sampled amplitudes are compared with it (complex64 bound
 1e-5 relative), and the norm and <Z_i> = 0 (uniform magnitudes) hold for the
-whole state.  Its probabilities are all 1/N, so the oracle's shot rule
-min{x : C_x > u C_{N-1}} over the logical index gives x = floor(u N): the
-relabelled state's shots must equal it except within 1e-9 of a boundary."""
+whole state.  Shots of the relabelled state follow the oracle's rule
+min{x : C_x > u C_{N-1}} over the logical index, applied to the state's own
+probabilities (complex64 probabilities differ from 1/N in the 7th digit, and
+the drift of their prefix sums exceeds the 1e-9 band), except for draws
+within 1e-9 of a boundary."""
 import numpy as np
 import pytest
 
@@ -49,11 +51,11 @@ def test_qft28_bench_configuration():
         # shots of the relabelled state under the logical-order rule
         shots = 4096
         samp, _ = S.sv_measure(h, shots, 1234)
-        t = oracle.uniforms(1234, shots) * N
-        x0 = np.floor(t).astype(np.int64)
-        near = np.minimum(t - x0, x0 + 1 - t) / N < U.BAND
-        bad = np.nonzero((samp.astype(np.int64) != x0) & ~near)[0]
-        assert len(bad) == 0, "shots %s: got %s want %s" % (bad[:5], samp[bad[:5]], x0[bad[:5]])
-        assert (~near).sum() > shots // 4
+        u = oracle.uniforms(1234, shots)
+        c_ref = oracle.cdf(S.sv_probs(h))  # logical order, FP64 prefix sums
+        compared, _ = U.compare_samples(samp.astype(np.int64), u, c_ref, U.BAND)
+        assert compared > shots // 4
+        # and the draws sit where the closed form puts them, up to the drift
+        assert np.abs(samp.astype(np.int64) - np.floor(u * N)).max() < 1e-6 * N
     finally:
         S.sv_free(h)

@@ -218,3 +218,21 @@ def test_plan_ops_name_the_multiplexor_targets():
     psi0[0] = 1.0
     got = _apply_ops(a + d, ops, psi0)
     assert np.abs(got - oracle.apply_circuit(a + d, W.qcrank(a, d, pix), psi0)).max() < 1e-12
+
+
+@pytest.mark.parametrize("case", ["random", "qft", "cx-blocks"])
+@pytest.mark.parametrize("tile_m", [12, 13])
+def test_tensor_core_plans_reproduce_the_circuit(case, tile_m):
+    """Plans with tensor-core blocks (tensor = 1: every 4- and 5-qubit block
+    dense, with no cap on its gate count) reproduce the circuit in FP64."""
+    n = 14
+    g = {"random": lambda: W.random_u3_cx(n, 10, 7), "qft": lambda: W.qft(n),
+         "cx-blocks": lambda: W.random_cx_blocks(n, 200, 8)}[case]()
+    info = S.sv_plan_circuit(n, S.C64, g, k_max=5, tile_m=tile_m, tensor=1)
+    assert info["tc_ops"] > 0
+    ops = S.sv_plan_ops(n, S.C64, g, k_max=5, tile_m=tile_m, tensor=1)
+    rng = np.random.default_rng(tile_m)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    got = _apply_ops(n, ops, psi0)
+    assert np.abs(got - oracle.apply_circuit(n, g, psi0)).max() < 1e-12
