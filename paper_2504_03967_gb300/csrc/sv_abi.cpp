@@ -586,9 +586,11 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     }
     const std::vector<CGate>& cgm = *gl;
     cudaEvent_t judge0 = nullptr, judge1 = nullptr;
+    std::shared_ptr<const Plan> learned;
     if (po.planner == SV_PLAN_MLP)
-        po = mlp_plan_options(h, gates, count, cgm, &muxes, po, salt, &judge0, &judge1);
-    plan_greedy(h->n, h->dtype, cgm, po, &plan, &muxes);
+        po = mlp_plan_options(h, gates, count, cgm, &muxes, po, salt, &judge0, &judge1, &learned);
+    if (learned) plan = *learned;
+    else plan_greedy(h->n, h->dtype, cgm, po, &plan, &muxes);
     h->last_opts.k_max = po.k_max;
     h->last_opts.tile_m = po.tile_m;
     h->last_opts.planner = opt ? opt->planner : SV_PLAN_GREEDY;

@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
         const uint64_t t = tile_of(j);
         V* tile = (V*)(smem + (size_t)s * lay.tile_bytes);
         if (P.ndiag) fold_diags<R>(P, stage, fold, dofs, t);
-        TcCtx T0{0u, nullptr, nullptr, err, 0u};  // (TMA-fed passes carry no tensor-core blocks)
+        TcCtx T0{0u, nullptr, nullptr, err, 0u, nullptr, nullptr};  // (TMA-fed passes carry no tensor-core blocks)
         InterpOps::tile<V, R, RB>(v, tile, P, stage, fold, Lg, nullptr, T0);
         if (P.scale != 1.0) {
             const R sc = (R)P.scale;

@@ -13,6 +13,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <unordered_map>
@@ -37,7 +39,8 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
 }
 
 struct Choice {
-    std::vector<PlanOptions> trial;  // model's top candidates, then the greedy plan
+    std::shared_ptr<const Plan> learned;  // the model's per-pass plan (trial 0), if it found one
+    std::vector<PlanOptions> trial;  // the learned plan's slot, the model's top whole-circuit candidates, greedy
     std::vector<double> measured;    // ms per trial (-1: not yet)
     double predicted = 0.0;
     int calls = 0;
@@ -104,10 +107,161 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const std::
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// The learned plan.  Passes are chosen one at a time: from the gates not yet
+// planned, every candidate option set (tile width m, fusion width k,
+// tensor-core blocks on or off) proposes its next greedy pass, and the model
+// predicts each proposal's time from its features.  A beam of kBeam partial
+// plans is kept, ranked by predicted time so far plus the gates still to plan
+// times the best predicted time per gate among the round's proposals, and
+// extended until every gate is planned; the complete plan with the smallest
+// predicted total wins.  Each pass may so take its own tile and fusion width
+// and its own choice of tensor-core blocks ("gate fusion = 5" of App. D.2 as
+// the upper bound of k).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kBeam = 3;
+
+std::vector<PlanOptions> pass_candidates(int n, int dtype, const PlanOptions& base) {
+    std::vector<PlanOptions> c;
+    const int ms_c64[] = {12, 13, 14}, ms_c128[] = {11, 12, 13};
+    const int ks_c64[] = {4, 5}, ks_c128[] = {3, 4};
+    for (int mi = 0; mi < 3; ++mi)
+        for (int ki = 0; ki < 2; ++ki)
+            for (int tc = 0; tc <= (dtype == SV_C64 ? 1 : 0); ++tc) {
+                PlanOptions po = base;
+                po.tile_m = std::min(n, dtype == SV_C64 ? ms_c64[mi] : ms_c128[mi]);
+                po.k_max = dtype == SV_C64 ? ks_c64[ki] : ks_c128[ki];
+                po.tc_auto = tc;
+                po.tensor = -1;
+                po.pass_kernel = 0;
+                bool dup = false;
+                for (const PlanOptions& q : c)
+                    dup |= q.tile_m == po.tile_m && q.k_max == po.k_max && q.tc_auto == po.tc_auto;
+                if (!dup) c.push_back(po);
+            }
+    return c;
+}
+
+struct BeamNode {
+    int parent;  // index into the node list, -1 for the root
+    HostPass hp;
+    std::vector<int> rem;  // gates still to plan
+    double t;              // predicted ms of the passes from the root to here
+};
+}  // namespace
+
+bool plan_learned(int n, int dtype, const std::vector<CGate>& gates, const std::vector<Mux>* muxes,
+                  const PlanOptions& base, Plan* out, double* predicted_ms) {
+    static const std::vector<Mux> no_muxes;
+    const std::vector<Mux>& mx = muxes ? *muxes : no_muxes;
+    const std::vector<PlanOptions> cands = pass_candidates(n, dtype, base);
+    Plan stub;  // register-kernel eligibility of a proposal
+    stub.n = n;
+    stub.dtype = dtype;
+    std::vector<BeamNode> nodes(1);
+    nodes[0].parent = -1;
+    nodes[0].t = 0.0;
+    nodes[0].rem.resize(gates.size());
+    for (size_t i = 0; i < gates.size(); ++i) nodes[0].rem[i] = (int)i;
+    std::vector<int> beam = {0};
+    int best = -1;
+    while (!beam.empty()) {
+        struct Prop {
+            int from;
+            HostPass hp;
+            std::vector<int> rem;
+            double ms = 0.0, score = 0.0;
+        };
+        std::vector<Prop> props;
+        std::vector<float> feat;
+        for (int b : beam) {
+            for (size_t c = 0; c < cands.size(); ++c) {
+                Prop pr;
+                pr.from = b;
+                greedy_pass(n, dtype, gates, mx, cands[c], nodes[b].rem, &pr.hp, &pr.rem, false);
+                const bool mux_pass = !pr.hp.mux.empty();
+                const std::vector<float> f = pass_features(n, dtype, pr.hp, cands[c].tc_auto != 0,
+                                                           mux_pass ? false : register_pass_eligible(stub, pr.hp));
+                feat.insert(feat.end(), f.begin(), f.end());
+                props.push_back(std::move(pr));
+                if (mux_pass) break;  // every candidate proposes the same multiplexor pass
+            }
+        }
+        std::vector<double> ms;
+        if (!cost_model_predict(feat, (int)props.size(), &ms)) return false;
+        double rate = 1e30;  // best predicted ms per gate this round
+        for (size_t i = 0; i < props.size(); ++i) {
+            props[i].ms = std::max(ms[i], 1e-6);
+            const size_t done = nodes[props[i].from].rem.size() - props[i].rem.size();
+            if (done) rate = std::min(rate, props[i].ms / (double)done);
+        }
+        if (rate >= 1e30) return false;  // no proposal makes progress
+        for (Prop& pr : props) pr.score = nodes[pr.from].t + pr.ms + rate * (double)pr.rem.size();
+        std::vector<int> order(props.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return props[a].score < props[b].score; });
+        std::vector<int> next;
+        for (int i : order) {
+            Prop& pr = props[i];
+            if (nodes[pr.from].rem.size() == pr.rem.size()) continue;  // no progress
+            bool dup = false;  // the same remaining gates reached at the same predicted time
+            for (int q : next)
+                dup |= nodes[q].rem == pr.rem && std::fabs(nodes[q].t - (nodes[pr.from].t + pr.ms)) <= 1e-9 * nodes[q].t;
+            if (dup) continue;
+            BeamNode nd;
+            nd.parent = pr.from;
+            nd.t = nodes[pr.from].t + pr.ms;
+            nd.hp = std::move(pr.hp);
+            nd.rem = std::move(pr.rem);
+            nodes.push_back(std::move(nd));
+            const int id = (int)nodes.size() - 1;
+            if (nodes[id].rem.empty()) {
+                if (best < 0 || nodes[id].t < nodes[best].t) best = id;
+            } else if ((int)next.size() < kBeam) {
+                next.push_back(id);
+            }
+            if ((int)next.size() >= kBeam) break;
+        }
+        // a complete plan already beats every open one's lower bound: stop
+        if (best >= 0) {
+            bool open_better = false;
+            for (int q : next) open_better |= nodes[q].t < nodes[best].t;
+            if (!open_better) break;
+        }
+        for (int q : beam) {  // free what no longer matters (parents keep their pass)
+            nodes[q].rem.clear();
+            nodes[q].rem.shrink_to_fit();
+        }
+        beam.swap(next);
+    }
+    if (best < 0) return false;
+    std::vector<int> chain;
+    for (int q = best; q > 0; q = nodes[q].parent) chain.push_back(q);
+    out->muxes = mx;
+    out->n = n;
+    out->dtype = dtype;
+    out->plain = false;
+    out->gates = (int64_t)gates.size();
+    out->tensor = -1;
+    out->no_register_passes = false;
+    out->use_tma = false;
+    out->jit = base.jit;
+    out->passes.clear();
+    for (auto it = chain.rbegin(); it != chain.rend(); ++it) {
+        HostPass hp = std::move(nodes[*it].hp);
+        form_dense_matrices(&hp);
+        out->passes.push_back(std::move(hp));
+    }
+    if (predicted_ms) *predicted_ms = nodes[best].t;
+    return true;
+}
+
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
                              const std::vector<Mux>* muxes, const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0,
-                             cudaEvent_t* ev1) {
+                             cudaEvent_t* ev1, std::shared_ptr<const Plan>* learned) {
     *ev0 = *ev1 = nullptr;
+    learned->reset();
     uint64_t key = fnv1a(g, count * sizeof(sv_gate), 1469598103934665603ull);
     const int meta[3] = {h->n, h->dtype, base.tensor};
     key = fnv1a(meta, sizeof(meta), key);
@@ -119,10 +273,16 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
         std::vector<double> rms;
         if (!rank_options(h->n, h->dtype, cg, muxes, base, &ranked, &rms)) return base;  // no model: greedy
         Choice c;
-        for (int i = 0; i < kExplore && i < (int)ranked.size(); ++i) c.trial.push_back(ranked[i]);
+        auto lp = std::make_shared<Plan>();
+        double lms = 0.0;
+        if (plan_learned(h->n, h->dtype, cg, muxes, base, lp.get(), &lms)) {
+            c.learned = lp;
+            c.trial.push_back(base);  // (placeholder options of the learned plan's slot)
+        }
+        for (int i = 0; i < kExplore - (c.learned ? 1 : 0) && i < (int)ranked.size(); ++i) c.trial.push_back(ranked[i]);
         c.trial.push_back(base);
         c.measured.assign(c.trial.size(), -1.0);
-        c.predicted = rms[0];
+        c.predicted = c.learned ? lms : rms[0];
         ++g_planned;
         if (g_cache.size() > 4096) g_cache.clear();
         it = g_cache.emplace(key, c).first;
@@ -149,8 +309,10 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
         c.pending = call;
         *ev0 = c.e0;
         *ev1 = c.e1;
+        if (call == 0 && c.learned) *learned = c.learned;
         return c.trial[call];
     }
+    if (c.best == 0 && c.learned) *learned = c.learned;
     return c.trial[c.best];
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <complex>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -179,6 +180,17 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt);
 void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out,
                  const std::vector<Mux>* muxes = nullptr);
 void plan_plain(int n, int dtype, const std::vector<CGate>& gates, Plan* out);
+// One greedy pass from the front of `remaining` (see plan_greedy); the gates
+// it leaves for later in *deferred_out.  form_matrices = false keeps dense
+// blocks as their gate list (HostOp::seq) until form_dense_matrices.
+void greedy_pass(int n, int dtype, const std::vector<CGate>& gates, const std::vector<Mux>& muxes,
+                 const PlanOptions& po, const std::vector<int>& remaining, HostPass* pass_out,
+                 std::vector<int>* deferred_out, bool form_matrices);
+void form_dense_matrices(HostPass* hp);
+// The cost model's own plan (SV_PLAN_MLP): passes chosen one at a time by
+// predicted time (see sv_costplan.cpp).  False without a model.
+bool plan_learned(int n, int dtype, const std::vector<CGate>& gates, const std::vector<Mux>* muxes,
+                  const PlanOptions& base, Plan* out, double* predicted_ms);
 void plan_summary(const Plan& p, sv_plan_info* info);
 
 // Cost-model features of one pass (fixed length kFeatures): qubit count,
@@ -193,9 +205,11 @@ bool register_pass_eligible(const Plan& p, const HostPass& hp);
 
 // Options for an apply under SV_PLAN_MLP; ev0/ev1 receive events to record
 // around the passes when the judge times this call (else nullptr).
+// *learned (may stay null): the model's per-pass plan to run instead of
+// plan_greedy with the returned options.
 PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const std::vector<CGate>& cg,
                              const std::vector<Mux>* muxes, const PlanOptions& base, uint64_t salt, cudaEvent_t* ev0,
-                             cudaEvent_t* ev1);
+                             cudaEvent_t* ev1, std::shared_ptr<const Plan>* learned);
 
 // Multiplexor pass (PassDev::rmode == kRmodeMux): the region is MuxDev
 // followed by one angle table per target: 2^nc entries of the state's real

@@ -252,6 +252,8 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
             for (int t = 0; t < tb; ++t) tpos[t] = tp[t];
             cur = ct_layout(dtype, RB, tb, rpos, tpos);
             emit_rw("reg_read_ct", cur, ++nl);
+            // passes with tensor-core blocks restore each tile's norm as loaded
+            if (!in_regs && P.tc_k) o << "warp_norm_to<RB>((const float2*)v, T.nin);\n";
             in_regs = true;
             break;
         }
@@ -325,17 +327,28 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     // Hadamard factors alone is a constant of the structure; one with rotation
     // factors depends on the angles and is read from the pass record.
     o << "template <typename V, typename R, int RB>\n"
-         "static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>&) {\n";
-    if (scaled) {
+         "static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>&,\n"
+         "                                              TcCtx& T) {\n";
+    if (P.tc_k) {
+        // the tile's norm as loaded (every op is unitary on the tile): the
+        // scale is sqrt(in / out) with the sign of the deferred factors, which
+        // it also undoes
+        o << "warp_norm_to<RB>((const float2*)v, T.nout);\n__syncthreads();\n"
+          << "scale_regs<V, RB>(v, copysignf(tile_norm_fix(T.nin, T.nout), (float)P.scale));\n";
+        emit_rw("reg_write_ct", cur, nl);
+        o << "}\n};\n}  // namespace sv\n";
+    } else if (scaled) {
         o << "scale_regs<V, RB>(v, (R)P.scale);\n";
     } else if (P.scale != 1.0) {
         char buf[64];
         snprintf(buf, sizeof(buf), "%.17g", P.scale);
         o << "scale_regs<V, RB>(v, (R)" << buf << ");\n";
     }
-    o << "__syncthreads();\n";
-    emit_rw("reg_write_ct", cur, nl);
-    o << "}\n};\n}  // namespace sv\n";
+    if (!P.tc_k) {
+        o << "__syncthreads();\n";
+        emit_rw("reg_write_ct", cur, nl);
+        o << "}\n};\n}  // namespace sv\n";
+    }
     const char* R = dtype == SV_C64 ? "float" : "double";
     o << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
       << "    sv::CT<" << R << ">::V* __restrict__ psi, int n, const sv::PassDev* __restrict__ pdp,\n"

@@ -597,6 +597,267 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
     return po;
 }
 
+// One pass of the greedy planner from the front of `remaining` (gate
+// indices in circuit order): the pass, and in *deferred_out the gates left
+// for later passes, in order.  form_matrices = false leaves the dense blocks'
+// matrices unformed (their gates in HostOp::seq; see form_dense_matrices).
+void greedy_pass(int n, int dtype, const std::vector<CGate>& gates, const std::vector<Mux>& muxes,
+                 const PlanOptions& po, const std::vector<int>& remaining, HostPass* pass_out,
+                 std::vector<int>* deferred_out, bool form_matrices) {
+    const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
+    // the tile holds the row bits plus room for any two-qubit gate
+    const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
+    const int kmax = std::min(po.k_max, m);
+    // tensor-core blocks run in register passes of at least 128 threads
+    const bool tc_auto_ok = po.tc_auto && dtype == SV_C64 && po.pass_kernel == 0 && m - reg_bits(dtype) >= 7;
+    std::vector<char> inT(n), blocked(n);
+    std::vector<int> executed, deferred;
+    int nblocked = 0;
+    auto block = [&](const CGate& g) {
+        for (int i = 0; i < g.nq; ++i)
+            if (!blocked[g.q[i]]) blocked[g.q[i]] = 1, ++nblocked;
+        if (g.kind == GK_MUX)
+            for (int c : muxes[g.mux].controls)
+                if (!blocked[c]) blocked[c] = 1, ++nblocked;
+    };
+    // A multiplexor at the front opens a multiplexor pass: it takes every
+    // later multiplexor that the gates skipped over commute with (no
+    // shared qubit), up to kMuxMaxTargets targets whose controls stay off
+    // the targets and number at most kMuxMaxControls together.
+    if (gates[remaining[0]].kind == GK_MUX) {
+        HostPass pass;
+        std::fill(blocked.begin(), blocked.end(), 0);
+        nblocked = 0;
+        uint64_t tmask = 0, cunion = 0;
+        deferred.clear();
+        for (size_t r = 0; r < remaining.size(); ++r) {
+            const int gi = remaining[r];
+            const CGate& g = gates[gi];
+            bool take = false;
+            uint64_t tm = 0, cm = 0;
+            if (g.kind == GK_MUX && (int)pass.mux.size() < kMuxMaxTargets && nblocked < n) {
+                const Mux& M = muxes[g.mux];
+                tm = 1ull << M.target;
+                bool fr = !blocked[M.target];
+                for (int c : M.controls) {
+                    cm |= 1ull << c;
+                    fr &= !blocked[c];
+                }
+                const uint64_t nu = cunion | cm;
+                take = fr && !(tmask & (tm | cm)) && !(nu & (tmask | tm)) &&
+                       __builtin_popcountll(nu) <= kMuxMaxControls;
+                if (take) cunion = nu;
+            }
+            if (take) {
+                const Mux& M = muxes[g.mux];
+                pass.mux.push_back(g.mux);
+                tmask |= tm;
+                pass.ngates += M.ngates;
+                for (int t = 0; t < 14; ++t) pass.type_count[t] += M.type_count[t];
+            } else {
+                deferred.push_back(gi);
+                block(g);
+            }
+        }
+        *pass_out = std::move(pass);
+        deferred_out->swap(deferred);
+        return;
+    }
+    // Scan 1: grow the tile set T from the front of the remaining list.
+    std::fill(inT.begin(), inT.end(), 0);
+    std::fill(blocked.begin(), blocked.end(), 0);
+    int cnt = 0;
+    nblocked = 0;
+    for (int q = 0; q < L; ++q) inT[q] = 1, ++cnt;
+    for (int gi : remaining) {
+        const CGate& g = gates[gi];
+        bool tb = false;
+        for (int i = 0; i < g.nq; ++i) tb |= blocked[g.q[i]] != 0;
+        if (tb || g.kind == GK_MUX) { block(g); }
+        else if (g.kind == GK_DENSE) {
+            int need = 0;
+            for (int i = 0; i < g.nq; ++i) need += !inT[g.q[i]];
+            if (cnt + need <= m) {
+                for (int i = 0; i < g.nq; ++i)
+                    if (!inT[g.q[i]]) inT[g.q[i]] = 1, ++cnt;
+            } else {
+                block(g);
+            }
+        }
+        if (nblocked == n) break;
+    }
+    // Fill the tile up to m qubits (lowest unused qubits first): a wider
+    // tile costs nothing extra and keeps all passes the same shape.
+    for (int q = 0; q < n && cnt < m; ++q)
+        if (!inT[q]) inT[q] = 1, ++cnt;
+
+    // Scan 2: partition with the final T.
+    std::fill(blocked.begin(), blocked.end(), 0);
+    nblocked = 0;
+    executed.clear();
+    deferred.clear();
+    for (int gi : remaining) {
+        const CGate& g = gates[gi];
+        if (nblocked == n) { deferred.push_back(gi); continue; }
+        bool tb = false, fits = true;
+        for (int i = 0; i < g.nq; ++i) {
+            tb |= blocked[g.q[i]] != 0;
+            fits &= inT[g.q[i]] != 0;
+        }
+        if (!tb && g.kind != GK_MUX && (g.kind == GK_DIAG || fits)) executed.push_back(gi);
+        else { deferred.push_back(gi); block(g); }
+    }
+
+    HostPass pass;
+    for (int q = 0; q < n; ++q)
+        if (inT[q]) pass.tile.push_back(q);
+    pass.L = L;
+    pass.ngates = (int)executed.size();
+    for (int gi : executed) pass.type_count[gates[gi].type < 14 ? gates[gi].type : 13]++;
+
+    // Fuse the executed gates into dense blocks and diagonal runs, in the
+    // given order (any order that keeps each qubit's gates in sequence).
+    // Blocks keep their qubits and gates; a dense op's matrix is formed
+    // when it is emitted, a gate sequence's only if a kernel needs it.
+    auto fuse = [&](const std::vector<int>& order, std::vector<HostOp>* ops_out) {
+        Block B;
+        DiagForm D;
+        D.init(n);
+        bool dpend = false;
+        auto flushB = [&]() {
+            if (!B.active()) return;
+            HostOp op;
+            op.qubits = B.qubits;
+            op.ngates = B.ngates;
+            const int kb = (int)B.qubits.size();
+            // tensor-core blocks: forced (tensor = 1) or where their cost
+            // is below the gate sequence's (the default)
+            const bool tc_forced = po.tensor == 0 && dtype == SV_C64 && kb >= 4;
+            const bool tc_auto = tc_auto_ok && (kb == 4 || kb == 5);
+            const bool seq = !tc_forced && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata);
+            const double seq_cost = seq ? gate_sequence_cost(op.recs, &op.gdata) : 1e30;
+            if (tc_forced || (tc_auto && seq_cost > tc_cost(kb))) {
+                op.kind = OP_DENSE;
+                op.tc = true;
+                if (form_matrices) op.mat = block_matrix(B.qubits, B.seq);
+                else op.seq = B.seq;
+                op.recs.clear();
+                op.gdata.clear();
+            } else if (seq && (seq_cost <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
+                // the cheaper representation: the dense 2^k matrix, or the
+                // gate sequence applied in registers (blocks wider than the
+                // register kernel's dense limit stay gate sequences, which
+                // keeps the pass on the register kernel)
+                op.kind = OP_GATES;
+                op.seq = B.seq;
+            } else {
+                op.kind = OP_DENSE;
+                // (the shared-memory kernel's 3xTF32 path also takes 3-qubit blocks)
+                op.tc = po.tensor == 0 && dtype == SV_C64 && kb >= kMinTcK && po.pass_kernel == 1;
+                if (form_matrices) op.mat = block_matrix(B.qubits, B.seq);
+                else op.seq = B.seq;
+                op.recs.clear();
+                op.gdata.clear();
+            }
+            ops_out->push_back(std::move(op));
+            B = Block();
+        };
+        int dgates = 0;
+        auto flushD = [&]() {
+            if (!dpend) return;
+            HostOp op;
+            op.kind = OP_DIAG;
+            op.diag = D;
+            op.ngates = dgates;
+            ops_out->push_back(std::move(op));
+            D.init(n);
+            dpend = false;
+            dgates = 0;
+        };
+        for (int gi : order) {
+            const CGate& g = gates[gi];
+            if (g.kind == GK_DIAG) {
+                bool inB = B.active();
+                for (int i = 0; inB && i < g.nq; ++i) inB = B.pos(g.q[i]) >= 0;
+                // A diagonal gate on tile qubits may also widen the current
+                // block (diagonals commute with the pending run D, so moving
+                // it into the block is exact).
+                bool widen = false;
+                std::vector<int> u;
+                if (!inB && B.active()) {
+                    bool inT_all = true;
+                    u = B.qubits;
+                    for (int i = 0; i < g.nq; ++i) {
+                        inT_all &= inT[g.q[i]] != 0;
+                        if (B.pos(g.q[i]) < 0) u.push_back(g.q[i]);
+                    }
+                    widen = inT_all && (int)u.size() <= kmax;
+                }
+                if (widen) {
+                    std::sort(u.begin(), u.end());
+                    B.qubits = u;
+                }
+                if (inB || widen) {
+                    B.seq.push_back(g);
+                    B.ngates++;
+                } else {
+                    diag_add(&D, n, g);
+                    dpend = true;
+                    dgates++;
+                }
+                continue;
+            }
+            if (dpend && touches(D, g)) {
+                flushB();
+                flushD();
+            }
+            std::vector<int> u = B.qubits;
+            for (int i = 0; i < g.nq; ++i)
+                if (std::find(u.begin(), u.end(), g.q[i]) == u.end()) u.push_back(g.q[i]);
+            std::sort(u.begin(), u.end());
+            // a block holds at most kMaxBlockGates gates, so that its gate
+            // sequence stays within the record and data limits
+            // (with tensor-core blocks available, 4- and 5-qubit blocks
+            // take any number of gates: their cost does not grow with it)
+            const int cap = (tc_auto_ok || (po.tensor == 0 && dtype == SV_C64)) && (int)B.qubits.size() >= 4
+                                ? kMaxTcBlockGates : kMaxBlockGates;
+            if (B.active() && ((int)u.size() > kmax || B.ngates >= cap)) {
+                flushB();
+                u.assign(g.q, g.q + g.nq);
+                std::sort(u.begin(), u.end());
+            }
+            B.qubits = u;
+            B.seq.push_back(g);
+            B.ngates++;
+        }
+        flushB();
+        flushD();
+    };
+    fuse(executed, &pass.ops);
+    // A reordering that groups gates by qubit set (each qubit's gates
+    // kept in sequence, so the circuit is the same) often needs fewer
+    // blocks; keep it when its estimated cost is lower.
+    if (kmax >= 2) {
+        const std::vector<int> reord = cluster_order(gates, executed, kmax);
+        if (reord != executed) {
+            std::vector<HostOp> alt;
+            fuse(reord, &alt);
+            if (ops_cost(alt) < ops_cost(pass.ops)) pass.ops.swap(alt);
+        }
+    }
+    *pass_out = std::move(pass);
+    deferred_out->swap(deferred);
+}
+
+// Dense blocks planned without their matrix get it now.
+void form_dense_matrices(HostPass* hp) {
+    for (HostOp& op : hp->ops)
+        if (op.kind == OP_DENSE && op.mat.empty() && !op.seq.empty()) {
+            op.mat = block_matrix(op.qubits, op.seq);
+            op.seq.clear();
+        }
+}
+
 void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOptions& po, Plan* out,
                  const std::vector<Mux>* muxes) {
     out->muxes.clear();
@@ -610,253 +871,14 @@ void plan_greedy(int n, int dtype, const std::vector<CGate>& gates, const PlanOp
     out->no_register_passes = po.pass_kernel == 1;
     out->use_tma = po.pass_kernel == 2;
     out->jit = po.jit;
-    const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
-    // the tile holds the row bits plus room for any two-qubit gate
-    const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
-    const int kmax = std::min(po.k_max, m);
-    // tensor-core blocks run in register passes of at least 128 threads
-    const bool tc_auto_ok = po.tc_auto && dtype == SV_C64 && po.pass_kernel == 0 && m - reg_bits(dtype) >= 7;
-
-    std::vector<int> remaining(gates.size());
+    std::vector<int> remaining(gates.size()), deferred;
     for (size_t i = 0; i < gates.size(); ++i) remaining[i] = (int)i;
-    std::vector<char> inT(n), blocked(n);
-    std::vector<int> executed, deferred;
-
-    int nblocked = 0;
-    auto block = [&](const CGate& g) {
-        for (int i = 0; i < g.nq; ++i)
-            if (!blocked[g.q[i]]) blocked[g.q[i]] = 1, ++nblocked;
-        if (g.kind == GK_MUX)
-            for (int c : out->muxes[g.mux].controls)
-                if (!blocked[c]) blocked[c] = 1, ++nblocked;
-    };
-
     while (!remaining.empty()) {
-        // A multiplexor at the front opens a multiplexor pass: it takes every
-        // later multiplexor that the gates skipped over commute with (no
-        // shared qubit), up to kMuxMaxTargets targets whose controls stay off
-        // the targets and number at most kMuxMaxControls together.
-        if (gates[remaining[0]].kind == GK_MUX) {
-            HostPass pass;
-            std::fill(blocked.begin(), blocked.end(), 0);
-            nblocked = 0;
-            uint64_t tmask = 0, cunion = 0;
-            deferred.clear();
-            for (size_t r = 0; r < remaining.size(); ++r) {
-                const int gi = remaining[r];
-                const CGate& g = gates[gi];
-                bool take = false;
-                uint64_t tm = 0, cm = 0;
-                if (g.kind == GK_MUX && (int)pass.mux.size() < kMuxMaxTargets && nblocked < n) {
-                    const Mux& M = out->muxes[g.mux];
-                    tm = 1ull << M.target;
-                    bool fr = !blocked[M.target];
-                    for (int c : M.controls) {
-                        cm |= 1ull << c;
-                        fr &= !blocked[c];
-                    }
-                    const uint64_t nu = cunion | cm;
-                    take = fr && !(tmask & (tm | cm)) && !(nu & (tmask | tm)) &&
-                           __builtin_popcountll(nu) <= kMuxMaxControls;
-                    if (take) cunion = nu;
-                }
-                if (take) {
-                    const Mux& M = out->muxes[g.mux];
-                    pass.mux.push_back(g.mux);
-                    tmask |= tm;
-                    pass.ngates += M.ngates;
-                    for (int t = 0; t < 14; ++t) pass.type_count[t] += M.type_count[t];
-                } else {
-                    deferred.push_back(gi);
-                    block(g);
-                }
-            }
-            out->passes.push_back(std::move(pass));
-            remaining.swap(deferred);
-            continue;
-        }
-        // Scan 1: grow the tile set T from the front of the remaining list.
-        std::fill(inT.begin(), inT.end(), 0);
-        std::fill(blocked.begin(), blocked.end(), 0);
-        int cnt = 0;
-        nblocked = 0;
-        for (int q = 0; q < L; ++q) inT[q] = 1, ++cnt;
-        for (int gi : remaining) {
-            const CGate& g = gates[gi];
-            bool tb = false;
-            for (int i = 0; i < g.nq; ++i) tb |= blocked[g.q[i]] != 0;
-            if (tb || g.kind == GK_MUX) { block(g); }
-            else if (g.kind == GK_DENSE) {
-                int need = 0;
-                for (int i = 0; i < g.nq; ++i) need += !inT[g.q[i]];
-                if (cnt + need <= m) {
-                    for (int i = 0; i < g.nq; ++i)
-                        if (!inT[g.q[i]]) inT[g.q[i]] = 1, ++cnt;
-                } else {
-                    block(g);
-                }
-            }
-            if (nblocked == n) break;
-        }
-        // Fill the tile up to m qubits (lowest unused qubits first): a wider
-        // tile costs nothing extra and keeps all passes the same shape.
-        for (int q = 0; q < n && cnt < m; ++q)
-            if (!inT[q]) inT[q] = 1, ++cnt;
-
-        // Scan 2: partition with the final T.
-        std::fill(blocked.begin(), blocked.end(), 0);
-        nblocked = 0;
-        executed.clear();
-        deferred.clear();
-        for (int gi : remaining) {
-            const CGate& g = gates[gi];
-            if (nblocked == n) { deferred.push_back(gi); continue; }
-            bool tb = false, fits = true;
-            for (int i = 0; i < g.nq; ++i) {
-                tb |= blocked[g.q[i]] != 0;
-                fits &= inT[g.q[i]] != 0;
-            }
-            if (!tb && g.kind != GK_MUX && (g.kind == GK_DIAG || fits)) executed.push_back(gi);
-            else { deferred.push_back(gi); block(g); }
-        }
-
         HostPass pass;
-        for (int q = 0; q < n; ++q)
-            if (inT[q]) pass.tile.push_back(q);
-        pass.L = L;
-        pass.ngates = (int)executed.size();
-        for (int gi : executed) pass.type_count[gates[gi].type < 14 ? gates[gi].type : 13]++;
-
-        // Fuse the executed gates into dense blocks and diagonal runs, in the
-        // given order (any order that keeps each qubit's gates in sequence).
-        // Blocks keep their qubits and gates; a dense op's matrix is formed
-        // when it is emitted, a gate sequence's only if a kernel needs it.
-        auto fuse = [&](const std::vector<int>& order, std::vector<HostOp>* ops_out) {
-            Block B;
-            DiagForm D;
-            D.init(n);
-            bool dpend = false;
-            auto flushB = [&]() {
-                if (!B.active()) return;
-                HostOp op;
-                op.qubits = B.qubits;
-                op.ngates = B.ngates;
-                const int kb = (int)B.qubits.size();
-                // tensor-core blocks: forced (tensor = 1) or where their cost
-                // is below the gate sequence's (the default)
-                const bool tc_forced = po.tensor == 0 && dtype == SV_C64 && kb >= 4;
-                const bool tc_auto = tc_auto_ok && (kb == 4 || kb == 5);
-                const bool seq = !tc_forced && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata);
-                const double seq_cost = seq ? gate_sequence_cost(op.recs, &op.gdata) : 1e30;
-                if (tc_forced || (tc_auto && seq_cost > tc_cost(kb))) {
-                    op.kind = OP_DENSE;
-                    op.tc = true;
-                    op.mat = block_matrix(B.qubits, B.seq);
-                    op.recs.clear();
-                    op.gdata.clear();
-                } else if (seq && (seq_cost <= dense_cost(kb) || (kb > kRegDenseMaxK && po.pass_kernel != 1))) {
-                    // the cheaper representation: the dense 2^k matrix, or the
-                    // gate sequence applied in registers (blocks wider than the
-                    // register kernel's dense limit stay gate sequences, which
-                    // keeps the pass on the register kernel)
-                    op.kind = OP_GATES;
-                    op.seq = B.seq;
-                } else {
-                    op.kind = OP_DENSE;
-                    // (the shared-memory kernel's 3xTF32 path also takes 3-qubit blocks)
-                    op.tc = po.tensor == 0 && dtype == SV_C64 && kb >= kMinTcK && po.pass_kernel == 1;
-                    op.mat = block_matrix(B.qubits, B.seq);
-                    op.recs.clear();
-                    op.gdata.clear();
-                }
-                ops_out->push_back(std::move(op));
-                B = Block();
-            };
-            int dgates = 0;
-            auto flushD = [&]() {
-                if (!dpend) return;
-                HostOp op;
-                op.kind = OP_DIAG;
-                op.diag = D;
-                op.ngates = dgates;
-                ops_out->push_back(std::move(op));
-                D.init(n);
-                dpend = false;
-                dgates = 0;
-            };
-            for (int gi : order) {
-                const CGate& g = gates[gi];
-                if (g.kind == GK_DIAG) {
-                    bool inB = B.active();
-                    for (int i = 0; inB && i < g.nq; ++i) inB = B.pos(g.q[i]) >= 0;
-                    // A diagonal gate on tile qubits may also widen the current
-                    // block (diagonals commute with the pending run D, so moving
-                    // it into the block is exact).
-                    bool widen = false;
-                    std::vector<int> u;
-                    if (!inB && B.active()) {
-                        bool inT_all = true;
-                        u = B.qubits;
-                        for (int i = 0; i < g.nq; ++i) {
-                            inT_all &= inT[g.q[i]] != 0;
-                            if (B.pos(g.q[i]) < 0) u.push_back(g.q[i]);
-                        }
-                        widen = inT_all && (int)u.size() <= kmax;
-                    }
-                    if (widen) {
-                        std::sort(u.begin(), u.end());
-                        B.qubits = u;
-                    }
-                    if (inB || widen) {
-                        B.seq.push_back(g);
-                        B.ngates++;
-                    } else {
-                        diag_add(&D, n, g);
-                        dpend = true;
-                        dgates++;
-                    }
-                    continue;
-                }
-                if (dpend && touches(D, g)) {
-                    flushB();
-                    flushD();
-                }
-                std::vector<int> u = B.qubits;
-                for (int i = 0; i < g.nq; ++i)
-                    if (std::find(u.begin(), u.end(), g.q[i]) == u.end()) u.push_back(g.q[i]);
-                std::sort(u.begin(), u.end());
-                // a block holds at most kMaxBlockGates gates, so that its gate
-                // sequence stays within the record and data limits
-                // (with tensor-core blocks available, 4- and 5-qubit blocks
-                // take any number of gates: their cost does not grow with it)
-                const int cap = (tc_auto_ok || (po.tensor == 0 && dtype == SV_C64)) && (int)B.qubits.size() >= 4
-                                    ? kMaxTcBlockGates : kMaxBlockGates;
-                if (B.active() && ((int)u.size() > kmax || B.ngates >= cap)) {
-                    flushB();
-                    u.assign(g.q, g.q + g.nq);
-                    std::sort(u.begin(), u.end());
-                }
-                B.qubits = u;
-                B.seq.push_back(g);
-                B.ngates++;
-            }
-            flushB();
-            flushD();
-        };
-        fuse(executed, &pass.ops);
-        // A reordering that groups gates by qubit set (each qubit's gates
-        // kept in sequence, so the circuit is the same) often needs fewer
-        // blocks; keep it when its estimated cost is lower.
-        if (kmax >= 2) {
-            const std::vector<int> reord = cluster_order(gates, executed, kmax);
-            if (reord != executed) {
-                std::vector<HostOp> alt;
-                fuse(reord, &alt);
-                if (ops_cost(alt) < ops_cost(pass.ops)) pass.ops.swap(alt);
-            }
-        }
+        greedy_pass(n, dtype, gates, out->muxes, po, remaining, &pass, &deferred, true);
         out->passes.push_back(std::move(pass));
         remaining.swap(deferred);
+        deferred.clear();
     }
 }
 
@@ -943,13 +965,15 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tenso
     f[2] = m / 14.0f;
     f[3] = p.L / 4.0f;
     double flops = 0.0, msize = 0.0;
-    int ndiag = 0;
+    int ndiag = 0, ntc = 0;
     for (const HostOp& o : p.ops) {
         if (o.kind == OP_DENSE || o.kind == OP_GATES) {
             const int k = (int)o.qubits.size();
             f[3 + k] += 1.0f / 8.0f;  // f[4..8]: dense blocks of width 1..5
-            flops += (o.kind == OP_GATES ? gate_sequence_cost(o.recs, &o.gdata) : dense_cost(k)) / 4.0;
+            flops += (o.kind == OP_GATES ? gate_sequence_cost(o.recs, &o.gdata)
+                                         : o.tc ? tc_cost(k) : dense_cost(k)) / 4.0;
             msize += ldexp(1.0, 2 * k);
+            ntc += o.tc;
         } else {
             ++ndiag;
         }
@@ -962,7 +986,7 @@ std::vector<float> pass_features(int n, int dtype, const HostPass& p, bool tenso
     for (int t = 0; t < 14; ++t) f[14 + t] = p.type_count[t] / 16.0f;  // f[14..27]
     f[28] = (float)(ldexp(1.0, n) * (dtype == SV_C64 ? 16.0 : 32.0) / ldexp(1.0, 36));
     f[29] = register_pass ? 1.0f : 0.0f;  // kernel: register-resident or shared-memory
-    f[30] = tensor_cores ? 1.0f : 0.0f;
+    f[30] = tensor_cores ? ntc / 4.0f : 0.0f;  // blocks on the tensor cores
     f[31] = 1.0f;
     return f;
 }

@@ -421,7 +421,42 @@ struct TcCtx {
     int* abort;      // per group: a bounded wait gave up, skip the remaining products
     int* err;        // device error word: set to 1 when a wait gives up
     uint32_t phase;  // waits this thread has completed (parity of the next)
+    float* nin;      // per warp: sum of |a|^2 of the tile as loaded (passes with tensor-core blocks)
+    float* nout;     // per warp: the same after the pass's ops
 };
+
+// Sum of |a|^2 over this thread's registers (four partial sums), then over
+// the warp; lane 0 writes it to slot[warp].  Passes with tensor-core blocks
+// use it to restore each tile's norm: every op of a pass acts on the tile
+// alone and is unitary, so the tile's norm is preserved exactly, while the
+// tensor cores' accumulation rounds toward zero (a systematic shrink of a few
+// 10^-7 per block that would add up over a circuit).
+template <int RB>
+__device__ __forceinline__ void warp_norm_to(const float2* v, float* slot) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < (1 << RB); ++k) {
+        s[k & 3] = fmaf(v[k].x, v[k].x, s[k & 3]);
+        s[k & 3] = fmaf(v[k].y, v[k].y, s[k & 3]);
+    }
+    float t = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sh);
+    if ((threadIdx.x & 31) == 0) slot[threadIdx.x >> 5] = t;
+}
+// sqrt(sum nin / sum nout) over the CTA's warps (read after a barrier that
+// follows both writes); 1 for a tile that is zero.  The write-back factor is
+// this with the sign of the pass's deferred factors (PassDev::scale), whose
+// magnitude it replaces.
+__device__ __forceinline__ float tile_norm_fix(const float* nin, const float* nout) {
+    const int nw = (int)(blockDim.x >> 5);
+    float a = 0.f, b = 0.f;
+    for (int w = 0; w < nw; ++w) {
+        a += nin[w];
+        b += nout[w];
+    }
+    return b > 0.f ? sqrtf(a / b) : 1.0f;
+}
 
 __device__ __forceinline__ uint32_t f16x2_pack(float lo, float hi) {  // round to nearest even
     uint32_t r;
@@ -794,7 +829,17 @@ struct InterpOps {
         rstore_tile(tile, psi, base, rowoff, L);
     }
     template <typename V, typename R, int RB>
-    static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>& Lg) {
+    static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>& Lg,
+                                                  TcCtx& T) {
+        if constexpr (sizeof(R) == 4 && RB == 5) {
+            if (P.tc_k) {  // the tile's norm as loaded: scale = sqrt(in / out)
+                warp_norm_to<RB>((const float2*)v, T.nout);
+                __syncthreads();
+                scale_regs<V, RB>(v, copysignf(tile_norm_fix(T.nin, T.nout), (float)P.scale));
+                reg_write<V, RB>(v, tile, Lg);
+                return;
+            }
+        }
         if (P.scale != 1.0) {
             const R sc = (R)P.scale;
 #pragma unroll
@@ -828,6 +873,8 @@ struct InterpOps {
             tpos = (const int*)(stage + op.mat_off);
             reg_layout<V, RB>(Lg, rpos, tpos, tb);
             reg_read<V, RB>(v, tile, Lg);
+            if constexpr (sizeof(R) == 4 && RB == 5)
+                if (!in_regs && P.tc_k) warp_norm_to<RB>((const float2*)v, T.nin);
             in_regs = true;
             break;
         case OP_GATES:
@@ -876,6 +923,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar[4];
     __shared__ int s_abort[4];
+    __shared__ float s_norm[2][16];  // per warp: tile norm in / out (passes with tensor-core blocks)
     {
         const int* src = (const int*)pdp;
         int* dst = (int*)&P;
@@ -923,7 +971,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     }
     __syncthreads();
     if (tcp) tc::fence_after();
-    TcCtx T{tcp ? s_tmem : 0u, s_mbar, s_abort, err, 0u};
+    TcCtx T{tcp ? s_tmem : 0u, s_mbar, s_abort, err, 0u, s_norm[0], s_norm[1]};
     const OpDev* ops = (const OpDev*)stage;
     if (threadIdx.x == 0)
         for (int i = 0; i < P.nops; ++i)
@@ -957,7 +1005,7 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
         V* tile = tiles[cur];
         if (nd) fold_diags<R>(P, stage, fold, dofs, t);
         Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg, sizeof(R) == 8 ? ttab : nullptr, T);
-        Ops::template finish<V, R, RB>(v, tile, P, Lg);
+        Ops::template finish<V, R, RB>(v, tile, P, Lg, T);
         __syncthreads();
         Ops::template store<V>(tile, psi, base, rowoff, L);
         __syncthreads();
