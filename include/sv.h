@@ -106,8 +106,8 @@ typedef enum {
  * angle, reduced modulo the gate's period (2 pi; 4 pi for RZ, as RZ(2 pi) =
  * -I), is smaller in magnitude than this many radians are left out; the result then differs from the exact circuit by at most
  * the sum of the dropped angles over 2 in norm (0, a negative value or NaN =
- * exact).  mux: multiplexor recognition (Sec. 2.3, QCrank's uniformly
- * controlled rotations): a run of RY (or RZ / P / Z) and X gates on one
+ * exact).  mux: multiplexor recognition (QCrank's uniformly
+ * controlled rotations, App. D.3): a run of RY (or RZ / P / Z) and X gates on one
  * target interleaved with CX gates into it, whose controls nothing else
  * changes meanwhile, becomes one block-diagonal operator with per-control-value
  * angles from a Walsh-Hadamard transform, and up to five such targets share
@@ -309,7 +309,7 @@ int sv_sample(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *host_out);
 int sv_sample_device(sv_handle h, uint64_t shots, uint64_t seed, uint64_t *dev_out);
 int sv_sample_uniforms(sv_handle h, const double *host_u, uint64_t shots, uint64_t *host_out);
 
-/* QCrank read-out (Sec. 2.3, Table 2).  A QCrank state holds a uniform
+/* QCrank read-out (Sec. 3 image encoding, App. D.3, Table 2).  A QCrank state holds a uniform
  * superposition over a address qubits (bits 0..a-1 of an outcome) with data
  * qubit k (bit a+k) rotated by RY(pi * pixel[j][k]), so that
  * P(bit a+k = 1 | address j) = sin^2(pi * pixel[j][k] / 2).  From shots:

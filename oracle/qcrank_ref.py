@@ -2,7 +2,7 @@
 ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs use it; the
 product never does).
 
-QCrank (Sec. 2.3, Table 2; the encoding of Balewski et al. that the paper
+QCrank (Sec. 3 image encoding, App. D.3, Table 2; the encoding of Balewski et al. that the paper
 cites) writes data qubit k of address j with a rotation RY(theta_jk) behind
 a uniform superposition over the a address qubits.  Hence
 

@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
         V* tile = (V*)(smem + (size_t)s * lay.tile_bytes);
         if (P.ndiag) fold_diags<R>(P, stage, fold, dofs, t);
         TcCtx T0{0u, nullptr, nullptr, err, 0u, nullptr, nullptr};  // (TMA-fed passes carry no tensor-core blocks)
-        InterpOps::tile<V, R, RB>(v, tile, P, stage, fold, Lg, nullptr, T0);
+        InterpOps<false>::tile<V, R, RB>(v, tile, P, stage, fold, Lg, nullptr, T0);
         if (P.scale != 1.0) {
             const R sc = (R)P.scale;
 #pragma unroll
@@ -886,6 +886,16 @@ PassLayout rpass_layout(int dtype, const PassDev& P) {
         if (lay.total < need) lay.total = need;
     }
     return lay;
+}
+
+int resident_ctas(int threads, int regs, int smem) {
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((std::max(regs, 1) * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+    const int by_regs = 65536 / std::max(1, regs_warp * warps);
+    const int by_smem = kSmemPerSm / std::max(1, smem + 1024);          // 1 KB per CTA reserved by the driver
+    const int by_tmem = 4 / std::max(1, threads >> 7);                    // 512 columns, 128 per 128 threads
+    const int by_warps = 64 / std::max(1, warps);
+    return std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_tmem, by_warps)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1191,7 +1201,7 @@ static cudaError_t pass_t(sv_state* h, const void* blob_dev, const PlanBlob& blo
     return cudaGetLastError();
 }
 
-template <typename R, int RB, int MAXT, int MINB>
+template <typename R, int RB, int MAXT, int MINB, bool TC>
 static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass) {
     using V = typename CT<R>::V;
     const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
@@ -1199,7 +1209,7 @@ static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& bl
     if (lay.total > kMaxDynSmem) return cudaErrorInvalidValue;
     static int attr_bytes = 0;
     if (lay.total > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_rpass<R, RB, MAXT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_rpass<R, RB, MAXT, MINB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              lay.total);
         if (e != cudaSuccess) return e;
         attr_bytes = lay.total;
@@ -1207,24 +1217,37 @@ static cudaError_t rpass_t(sv_state* h, const void* blob_dev, const PlanBlob& bl
     const int threads = 1 << (pdh->m - RB);
     if (threads > MAXT) return cudaErrorInvalidValue;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass<R, RB, MAXT, MINB>, threads, lay.total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass<R, RB, MAXT, MINB, TC>, threads, lay.total);
     if (per_sm < 1) per_sm = 1;
+    if (TC) {  // (see resident_ctas: the query counts one CTA per SM for kernels with TMEM allocations)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_rpass<R, RB, MAXT, MINB, TC>) == cudaSuccess)
+            per_sm = std::max(per_sm, resident_ctas(threads, fa.numRegs, (int)fa.sharedSizeBytes + lay.total));
+    }
     const uint64_t ntiles = 1ull << (h->n - pdh->m);
     uint64_t grid = (uint64_t)num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
     const unsigned char* b = (const unsigned char*)blob_dev;
     count_launch();
-    k_rpass<R, RB, MAXT, MINB><<<(unsigned)grid, threads, lay.total, h->stream>>>(
+    k_rpass<R, RB, MAXT, MINB, TC><<<(unsigned)grid, threads, lay.total, h->stream>>>(
         (V*)h->amps, h->n, (const PassDev*)(b + blob.pass_off) + pass, b, lay, (int*)h->err.ptr);
     return cudaGetLastError();
 }
 
+template <typename R, int RB, bool TC>
+static cudaError_t rpass_tc(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, int m) {
+    const int tb = m - RB;
+    if (tb <= 7) return rpass_t<R, RB, 128, 2, TC>(h, blob_dev, blob, pass);
+    if (tb == 8) return rpass_t<R, RB, 256, 2, TC>(h, blob_dev, blob, pass);
+    return rpass_t<R, RB, 512, 1, TC>(h, blob_dev, blob, pass);
+}
+// Passes with tensor-core blocks run the instance that holds the TMEM code.
 template <typename R, int RB>
 static cudaError_t rpass_any(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass, int m) {
-    const int tb = m - RB;
-    if (tb <= 7) return rpass_t<R, RB, 128, 2>(h, blob_dev, blob, pass);
-    if (tb == 8) return rpass_t<R, RB, 256, 2>(h, blob_dev, blob, pass);
-    return rpass_t<R, RB, 512, 1>(h, blob_dev, blob, pass);
+    const PassDev* pdh = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
+    if constexpr (sizeof(R) == 4 && RB == 5)
+        if (pdh->tc_k > 0) return rpass_tc<R, RB, true>(h, blob_dev, blob, pass, m);
+    return rpass_tc<R, RB, false>(h, blob_dev, blob, pass, m);
 }
 
 // ---- TMA-fed register passes: tensor map and ring layout -----------------

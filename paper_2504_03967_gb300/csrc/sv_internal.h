@@ -89,7 +89,7 @@ struct HostOp {
 
 // ---------------------------------------------------------------------------
 // Multiplexors (uniformly controlled rotations, the building block of the
-// QCrank encoder, Sec. 2.3, and of the Mottonen et al. decompositions the
+// QCrank encoder, App. D.3, and of the Mottonen et al. decompositions the
 // paper cites).  A run of gates on one target t whose other qubits are only
 // CX controls collapses to: for each value j of the control bits,
 //     U_j = X^(popcount(j & flip) ^ flip_c)  R_j
@@ -351,6 +351,10 @@ cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob,
                         const HostPass& hp);
 cudaError_t launch_mux(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass);
 PassLayout rpass_layout(int dtype, const PassDev& P);
+// CTAs of `threads` threads an SM holds by registers (regs per thread),
+// shared memory (smem bytes per CTA, static + dynamic) and TMEM columns (128
+// per 128 threads, for passes with tensor-core blocks).
+int resident_ctas(int threads, int regs, int smem);
 int num_sms_pub();
 // Run-time compiled register passes (sv_jit.cpp).  jit_prepare: per pass of
 // the blob, the compiled kernel ready for it (else nullptr); policy 1

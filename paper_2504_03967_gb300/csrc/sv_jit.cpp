@@ -53,6 +53,7 @@ struct Driver {
     CUresult (*get_function)(CUfunction*, CUmodule, const char*) = nullptr;
     CUresult (*set_attr)(CUfunction, CUfunction_attribute, int) = nullptr;
     CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
+    CUresult (*get_attr)(int*, CUfunction_attribute, CUfunction) = nullptr;
     CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
                        void**, void**) = nullptr;
 };
@@ -98,7 +99,7 @@ const Driver& driver() {
         d.ok = entry("cuModuleLoadData", &d.module_load) && entry("cuModuleGetFunction", &d.get_function) &&
                entry("cuFuncSetAttribute", &d.set_attr) &&
                entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy) &&
-               entry("cuLaunchKernel", &d.launch);
+               entry("cuFuncGetAttribute", &d.get_attr) && entry("cuLaunchKernel", &d.launch);
     });
     return d;
 }
@@ -353,7 +354,8 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     o << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
       << "    sv::CT<" << R << ">::V* __restrict__ psi, int n, const sv::PassDev* __restrict__ pdp,\n"
       << "    const unsigned char* __restrict__ blob, const sv::PassLayout lay, int* __restrict__ err) {\n"
-      << "    sv::rpass_body<" << R << ", " << RB << ", sv::GenOps>(psi, n, pdp, blob, lay, err);\n}\n";
+      << "    sv::rpass_body<" << R << ", " << RB << ", sv::GenOps, " << (P.tc_k ? "true" : "false")
+      << ">(psi, n, pdp, blob, lay, err);\n}\n";
     *out = o.str();
     return true;
 }
@@ -513,6 +515,16 @@ cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const Pla
     const int threads = 1 << tb;
     int per_sm = 1;
     if (dr.occupancy(&per_sm, e.fn, threads, (size_t)lay.total) != CUDA_SUCCESS || per_sm < 1) per_sm = 1;
+    if (pd->tc_k > 0) {
+        // the occupancy query counts one CTA per SM for a kernel with TMEM
+        // allocations; the CTAs an SM holds by registers, shared memory and
+        // TMEM columns (rpass_layout pads the shared memory so that these
+        // never ask for more than the SM's 512 columns)
+        int regs = 0, sstat = 0;
+        if (dr.get_attr(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, e.fn) == CUDA_SUCCESS &&
+            dr.get_attr(&sstat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, e.fn) == CUDA_SUCCESS)
+            per_sm = std::max(per_sm, resident_ctas(threads, regs, sstat + lay.total));
+    }
     const uint64_t ntiles = 1ull << (h->n - pd->m);
     uint64_t grid = (uint64_t)num_sms_pub() * per_sm;
     if (grid > ntiles) grid = ntiles;

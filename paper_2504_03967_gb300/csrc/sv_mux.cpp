@@ -1,6 +1,6 @@
 // Multiplexor recognition (host).
 //
-// QCrank (Sec. 2.3) writes every data qubit with a uniformly controlled RY
+// QCrank (App. D.3) writes every data qubit with a uniformly controlled RY
 // over the address qubits, which the circuit spells out as 2^a alternating
 // RY / CX steps (the Mottonen et al. decomposition the paper cites).  Played
 // gate by gate that is 2 * 2^a full passes over the state per data qubit;

@@ -1,4 +1,4 @@
-// QCrank read-out on the device (Sec. 2.3, Table 2).
+// QCrank read-out on the device (Sec. 3 image encoding, App. D.3, Table 2).
 //
 // A QCrank state holds a uniform superposition over the a address qubits
 // (bits 0..a-1) with data qubit k (bit a + k) rotated by RY(pi * pixel_jk),

@@ -484,17 +484,17 @@ __device__ __forceinline__ void reg_dense_tc(float2* v, const unsigned char* bma
     const uint32_t cols = T.tmem + (uint32_t)grp * 128u;
     const uint32_t lane = cols + (((uint32_t)((tid >> 5) & 3) * 32u) << 16);
 #pragma unroll
-    for (int c0 = 0; c0 < 32; c0 += 16) {
-        uint32_t h[16], l[16];
+    for (int c0 = 0; c0 < 32; c0 += 8) {  // (eight at a time: fewer live registers)
+        uint32_t h[8], l[8];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < 8; ++j) {
             const float xr = v[c0 + j].x * s_in, xi = v[c0 + j].y * s_in;
             h[j] = f16x2_pack(xr, xi);
             const float2 hf = f16x2_unpack(h[j]);
             l[j] = f16x2_pack(xr - hf.x, xi - hf.y);
         }
-        tc::tmem_st16(lane + c0, h);
-        tc::tmem_st16(lane + 32 + c0, l);
+        tc::tmem_st8(lane + c0, h);
+        tc::tmem_st8(lane + 32 + c0, l);
     }
     tc::tmem_wait_st();
     tc::fence_before();
@@ -817,6 +817,7 @@ __device__ __forceinline__ void fold_diags(const PassDev& P, const unsigned char
 // return the amplitudes are in registers in the last layout (Lg).  issue /
 // store move a tile between the state and shared memory; finish applies the
 // pass's write-back scale and puts the registers back into the tile.
+template <bool TC>
 struct InterpOps {
     template <typename V>
     static __device__ __forceinline__ void issue(V* tile, const V* __restrict__ psi, uint64_t base,
@@ -831,7 +832,7 @@ struct InterpOps {
     template <typename V, typename R, int RB>
     static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>& Lg,
                                                   TcCtx& T) {
-        if constexpr (sizeof(R) == 4 && RB == 5) {
+        if constexpr (TC && sizeof(R) == 4 && RB == 5) {
             if (P.tc_k) {  // the tile's norm as loaded: scale = sqrt(in / out)
                 warp_norm_to<RB>((const float2*)v, T.nout);
                 __syncthreads();
@@ -873,7 +874,7 @@ struct InterpOps {
             tpos = (const int*)(stage + op.mat_off);
             reg_layout<V, RB>(Lg, rpos, tpos, tb);
             reg_read<V, RB>(v, tile, Lg);
-            if constexpr (sizeof(R) == 4 && RB == 5)
+            if constexpr (TC && sizeof(R) == 4 && RB == 5)
                 if (!in_regs && P.tc_k) warp_norm_to<RB>((const float2*)v, T.nin);
             in_regs = true;
             break;
@@ -890,7 +891,7 @@ struct InterpOps {
             break;
         }
         case OP_DENSE_TC:
-            if constexpr (sizeof(R) == 4 && RB == 5) {
+            if constexpr (TC && sizeof(R) == 4 && RB == 5) {
                 if (op.k == 5) reg_dense_tc<RB, 5>((float2*)v, stage + op.mat_off, op.tc_scale, T);
                 else reg_dense_tc<RB, 4>((float2*)v, stage + op.mat_off, op.tc_scale, T);
             }
@@ -911,7 +912,7 @@ struct InterpOps {
 // columns per group of 128 threads for the whole kernel; every wait on the
 // tensor cores is bounded (expiry: *err = 1, the group skips its remaining
 // products, the TMEM is still freed).
-template <typename R, int RB, class Ops>
+template <typename R, int RB, class Ops, bool TC = false>
 __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, int n,
                                            const PassDev* __restrict__ pdp, const unsigned char* __restrict__ blob,
                                            const PassLayout& lay, int* __restrict__ err) {
@@ -932,7 +933,9 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     __syncthreads();
     const int ngroups = (int)(blockDim.x >> 7);
     const uint32_t tmem_cols = 128u * (uint32_t)ngroups;  // 128, 256 or 512
-    const bool tcp = sizeof(R) == 4 && RB == 5 && P.tc_k > 0 && ngroups >= 1;
+    // (TC: the instance for passes with tensor-core blocks; the others carry
+    // none of the TMEM code)
+    const bool tcp = TC && sizeof(R) == 4 && RB == 5 && P.tc_k > 0 && ngroups >= 1;
     if (tcp) {
         if (threadIdx.x < 32) {
             tc::tmem_alloc(&s_tmem, tmem_cols);
@@ -1019,12 +1022,12 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
 }
 
 #ifndef __CUDACC_RTC__
-template <typename R, int RB, int MAXT, int MINB>
+template <typename R, int RB, int MAXT, int MINB, bool TC>
 __global__ void __launch_bounds__(MAXT, MINB) k_rpass(typename CT<R>::V* __restrict__ psi, int n,
                                                   const PassDev* __restrict__ pdp,
                                                   const unsigned char* __restrict__ blob, const PassLayout lay,
                                                   int* __restrict__ err) {
-    rpass_body<R, RB, InterpOps>(psi, n, pdp, blob, lay, err);
+    rpass_body<R, RB, InterpOps<TC>, TC>(psi, n, pdp, blob, lay, err);
 }
 #endif
 

@@ -1,4 +1,4 @@
-"""Multiplexor recognition (uniformly controlled rotations, QCrank Sec. 2.3)
+"""Multiplexor recognition (uniformly controlled rotations, QCrank, Sec. 3 image encoding and App. D.3)
 through the C ABI against the FP64 oracle, which plays every gate.
 
 Pins: the oracle state element by element; for QCrank also the closed-form

@@ -6,7 +6,7 @@ rounding.  This pins the planner's exact rewrites without a GPU: grouping a
 pass's gates by qubit set, phase tables kept pending past gates they commute
 with and moved through CX / SWAP, U3 = P(phi) RY(theta) P(lambda), diagonal
 gates folded into blocks or runs (App. D.2 "gate fusion", Eq. "cr1"), and
-runs recognised as multiplexors (Sec. 2.3)."""
+runs recognised as multiplexors (QCrank, App. D.3)."""
 import numpy as np
 import pytest
 
@@ -190,7 +190,7 @@ def test_multiplexors_reproduce_the_circuit(seed):
     """Runs of both recognised families (RY with X and CX from scattered
     controls; RZ, P, Z, X and CX), interleaved with gates that commute with
     them, become multiplexors whose angles (one Walsh-Hadamard transform of
-    the run's angles, Sec. 2.3's uniformly controlled rotations) reproduce the
+    the run's angles, QCrank's uniformly controlled rotations, App. D.3) reproduce the
     oracle's gate-by-gate state."""
     from tests.test_mux_gpu import _ladder_mix
 

@@ -1,4 +1,4 @@
-"""QCrank read-out on the device (Sec. 2.3, Table 2) against the oracle's
+"""QCrank read-out on the device (Sec. 3 image encoding, App. D.3, Table 2) against the oracle's
 decoding of the same shots: counts bit-exact, pixels to FP64 rounding; and
 against the image itself through the shot-noise law (pixel error variance
 1 / (pi^2 s) with s shots per address) and the reconstruction correlation."""
