@@ -14,6 +14,13 @@ constexpr int kPassThreads = 256;
 // on the tensor cores (FP16 hi/lo split, three products, FP32 accumulation).
 enum OpKind { OP_DENSE = 0, OP_DIAG = 1, OP_GATES = 2, OP_REMAP = 3, OP_DENSE_TC = 4 };
 
+// Launch bounds of a register pass with tb thread bits: 128 threads at least
+// 2 CTAs per SM, 256 threads 2 (128 registers), 512 threads 1.  (A cap of 128
+// registers on 128-thread passes measured no faster: it trades spills for
+// residency.)
+__host__ __device__ inline int pass_max_threads(int tb) { return tb <= 7 ? 128 : (tb == 8 ? 256 : 512); }
+__host__ __device__ inline int pass_min_blocks(int tb) { return tb <= 8 ? 2 : 1; }
+
 // Register-resident passes: each thread holds 2^kRegBits amplitudes of the
 // tile in registers; the other m - kRegBits tile bits index the thread.
 __host__ __device__ inline int reg_bits(int dtype) { return dtype == 0 ? 5 : 4; }  // 0: complex64

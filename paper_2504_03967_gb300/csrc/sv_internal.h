@@ -157,7 +157,7 @@ struct Plan {
 // Default of the tensor-core choice (sv_options.tensor = 0): 1 = 4- and
 // 5-qubit blocks go to the tensor cores where their estimated cost is below
 // the gate sequence's, 0 = CUDA cores only.
-constexpr int kTcAutoDefault = 0;
+constexpr int kTcAutoDefault = 1;
 
 struct PlanOptions {
     int k_max = 5;

@@ -467,8 +467,8 @@ void jit_prepare(sv_state* h, const PlanBlob& blob, int policy, long long basis,
             const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + (fill ? 0 : p);
             if ((fill && blob.npasses == 0) || pd->rmode != 1) continue;
             const int tb = pd->m - reg_bits(h->dtype);
-            if (!pass_source(*pd, blob.bytes.data() + pd->region_off, h->dtype, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
-                             tb <= 8 ? 2 : 1, &srcs[p], fill))
+            if (!pass_source(*pd, blob.bytes.data() + pd->region_off, h->dtype, pass_max_threads(tb),
+                             pass_min_blocks(tb), &srcs[p], fill))
                 srcs[p].clear();
         }
     }
@@ -622,8 +622,8 @@ extern "C" int sv_jit_check(int n, sv_dtype dt, const sv_gate* gates, size_t cou
         if (pd->rmode != 1) continue;
         const int tb = pd->m - reg_bits(dt);
         std::string src;
-        if (!pass_source(*pd, blob.bytes.data() + pd->region_off, dt, tb <= 7 ? 128 : (tb == 8 ? 256 : 512),
-                         tb <= 8 ? 2 : 1, &src, fill))
+        if (!pass_source(*pd, blob.bytes.data() + pd->region_off, dt, pass_max_threads(tb), pass_min_blocks(tb),
+                         &src, fill))
             continue;
         nvrtcProgram prog;
         if (nv.create(&prog, src.c_str(), "sv_jit_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)

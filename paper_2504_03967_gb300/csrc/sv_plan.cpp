@@ -214,10 +214,14 @@ double dense_cost(int k) { return 4.0 * (double)(1 << k) + 2.0; }
 // deferred to the write-back), another real 2x2 4.
 double gate_sequence_cost(const std::vector<GateRec>& recs, const std::vector<cd>* data = nullptr) {
     double c = 2.0;
+    const double hs = 1.0 / std::sqrt(2.0);
     for (const GateRec& r : recs) {
         if (r.kind == GR_UR && data) {
             const cd* m = data->data() + r.off;
-            c += m[0] == m[3] && m[1] == -m[2] ? 2.0 : 4.0;
+            // a Hadamard becomes a butterfly (its factor deferred), a rotation
+            // a two-FMA form; other real 2x2 products cost 4
+            const bool had = m[0] == cd(hs, 0.0) && m[1] == cd(hs, 0.0) && m[2] == cd(hs, 0.0) && m[3] == cd(-hs, 0.0);
+            c += had ? 1.0 : (m[0] == m[3] && m[1] == -m[2] ? 2.0 : 4.0);
         } else {
             c += r.kind == GR_U ? 8.0 : r.kind == GR_UR ? 4.0 : r.kind == GR_DT ? 5.0 : 1.0;
         }
@@ -225,10 +229,12 @@ double gate_sequence_cost(const std::vector<GateRec>& recs, const std::vector<cd
     return c;
 }
 
-// A 4- or 5-qubit block on the tensor cores (register passes): the FP16
-// split of the registers, the TMEM traffic and the products' share of the
-// tensor pipe, in the same units.
-double tc_cost(int k) { return k >= 5 ? 14.0 : 12.0; }
+// A 4- or 5-qubit block on the tensor cores (register passes), in the same
+// units: the FP16 split of the registers (about 11 instructions per
+// amplitude), the TMEM traffic and the exposed latency of the products
+// (measured: random U3+CX blocks of about 45 run faster on the tensor cores,
+// QFT blocks of about 27 slower).
+double tc_cost(int k) { return k >= 5 ? 32.0 : 28.0; }
 
 bool is_real(const cd* m, int cnt) {
     for (int i = 0; i < cnt; ++i)
