@@ -17,6 +17,7 @@
 #include "sv_philox.cuh"
 #include "sv_rpass.cuh"
 #include "sv_tc.cuh"
+#include "sv_mux.cuh"
 
 namespace sv {
 
@@ -1248,6 +1249,201 @@ static cudaError_t rpass_any(sv_state* h, const void* blob_dev, const PlanBlob& 
     if constexpr (sizeof(R) == 4 && RB == 5)
         if (pdh->tc_k > 0) return rpass_tc<R, RB, true>(h, blob_dev, blob, pass, m);
     return rpass_tc<R, RB, false>(h, blob_dev, blob, pass, m);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent executor of a wave of circuits (the paper's parallel mode of
+// many circuits, Sec. 2.4; see WaveItem).  A CTA takes items from a device
+// counter in order, waits until the item's circuit has finished its earlier
+// passes (the per-circuit counter of finished items reaches `need`; bounded),
+// stages the pass's region when the pass changes, runs its tiles (or
+// multiplexor columns) and counts the item finished.  An item only ever waits
+// for items of smaller index, which CTAs that are running hold, so the queue
+// cannot deadlock; a wait that gives up sets *err = 2 and every CTA stops.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(256, 1) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
+                                                 const int* __restrict__ nq, const unsigned char* __restrict__ blob,
+                                                 const PassDev* __restrict__ pds, const WaveItem* __restrict__ items,
+                                                 int nitems, int* __restrict__ head, int* __restrict__ done,
+                                                 int* __restrict__ err, const PassLayout lay, unsigned limit) {
+    using V = typename CT<R>::V;
+    using T = decltype(V().x);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ PassDev P;
+    __shared__ uint32_t tbase[3][256];
+    __shared__ double2 ttab[sizeof(R) == 8 ? 256 : 1];
+    __shared__ int s_item, s_stop, s_staged;
+    V* tile = (V*)smem;
+    uint32_t* rowoff = (uint32_t*)(smem + lay.rowoff_off);
+    unsigned char* stage = smem + lay.stage_off;
+    uint64_t* fold = (uint64_t*)(smem + lay.work_off);
+    const int tid = threadIdx.x;
+    if (tid == 0) s_staged = -1;
+    if constexpr (sizeof(R) == 8) build_turn_table(ttab);
+    TcCtx T0{0u, nullptr, nullptr, err, 0u, nullptr, nullptr};
+    V v[1 << RB];
+    RegLayout<V, RB> Lg;
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(head, 1);
+            s_stop = 0;
+            if (s_item < nitems) {
+                const WaveItem& I = items[s_item];
+                if (I.need > 0) {
+                    unsigned k = 0;
+                    while (ld_acquire(&done[I.circ]) < I.need && ld_acquire(err) == 0) {
+                        if (++k > limit) {
+                            atomicExch(err, 2);
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+                if (ld_acquire(err) != 0) s_stop = 1;
+            }
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems || s_stop) break;
+        const WaveItem I = items[it];
+        V* psi = base + offs[I.circ];
+        if (I.kind == 1) {  // multiplexor columns
+            const unsigned char* region = blob + pds[I.pass].region_off;
+            const MuxDev& D = *(const MuxDev*)region;
+            switch (D.K) {
+            case 1: mux_columns<T, V, 1>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
+            case 2: mux_columns<T, V, 2>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
+            case 3: mux_columns<T, V, 3>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
+            case 4: mux_columns<T, V, 4>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
+            default: mux_columns<T, V, 5>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
+            }
+        } else {
+            if (I.pass != s_staged) {  // stage the pass: record, region, row offsets, base tables
+                __syncthreads();
+                const int* src = (const int*)(pds + I.pass);
+                int* dst = (int*)&P;
+                for (int i = tid; i < (int)(sizeof(PassDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+                __syncthreads();
+                const unsigned char* greg = blob + P.region_off;
+                for (int e = tid; e < P.region_bytes / 16; e += blockDim.x) cp_async16(stage + 16 * e, greg + 16 * e);
+                cp_async_commit();
+                const int nrows = 1 << (P.m - P.L);
+                for (int r = tid; r < nrows; r += blockDim.x) {
+                    uint32_t o = 0;
+                    for (int b = 0; b < P.m - P.L; ++b)
+                        if ((r >> b) & 1) o |= 1u << (P.tq[P.L + b] - P.L);
+                    rowoff[r] = o;
+                }
+                build_base_tables(tbase, P);
+                cp_async_wait_group<0>();
+                __syncthreads();
+                if (tid == 0) s_staged = I.pass;
+            }
+            const OpDev* ops = (const OpDev*)stage;
+            int* dofs = (int*)(fold + (size_t)P.ndiag * (P.m + 1));
+            if (tid == 0)
+                for (int i = 0; i < P.nops; ++i)
+                    if (ops[i].kind == OP_DIAG) dofs[ops[i].ord] = ops[i].diag_off;
+            __syncthreads();
+            for (uint64_t t = I.lo; t < I.hi; ++t) {
+                const uint64_t b = table_base(tbase, t, P.L);
+                rissue_tile(tile, psi, b, rowoff, P.L);
+                cp_async_commit();
+                cp_async_wait_group<0>();
+                __syncthreads();
+                if (P.ndiag) fold_diags<R>(P, stage, fold, dofs, t);
+                InterpOps<false>::tile<V, R, RB>(v, tile, P, stage, fold, Lg, sizeof(R) == 8 ? ttab : nullptr, T0);
+                InterpOps<false>::finish<V, R, RB>(v, tile, P, Lg, T0);
+                __syncthreads();
+                rstore_tile(tile, psi, b, rowoff, P.L);
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {  // the item's writes before the count (release)
+            __threadfence();
+            atomicAdd(&done[I.circ], 1);
+        }
+    }
+}
+}  // namespace
+
+namespace {
+// |0...0> for every circuit of a wave (the buffer zeroed beforehand).
+template <typename V> __global__ void k_wave_init(V* __restrict__ base, const uint64_t* __restrict__ offs, int C) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) base[offs[c]].x = 1;
+}
+}  // namespace
+
+cudaError_t launch_wave_init(int dtype, void* base, const uint64_t* offs, int C, cudaStream_t st) {
+    count_launch();
+    const unsigned g = (unsigned)((C + 127) / 128);
+    if (dtype == SV_C64) k_wave_init<float2><<<g, 128, 0, st>>>((float2*)base, offs, C);
+    else k_wave_init<double2><<<g, 128, 0, st>>>((double2*)base, offs, C);
+    return cudaGetLastError();
+}
+
+PassLayout wave_layout(int dtype, const PlanBlob& blob) {
+    PassLayout lay;
+    memset(&lay, 0, sizeof(lay));
+    const size_t csz = dtype == SV_C64 ? 8 : 16;
+    int m = 0, nrows = 1, region = 16, work = 16;
+    for (int p = 0; p < blob.npasses; ++p) {
+        const PassDev& P = ((const PassDev*)(blob.bytes.data() + blob.pass_off))[p];
+        if (P.rmode != 1) continue;
+        m = std::max(m, P.m);
+        nrows = std::max(nrows, 1 << (P.m - P.L));
+        region = std::max(region, P.region_bytes);
+        work = std::max(work, (int)(sizeof(uint64_t) * (size_t)P.ndiag * (P.m + 1) + sizeof(int) * (size_t)P.ndiag));
+    }
+    lay.nbuf = 1;
+    lay.tile_bytes = round128(csz << m);
+    lay.rowoff_off = lay.tile_bytes;
+    lay.bres_off = lay.rowoff_off + round128(4 * (size_t)nrows);
+    lay.stage_off = lay.bres_off;
+    lay.stage_bytes = region;
+    lay.staged = 1;
+    lay.work_off = lay.stage_off + round128(region);
+    lay.total = lay.work_off + round128(work);
+    return lay;
+}
+
+cudaError_t launch_wave(int dtype, void* base, const uint64_t* offs, const int* nq, const void* blob_dev,
+                        const PlanBlob& blob, const WaveItem* items, int nitems, int* head, int* done, int* err,
+                        unsigned limit, cudaStream_t st) {
+    const PassLayout lay = wave_layout(dtype, blob);
+    if (lay.total > kMaxDynSmem) return cudaErrorInvalidValue;
+    const unsigned char* b = (const unsigned char*)blob_dev;
+    const PassDev* pds = (const PassDev*)(b + blob.pass_off);
+    int per_sm = 1;
+    cudaError_t e = cudaSuccess;
+    if (dtype == SV_C64) {
+        e = cudaFuncSetAttribute(k_wave<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+        if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<float, 5>, 256, lay.total);
+    } else {
+        e = cudaFuncSetAttribute(k_wave<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+        if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<double, 4>, 256, lay.total);
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = std::max(1, std::min(num_sms() * per_sm, nitems));
+    count_launch();
+    if (dtype == SV_C64)
+        k_wave<float, 5><<<grid, 256, lay.total, st>>>((float2*)base, offs, nq, b, pds, items, nitems, head, done, err,
+                                                       lay, limit);
+    else
+        k_wave<double, 4><<<grid, 256, lay.total, st>>>((double2*)base, offs, nq, b, pds, items, nitems, head, done,
+                                                        err, lay, limit);
+    return cudaGetLastError();
 }
 
 // ---- TMA-fed register passes: tensor map and ring layout -----------------

@@ -48,6 +48,151 @@ struct Slot {
 };
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Waves: up to kWaveCircuits circuits whose every pass runs in the persistent
+// wave kernel (register tile passes of 256 threads, multiplexor passes).
+// ---------------------------------------------------------------------------
+constexpr int kWaveCircuits = 64;
+constexpr uint64_t kWaveTiles = 4;      // tiles per item
+constexpr uint64_t kWaveColumns = 4096; // multiplexor columns per item
+constexpr unsigned kWaveWaitLimit = 1u << 24;  // polls of about 128 ns: a wait gives up after about 2 s
+
+bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w) {
+    serialise_plans(plans, &w->blob);
+    const int RB = reg_bits(dtype);
+    const unsigned char* b = w->blob.bytes.data();
+    const PassDev* pds = (const PassDev*)(b + w->blob.pass_off);
+    for (int p = 0; p < w->blob.npasses; ++p)
+        if (!(pds[p].rmode == kRmodeMux || (pds[p].rmode == 1 && pds[p].m - RB == 8 && pds[p].tc_k == 0)))
+            return false;
+    const int C = (int)plans.size();
+    std::vector<int> first(C + 1, 0);
+    for (int c = 0; c < C; ++c) first[c + 1] = first[c] + (int)plans[c]->passes.size();
+    w->offs.resize(C);
+    w->nq.resize(C);
+    w->amps = 0;
+    int levels = 0;
+    for (int c = 0; c < C; ++c) {
+        w->offs[c] = w->amps;
+        w->nq[c] = plans[c]->n;
+        w->amps += 1ull << plans[c]->n;
+        levels = std::max(levels, first[c + 1] - first[c]);
+    }
+    w->items.clear();
+    std::vector<int> cum(C, 0);
+    for (int l = 0; l < levels; ++l)
+        for (int c = 0; c < C; ++c) {
+            const int p = first[c] + l;
+            if (p >= first[c + 1]) continue;
+            const int need = cum[c];
+            WaveItem I;
+            I.circ = c;
+            I.pass = p;
+            I.need = need;
+            if (pds[p].rmode == kRmodeMux) {
+                MuxDev D;
+                memcpy(&D, b + pds[p].region_off, sizeof(D));
+                const uint64_t ncols = 1ull << (plans[c]->n - D.K);
+                I.kind = 1;
+                for (uint64_t c0 = 0; c0 < ncols; c0 += kWaveColumns) {
+                    I.lo = c0;
+                    I.hi = std::min(ncols, c0 + kWaveColumns);
+                    w->items.push_back(I);
+                    ++cum[c];
+                }
+            } else {
+                const uint64_t ntiles = 1ull << (plans[c]->n - pds[p].m);
+                I.kind = 0;
+                for (uint64_t t0 = 0; t0 < ntiles; t0 += kWaveTiles) {
+                    I.lo = t0;
+                    I.hi = std::min(ntiles, t0 + kWaveTiles);
+                    w->items.push_back(I);
+                    ++cum[c];
+                }
+            }
+        }
+    return true;
+}
+
+int run_wave(int dtype, const WaveHost& w, cudaStream_t st, void** dev_base, unsigned limit) {
+    const size_t csz = dtype == SV_C64 ? 8 : 16, C = w.offs.size();
+    void *base = nullptr, *blob = nullptr, *pin = nullptr;
+    uint64_t* offs = nullptr;
+    int *nq = nullptr, *cnt = nullptr;
+    WaveItem* items = nullptr;
+    const size_t ib = sizeof(WaveItem) * w.items.size(), ob = sizeof(uint64_t) * C, nb = sizeof(int) * C;
+    const size_t pinb = w.blob.bytes.size() + ib + ob + nb;
+    cudaError_t e = cudaMallocAsync(&base, csz * w.amps, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&blob, w.blob.bytes.size(), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&items, ib, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&offs, ob, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&nq, nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, sizeof(int) * (C + 2), st);  // head, err, done[C]
+    if (e == cudaSuccess) e = cudaMallocHost(&pin, pinb);
+    auto freeall = [&](bool keep_base) {
+        if (!keep_base && base) cudaFreeAsync(base, st);
+        if (blob) cudaFreeAsync(blob, st);
+        if (items) cudaFreeAsync(items, st);
+        if (offs) cudaFreeAsync(offs, st);
+        if (nq) cudaFreeAsync(nq, st);
+        if (cnt) cudaFreeAsync(cnt, st);
+        if (pin) {
+            cudaStreamSynchronize(st);
+            cudaFreeHost(pin);
+        }
+        cudaGetLastError();
+    };
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        freeall(false);
+        return set_error(SV_ENOMEM, "sv_batch_run: wave allocation failed");
+    }
+    unsigned char* pc = (unsigned char*)pin;
+    memcpy(pc, w.blob.bytes.data(), w.blob.bytes.size());
+    memcpy(pc + w.blob.bytes.size(), w.items.data(), ib);
+    memcpy(pc + w.blob.bytes.size() + ib, w.offs.data(), ob);
+    memcpy(pc + w.blob.bytes.size() + ib + ob, w.nq.data(), nb);
+    e = cudaMemcpyAsync(blob, pc, w.blob.bytes.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(items, pc + w.blob.bytes.size(), ib, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(offs, pc + w.blob.bytes.size() + ib, ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nq, pc + w.blob.bytes.size() + ib + ob, nb, cudaMemcpyHostToDevice, st);
+    // the counters, the |0...0> states and the persistent launch, from one graph
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 2), cs);
+        cudaMemsetAsync(base, 0, csz * w.amps, cs);
+        launch_wave_init(dtype, base, offs, (int)C, cs);
+        launch_wave(dtype, base, offs, nq, blob, w.blob, items, (int)w.items.size(), cnt, cnt + 2, cnt + 1, limit, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gexec, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    int rc = SV_OK;
+    if (e != cudaSuccess) rc = cuda_fail(e, "wave");
+    else if (err == 2) rc = set_error(SV_ETIMEOUT, "sv_batch_run: a wait of the wave kernel gave up");
+    freeall(rc == SV_OK);
+    *dev_base = rc == SV_OK ? base : nullptr;
+    return rc;
+}
+
 }  // namespace sv
 
 using namespace sv;
@@ -92,7 +237,9 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
         const int n = n_qubits[c];
         bad[c] = canonicalise(n, gates + gate_offsets[c], (size_t)gate_counts[c], &cg[c], &b) != SV_OK;
         if (bad[c] || n <= small_limit(dt) || !host_plans) return;
-        const PlanOptions po = resolve_options(n, dt, opt);
+        PlanOptions po = resolve_options(n, dt, opt);
+        po.tc_auto = 0;  // the wave kernel runs the interpreting pass body, without tensor-core blocks
+        if (po.tensor == 0) po.tensor = -1;
         std::vector<CGate>& g = cg[c];
         drop_small_phases(&g, po.drop_phase_below);
         std::vector<CGate> muxed;
@@ -114,6 +261,9 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
     std::vector<int> small, large;
     for (int c = 0; c < C; ++c) (n_qubits[c] <= small_limit(dt) ? small : large).push_back(c);
     const int Cs = (int)small.size();
+    std::vector<int> slot(C);  // row of circuit c in the device outputs: [small..., large...]
+    for (int i = 0; i < Cs; ++i) slot[small[i]] = i;
+    for (size_t i = 0; i < large.size(); ++i) slot[large[i]] = Cs + (int)i;
 
     // device outputs in [small..., large...] order
     uint64_t* d_samples = nullptr;
@@ -197,14 +347,69 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
         if (e != cudaSuccess) rc = cuda_fail(e, "batched small circuits");
     }
 
-    // 3. large circuits: fused passes on a few streams
-    if (rc == SV_OK && !large.empty()) {
+    // 3a. large circuits planned on the host: waves of up to kWaveCircuits
+    //     circuits (and a bounded state budget), each one persistent launch
+    std::vector<int> rest;
+    if (rc == SV_OK) {
+        size_t freeb = 0, totb = 0;
+        cudaMemGetInfo(&freeb, &totb);
+        const uint64_t budget = std::max<uint64_t>(freeb / 4, 1ull << 28);
+        const size_t csz = dt == SV_C64 ? 8 : 16;
+        sv_state hv{};  // a view of one circuit's state for its read-outs
+        hv.dtype = dt;
+        hv.stream = st;
+        hv.pending_basis = -1;
+        size_t i = 0;
+        while (rc == SV_OK && i < large.size()) {
+            std::vector<int> wc;
+            std::vector<const Plan*> plans;
+            uint64_t bytes = 0;
+            for (; i < large.size() && (int)wc.size() < kWaveCircuits; ++i) {
+                const int c = large[i];
+                const uint64_t sb = (uint64_t)csz << n_qubits[c];
+                if (!prep[c] || prep[c]->plan.passes.empty()) {
+                    rest.push_back(c);
+                    continue;
+                }
+                if (!wc.empty() && bytes + sb > budget) break;
+                wc.push_back(c);
+                plans.push_back(&prep[c]->plan);
+                bytes += sb;
+            }
+            if (wc.empty()) continue;
+            WaveHost w;
+            if (!build_wave(dt, plans, &w)) {
+                rest.insert(rest.end(), wc.begin(), wc.end());
+                continue;
+            }
+            void* base = nullptr;
+            rc = run_wave(dt, w, st, &base, kWaveWaitLimit);
+            for (size_t k = 0; rc == SV_OK && k < wc.size(); ++k) {
+                const int c = wc[k];
+                const int idx = slot[c];
+                hv.n = n_qubits[c];
+                hv.amps = (char*)base + csz * w.offs[k];
+                reset_perm(&hv);
+                if (host_samples)
+                    rc = measure_sample(&hv, shots, seed + (uint64_t)c, nullptr, d_samples + (size_t)idx * shots);
+                if (rc == SV_OK && host_expz) rc = measure_expect_z(&hv, d_expz + (size_t)idx * nmax);
+            }
+            if (base) cudaFreeAsync(base, st);
+            for (int c : wc) prep[c].reset();
+        }
+        cudaStreamSynchronize(st);
+        if (hv.red.ptr) cudaFree(hv.red.ptr);
+        if (hv.perm_tmp.ptr) cudaFree(hv.perm_tmp.ptr);
+        if (hv.lcdf.ptr) cudaFree(hv.lcdf.ptr);
+    }
+    // 3b. the other large circuits: fused passes on a few streams
+    if (rc == SV_OK && !rest.empty()) {
         int nl = 0;
-        for (int c : large) nl = std::max(nl, n_qubits[c]);
+        for (int c : rest) nl = std::max(nl, n_qubits[c]);
         const size_t bytes = (size_t)(dt == SV_C64 ? 8 : 16) << nl;
         size_t freeb = 0, totb = 0;
         cudaMemGetInfo(&freeb, &totb);
-        int ns = (int)std::min<size_t>(std::min<size_t>(4, large.size()), std::max<size_t>(1, freeb / (2 * bytes)));
+        int ns = (int)std::min<size_t>(std::min<size_t>(4, rest.size()), std::max<size_t>(1, freeb / (2 * bytes)));
         slots.resize(ns);
         for (int s = 0; e == cudaSuccess && s < ns; ++s) {
             e = cudaStreamCreateWithFlags(&slots[s].st, cudaStreamNonBlocking);
@@ -224,9 +429,9 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
             cudaGetLastError();
             rc = set_error(SV_ENOMEM, "sv_batch_run: large-circuit state buffers");
         }
-        for (size_t i = 0; rc == SV_OK && i < large.size(); ++i) {
-            const int c = large[i];
-            const int idx = Cs + (int)i;
+        for (size_t i = 0; rc == SV_OK && i < rest.size(); ++i) {
+            const int c = rest[i];
+            const int idx = slot[c];
             sv_state* h = &slots[i % slots.size()].h;
             h->n = n_qubits[c];
             reset_perm(h);
@@ -284,4 +489,46 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
     if (d_gidx) cudaFree(d_gidx);
     cudaGetLastError();
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Failure detection of the wave kernel without a GPU fault: one circuit of 14
+// qubits (an H on every qubit, one pass of 2 tiles, one item) whose only item
+// is made to wait for one finished item of its circuit, which never comes:
+// the bounded wait gives up after `limit` polls, the kernel records it and
+// returns, and the call reports SV_ETIMEOUT.  *host_status = 1 when it did.
+// ---------------------------------------------------------------------------
+extern "C" int sv_selftest_wave_timeout(unsigned limit, int* host_status) {
+    if (!host_status) return set_error(SV_EINVAL, "NULL argument");
+    if (limit == 0 || limit > (1u << 22)) return set_error(SV_EINVAL, "limit must be in 1..2^22");
+    const int n = 14;
+    std::vector<sv_gate> g(n);
+    for (int q = 0; q < n; ++q) {
+        memset(&g[q], 0, sizeof(sv_gate));
+        g[q].type = SV_H;
+        g[q].nq = 1;
+        g[q].q[0] = (uint32_t)q;
+    }
+    std::vector<CGate> cg;
+    size_t bad = 0;
+    if (canonicalise(n, g.data(), g.size(), &cg, &bad) != SV_OK) return set_error(SV_EINVAL, "internal: circuit");
+    PlanOptions po = resolve_options(n, SV_C64, nullptr);
+    po.tc_auto = 0;
+    Plan plan;
+    plan_greedy(n, SV_C64, cg, po, &plan);
+    WaveHost w;
+    if (!build_wave(SV_C64, {&plan}, &w) || w.items.empty()) return set_error(SV_EINVAL, "internal: wave");
+    w.items[0].need = 1;  // the unsatisfiable dependency
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "stream");
+    void* base = nullptr;
+    const int rc = run_wave(SV_C64, w, st, &base, limit);
+    if (base) cudaFreeAsync(base, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    cudaGetLastError();
+    *host_status = rc == SV_ETIMEOUT ? 1 : 0;
+    if (rc != SV_OK && rc != SV_ETIMEOUT) return rc;
+    return SV_OK;
 }

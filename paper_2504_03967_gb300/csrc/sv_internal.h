@@ -378,6 +378,46 @@ cudaError_t launch_batch_small(int dtype, const void* blob_dev, const PlanBlob& 
                                int nmax, int* counter, cudaStream_t st);
 size_t batch_small_smem_bytes(int dtype, int mmax);
 
+// Persistent executor of a wave of circuits (sv_batch_run): one launch runs
+// every pass of every circuit of the wave.  Items are (circuit, pass, range)
+// in pass-level order; an item may start once `need` items of its circuit
+// have finished (its earlier passes).  kind 0: register tile pass over tiles
+// [lo, hi) (all tile passes of a wave have the same tile width, 2^(m - RB) =
+// 256 threads); kind 1: multiplexor pass over columns [lo, hi).
+struct WaveItem {
+    int circ;
+    int pass;
+    int need;
+    int kind;
+    uint64_t lo, hi;
+};
+// States of the wave's circuits at base + offs[c] (amplitudes), n qubits
+// nq[c]; counters: head (1 int, zero) and done (one int per circuit, zero);
+// err set to 2 when a wait gives up after `limit` polls (every CTA then
+// stops taking items).  Launch on st; the caller captures it in a graph.
+cudaError_t launch_wave(int dtype, void* base, const uint64_t* offs, const int* nq, const void* blob_dev,
+                        const PlanBlob& blob, const WaveItem* items, int nitems, int* head, int* done, int* err,
+                        unsigned limit, cudaStream_t st);
+// Dynamic shared memory of the wave kernel for a blob's register passes.
+PassLayout wave_layout(int dtype, const PlanBlob& blob);
+// Amplitude 0 of every circuit of a wave set to 1 (the buffer zeroed first).
+cudaError_t launch_wave_init(int dtype, void* base, const uint64_t* offs, int C, cudaStream_t st);
+// A wave's plans and item list (host).  Returns false when some pass cannot
+// run in the wave kernel (a pass not register-resident with 2^(m - RB) = 256
+// threads, nor a multiplexor pass).
+struct WaveHost {
+    PlanBlob blob;
+    std::vector<WaveItem> items;
+    std::vector<uint64_t> offs;  // amplitudes, per circuit
+    std::vector<int> nq;
+    uint64_t amps = 0;           // total
+};
+bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w);
+// Run a built wave on st in one captured graph; the states stay in *dev_base
+// (allocated here, Σ 2^n amplitudes; the caller frees it).  SV_ETIMEOUT when
+// a wait gave up (limit polls).
+int run_wave(int dtype, const WaveHost& w, cudaStream_t st, void** dev_base, unsigned limit);
+
 // Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
 int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks, int blog_cap = 10);
 cudaError_t launch_probs(sv_state* h, double* dev_out);
