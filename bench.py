@@ -490,6 +490,8 @@ def main():
             step(i, planner, 0)
         torch.cuda.synchronize()
         cm["chosen"] = S.sv_last_plan(h)
+        # trial 0: the model's per-pass plan; then its best option sets; last: greedy
+        cm["trials"] = S.sv_cost_model_last_trials()
     with Clocks(local) as clk:
         ms, launches = timed(planner, args.steps, args.warmup, 1)
     fills = timed.fills  # first passes that built their tiles from the deferred basis state

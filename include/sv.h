@@ -466,6 +466,15 @@ int sv_cost_model_stats(int64_t *planned, int64_t *mispredicted);
 int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate *gates, size_t count, sv_options *out,
                          double *measured_ms);
 
+/* The trials the judge timed for the circuit the cost-model planner saw
+ * last: trial 0 is the model's own plan (passes chosen one at a time by
+ * predicted time) when it found one (*learned = 1), then the model's best
+ * whole-circuit option sets, last the greedy plan.  predicted[i] and
+ * measured[i] in ms (-1 where not known) for i < min(cap, *ntrials);
+ * *chosen = the trial kept (-1 until every trial was timed). */
+int sv_cost_model_last_trials(double *predicted, double *measured, int cap, int *ntrials, int *chosen,
+                              int *learned);
+
 /* ---- misc -------------------------------------------------------------- */
 
 /* Message for the calling thread's last failing call ("" if none). */

@@ -609,3 +609,19 @@ def sv_batch_run(circuits, dtype=C64, shots=0, seed=0, expz=True, k_max=0, tile_
                           ctypes.byref(o), _ptr(samp) if samp is not None else None,
                           _ptr(ez) if ez is not None else None, nmax, stream))
     return samp, ez
+
+
+def sv_cost_model_last_trials(cap=8):
+    """Trials the judge timed for the circuit the cost-model planner saw last:
+    dict(predicted_ms, measured_ms, chosen, learned)."""
+    L = lib()
+    f = L.sv_cost_model_last_trials
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    f.restype = ctypes.c_int
+    pred = np.zeros(cap, np.float64)
+    meas = np.zeros(cap, np.float64)
+    nt, ch, le = ctypes.c_int(0), ctypes.c_int(-1), ctypes.c_int(0)
+    _check(f(_ptr(pred), _ptr(meas), cap, ctypes.byref(nt), ctypes.byref(ch), ctypes.byref(le)))
+    k = min(cap, nt.value)
+    return {"predicted_ms": pred[:k].tolist(), "measured_ms": meas[:k].tolist(), "chosen": ch.value,
+            "learned": bool(le.value)}

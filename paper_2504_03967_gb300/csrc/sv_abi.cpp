@@ -594,7 +594,7 @@ int apply_canonical(sv_state* h, const sv_gate* gates, size_t count, const std::
     h->last_opts.k_max = po.k_max;
     h->last_opts.tile_m = po.tile_m;
     h->last_opts.planner = opt ? opt->planner : SV_PLAN_GREEDY;
-    h->last_opts.tensor = po.tensor == 0 ? 1 : -1;
+    h->last_opts.tensor = po.tensor == 0 ? 1 : (po.tc_auto ? 0 : -1);
     h->last_opts.pass_kernel = po.pass_kernel;
     h->last_opts.relabel = po.relabel;
     h->last_opts.mux = po.mux;

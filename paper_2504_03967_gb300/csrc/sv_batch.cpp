@@ -58,8 +58,47 @@ constexpr uint64_t kWaveTiles = 4;      // tiles per item
 constexpr uint64_t kWaveColumns = 4096; // multiplexor columns per item
 constexpr unsigned kWaveWaitLimit = 1u << 24;  // polls of about 128 ns: a wait gives up after about 2 s
 
-bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w) {
-    serialise_plans(plans, &w->blob);
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// One blob from several (passes in order): the pass records first, then
+// every blob's region area, region offsets moved with it.  Tensor-core B
+// operands of the shared-memory kernel are not carried (wave passes have none).
+void merge_blobs(const std::vector<const PlanBlob*>& bl, PlanBlob* out) {
+    int np = 0;
+    for (const PlanBlob* b : bl) np += b->npasses;
+    out->npasses = np;
+    out->pass_off = 0;
+    out->tc_off = align16(sizeof(PassDev) * (size_t)np);
+    size_t cur = out->tc_off, total = cur;
+    std::vector<size_t> r0(bl.size(), 0);
+    for (size_t i = 0; i < bl.size(); ++i) {
+        const PassDev* pd = (const PassDev*)(bl[i]->bytes.data() + bl[i]->pass_off);
+        size_t lo = bl[i]->bytes.size();
+        for (int p = 0; p < bl[i]->npasses; ++p) lo = std::min(lo, (size_t)pd[p].region_off);
+        r0[i] = lo;
+        total += bl[i]->bytes.size() - lo;
+    }
+    out->bytes.assign(total, 0);
+    out->max_region = 0;
+    PassDev* dst = (PassDev*)(out->bytes.data() + out->pass_off);
+    int k = 0;
+    for (size_t i = 0; i < bl.size(); ++i) {
+        const PlanBlob& b = *bl[i];
+        const PassDev* pd = (const PassDev*)(b.bytes.data() + b.pass_off);
+        for (int p = 0; p < b.npasses; ++p, ++k) {
+            dst[k] = pd[p];
+            dst[k].region_off = (int)(pd[p].region_off - r0[i] + cur);
+        }
+        if (b.bytes.size() > r0[i]) memcpy(out->bytes.data() + cur, b.bytes.data() + r0[i], b.bytes.size() - r0[i]);
+        cur += b.bytes.size() - r0[i];
+        out->max_region = std::max(out->max_region, b.max_region);
+    }
+}
+
+bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w,
+                const std::vector<const PlanBlob*>* blobs) {
+    if (blobs) merge_blobs(*blobs, &w->blob);
+    else serialise_plans(plans, &w->blob);
     const int RB = reg_bits(dtype);
     const unsigned char* b = w->blob.bytes.data();
     const PassDev* pds = (const PassDev*)(b + w->blob.pass_off);
@@ -378,7 +417,9 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
             }
             if (wc.empty()) continue;
             WaveHost w;
-            if (!build_wave(dt, plans, &w)) {
+            std::vector<const PlanBlob*> blobs;
+            for (int c : wc) blobs.push_back(&prep[c]->blob);
+            if (!build_wave(dt, plans, &w, &blobs)) {
                 rest.insert(rest.end(), wc.begin(), wc.end());
                 continue;
             }

@@ -40,6 +40,7 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
 
 struct Choice {
     std::shared_ptr<const Plan> learned;  // the model's per-pass plan (trial 0), if it found one
+    std::vector<double> pred;             // predicted ms per trial
     std::vector<PlanOptions> trial;  // the learned plan's slot, the model's top whole-circuit candidates, greedy
     std::vector<double> measured;    // ms per trial (-1: not yet)
     double predicted = 0.0;
@@ -51,6 +52,7 @@ struct Choice {
 
 std::mutex g_mu;
 std::unordered_map<uint64_t, Choice> g_cache;
+uint64_t g_last_key = 0;  // the circuit the planner saw last
 int64_t g_planned = 0, g_mispredicted = 0;
 
 }  // namespace
@@ -278,15 +280,26 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
         if (plan_learned(h->n, h->dtype, cg, muxes, base, lp.get(), &lms)) {
             c.learned = lp;
             c.trial.push_back(base);  // (placeholder options of the learned plan's slot)
+            c.pred.push_back(lms);
         }
-        for (int i = 0; i < kExplore - (c.learned ? 1 : 0) && i < (int)ranked.size(); ++i) c.trial.push_back(ranked[i]);
+        for (int i = 0; i < kExplore - (c.learned ? 1 : 0) && i < (int)ranked.size(); ++i) {
+            c.trial.push_back(ranked[i]);
+            c.pred.push_back(rms[i]);
+        }
         c.trial.push_back(base);
+        double gms = -1.0;  // the greedy plan's prediction, where the ranking had its options
+        for (size_t i = 0; i < ranked.size(); ++i)
+            if (ranked[i].k_max == base.k_max && ranked[i].tile_m == base.tile_m && ranked[i].tensor == base.tensor &&
+                ranked[i].pass_kernel == base.pass_kernel && ranked[i].tc_auto == base.tc_auto)
+                gms = rms[i];
+        c.pred.push_back(gms);
         c.measured.assign(c.trial.size(), -1.0);
         c.predicted = c.learned ? lms : rms[0];
         ++g_planned;
         if (g_cache.size() > 4096) g_cache.clear();
         it = g_cache.emplace(key, c).first;
     }
+    g_last_key = key;
     Choice& c = it->second;
     if (c.pending >= 0 && c.e1) {  // collect the previous judged call
         float ms = 0.f;
@@ -337,7 +350,7 @@ extern "C" int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate* gates, si
     chosen->k_max = ranked[0].k_max;
     chosen->tile_m = ranked[0].tile_m;
     chosen->planner = SV_PLAN_GREEDY;
-    chosen->tensor = ranked[0].tensor == 0 ? 1 : -1;
+    chosen->tensor = ranked[0].tensor == 0 ? 1 : (ranked[0].tc_auto ? 0 : -1);
     chosen->pass_kernel = ranked[0].pass_kernel;
     *predicted_ms = rms[0];
     return SV_OK;
@@ -378,8 +391,40 @@ extern "C" int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate* gates, si
     memset(out, 0, sizeof(*out));
     out->k_max = po.k_max;
     out->tile_m = po.tile_m;
-    out->tensor = po.tensor == 0 ? 1 : -1;
+    out->tensor = po.tensor == 0 ? 1 : (po.tc_auto ? 0 : -1);
     out->pass_kernel = po.pass_kernel;
     if (measured_ms) *measured_ms = c.measured[c.calls == (int)c.trial.size() ? c.best : 0];
+    return SV_OK;
+}
+
+// The trials of the circuit the cost-model planner saw last: predicted and
+// measured ms per trial (-1 where not known), the kept trial (-1 before all
+// were timed) and whether trial 0 is the model's own per-pass plan.
+extern "C" int sv_cost_model_last_trials(double* predicted, double* measured, int cap, int* ntrials, int* chosen,
+                                         int* learned) {
+    if (!ntrials || !chosen || !learned || (cap > 0 && (!predicted || !measured)))
+        return set_error(SV_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(g_last_key);
+    if (it == g_cache.end()) return set_error(SV_EINVAL, "no circuit planned by the cost model yet");
+    Choice& c = it->second;
+    if (c.pending >= 0 && c.e1) {  // finish the last judged call
+        float ms = 0.f;
+        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess)
+            c.measured[c.pending] = ms;
+        cudaGetLastError();
+        c.pending = -1;
+        if (c.calls == (int)c.trial.size()) {
+            c.best = (int)(std::min_element(c.measured.begin(), c.measured.end()) - c.measured.begin());
+            if (c.best != 0) ++g_mispredicted;
+        }
+    }
+    *ntrials = (int)c.trial.size();
+    for (int i = 0; i < cap && i < (int)c.trial.size(); ++i) {
+        predicted[i] = i < (int)c.pred.size() ? c.pred[i] : -1.0;
+        measured[i] = c.measured[i];
+    }
+    *chosen = c.calls == (int)c.trial.size() && c.pending < 0 ? c.best : -1;
+    *learned = c.learned ? 1 : 0;
     return SV_OK;
 }

@@ -412,7 +412,11 @@ struct WaveHost {
     std::vector<int> nq;
     uint64_t amps = 0;           // total
 };
-bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w);
+// blobs (optional): the plans' serialised blobs, merged instead of
+// serialising the plans again (the batch frees a plan's multiplexor tables
+// once its blob holds them).
+bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w,
+                const std::vector<const PlanBlob*>* blobs = nullptr);
 // Run a built wave on st in one captured graph; the states stay in *dev_base
 // (allocated here, Σ 2^n amplitudes; the caller frees it).  SV_ETIMEOUT when
 // a wait gave up (limit polls).
