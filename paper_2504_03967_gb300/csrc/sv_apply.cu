@@ -1268,8 +1268,23 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
+// Multiplexor columns of an item (kept out of line: its 2^K-amplitude columns
+// would otherwise raise the register count of the whole kernel).
+template <typename T, typename V>
+__device__ __noinline__ void wave_mux(const unsigned char* __restrict__ region, V* __restrict__ psi, uint64_t lo,
+                                      uint64_t hi) {
+    const MuxDev& D = *(const MuxDev*)region;
+    switch (D.K) {
+    case 1: mux_columns<T, V, 1>(D, region, psi, lo, hi, threadIdx.x, blockDim.x); break;
+    case 2: mux_columns<T, V, 2>(D, region, psi, lo, hi, threadIdx.x, blockDim.x); break;
+    case 3: mux_columns<T, V, 3>(D, region, psi, lo, hi, threadIdx.x, blockDim.x); break;
+    case 4: mux_columns<T, V, 4>(D, region, psi, lo, hi, threadIdx.x, blockDim.x); break;
+    default: mux_columns<T, V, 5>(D, region, psi, lo, hi, threadIdx.x, blockDim.x); break;
+    }
+}
+
 template <typename R, int RB>
-__global__ void __launch_bounds__(256, 1) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
+__global__ void __launch_bounds__(256, 2) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
                                                  const int* __restrict__ nq, const unsigned char* __restrict__ blob,
                                                  const PassDev* __restrict__ pds, const WaveItem* __restrict__ items,
                                                  int nitems, int* __restrict__ head, int* __restrict__ done,
@@ -1316,15 +1331,7 @@ __global__ void __launch_bounds__(256, 1) k_wave(typename CT<R>::V* __restrict__
         const WaveItem I = items[it];
         V* psi = base + offs[I.circ];
         if (I.kind == 1) {  // multiplexor columns
-            const unsigned char* region = blob + pds[I.pass].region_off;
-            const MuxDev& D = *(const MuxDev*)region;
-            switch (D.K) {
-            case 1: mux_columns<T, V, 1>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
-            case 2: mux_columns<T, V, 2>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
-            case 3: mux_columns<T, V, 3>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
-            case 4: mux_columns<T, V, 4>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
-            default: mux_columns<T, V, 5>(D, region, psi, I.lo, I.hi, tid, blockDim.x); break;
-            }
+            wave_mux<T, V>(blob + pds[I.pass].region_off, psi, I.lo, I.hi);
         } else {
             if (I.pass != s_staged) {  // stage the pass: record, region, row offsets, base tables
                 __syncthreads();

@@ -53,9 +53,10 @@ struct Slot {
 // Waves: up to kWaveCircuits circuits whose every pass runs in the persistent
 // wave kernel (register tile passes of 256 threads, multiplexor passes).
 // ---------------------------------------------------------------------------
-constexpr int kWaveCircuits = 64;
-constexpr uint64_t kWaveTiles = 4;      // tiles per item
-constexpr uint64_t kWaveColumns = 4096; // multiplexor columns per item
+constexpr int kWaveCircuits = 256;
+// Items hold as many of a pass's tiles (1..64; a CTA stages the pass's region
+// once per item) or multiplexor columns (at least 1024) as make about four
+// items per CTA at each pass level.
 constexpr unsigned kWaveWaitLimit = 1u << 24;  // polls of about 128 ns: a wait gives up after about 2 s
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -120,7 +121,22 @@ bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w,
     }
     w->items.clear();
     std::vector<int> cum(C, 0);
-    for (int l = 0; l < levels; ++l)
+    const uint64_t target = (uint64_t)device_sms() * 2 * 4;  // about four items per CTA per pass level
+    for (int l = 0; l < levels; ++l) {
+        uint64_t tiles = 0, cols = 0;  // the level's work
+        for (int c = 0; c < C; ++c) {
+            const int p = first[c] + l;
+            if (p >= first[c + 1]) continue;
+            if (pds[p].rmode == kRmodeMux) {
+                MuxDev D;
+                memcpy(&D, b + pds[p].region_off, sizeof(D));
+                cols += 1ull << (plans[c]->n - D.K);
+            } else {
+                tiles += 1ull << (plans[c]->n - pds[p].m);
+            }
+        }
+        const uint64_t tper = std::min<uint64_t>(64, std::max<uint64_t>(1, tiles / target));
+        const uint64_t cper = std::max<uint64_t>(1024, cols / target);
         for (int c = 0; c < C; ++c) {
             const int p = first[c] + l;
             if (p >= first[c + 1]) continue;
@@ -134,27 +150,46 @@ bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w,
                 memcpy(&D, b + pds[p].region_off, sizeof(D));
                 const uint64_t ncols = 1ull << (plans[c]->n - D.K);
                 I.kind = 1;
-                for (uint64_t c0 = 0; c0 < ncols; c0 += kWaveColumns) {
+                const uint64_t per = cper;
+                for (uint64_t c0 = 0; c0 < ncols; c0 += per) {
                     I.lo = c0;
-                    I.hi = std::min(ncols, c0 + kWaveColumns);
+                    I.hi = std::min(ncols, c0 + per);
                     w->items.push_back(I);
                     ++cum[c];
                 }
             } else {
                 const uint64_t ntiles = 1ull << (plans[c]->n - pds[p].m);
                 I.kind = 0;
-                for (uint64_t t0 = 0; t0 < ntiles; t0 += kWaveTiles) {
+                const uint64_t per = tper;
+                for (uint64_t t0 = 0; t0 < ntiles; t0 += per) {
                     I.lo = t0;
-                    I.hi = std::min(ntiles, t0 + kWaveTiles);
+                    I.hi = std::min(ntiles, t0 + per);
                     w->items.push_back(I);
                     ++cum[c];
                 }
             }
         }
+    }
     return true;
 }
 
-int run_wave(int dtype, const WaveHost& w, cudaStream_t st, void** dev_base, unsigned limit) {
+void WaveKeep::release() {
+    for (cudaGraphExec_t x : execs) cudaGraphExecDestroy(x);
+    for (cudaGraph_t g : graphs) cudaGraphDestroy(g);
+    for (void* p : pinned) cudaFreeHost(p);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    execs.clear();
+    graphs.clear();
+    pinned.clear();
+    ev = nullptr;
+    cs = nullptr;
+    cudaGetLastError();
+}
+
+int enqueue_wave(int dtype, const WaveHost& w, cudaStream_t st, unsigned limit, int* dev_err, WaveKeep* keep,
+                 void** dev_base) {
+    *dev_base = nullptr;
     const size_t csz = dtype == SV_C64 ? 8 : 16, C = w.offs.size();
     void *base = nullptr, *blob = nullptr, *pin = nullptr;
     uint64_t* offs = nullptr;
@@ -167,24 +202,21 @@ int run_wave(int dtype, const WaveHost& w, cudaStream_t st, void** dev_base, uns
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&items, ib, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&offs, ob, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&nq, nb, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, sizeof(int) * (C + 2), st);  // head, err, done[C]
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, sizeof(int) * (C + 1), st);  // head, done[C]
     if (e == cudaSuccess) e = cudaMallocHost(&pin, pinb);
-    auto freeall = [&](bool keep_base) {
-        if (!keep_base && base) cudaFreeAsync(base, st);
+    if (pin) keep->pinned.push_back(pin);
+    auto free_tmp = [&]() {  // stream-ordered: after the wave
         if (blob) cudaFreeAsync(blob, st);
         if (items) cudaFreeAsync(items, st);
         if (offs) cudaFreeAsync(offs, st);
         if (nq) cudaFreeAsync(nq, st);
         if (cnt) cudaFreeAsync(cnt, st);
-        if (pin) {
-            cudaStreamSynchronize(st);
-            cudaFreeHost(pin);
-        }
-        cudaGetLastError();
     };
     if (e != cudaSuccess) {
         cudaGetLastError();
-        freeall(false);
+        free_tmp();
+        if (base) cudaFreeAsync(base, st);
+        cudaGetLastError();
         return set_error(SV_ENOMEM, "sv_batch_run: wave allocation failed");
     }
     unsigned char* pc = (unsigned char*)pin;
@@ -197,39 +229,37 @@ int run_wave(int dtype, const WaveHost& w, cudaStream_t st, void** dev_base, uns
     if (e == cudaSuccess) e = cudaMemcpyAsync(offs, pc + w.blob.bytes.size() + ib, ob, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(nq, pc + w.blob.bytes.size() + ib + ob, nb, cudaMemcpyHostToDevice, st);
     // the counters, the |0...0> states and the persistent launch, from one graph
-    cudaStream_t cs = nullptr;
-    cudaEvent_t ev = nullptr;
+    // captured on a private stream (the caller's may be the legacy stream)
+    if (e == cudaSuccess && !keep->cs) e = cudaStreamCreateWithFlags(&keep->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !keep->ev) e = cudaEventCreateWithFlags(&keep->ev, cudaEventDisableTiming);
+    cudaStream_t cs = keep->cs;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(keep->ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, keep->ev, 0);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 2), cs);
+        cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), cs);
         cudaMemsetAsync(base, 0, csz * w.amps, cs);
         launch_wave_init(dtype, base, offs, (int)C, cs);
-        launch_wave(dtype, base, offs, nq, blob, w.blob, items, (int)w.items.size(), cnt, cnt + 2, cnt + 1, limit, cs);
+        launch_wave(dtype, base, offs, nq, blob, w.blob, items, (int)w.items.size(), cnt, cnt + 1, dev_err, limit,
+                    cs);
         e = cudaStreamEndCapture(cs, &graph);
     }
+    if (graph) keep->graphs.push_back(graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (gexec) keep->execs.push_back(gexec);
     if (e == cudaSuccess) e = cudaGraphLaunch(gexec, cs);
-    if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
-    int err = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, cs);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
-    if (ev) cudaEventDestroy(ev);
-    if (cs) cudaStreamDestroy(cs);
-    int rc = SV_OK;
-    if (e != cudaSuccess) rc = cuda_fail(e, "wave");
-    else if (err == 2) rc = set_error(SV_ETIMEOUT, "sv_batch_run: a wait of the wave kernel gave up");
-    freeall(rc == SV_OK);
-    *dev_base = rc == SV_OK ? base : nullptr;
-    return rc;
+    if (e == cudaSuccess) e = cudaEventRecord(keep->ev, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, keep->ev, 0);
+    free_tmp();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, st);
+        cudaGetLastError();
+        return cuda_fail(e, "wave");
+    }
+    *dev_base = base;
+    return SV_OK;
 }
 
 }  // namespace sv
@@ -394,10 +424,25 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
         cudaMemGetInfo(&freeb, &totb);
         const uint64_t budget = std::max<uint64_t>(freeb / 4, 1ull << 28);
         const size_t csz = dt == SV_C64 ? 8 : 16;
-        sv_state hv{};  // a view of one circuit's state for its read-outs
-        hv.dtype = dt;
-        hv.stream = st;
-        hv.pending_basis = -1;
+        // views of one circuit's state for its read-outs, on 4 streams
+        constexpr int kViews = 4;
+        sv_state hv[kViews] = {};
+        cudaStream_t vs[kViews] = {};
+        cudaEvent_t vev = nullptr;
+        cudaEventCreateWithFlags(&vev, cudaEventDisableTiming);
+        for (int v = 0; v < kViews; ++v) {
+            cudaStreamCreateWithFlags(&vs[v], cudaStreamNonBlocking);
+            hv[v].dtype = dt;
+            hv[v].stream = vs[v];
+            hv[v].pending_basis = -1;
+        }
+        int* d_err = nullptr;  // a wait of any wave gave up (2)
+        if (cudaMallocAsync((void**)&d_err, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(SV_ENOMEM, "sv_batch_run: wave error word");
+        }
+        WaveKeep keep;
         size_t i = 0;
         while (rc == SV_OK && i < large.size()) {
             std::vector<int> wc;
@@ -424,24 +469,46 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
                 continue;
             }
             void* base = nullptr;
-            rc = run_wave(dt, w, st, &base, kWaveWaitLimit);
+            rc = enqueue_wave(dt, w, st, kWaveWaitLimit, d_err, &keep, &base);
+            if (rc == SV_OK) {  // the read-out streams start after the wave
+                cudaEventRecord(vev, st);
+                for (int v = 0; v < kViews; ++v) cudaStreamWaitEvent(vs[v], vev, 0);
+            }
             for (size_t k = 0; rc == SV_OK && k < wc.size(); ++k) {
                 const int c = wc[k];
                 const int idx = slot[c];
-                hv.n = n_qubits[c];
-                hv.amps = (char*)base + csz * w.offs[k];
-                reset_perm(&hv);
+                sv_state& h = hv[k % kViews];
+                h.n = n_qubits[c];
+                h.amps = (char*)base + csz * w.offs[k];
+                reset_perm(&h);
                 if (host_samples)
-                    rc = measure_sample(&hv, shots, seed + (uint64_t)c, nullptr, d_samples + (size_t)idx * shots);
-                if (rc == SV_OK && host_expz) rc = measure_expect_z(&hv, d_expz + (size_t)idx * nmax);
+                    rc = measure_sample(&h, shots, seed + (uint64_t)c, nullptr, d_samples + (size_t)idx * shots);
+                if (rc == SV_OK && host_expz) rc = measure_expect_z(&h, d_expz + (size_t)idx * nmax);
+            }
+            for (int v = 0; v < kViews; ++v) {  // the wave's buffer is freed after its read-outs
+                cudaEventRecord(vev, vs[v]);
+                cudaStreamWaitEvent(st, vev, 0);
             }
             if (base) cudaFreeAsync(base, st);
             for (int c : wc) prep[c].reset();
         }
-        cudaStreamSynchronize(st);
-        if (hv.red.ptr) cudaFree(hv.red.ptr);
-        if (hv.perm_tmp.ptr) cudaFree(hv.perm_tmp.ptr);
-        if (hv.lcdf.ptr) cudaFree(hv.lcdf.ptr);
+        int herr = 0;
+        if (d_err) {
+            if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) herr = -1;
+            cudaFreeAsync(d_err, st);
+        }
+        const cudaError_t es = cudaStreamSynchronize(st);
+        if (rc == SV_OK && es != cudaSuccess) rc = cuda_fail(es, "waves");
+        else if (rc == SV_OK && herr == 2) rc = set_error(SV_ETIMEOUT, "sv_batch_run: a wait of the wave kernel gave up");
+        keep.release();
+        for (int v = 0; v < kViews; ++v) {
+            cudaStreamSynchronize(vs[v]);
+            if (hv[v].red.ptr) cudaFree(hv[v].red.ptr);
+            if (hv[v].perm_tmp.ptr) cudaFree(hv[v].perm_tmp.ptr);
+            if (hv[v].lcdf.ptr) cudaFree(hv[v].lcdf.ptr);
+            cudaStreamDestroy(vs[v]);
+        }
+        cudaEventDestroy(vev);
     }
     // 3b. the other large circuits: fused passes on a few streams
     if (rc == SV_OK && !rest.empty()) {
@@ -564,12 +631,24 @@ extern "C" int sv_selftest_wave_timeout(unsigned limit, int* host_status) {
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "stream");
     void* base = nullptr;
-    const int rc = run_wave(SV_C64, w, st, &base, limit);
+    int* d_err = nullptr;
+    int herr = 0;
+    WaveKeep keep;
+    int rc = SV_OK;
+    if (cudaMallocAsync((void**)&d_err, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "error word");
+    if (rc == SV_OK) rc = enqueue_wave(SV_C64, w, st, limit, d_err, &keep, &base);
     if (base) cudaFreeAsync(base, st);
-    cudaStreamSynchronize(st);
+    if (d_err) {
+        cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(d_err, st);
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    keep.release();
     cudaStreamDestroy(st);
+    if (rc == SV_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "wave self-test");
     cudaGetLastError();
-    *host_status = rc == SV_ETIMEOUT ? 1 : 0;
-    if (rc != SV_OK && rc != SV_ETIMEOUT) return rc;
-    return SV_OK;
+    *host_status = herr == 2 ? 1 : 0;
+    return rc;
 }

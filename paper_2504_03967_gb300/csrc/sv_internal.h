@@ -417,10 +417,23 @@ struct WaveHost {
 // once its blob holds them).
 bool build_wave(int dtype, const std::vector<const Plan*>& plans, WaveHost* w,
                 const std::vector<const PlanBlob*>* blobs = nullptr);
-// Run a built wave on st in one captured graph; the states stay in *dev_base
-// (allocated here, Σ 2^n amplitudes; the caller frees it).  SV_ETIMEOUT when
-// a wait gave up (limit polls).
-int run_wave(int dtype, const WaveHost& w, cudaStream_t st, void** dev_base, unsigned limit);
+// Host objects of enqueued waves (pinned staging, graphs, the capture stream),
+// released once the caller's stream has been synchronised.
+struct WaveKeep {
+    std::vector<void*> pinned;
+    std::vector<cudaGraphExec_t> execs;
+    std::vector<cudaGraph_t> graphs;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    void release();
+};
+// Enqueue a built wave on st (one captured graph; nothing waits on the host).
+// The states land in *dev_base (allocated on st, Σ 2^n amplitudes; the caller
+// frees it, stream-ordered).  A wait that gives up after `limit` polls sets
+// *dev_err = 2 (device memory, zeroed by the caller); every CTA of every later
+// wave then stops at once.
+int enqueue_wave(int dtype, const WaveHost& w, cudaStream_t st, unsigned limit, int* dev_err, WaveKeep* keep,
+                 void** dev_base);
 
 // Read-out (sv_measure.cu).  Device outputs; scratch comes from h->red.
 int measure_block_sums(sv_state* h, double** block_sums, int* blog, int64_t* nblocks, int blog_cap = 10);
