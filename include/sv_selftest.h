@@ -51,8 +51,8 @@ int sv_selftest_wait_timeout(unsigned limit, int *host_status);
 
 /* Failure detection in the batch executor's persistent wave kernel
  * (sv_batch_run), without a GPU fault: a wave of one 14-qubit circuit whose
- * only work item is made to wait for a finished item of its circuit that
- * never comes; the wait gives up after limit polls (1..2^22, about 128 ns
+ * first work item is made to wait for more finished items of its circuit
+ * than there can be; the wait gives up after limit polls (1..2^22, about 128 ns
  * each), the kernel records it and returns, and the wave reports
  * SV_ETIMEOUT.  *host_status = 1 when the wait gave up (the expected
  * outcome), 0 otherwise.  Returns SV_OK, SV_EINVAL or SV_ECUDA. */

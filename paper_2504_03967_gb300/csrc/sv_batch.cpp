@@ -601,8 +601,8 @@ extern "C" int sv_batch_run(int C, const int* n_qubits, const int64_t* gate_offs
 
 // ---------------------------------------------------------------------------
 // Failure detection of the wave kernel without a GPU fault: one circuit of 14
-// qubits (an H on every qubit, one pass of 2 tiles, one item) whose only item
-// is made to wait for one finished item of its circuit, which never comes:
+// qubits (an H on every qubit, one pass of 2 tiles) whose first item is made
+// to wait for more finished items of its circuit than there can be:
 // the bounded wait gives up after `limit` polls, the kernel records it and
 // returns, and the call reports SV_ETIMEOUT.  *host_status = 1 when it did.
 // ---------------------------------------------------------------------------
@@ -626,7 +626,9 @@ extern "C" int sv_selftest_wave_timeout(unsigned limit, int* host_status) {
     plan_greedy(n, SV_C64, cg, po, &plan);
     WaveHost w;
     if (!build_wave(SV_C64, {&plan}, &w) || w.items.empty()) return set_error(SV_EINVAL, "internal: wave");
-    w.items[0].need = 1;  // the unsatisfiable dependency
+    // the unsatisfiable dependency: as many finished items as the wave has,
+    // which cannot happen while this one waits
+    w.items[0].need = (int)w.items.size();
     cudaStream_t st = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "stream");
