@@ -1268,10 +1268,9 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
-// Multiplexor columns of an item (kept out of line: its 2^K-amplitude columns
-// would otherwise raise the register count of the whole kernel).
+// Multiplexor columns of an item.
 template <typename T, typename V>
-__device__ __noinline__ void wave_mux(const unsigned char* __restrict__ region, V* __restrict__ psi, uint64_t lo,
+__device__ __forceinline__ void wave_mux(const unsigned char* __restrict__ region, V* __restrict__ psi, uint64_t lo,
                                       uint64_t hi) {
     const MuxDev& D = *(const MuxDev*)region;
     switch (D.K) {
@@ -1283,8 +1282,10 @@ __device__ __noinline__ void wave_mux(const unsigned char* __restrict__ region, 
     }
 }
 
-template <typename R, int RB>
-__global__ void __launch_bounds__(256, 2) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
+// MUX: the instance for waves with multiplexor passes (their 2^K-amplitude
+// columns need the registers of one CTA per SM); the other runs two CTAs per SM.
+template <typename R, int RB, bool MUX>
+__global__ void __launch_bounds__(256, MUX ? 1 : 2) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
                                                  const int* __restrict__ nq, const unsigned char* __restrict__ blob,
                                                  const PassDev* __restrict__ pds, const WaveItem* __restrict__ items,
                                                  int nitems, int* __restrict__ head, int* __restrict__ done,
@@ -1331,7 +1332,7 @@ __global__ void __launch_bounds__(256, 2) k_wave(typename CT<R>::V* __restrict__
         const WaveItem I = items[it];
         V* psi = base + offs[I.circ];
         if (I.kind == 1) {  // multiplexor columns
-            wave_mux<T, V>(blob + pds[I.pass].region_off, psi, I.lo, I.hi);
+            if constexpr (MUX) wave_mux<T, V>(blob + pds[I.pass].region_off, psi, I.lo, I.hi);
         } else {
             if (I.pass != s_staged) {  // stage the pass: record, region, row offsets, base tables
                 __syncthreads();
@@ -1424,6 +1425,22 @@ PassLayout wave_layout(int dtype, const PlanBlob& blob) {
     return lay;
 }
 
+template <typename R, int RB, bool MUX>
+static cudaError_t wave_t(void* base, const uint64_t* offs, const int* nq, const unsigned char* b, const PassDev* pds,
+                          const WaveItem* items, int nitems, int* head, int* done, int* err, const PassLayout& lay,
+                          unsigned limit, cudaStream_t st) {
+    int per_sm = 1;
+    cudaError_t e = cudaFuncSetAttribute(k_wave<R, RB, MUX>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+    if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<R, RB, MUX>, 256, lay.total);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = std::max(1, std::min(num_sms() * per_sm, nitems));
+    count_launch();
+    k_wave<R, RB, MUX><<<grid, 256, lay.total, st>>>((typename CT<R>::V*)base, offs, nq, b, pds, items, nitems, head,
+                                                    done, err, lay, limit);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wave(int dtype, void* base, const uint64_t* offs, const int* nq, const void* blob_dev,
                         const PlanBlob& blob, const WaveItem* items, int nitems, int* head, int* done, int* err,
                         unsigned limit, cudaStream_t st) {
@@ -1431,26 +1448,15 @@ cudaError_t launch_wave(int dtype, void* base, const uint64_t* offs, const int* 
     if (lay.total > kMaxDynSmem) return cudaErrorInvalidValue;
     const unsigned char* b = (const unsigned char*)blob_dev;
     const PassDev* pds = (const PassDev*)(b + blob.pass_off);
-    int per_sm = 1;
-    cudaError_t e = cudaSuccess;
+    bool mux = false;
+    for (int p = 0; p < blob.npasses; ++p)
+        mux |= ((const PassDev*)(blob.bytes.data() + blob.pass_off))[p].rmode == kRmodeMux;
     if (dtype == SV_C64) {
-        e = cudaFuncSetAttribute(k_wave<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
-        if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<float, 5>, 256, lay.total);
-    } else {
-        e = cudaFuncSetAttribute(k_wave<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
-        if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<double, 4>, 256, lay.total);
+        if (mux) return wave_t<float, 5, true>(base, offs, nq, b, pds, items, nitems, head, done, err, lay, limit, st);
+        return wave_t<float, 5, false>(base, offs, nq, b, pds, items, nitems, head, done, err, lay, limit, st);
     }
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int grid = std::max(1, std::min(num_sms() * per_sm, nitems));
-    count_launch();
-    if (dtype == SV_C64)
-        k_wave<float, 5><<<grid, 256, lay.total, st>>>((float2*)base, offs, nq, b, pds, items, nitems, head, done, err,
-                                                       lay, limit);
-    else
-        k_wave<double, 4><<<grid, 256, lay.total, st>>>((double2*)base, offs, nq, b, pds, items, nitems, head, done,
-                                                        err, lay, limit);
-    return cudaGetLastError();
+    if (mux) return wave_t<double, 4, true>(base, offs, nq, b, pds, items, nitems, head, done, err, lay, limit, st);
+    return wave_t<double, 4, false>(base, offs, nq, b, pds, items, nitems, head, done, err, lay, limit, st);
 }
 
 // ---- TMA-fed register passes: tensor map and ring layout -----------------
