@@ -870,7 +870,13 @@ PassLayout rpass_layout(int dtype, const PassDev& P) {
     lay.stage_bytes = P.region_bytes;
     const size_t work = sizeof(uint64_t) * (size_t)P.ndiag * (m + 1) + sizeof(int) * (size_t)P.ndiag;
     const int rest = round128(4 * (size_t)nrows) + round128(lay.stage_bytes) + round128(work);
-    lay.nbuf = 2 * lay.tile_bytes + rest <= kTwoCtaBudget ? 2 : 1;
+    // double-buffered while two CTAs per SM still fit; and also when even one
+    // single-buffered CTA leaves no room for a second (a pass staging several
+    // tensor-core matrices): the SM's only CTA then loads the next tile while
+    // it computes the current one
+    const bool two_single = lay.tile_bytes + rest <= kTwoCtaBudget;
+    lay.nbuf = (2 * lay.tile_bytes + rest <= kTwoCtaBudget ||
+                (!two_single && 2 * lay.tile_bytes + rest + 4096 <= kMaxDynSmem)) ? 2 : 1;
     lay.rowoff_off = lay.nbuf * lay.tile_bytes;
     lay.bres_off = lay.rowoff_off + round128(4 * (size_t)nrows);
     lay.stage_off = lay.bres_off;
@@ -1282,10 +1288,12 @@ __device__ __forceinline__ void wave_mux(const unsigned char* __restrict__ regio
     }
 }
 
-// MUX: the instance for waves with multiplexor passes (their 2^K-amplitude
-// columns need the registers of one CTA per SM); the other runs two CTAs per SM.
+// MUX: the instance for waves with multiplexor passes.  One CTA per SM: the
+// interpreting tile body and the 2^K-amplitude columns keep their registers
+// (measured: at two CTAs per SM the spills' local-memory traffic outweighed
+// the state's).
 template <typename R, int RB, bool MUX>
-__global__ void __launch_bounds__(256, MUX ? 1 : 2) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
+__global__ void __launch_bounds__(256, 1) k_wave(typename CT<R>::V* __restrict__ base, const uint64_t* __restrict__ offs,
                                                  const int* __restrict__ nq, const unsigned char* __restrict__ blob,
                                                  const PassDev* __restrict__ pds, const WaveItem* __restrict__ items,
                                                  int nitems, int* __restrict__ head, int* __restrict__ done,

@@ -20,7 +20,9 @@ namespace sv {
 namespace {
 
 template <typename T, typename C, int K>
-__global__ void __launch_bounds__(256) k_mux(const MuxDev D, const unsigned char* __restrict__ region,
+// Two CTAs per SM (at most 128 registers) except for FP64 columns of 16 or 32
+// amplitudes, which would spill heavily there.
+__global__ void __launch_bounds__(256, (sizeof(T) == 8 && K >= 4) ? 1 : 2) k_mux(const MuxDev D, const unsigned char* __restrict__ region,
                                              C* __restrict__ amps, int n) {
     mux_columns<T, C, K>(D, region, amps, 0, 1ull << (n - K), (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                          (uint64_t)gridDim.x * blockDim.x);

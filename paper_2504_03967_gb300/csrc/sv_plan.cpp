@@ -392,6 +392,11 @@ bool best_gate_sequence(const Block& B, std::vector<GateRec>* recs, std::vector<
 
 constexpr int kMaxBlockGates = 40;  // 20 one-qubit gates and 20 phase tables fit kMaxGateData
 constexpr int kMaxTcBlockGates = 4096;  // a tensor-core block is a dense matrix: any gate count
+// Tensor-core matrices (hi and lo operands) one register pass may stage when
+// the planner chooses them itself: two 5-qubit blocks, which keeps a 13-qubit
+// complex64 pass at two CTAs per SM (measured: a pass staging three ran on one
+// CTA per SM at less than half the speed).
+constexpr int kTcStageBudget = 2 * 2 * (8 << 10);
 
 // Estimated instructions per amplitude of a pass's ops: each block pays its
 // own cost plus a register remap (a shared-memory round trip of the tile),
@@ -730,6 +735,7 @@ void greedy_pass(int n, int dtype, const std::vector<CGate>& gates, const std::v
         DiagForm D;
         D.init(n);
         bool dpend = false;
+        int tc_bytes = 0;  // tensor-core matrices the pass stages so far
         auto flushB = [&]() {
             if (!B.active()) return;
             HostOp op;
@@ -739,12 +745,15 @@ void greedy_pass(int n, int dtype, const std::vector<CGate>& gates, const std::v
             // tensor-core blocks: forced (tensor = 1) or where their cost
             // is below the gate sequence's (the default)
             const bool tc_forced = po.tensor == 0 && dtype == SV_C64 && kb >= 4;
-            const bool tc_auto = tc_auto_ok && (kb == 4 || kb == 5);
+            // (the automatic choice keeps the pass's staged matrices within
+            // kTcStageBudget: beyond it the pass would hold one CTA per SM)
+            const bool tc_auto = tc_auto_ok && (kb == 4 || kb == 5) && tc_bytes + 2 * tc16_bytes(kb) <= kTcStageBudget;
             const bool seq = !tc_forced && kb <= max_gates_k(dtype) && best_gate_sequence(B, &op.recs, &op.gdata);
             const double seq_cost = seq ? gate_sequence_cost(op.recs, &op.gdata) : 1e30;
             if (tc_forced || (tc_auto && seq_cost > tc_cost(kb))) {
                 op.kind = OP_DENSE;
                 op.tc = true;
+                tc_bytes += 2 * tc16_bytes(kb);
                 if (form_matrices) op.mat = block_matrix(B.qubits, B.seq);
                 else op.seq = B.seq;
                 op.recs.clear();
