@@ -94,6 +94,11 @@ def workload(name):
         n = int(name[6:])
         g = W.random_u3_cx(n, 60, W.SEED[4])
         return n, g, 0, "random U3+CX n=%d, 60 layers (%d gates) from |0>" % (n, len(g))
+    if name.startswith("qcrank"):
+        # qcrank<a>x<d>: one QCrank image circuit (2^a addresses, d data qubits)
+        a, d = (int(v) for v in name[6:].split("x"))
+        pix = np.random.default_rng(W.SEED[3]).uniform(0, 1, size=(1 << a, d))
+        return a + d, W.qcrank(a, d, pix), 0, "QCrank a=%d d=%d (n=%d) from |0>" % (a, d, a + d)
     raise SystemExit("unknown workload " + name)
 
 
@@ -341,6 +346,17 @@ def report_batch(args):
     import paper_2504_03967_gb300 as S
 
     out = {"report": "batches and QCrank read-out"}
+    parts = set(args.parts.split(","))
+    if "qcrank" in parts:
+        report_qcrank_batch(S, out)
+    if "ansatz" in parts:
+        report_ansatz(S, out)
+    if "readout" in parts:
+        report_qcrank_readout(S, out, torch)
+    print(json.dumps(out), flush=True)
+
+
+def report_qcrank_batch(S, out):
     batch = W.qcrank_batch(512, W.SEED[3], a_range=(8, 14))
     circuits = [(a + d, W.qcrank(a, d, pix)) for a, d, pix in batch]
     gates = int(sum(len(gl) for _, gl in circuits))
@@ -356,6 +372,9 @@ def report_batch(args):
         S.sv_batch_run(circuits[:32], dtype=S.C64, shots=100000, seed=31, mux=mux)
         dt = time.perf_counter() - t0
         out[tag] = {"circuits": 32, "seconds": dt, "circuits_per_s": 32 / dt}
+
+
+def report_ansatz(S, out):
     params = W.hea_params(4096, 20, 8, W.SEED[5])
     hc = [(20, W.hea(20, 8, params[s])) for s in range(4096)]
     S.sv_batch_run(hc[:256], dtype=S.C64, shots=0)
@@ -363,6 +382,9 @@ def report_batch(args):
     S.sv_batch_run(hc, dtype=S.C64, shots=0)
     dt = time.perf_counter() - t0
     out["ansatz_sweep"] = {"circuits": 4096, "n": 20, "seconds": dt, "circuits_per_s": 4096 / dt}
+
+
+def report_qcrank_readout(S, out, torch):
     a, d = 14, 6
     pix = np.random.default_rng(5).uniform(0, 1, size=(1 << a, d))
     h = S.sv_alloc(a + d, S.C64)
@@ -380,7 +402,6 @@ def report_batch(args):
     out["qcrank_readout"] = {"a": a, "d": d, "shots": shots, "seconds": dt, "shots_per_s": shots / dt,
                              "rms_pixel_error": float(np.sqrt(np.mean(err ** 2))),
                              "shot_noise_rms": float(1.0 / (np.pi * np.sqrt(3000))), "correlation": float(c)}
-    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -403,6 +424,7 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=4)
     ap.add_argument("--no-relabel", action="store_true", help="SWAP gates move amplitudes instead of relabelling")
     ap.add_argument("--no-jit", action="store_true", help="register passes on the interpreting kernel only")
+    ap.add_argument("--parts", default="qcrank,ansatz,readout", help="parts of --report batch to run")
     ap.add_argument("--report", default=None, choices=["approx", "batch"],
                     help="secondary measurements instead of the bench line: approx = QFT fidelity loss and time "
                          "against the rotation-dropping threshold; batch = circuits/s of the QCrank and "

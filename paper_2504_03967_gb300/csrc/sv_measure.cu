@@ -4,8 +4,9 @@
 // Sampling (Sec. 3: shots per circuit) draws outcome = min{x : C_x > u S},
 // C the inclusive CDF of p_x = |a_x|^2 and S = C_{N-1}: a binary search over
 // the FP64 block CDF finds the block, then one warp rescans that block's
-// 2^B amplitudes in FP64 (lane partial sums, warp scan, sequential finish in
-// the chosen lane).
+// 2^B amplitudes in FP64, 32 consecutive amplitudes per step (a coalesced
+// load, a warp scan on top of the running CDF, a ballot for the first lane
+// above u S).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -459,7 +460,6 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const double S = cdf[nblocks - 1];
     const uint64_t len = 1ull << blog;
-    const int per = (int)(len >= 32 ? len / 32 : 1);
     for (uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < shots; s += warps) {
         const double u = u_in ? u_in[s] : philox_uniform(seed, s);
         const double t = u * S;
@@ -473,37 +473,31 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
         const uint64_t j = lo;
         const double before = j ? cdf[j - 1] : 0.0;
         const uint64_t b0 = j << blog;
-        // lane chunk sums over contiguous sub-ranges of the block
-        const uint64_t c0 = b0 + (uint64_t)lane * per;
-        double ls = 0.0;
-        if ((uint64_t)lane * per < len)
-            for (int i = 0; i < per; ++i) ls += prob(amp(c0 + i));
-        double inc = ls;
+        // rescan the block 32 amplitudes at a time (one coalesced load per
+        // step): an FP64 warp scan of the step's probabilities on top of the
+        // running CDF, and the first lane whose CDF exceeds t (and whose
+        // probability is not zero) is the outcome
+        double base = before;
+        uint64_t pick = UINT64_MAX, last_nz = b0;
+        for (uint64_t c = 0; c < len; c += 32) {
+            const bool valid = c + lane < len;
+            const double p = valid ? prob(amp(b0 + c + lane)) : 0.0;
+            double inc = p;
 #pragma unroll
-        for (int sh = 1; sh < 32; sh <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, inc, sh);
-            if (lane >= sh) inc += y;
-        }
-        const unsigned hit = __ballot_sync(0xffffffffu, before + inc > t && (uint64_t)lane * per < len);
-        // last lane holding a non-zero probability (fallback when rounding
-        // leaves no lane above t)
-        const unsigned nz = __ballot_sync(0xffffffffu, ls > 0.0);
-        int L = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);
-        if (lane == L) {
-            double acc = before + (inc - ls);
-            const uint64_t cb = b0 + (uint64_t)L * per;
-            uint64_t pick = UINT64_MAX, last_nz = cb;
-            for (int i = 0; i < per && (uint64_t)L * per + i < len; ++i) {
-                const double p = prob(amp(cb + i));
-                if (p > 0.0) last_nz = cb + i;
-                acc += p;
-                if (acc > t && p > 0.0) {
-                    pick = cb + i;
-                    break;
-                }
+            for (int sh = 1; sh < 32; sh <<= 1) {
+                const double y = __shfl_up_sync(0xffffffffu, inc, sh);
+                if (lane >= sh) inc += y;
             }
-            out[s] = pick == UINT64_MAX ? last_nz : pick;
+            const unsigned hit = __ballot_sync(0xffffffffu, valid && p > 0.0 && base + inc > t);
+            if (hit) {
+                pick = b0 + c + (uint64_t)(__ffs(hit) - 1);
+                break;
+            }
+            const unsigned nz = __ballot_sync(0xffffffffu, p > 0.0);
+            if (nz) last_nz = b0 + c + (uint64_t)(31 - __clz(nz));  // fallback when rounding leaves no x above t
+            base += __shfl_sync(0xffffffffu, inc, 31);
         }
+        if (lane == 0) out[s] = pick == UINT64_MAX ? last_nz : pick;
     }
 }
 
