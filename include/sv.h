@@ -152,6 +152,8 @@ typedef struct {
     int64_t mux_ops;      /* recognised multiplexors (each one target) */
     int64_t mux_passes;   /* passes that apply multiplexors */
     int64_t tc_ops;       /* of dense_ops, the blocks applied on the tensor cores */
+    int64_t warp_remaps;  /* of remaps, those that keep every warp's amplitudes
+                             within the warp (ordered by a warp barrier) */
 } sv_plan_info;
 
 /* ---- state lifetime (App. A, Eq. "hilbert") ---------------------------- */
@@ -433,9 +435,11 @@ int sv_autotune(sv_handle h, const sv_gate *gates, size_t count, const char *cac
  * every candidate fusion width k (2..5), tile width m and tensor-core choice,
  * predicts the total time and keeps the fastest; the greedy fixed-width plan
  * is the fallback when no model is loaded and the judge of the prediction:
- * the first calls for a circuit time the model's three best candidates and
- * the greedy plan with CUDA events, and later calls use whichever measured
- * fastest.  Plans are exact either way. */
+ * the first 2T calls for a circuit (T trials: the model's per-pass plan and
+ * best whole-circuit candidates, and the greedy plan) time every trial twice
+ * with CUDA events, rounds interleaved, and later calls use the trial with
+ * the fastest time, the greedy plan unless another beats it by more than 1%.
+ * Plans are exact either way. */
 
 /* Train on count recorded passes (features count x sv_feature_count()
  * floats, times in ms) on the GPU with the library's own forward, backward and
@@ -457,8 +461,7 @@ int sv_cost_model_predict(const float *host_feat, int count, double *host_ms);
 int sv_cost_model_choose(int n, sv_dtype dt, const sv_gate *gates, size_t count, sv_options *chosen,
                          double *predicted_ms);
 /* Counters: circuits planned by the model, and judged mispredictions (the
- * model's first choice was not the fastest of the plans the judge timed: its
- * top three and the greedy plan). */
+ * judge did not keep the model's first choice). */
 int sv_cost_model_stats(int64_t *planned, int64_t *mispredicted);
 /* The options the judge settled on for a circuit already applied with
  * SV_PLAN_MLP (the model's first choice until all judged calls are done) and
@@ -470,7 +473,8 @@ int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate *gates, size_t count,
  * last: trial 0 is the model's own plan (passes chosen one at a time by
  * predicted time) when it found one (*learned = 1), then the model's best
  * whole-circuit option sets, last the greedy plan.  predicted[i] and
- * measured[i] in ms (-1 where not known) for i < min(cap, *ntrials);
+ * measured[i] in ms (the faster of its timed calls, -1 where not known) for
+ * i < min(cap, *ntrials);
  * *chosen = the trial kept (-1 until every trial was timed). */
 int sv_cost_model_last_trials(double *predicted, double *measured, int cap, int *ntrials, int *chosen,
                               int *learned);

@@ -48,7 +48,7 @@ class sv_plan_info(ctypes.Structure):
                 ("diag_ops", ctypes.c_int64), ("max_k", ctypes.c_int64), ("bytes_moved", ctypes.c_int64),
                 ("gate_ops", ctypes.c_int64), ("reg_passes", ctypes.c_int64), ("remaps", ctypes.c_int64),
                 ("mux_ops", ctypes.c_int64), ("mux_passes", ctypes.c_int64),
-                ("tc_ops", ctypes.c_int64)]
+                ("tc_ops", ctypes.c_int64), ("warp_remaps", ctypes.c_int64)]
 
 
 class sv_plan_op(ctypes.Structure):

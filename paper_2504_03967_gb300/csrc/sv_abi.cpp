@@ -392,7 +392,10 @@ int sv_plan_circuit(int n, sv_dtype dt, const sv_gate* gates, size_t count, cons
             if (pd[i].rmode != 1 && pd[i].rmode != 2) continue;
             info->reg_passes++;
             const OpDev* od = (const OpDev*)(blob.bytes.data() + pd[i].region_off);
-            for (int o = 0; o < pd[i].nops; ++o) info->remaps += od[o].kind == OP_REMAP;
+            for (int o = 0; o < pd[i].nops; ++o) {
+                info->remaps += od[o].kind == OP_REMAP;
+                info->warp_remaps += od[o].kind == OP_REMAP && od[o].nrec == 1;
+            }
         }
     }
     return SV_OK;
@@ -635,6 +638,9 @@ int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, c
     std::vector<void*> jit_fns;
     void* fill0 = nullptr;
     jit_prepare(h, blob, plan.jit, h->pending_basis, &jit_fns, &fill0, jit_srcs);
+    // the judge times everything the call puts on the stream from here on
+    // (a deferred |x> written by its own kernel included), as a caller does
+    if (judge0) cudaEventRecord(judge0, h->stream);
     long long basis = -1;
     if (h->pending_basis >= 0) {
         if (fill0) {
@@ -675,7 +681,6 @@ int launch_plan(sv_state* h, const Plan& plan, const PlanBlob& blob, bool rec, c
     e = cudaEventRecord(h->upload_ev, h->stream);
     if (e != cudaSuccess) return fail_state(h, cuda_fail(e, "upload event"));
     h->upload_pending = true;
-    if (judge0) cudaEventRecord(judge0, h->stream);
     for (int p = 0; p < blob.npasses; ++p) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (rec && (e0 = next_event(h)) && (e1 = next_event(h))) cudaEventRecord(e0, h->stream);

@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_rpass_tma(int n, const PassDev* __r
     }
 }
 
-PassLayout rpass_layout(int dtype, const PassDev& P) {
+PassLayout rpass_layout(int dtype, const PassDev& P, bool single) {
     const size_t csz = dtype == SV_C64 ? 8 : 16;
     const int m = P.m;
     const int nrows = 1 << (m - P.L);
@@ -875,8 +875,8 @@ PassLayout rpass_layout(int dtype, const PassDev& P) {
     // tensor-core matrices): the SM's only CTA then loads the next tile while
     // it computes the current one
     const bool two_single = lay.tile_bytes + rest <= kTwoCtaBudget;
-    lay.nbuf = (2 * lay.tile_bytes + rest <= kTwoCtaBudget ||
-                (!two_single && 2 * lay.tile_bytes + rest + 4096 <= kMaxDynSmem)) ? 2 : 1;
+    lay.nbuf = !single && (2 * lay.tile_bytes + rest <= kTwoCtaBudget ||
+                           (!two_single && 2 * lay.tile_bytes + rest + 4096 <= kMaxDynSmem)) ? 2 : 1;
     lay.rowoff_off = lay.nbuf * lay.tile_bytes;
     lay.bres_off = lay.rowoff_off + round128(4 * (size_t)nrows);
     lay.stage_off = lay.bres_off;

@@ -7,8 +7,9 @@
 // candidates by predicted total.  The greedy fixed-width plan is the fallback
 // when no model is loaded and the judge of the prediction: the first calls
 // for a circuit time the model's top few candidates and the greedy plan with
-// CUDA events, and later calls keep whichever measured fastest.  A
-// misprediction is counted when the model's first choice was not the fastest.
+// CUDA events (two interleaved rounds), and later calls keep whichever
+// measured fastest, the greedy plan unless another beats it by more than 1%.
+// A misprediction is counted when the model's first choice was not kept.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -54,6 +55,35 @@ std::mutex g_mu;
 std::unordered_map<uint64_t, Choice> g_cache;
 uint64_t g_last_key = 0;  // the circuit the planner saw last
 int64_t g_planned = 0, g_mispredicted = 0;
+
+// The judge times every trial twice, the rounds interleaved, and keeps each
+// trial's faster time; another trial replaces the greedy plan only when it
+// beats it by more than kKeepGreedy (one timing's noise is not a gain).
+constexpr int kRounds = 2;
+constexpr double kKeepGreedy = 0.01;
+
+bool judged(const Choice& c) { return c.calls == kRounds * (int)c.trial.size(); }
+
+// Collect the timing of the last judged call (g_mu held); settle once every
+// round has been timed.  The greedy plan is the last trial.
+void collect(Choice& c) {
+    if (c.pending < 0 || !c.e1) return;
+    float ms = 0.f;
+    if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess) {
+        double& t = c.measured[c.pending];
+        t = t < 0 ? (double)ms : std::min(t, (double)ms);
+    }
+    cudaGetLastError();
+    c.pending = -1;
+    if (!judged(c)) return;
+    const int g = (int)c.trial.size() - 1;
+    int best = -1;
+    for (int i = 0; i <= g; ++i)
+        if (c.measured[i] >= 0 && (best < 0 || c.measured[i] < c.measured[best])) best = i;
+    if (best < 0 || (c.measured[g] >= 0 && c.measured[g] <= (1.0 + kKeepGreedy) * c.measured[best])) best = g;
+    c.best = best;
+    if (c.best != 0) ++g_mispredicted;
+}
 
 }  // namespace
 
@@ -301,29 +331,19 @@ PlanOptions mlp_plan_options(sv_state* h, const sv_gate* g, size_t count, const 
     }
     g_last_key = key;
     Choice& c = it->second;
-    if (c.pending >= 0 && c.e1) {  // collect the previous judged call
-        float ms = 0.f;
-        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess)
-            c.measured[c.pending] = ms;
-        cudaGetLastError();
-        c.pending = -1;
-        if (c.calls == (int)c.trial.size()) {
-            c.best = (int)(std::min_element(c.measured.begin(), c.measured.end()) - c.measured.begin());
-            if (c.best != 0) ++g_mispredicted;
-        }
-    }
-    const int call = c.calls;
-    if (call < (int)c.trial.size()) {
+    collect(c);  // the previous judged call
+    const int call = c.calls, T = (int)c.trial.size();
+    if (call < kRounds * T) {
         ++c.calls;
         if (!c.e0) {
             cudaEventCreate(&c.e0);
             cudaEventCreate(&c.e1);
         }
-        c.pending = call;
+        c.pending = call % T;
         *ev0 = c.e0;
         *ev1 = c.e1;
-        if (call == 0 && c.learned) *learned = c.learned;
-        return c.trial[call];
+        if (call % T == 0 && c.learned) *learned = c.learned;
+        return c.trial[call % T];
     }
     if (c.best == 0 && c.learned) *learned = c.learned;
     return c.trial[c.best];
@@ -376,24 +396,14 @@ extern "C" int sv_cost_model_judged(int n, sv_dtype dt, const sv_gate* gates, si
     auto it = g_cache.find(key);
     if (it == g_cache.end()) return set_error(SV_EINVAL, "circuit not planned by the cost model yet");
     Choice& c = it->second;
-    if (c.pending >= 0 && c.e1) {  // finish the last judged call
-        float ms = 0.f;
-        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess)
-            c.measured[c.pending] = ms;
-        cudaGetLastError();
-        c.pending = -1;
-        if (c.calls == (int)c.trial.size()) {
-            c.best = (int)(std::min_element(c.measured.begin(), c.measured.end()) - c.measured.begin());
-            if (c.best != 0) ++g_mispredicted;
-        }
-    }
-    const PlanOptions& po = c.trial[c.calls == (int)c.trial.size() ? c.best : 0];
+    collect(c);  // the last judged call
+    const PlanOptions& po = c.trial[judged(c) ? c.best : 0];
     memset(out, 0, sizeof(*out));
     out->k_max = po.k_max;
     out->tile_m = po.tile_m;
     out->tensor = po.tensor == 0 ? 1 : (po.tc_auto ? 0 : -1);
     out->pass_kernel = po.pass_kernel;
-    if (measured_ms) *measured_ms = c.measured[c.calls == (int)c.trial.size() ? c.best : 0];
+    if (measured_ms) *measured_ms = c.measured[judged(c) ? c.best : 0];
     return SV_OK;
 }
 
@@ -408,23 +418,13 @@ extern "C" int sv_cost_model_last_trials(double* predicted, double* measured, in
     auto it = g_cache.find(g_last_key);
     if (it == g_cache.end()) return set_error(SV_EINVAL, "no circuit planned by the cost model yet");
     Choice& c = it->second;
-    if (c.pending >= 0 && c.e1) {  // finish the last judged call
-        float ms = 0.f;
-        if (cudaEventSynchronize(c.e1) == cudaSuccess && cudaEventElapsedTime(&ms, c.e0, c.e1) == cudaSuccess)
-            c.measured[c.pending] = ms;
-        cudaGetLastError();
-        c.pending = -1;
-        if (c.calls == (int)c.trial.size()) {
-            c.best = (int)(std::min_element(c.measured.begin(), c.measured.end()) - c.measured.begin());
-            if (c.best != 0) ++g_mispredicted;
-        }
-    }
+    collect(c);  // the last judged call
     *ntrials = (int)c.trial.size();
     for (int i = 0; i < cap && i < (int)c.trial.size(); ++i) {
         predicted[i] = i < (int)c.pred.size() ? c.pred[i] : -1.0;
         measured[i] = c.measured[i];
     }
-    *chosen = c.calls == (int)c.trial.size() && c.pending < 0 ? c.best : -1;
+    *chosen = judged(c) && c.pending < 0 ? c.best : -1;
     *learned = c.learned ? 1 : 0;
     return SV_OK;
 }

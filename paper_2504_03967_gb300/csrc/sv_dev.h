@@ -64,7 +64,7 @@ struct OpDev {
     int ngates;
     int tc;        // dense on the tensor cores (c64, k >= 3)
     int tc_off;    // float offset of its B operands [hi | lo] in the tc section
-    int nrec;      // gates: number of records
+    int nrec;      // gates: number of records; remap: 1 when every warp's amplitudes stay within the warp
     int rec_off;   // gates: byte offset of the records
     int ndata;     // gates: complex values at mat_off
     int ord;       // register passes, diag: ordinal of the run within the pass

@@ -350,7 +350,7 @@ cudaError_t launch_plain_op(sv_state* h, const PlainOp& op);
 cudaError_t launch_pass(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass,
                         const HostPass& hp);
 cudaError_t launch_mux(sv_state* h, const void* blob_dev, const PlanBlob& blob, int pass);
-PassLayout rpass_layout(int dtype, const PassDev& P);
+PassLayout rpass_layout(int dtype, const PassDev& P, bool single = false);  // single: one tile buffer
 // CTAs of `threads` threads an SM holds by registers (regs per thread),
 // shared memory (smem bytes per CTA, static + dynamic) and TMEM columns (128
 // per 128 threads, for passes with tensor-core blocks).

@@ -157,6 +157,72 @@ CtLayout ct_layout(int dtype, int RB, int tb, const int* rp, const int* tp) {
     return L;
 }
 
+// A register layout whose warp accesses to global memory cover runs of at
+// least 32 bytes: the lanes (thread bits 0..4) hold tile positions 0 and 1
+// (complex64 with position 0 at register bit 0, moved as 16-byte pairs:
+// position 1; complex128: position 0).  Tile positions 0..L-1 are qubits
+// 0..L-1, contiguous in the state.
+bool direct_ok(int dtype, int RB, int tb, const int* rp, const int* tp) {
+    const int nl = std::min(5, tb);
+    auto lane = [&](int q) { return std::find(tp, tp + nl, q) != tp + nl; };
+    (void)RB;
+    if (dtype != SV_C64) return lane(0);
+    return rp[0] == 0 ? lane(1) : lane(0) && lane(1);
+}
+
+// load (name "ld") / store_regs ("st"): the registers of layout rp/tp moved
+// straight between the state and registers.  Register k of thread t is
+// amplitude base + G(t) + KR[k], G(t) = the thread bits at their qubits; the
+// deferred-basis variant (fill) builds |x> in the registers instead.
+void emit_direct(std::ostringstream& o, const char* name, const PassDev& P, int dtype, int RB, int tb, const int* rp,
+                 const int* tp, bool load, bool fill) {
+    const bool pair = dtype == SV_C64 && rp[0] == 0;  // registers 2j, 2j + 1 adjacent in the state
+    o << "static constexpr unsigned long long " << name << "_KR[" << (1 << RB) << "] = {";
+    for (int k = 0; k < (1 << RB); ++k) {
+        unsigned long long off = 0;
+        for (int b = 0; b < RB; ++b)
+            if ((k >> b) & 1) off |= 1ull << P.tq[rp[b]];
+        o << (k ? ", " : "") << off << "ull";
+    }
+    o << "};\n";
+    o << "static constexpr int " << name << "_TQ[" << tb << "] = {";
+    for (int t = 0; t < tb; ++t) o << (t ? ", " : "") << P.tq[tp[t]];
+    o << "};\n";
+    o << "static __device__ __forceinline__ uint64_t " << name << "_goff() {\nuint64_t g = 0;\n#pragma unroll\n"
+      << "for (int t = 0; t < " << tb << "; ++t) g |= (uint64_t)((threadIdx.x >> t) & 1) << " << name
+      << "_TQ[t];\nreturn g;\n}\n";
+    if (load) {
+        o << "template <typename V>\nstatic __device__ __forceinline__ void load(V* v, const V* __restrict__ psi, "
+             "uint64_t base, const PassDev& P) {\n"
+          << "const uint64_t g = base + " << name << "_goff();\n";
+        if (fill) {
+            o << "const unsigned long long x = (unsigned long long)P.basis;\n#pragma unroll\n"
+              << "for (int k = 0; k < " << (1 << RB) << "; ++k) {\nv[k].x = g + " << name
+              << "_KR[k] == x ? 1 : 0;\nv[k].y = 0;\n}\n";
+        } else if (pair) {
+            o << "#pragma unroll\nfor (int k = 0; k < " << (1 << RB) << "; k += 2) {\n"
+              << "const float4 q = *reinterpret_cast<const float4*>(psi + g + " << name << "_KR[k]);\n"
+              << "v[k].x = q.x;\nv[k].y = q.y;\nv[k + 1].x = q.z;\nv[k + 1].y = q.w;\n}\n";
+        } else {
+            o << "#pragma unroll\nfor (int k = 0; k < " << (1 << RB) << "; ++k) v[k] = psi[g + " << name
+              << "_KR[k]];\n";
+        }
+        o << "}\n";
+    } else {
+        o << "template <typename V>\nstatic __device__ __forceinline__ void store_regs(const V* v, V* __restrict__ psi, "
+             "uint64_t base) {\n"
+          << "const uint64_t g = base + " << name << "_goff();\n";
+        if (pair) {
+            o << "#pragma unroll\nfor (int k = 0; k < " << (1 << RB) << "; k += 2)\n"
+              << "*reinterpret_cast<float4*>(psi + g + " << name
+              << "_KR[k]) = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);\n";
+        } else {
+            o << "#pragma unroll\nfor (int k = 0; k < " << (1 << RB) << "; ++k) psi[g + " << name << "_KR[k]] = v[k];\n";
+        }
+        o << "}\n";
+    }
+}
+
 // The pass as straight-line code (mirrors InterpOps op by op).  Returns
 // false for a structure it does not take.
 bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int maxt, int minb, std::string* out,
@@ -225,8 +291,8 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
          "static __device__ __forceinline__ void tile(V* v, V* tile, const PassDev& P, const unsigned char* stage,\n"
          "                                            const uint64_t* fold, RegLayout<V, RB>& Lg, const double2* ttab,\n"
          "                                            TcCtx& T) {\n";
-    int rpos[8] = {0}, tpos[16] = {0};
-    bool in_regs = false;
+    int rpos[8] = {0}, tpos[16] = {0}, nrpos[8] = {0}, ntpos[16] = {0}, frpos[8] = {0}, ftpos[16] = {0};
+    bool in_regs = false, direct_load = false;
     CtLayout cur;
     int nl = 0;
     auto emit_rw = [&](const char* fn, const CtLayout& Lc, int id) {
@@ -243,16 +309,28 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
         const OpDev& op = ops[oi];
         switch (op.kind) {
         case OP_REMAP: {
-            if (in_regs) {
-                o << "__syncthreads();\n";
-                emit_rw("reg_write_ct", cur, nl);
-            }
-            o << "__syncthreads();\n";
-            for (int b = 0; b < RB; ++b) rpos[b] = op.lq[b];
+            // no barrier before the write (a warp writes exactly the positions
+            // it read last); a warp barrier after it when every warp's
+            // amplitudes stay within the warp (nrec = 1), else a block barrier
+            for (int b = 0; b < RB; ++b) nrpos[b] = op.lq[b];
             const int* tp = (const int*)(region + op.mat_off);
-            for (int t = 0; t < tb; ++t) tpos[t] = tp[t];
+            for (int t = 0; t < tb; ++t) ntpos[t] = tp[t];
+            if (in_regs) {
+                emit_rw("reg_write_ct", cur, nl);
+                o << (op.nrec == 1 ? "__syncwarp();\n" : "__syncthreads();\n");
+            } else {
+                // the first layout: loaded straight into registers when its
+                // warp accesses cover runs of 32 bytes or more
+                direct_load = direct_ok(dtype, RB, tb, nrpos, ntpos);
+                std::copy(nrpos, nrpos + RB, frpos);
+                std::copy(ntpos, ntpos + tb, ftpos);
+                if (!direct_load) o << "__syncthreads();\n";
+            }
+            std::copy(nrpos, nrpos + RB, rpos);
+            std::copy(ntpos, ntpos + tb, tpos);
             cur = ct_layout(dtype, RB, tb, rpos, tpos);
-            emit_rw("reg_read_ct", cur, ++nl);
+            ++nl;
+            if (in_regs || !direct_load) emit_rw("reg_read_ct", cur, nl);
             // passes with tensor-core blocks restore each tile's norm as loaded
             if (!in_regs && P.tc_k) o << "warp_norm_to<RB>((const float2*)v, T.nin);\n";
             in_regs = true;
@@ -330,14 +408,15 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
     o << "template <typename V, typename R, int RB>\n"
          "static __device__ __forceinline__ void finish(V* v, V* tile, const PassDev& P, const RegLayout<V, RB>&,\n"
          "                                              TcCtx& T) {\n";
+    // the last layout goes straight to global memory when its warp accesses
+    // cover runs of 32 bytes or more
+    const bool direct_store = direct_ok(dtype, RB, tb, rpos, tpos);
     if (P.tc_k) {
         // the tile's norm as loaded (every op is unitary on the tile): the
         // scale is sqrt(in / out) with the sign of the deferred factors, which
         // it also undoes
         o << "warp_norm_to<RB>((const float2*)v, T.nout);\n__syncthreads();\n"
           << "scale_regs<V, RB>(v, copysignf(tile_norm_fix(T.nin, T.nout), (float)P.scale));\n";
-        emit_rw("reg_write_ct", cur, nl);
-        o << "}\n};\n}  // namespace sv\n";
     } else if (scaled) {
         o << "scale_regs<V, RB>(v, (R)P.scale);\n";
     } else if (P.scale != 1.0) {
@@ -345,11 +424,14 @@ bool pass_source(const PassDev& P, const unsigned char* region, int dtype, int m
         snprintf(buf, sizeof(buf), "%.17g", P.scale);
         o << "scale_regs<V, RB>(v, (R)" << buf << ");\n";
     }
-    if (!P.tc_k) {
-        o << "__syncthreads();\n";
-        emit_rw("reg_write_ct", cur, nl);
-        o << "}\n};\n}  // namespace sv\n";
-    }
+    // else each warp writes back the positions it read last (no barrier needed)
+    if (!direct_store) emit_rw("reg_write_ct", cur, nl);
+    o << "}\n";
+    o << "static constexpr bool kDirectLoad = " << (direct_load ? "true" : "false")
+      << ", kDirectStore = " << (direct_store ? "true" : "false") << ";\n";
+    if (direct_load) emit_direct(o, "ld", P, dtype, RB, tb, frpos, ftpos, true, fill);
+    if (direct_store) emit_direct(o, "st", P, dtype, RB, tb, rpos, tpos, false, false);
+    o << "};\n}  // namespace sv\n";
     const char* R = dtype == SV_C64 ? "float" : "double";
     o << "extern \"C\" __global__ void __launch_bounds__(" << maxt << ", " << minb << ") sv_jit_pass(\n"
       << "    sv::CT<" << R << ">::V* __restrict__ psi, int n, const sv::PassDev* __restrict__ pdp,\n"
@@ -375,6 +457,7 @@ struct Entry {
     int state = JIT_NEW;
     CUfunction fn = nullptr;
     int attr_bytes = 0;
+    bool direct_load = false;  // the kernel loads its first layout straight into registers (one tile buffer)
 };
 
 std::mutex g_mu;
@@ -439,6 +522,7 @@ void compile_all(const std::vector<std::string>& srcs) {
     for (size_t i = 0; i < srcs.size(); ++i) {
         Entry& e = g_cache[srcs[i]];
         e.fn = fns[i];
+        e.direct_load = srcs[i].find("kDirectLoad = true") != std::string::npos;
         e.state = fns[i] ? JIT_READY : JIT_FAILED;
         (fns[i] ? g_compiled : g_failed)++;
         if (!logs[i].empty()) g_last_log = logs[i];
@@ -503,7 +587,7 @@ cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const Pla
     const Driver& dr = driver();
     const PassDev* pd = (const PassDev*)(blob.bytes.data() + blob.pass_off) + pass;
     const int tb = pd->m - reg_bits(h->dtype);
-    const PassLayout lay = rpass_layout(h->dtype, *pd);
+    const PassLayout lay = rpass_layout(h->dtype, *pd, e.direct_load);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (lay.total > e.attr_bytes) {

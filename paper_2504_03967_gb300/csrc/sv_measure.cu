@@ -51,6 +51,19 @@ __device__ __forceinline__ void ff_add(FF& a, float x, float xl) {
     a.hi = s;
 }
 __device__ __forceinline__ double ff_val(FF a) { return (double)a.hi + (double)a.lo; }
+// A double as a float pair (hi + lo carries about 48 of its bits).
+__device__ __forceinline__ FF ff_of(double d) {
+    const float h = (float)d;
+    return FF{h, (float)(d - (double)h)};
+}
+// |a|^2 of a complex64 amplitude as an unevaluated float pair: the squares
+// exactly by fma, their sum by TwoSum.
+__device__ __forceinline__ FF ff_prob(float2 v) {
+    const float r2 = v.x * v.x, r2e = fmaf(v.x, v.x, -r2);
+    const float i2 = v.y * v.y, i2e = fmaf(v.y, v.y, -i2);
+    const float sum = r2 + i2, bb = sum - r2;
+    return FF{sum, ((r2 - (sum - bb)) + (i2 - bb)) + r2e + i2e};
+}
 // Sum over the warp in double-float (every lane gets it); no FP64 instruction.
 __device__ __forceinline__ FF ff_allreduce(FF a) {
 #pragma unroll
@@ -463,22 +476,60 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
     for (uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < shots; s += warps) {
         const double u = u_in ? u_in[s] : philox_uniform(seed, s);
         const double t = u * S;
-        // first block j with cdf[j] > t
-        uint64_t lo = 0, hi = nblocks - 1;
-        while (lo < hi) {
-            const uint64_t mid = lo + (hi - lo) / 2;
-            if (cdf[mid] > t) hi = mid;
-            else lo = mid + 1;
+        // first block j with cdf[j] > t (the last block if rounding leaves
+        // none): a 32-way search, each lane testing one of 32 evenly spaced
+        // entries of [lo, hi), so 2^18 blocks take four steps; the answer
+        // stays in [lo, hi) and lane 31 always tests hi - 1
+        uint64_t lo = 0, hi = nblocks;
+        while (hi - lo > 1) {
+            const uint64_t step = (hi - lo + 31) >> 5;
+            const uint64_t at = min(lo + (uint64_t)(lane + 1) * step, hi) - 1;
+            const unsigned yes = __ballot_sync(0xffffffffu, at == nblocks - 1 || cdf[at] > t);
+            const int f = __ffs(yes) - 1;
+            const uint64_t at_f = __shfl_sync(0xffffffffu, at, f);
+            const uint64_t at_p = __shfl_sync(0xffffffffu, at, f > 0 ? f - 1 : 0);
+            hi = at_f + 1;
+            if (f > 0) lo = at_p + 1;
         }
         const uint64_t j = lo;
         const double before = j ? cdf[j - 1] : 0.0;
         const uint64_t b0 = j << blog;
         // rescan the block 32 amplitudes at a time (one coalesced load per
-        // step): an FP64 warp scan of the step's probabilities on top of the
+        // step): a warp scan of the step's probabilities on top of the
         // running CDF, and the first lane whose CDF exceeds t (and whose
-        // probability is not zero) is the outcome
-        double base = before;
+        // probability is not zero) is the outcome.  complex64: |a|^2 as an
+        // exact float pair and the scan in double-float (about 48 bits; no
+        // FP64 instruction in the loop); complex128: FP64.
         uint64_t pick = UINT64_MAX, last_nz = b0;
+        if constexpr (sizeof(V) == 8) {
+            const FF tf = ff_of(t);
+            FF base = ff_of(before);
+            for (uint64_t c = 0; c < len; c += 32) {
+                const bool valid = c + lane < len;
+                FF p = {0.f, 0.f};
+                if (valid) p = ff_prob(amp(b0 + c + lane));
+                FF inc = p;
+#pragma unroll
+                for (int sh = 1; sh < 32; sh <<= 1) {
+                    const float h = __shfl_up_sync(0xffffffffu, inc.hi, sh), l = __shfl_up_sync(0xffffffffu, inc.lo, sh);
+                    if (lane >= sh) ff_add(inc, h, l);
+                }
+                FF cum = base;
+                ff_add(cum, inc.hi, inc.lo);
+                const float above = (cum.hi - tf.hi) + (cum.lo - tf.lo);  // sign of cum - t
+                const unsigned hit = __ballot_sync(0xffffffffu, valid && p.hi > 0.f && above > 0.f);
+                if (hit) {
+                    pick = b0 + c + (uint64_t)(__ffs(hit) - 1);
+                    break;
+                }
+                const unsigned nz = __ballot_sync(0xffffffffu, p.hi > 0.f);
+                if (nz) last_nz = b0 + c + (uint64_t)(31 - __clz(nz));
+                ff_add(base, __shfl_sync(0xffffffffu, inc.hi, 31), __shfl_sync(0xffffffffu, inc.lo, 31));
+            }
+            if (lane == 0) out[s] = pick == UINT64_MAX ? last_nz : pick;
+            continue;
+        }
+        double base = before;
         for (uint64_t c = 0; c < len; c += 32) {
             const bool valid = c + lane < len;
             const double p = valid ? prob(amp(b0 + c + lane)) : 0.0;

@@ -1280,6 +1280,76 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
     std::vector<OpDev> ops;
     Payload pay;
     std::vector<int> rpos, tpos;
+    // Thread bits 0..4 are the lane bits, the others the warp bits.  A remap
+    // whose incoming register positions all sit at lane bits can hand each
+    // lane bit it frees to an outgoing register position: every warp's
+    // amplitudes then stay within the warp, and the kernels order the remap
+    // with a warp barrier instead of a block barrier.  Other remaps lay the
+    // thread bits out afresh: lane bits for the positions used soonest (so
+    // that later remaps stay within warps), subject to the lanes' shared-
+    // memory offsets reaching as many bank groups as the candidates allow.
+    const bool c64 = p.dtype == SV_C64;
+    auto bank_vec = [&](int pos, bool wide) {
+        int s = 1 << pos;
+        s = c64 ? (s ^ (((s >> 4) & 7) << 1)) : (s ^ ((s >> 3) & 7));  // the tile swizzle
+        return c64 ? (wide ? (s >> 1) & 7 : s & 15) : s & 7;
+    };
+    auto reduce = [](int* basis, int v) {  // GF(2) elimination: true when v is independent
+        for (int b = 3; b >= 0; --b)
+            if ((v >> b) & 1) {
+                if (!basis[b]) {
+                    basis[b] = v;
+                    return true;
+                }
+                v ^= basis[b];
+            }
+        return false;
+    };
+    auto lane_rank = [&](const std::vector<int>& lanes, bool wide) {
+        int basis[4] = {0, 0, 0, 0}, rank = 0;
+        for (int q : lanes) rank += reduce(basis, bank_vec(q, wide));
+        return rank;
+    };
+    // A layout whose lanes hold tile positions 0 and 1 (complex64 with
+    // position 0 at register bit 0: position 1; complex128: position 0) moves
+    // runs of at least 32 bytes per warp access, so the compiled kernels load
+    // a pass's first layout and store its last straight between registers and
+    // global memory.  The first and the last remap of a pass (edge) take the
+    // row positions 0..L-1 into the lanes first.
+    auto coalesced = [&](const std::vector<int>& rp, const std::vector<int>& tp) {
+        const int nl = std::min(5, tb);
+        auto lane = [&](int q) { return std::find(tp.begin(), tp.begin() + nl, q) != tp.begin() + nl; };
+        if (!c64) return lane(0);
+        return rp[0] == 0 ? lane(1) : lane(0) && lane(1);
+    };
+    auto fresh_threads = [&](int i, const std::vector<int>& regs, bool wide, bool edge) {
+        std::vector<int> cand;
+        for (int q = 0; q < m; ++q)
+            if (std::find(regs.begin(), regs.end(), q) == regs.end()) cand.push_back(q);
+        std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+            const int na = edge && a < P->L ? -1 : next_use(a, i + 1);
+            const int nb = edge && b < P->L ? -1 : next_use(b, i + 1);
+            return na < nb;
+        });
+        const int nl = std::min(5, tb);
+        const int target = std::min(lane_rank(cand, wide), c64 ? (wide ? 3 : 4) : 3);
+        int basis[4] = {0, 0, 0, 0}, rank = 0;
+        std::vector<int> lanes, rest;
+        for (int q : cand) {
+            int trial[4] = {basis[0], basis[1], basis[2], basis[3]};
+            const bool indep = reduce(trial, bank_vec(q, wide));
+            const int left = nl - (int)lanes.size();
+            if (left > 0 && (indep || left > target - rank)) {
+                lanes.push_back(q);
+                if (indep) std::copy(trial, trial + 4, basis), ++rank;
+            } else {
+                rest.push_back(q);
+            }
+        }
+        std::sort(lanes.begin(), lanes.end());
+        lanes.insert(lanes.end(), rest.begin(), rest.end());
+        return lanes;
+    };
     auto remap = [&](int i, const std::vector<int>& PQ) {
         std::vector<int> cand;
         for (int q = 0; q < m; ++q)
@@ -1301,14 +1371,41 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
             const auto z = std::find(slots.begin(), slots.end(), 0);
             if (z != slots.end()) std::iter_swap(slots.begin(), z);
         }
+        const bool wide = c64 && slots[0] == 0;
+        // the last remap when every later block finds its qubits in registers
+        bool last = true;
+        for (int j = i + 1; last && j < nops; ++j)
+            for (int q : used[j])
+                if (std::find(slots.begin(), slots.end(), q) == slots.end()) last = false;
+        std::vector<int> fresh = fresh_threads(i, slots, wide, rpos.empty() || last);
+        bool local = false;
+        if (!rpos.empty()) {
+            std::vector<int> in, out, tp = tpos;
+            for (int q : slots)
+                if (std::find(rpos.begin(), rpos.end(), q) == rpos.end()) in.push_back(q);
+            for (int q : rpos)
+                if (std::find(slots.begin(), slots.end(), q) == slots.end()) out.push_back(q);
+            local = true;
+            for (size_t j = 0; local && j < in.size(); ++j) {
+                const int t = (int)(std::find(tpos.begin(), tpos.end(), in[j]) - tpos.begin());
+                if (t >= 5) local = false;
+                else tp[t] = out[j];
+            }
+            const int nl = std::min(5, tb);
+            const std::vector<int> lanes_l(tp.begin(), tp.begin() + nl), lanes_f(fresh.begin(), fresh.begin() + nl);
+            if (local && lane_rank(lanes_l, wide) >= lane_rank(lanes_f, wide) &&
+                (!last || coalesced(slots, tp) || !coalesced(slots, fresh)))
+                fresh = tp;
+            else
+                local = false;
+        }
         rpos = slots;
-        tpos.clear();
-        for (int q = 0; q < m; ++q)
-            if (std::find(rpos.begin(), rpos.end(), q) == rpos.end()) tpos.push_back(q);
+        tpos = fresh;
         OpDev O;
         memset(&O, 0, sizeof(O));
         O.kind = OP_REMAP;
         O.k = r;
+        O.nrec = local ? 1 : 0;
         for (int b = 0; b < r; ++b) O.lq[b] = rpos[b];
         int tp[16];
         for (int t = 0; t < 16; ++t) tp[t] = t < (int)tpos.size() ? tpos[t] : -1;

@@ -819,6 +819,9 @@ __device__ __forceinline__ void fold_diags(const PassDev& P, const unsigned char
 // pass's write-back scale and puts the registers back into the tile.
 template <bool TC>
 struct InterpOps {
+    // tiles move through shared memory (the compiled passes may load their
+    // first layout and store their last straight to and from registers)
+    static constexpr bool kDirectLoad = false, kDirectStore = false;
     template <typename V>
     static __device__ __forceinline__ void issue(V* tile, const V* __restrict__ psi, uint64_t base,
                                                  const uint32_t* rowoff, int L, const PassDev&) {
@@ -849,7 +852,8 @@ struct InterpOps {
                 v[k].y *= sc;
             }
         }
-        __syncthreads();
+        // each warp writes back the positions it read last, which no other
+        // warp reads: the caller's barrier before the store orders the rest
         reg_write<V, RB>(v, tile, Lg);
     }
     template <typename V, typename R, int RB>
@@ -865,11 +869,17 @@ struct InterpOps {
         const OpDev& op = ops[oi];
         switch (op.kind) {
         case OP_REMAP:
+            // the write needs no barrier before it (a warp writes exactly the
+            // positions it read last); the read after it needs the other
+            // writers: the warp's own lanes when the remap keeps every warp's
+            // amplitudes within the warp (nrec = 1), else the whole block
             if (in_regs) {
-                __syncthreads();
                 reg_write<V, RB>(v, tile, Lg);
+                if (op.nrec == 1) __syncwarp();
+                else __syncthreads();
+            } else {
+                __syncthreads();
             }
-            __syncthreads();
             rpos = op.lq;
             tpos = (const int*)(stage + op.mat_off);
             reg_layout<V, RB>(Lg, rpos, tpos, tb);
@@ -982,36 +992,55 @@ __device__ __forceinline__ void rpass_body(typename CT<R>::V* __restrict__ psi, 
     const uint64_t ntiles = 1ull << (n - m);
     auto tile_base = [&](uint64_t t) { return table_base(tbase, t, L); };
     int cur = 0;
-    if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
-        Ops::template issue<V>(tiles[0], psi, tile_base(blockIdx.x), rowoff, L, P);
-        cp_async_commit();
+    if constexpr (!Ops::kDirectLoad) {
+        if (lay.nbuf == 2 && (uint64_t)blockIdx.x < ntiles) {
+            Ops::template issue<V>(tiles[0], psi, tile_base(blockIdx.x), rowoff, L, P);
+            cp_async_commit();
+        }
     }
     V v[1 << RB];
     RegLayout<V, RB> Lg;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint64_t base = tile_base(t);
-        const uint64_t tn = t + gridDim.x;
-        if (lay.nbuf == 2) {
-            if (tn < ntiles) {
-                Ops::template issue<V>(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L, P);
-                cp_async_commit();
-                cp_async_wait_group<1>();
+        if constexpr (Ops::kDirectLoad) {
+            // the first layout straight from global memory into registers;
+            // the barrier keeps this tile's shared-memory writes behind the
+            // previous tile's reads
+            Ops::template load<V>(v, psi, base, P);
+            __syncthreads();
+        } else {
+            const uint64_t tn = t + gridDim.x;
+            if (lay.nbuf == 2) {
+                if (tn < ntiles) {
+                    Ops::template issue<V>(tiles[cur ^ 1], psi, tile_base(tn), rowoff, L, P);
+                    cp_async_commit();
+                    cp_async_wait_group<1>();
+                } else {
+                    cp_async_wait_group<0>();
+                }
             } else {
+                Ops::template issue<V>(tiles[0], psi, base, rowoff, L, P);
+                cp_async_commit();
                 cp_async_wait_group<0>();
             }
-        } else {
-            Ops::template issue<V>(tiles[0], psi, base, rowoff, L, P);
-            cp_async_commit();
-            cp_async_wait_group<0>();
+            __syncthreads();
         }
-        __syncthreads();
         V* tile = tiles[cur];
-        if (nd) fold_diags<R>(P, stage, fold, dofs, t);
+        if (nd) {
+            fold_diags<R>(P, stage, fold, dofs, t);
+            if constexpr (Ops::kDirectLoad) __syncthreads();
+        }
         Ops::template tile<V, R, RB>(v, tile, P, stage, fold, Lg, sizeof(R) == 8 ? ttab : nullptr, T);
         Ops::template finish<V, R, RB>(v, tile, P, Lg, T);
-        __syncthreads();
-        Ops::template store<V>(tile, psi, base, rowoff, L);
-        __syncthreads();
+        if constexpr (Ops::kDirectStore) {
+            // the last layout straight from registers to global memory
+            Ops::template store_regs<V>(v, psi, base);
+            if constexpr (!Ops::kDirectLoad) __syncthreads();  // this tile's reads before the next copies land
+        } else {
+            __syncthreads();
+            Ops::template store<V>(tile, psi, base, rowoff, L);
+            __syncthreads();
+        }
         if (lay.nbuf == 2) cur ^= 1;
     }
     if (tcp) {
