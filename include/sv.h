@@ -91,9 +91,11 @@ typedef enum {
  * "default".  k_max: widest fused dense block, 1..5 (App. D.2: gate fusion =
  * 5); tile_m: qubits per shared-memory tile pass (c64 9..14, c128 9..13);
  * planner: sv_planner; record: store per-pass CUDA-event times for the cost
- * model (sv_pass_times); tensor: 1 = complex64 dense blocks of 3..5 qubits
- * run on the tensor cores (3xTF32, FP32 accumulation), -1 = CUDA cores only,
- * 0 = the library's default (CUDA cores; the cost-model planner may choose).
+ * model (sv_pass_times); tensor: 1 = complex64 dense blocks run on the
+ * tensor cores (register passes: 4..5 qubits, FP16 hi/lo splits, three
+ * products; shared-memory passes: 3..5 qubits, 3xTF32; FP32 accumulation),
+ * -1 = CUDA cores only, 0 = the library's default (CUDA cores; the
+ * cost-model planner may choose either).
  * pass_kernel: 0 = default (passes run register-resident where they can:
  * every thread keeps 2^5 (c64) / 2^4 (c128) amplitudes of the tile in
  * registers; tiles move by 16-byte cp.async copies), 1 = always the
@@ -231,6 +233,12 @@ int sv_apply_circuit(sv_handle h, const sv_gate *gates, size_t count, const sv_o
  * inside the apply that starts them). */
 int sv_jit_stats(uint64_t *compiled, uint64_t *failed, uint64_t *launched, double *compile_ms);
 int sv_jit_fills(uint64_t *filled);
+/* Of the passes launched on compiled kernels (process totals): those whose
+ * kernel loads the pass's first register layout straight from the state, and
+ * those that store its last layout straight back (no shared-memory copy),
+ * which it does when the layout's warp accesses cover runs of 32 bytes or
+ * more. */
+int sv_jit_direct(uint64_t *loads, uint64_t *stores);
 int sv_jit_wait(void);
 /* Host-only check of the pass compiler (no GPU needed): plan the circuit,
  * write the run-time kernel source of every register-resident pass (and of

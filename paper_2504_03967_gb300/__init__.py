@@ -360,7 +360,8 @@ def sv_jit_check(n, dtype, gates, arch=103, **opts):
 
 
 def sv_jit_stats():
-    """(kernels compiled, compiles failed, passes launched on them, compile ms)."""
+    """Kernels compiled, compiles failed, passes launched on them, compile ms,
+    passes built from a deferred basis state, passes with direct loads/stores."""
     L = lib()
     f = L.sv_jit_stats
     f.argtypes = [ctypes.c_void_p] * 4
@@ -373,8 +374,13 @@ def sv_jit_stats():
     g.argtypes = [ctypes.c_void_p]
     g.restype = ctypes.c_int
     _check(g(ctypes.byref(fi)))
+    dl, ds = ctypes.c_uint64(), ctypes.c_uint64()
+    d = L.sv_jit_direct
+    d.argtypes = [ctypes.c_void_p] * 2
+    d.restype = ctypes.c_int
+    _check(d(ctypes.byref(dl), ctypes.byref(ds)))
     return {"compiled": c.value, "failed": fl.value, "launched": ln.value, "compile_ms": ms.value,
-            "filled": fi.value}
+            "filled": fi.value, "direct_load": dl.value, "direct_store": ds.value}
 
 
 def sv_jit_wait():

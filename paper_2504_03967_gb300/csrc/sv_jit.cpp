@@ -457,12 +457,13 @@ struct Entry {
     int state = JIT_NEW;
     CUfunction fn = nullptr;
     int attr_bytes = 0;
-    bool direct_load = false;  // the kernel loads its first layout straight into registers (one tile buffer)
+    bool direct_load = false;   // the kernel loads its first layout straight into registers (one tile buffer)
+    bool direct_store = false;  // and stores its last layout straight from registers
 };
 
 std::mutex g_mu;
 std::unordered_map<std::string, Entry> g_cache;
-uint64_t g_compiled = 0, g_failed = 0, g_launched = 0, g_filled = 0;
+uint64_t g_compiled = 0, g_failed = 0, g_launched = 0, g_filled = 0, g_direct_ld = 0, g_direct_st = 0;
 double g_compile_ms = 0.0;
 std::string g_last_log;
 
@@ -523,6 +524,7 @@ void compile_all(const std::vector<std::string>& srcs) {
         Entry& e = g_cache[srcs[i]];
         e.fn = fns[i];
         e.direct_load = srcs[i].find("kDirectLoad = true") != std::string::npos;
+        e.direct_store = srcs[i].find("kDirectStore = true") != std::string::npos;
         e.state = fns[i] ? JIT_READY : JIT_FAILED;
         (fns[i] ? g_compiled : g_failed)++;
         if (!logs[i].empty()) g_last_log = logs[i];
@@ -626,6 +628,8 @@ cudaError_t jit_launch(sv_state* h, void* entry, const void* blob_dev, const Pla
     {
         std::lock_guard<std::mutex> lk(g_mu);
         ++g_launched;
+        g_direct_ld += e.direct_load;
+        g_direct_st += e.direct_store;
     }
     *used = true;
     return cudaSuccess;
@@ -655,6 +659,13 @@ extern "C" int sv_jit_stats(uint64_t* compiled, uint64_t* failed, uint64_t* laun
     if (failed) *failed = g_failed;
     if (launched) *launched = g_launched;
     if (compile_ms) *compile_ms = g_compile_ms;
+    return SV_OK;
+}
+
+extern "C" int sv_jit_direct(uint64_t* loads, uint64_t* stores) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (loads) *loads = g_direct_ld;
+    if (stores) *stores = g_direct_st;
     return SV_OK;
 }
 
