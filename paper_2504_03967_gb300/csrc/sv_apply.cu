@@ -1540,6 +1540,9 @@ static cudaError_t rpass_tma_t(sv_state* h, const void* blob_dev, const PlanBlob
     RingLayout lay;
     int ctas = 1;
     EncodeTiledFn enc = encode_fn();
+    // the tensor map's rows are 128 bytes: passes with other row widths stay
+    // on the copy-based kernel
+    if (pdh->L != (h->dtype == SV_C64 ? 4 : 3)) return cudaSuccess;
     if (!enc || !ring_layout(h->dtype, *pdh, &lay, &ctas)) return cudaSuccess;
     const int threads = 1 << (pdh->m - RB);
     if (threads > MAXT || ((uintptr_t)h->amps & 15)) return cudaSuccess;

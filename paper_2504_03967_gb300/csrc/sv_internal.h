@@ -55,6 +55,16 @@ int canonicalise(int n, const sv_gate* g, size_t count, std::vector<CGate>* out,
 // qubit less and runs wider blocks from their dense matrix.
 inline int max_gates_k(int dtype) { return dtype == SV_C64 ? 5 : 4; }
 inline int smem_gates_max_k(int dtype) { return dtype == SV_C64 ? 4 : 3; }
+// Tile rows: qubits 0..L-1 are always tile qubits, so a tile is made of rows
+// of 2^L contiguous amplitudes, 128 bytes (the TMA-fed kernel's tensor-map
+// row).  256-byte rows copy faster when the other tile qubits are far apart
+// (in-place tile copies at n=30: 0.94 of a plain copy against 0.73), but a
+// 60-layer random circuit at n=30 then needed 11% more 13-qubit passes for 9%
+// faster passes, and the QFT's passes slowed: 128 bytes it is.
+inline int row_bits(int dtype, int pass_kernel) {
+    (void)pass_kernel;
+    return dtype == SV_C64 ? 4 : 3;
+}
 
 struct DiagForm {
     // phase(x) = c + sum_q a[q] x_q + sum_{p<q} b[p*n+q] x_p x_q  (radians)

@@ -615,7 +615,7 @@ PlanOptions resolve_options(int n, int dtype, const sv_options* opt) {
 void greedy_pass(int n, int dtype, const std::vector<CGate>& gates, const std::vector<Mux>& muxes,
                  const PlanOptions& po, const std::vector<int>& remaining, HostPass* pass_out,
                  std::vector<int>* deferred_out, bool form_matrices) {
-    const int L = std::min(dtype == SV_C64 ? 4 : 3, n);
+    const int L = std::min(row_bits(dtype, po.pass_kernel), n);
     // the tile holds the row bits plus room for any two-qubit gate
     const int m = std::max(std::min(n, L + 2), std::min(po.tile_m, n));
     const int kmax = std::min(po.k_max, m);
