@@ -1354,7 +1354,18 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
         std::vector<int> cand;
         for (int q = 0; q < m; ++q)
             if (std::find(PQ.begin(), PQ.end(), q) == PQ.end()) cand.push_back(q);
+        // when the block's own qubits can come in from lane bits, the other
+        // register slots are filled from registers and lanes only, so that a
+        // filler at a warp bit does not turn the remap into a block-wide one
+        const int nl0 = std::min(5, tb);
+        auto at_warp = [&](int q) {
+            const auto it = std::find(tpos.begin(), tpos.end(), q);
+            return it != tpos.end() && it - tpos.begin() >= nl0;
+        };
+        bool pq_local = !rpos.empty();
+        for (int q : PQ) pq_local = pq_local && !at_warp(q);
         std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+            if (pq_local && at_warp(a) != at_warp(b)) return !at_warp(a);
             const int na = next_use(a, i + 1), nb = next_use(b, i + 1);
             if (na != nb) return na < nb;
             const bool ia = std::find(rpos.begin(), rpos.end(), a) != rpos.end();
