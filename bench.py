@@ -94,6 +94,10 @@ def workload(name):
         n = int(name[6:])
         g = W.random_u3_cx(n, 60, W.SEED[4])
         return n, g, 0, "random U3+CX n=%d, 60 layers (%d gates) from |0>" % (n, len(g))
+    if name.startswith("cxblocks"):
+        # cxblocks<n>: the random CX-block circuits of App. D.1 Alg. 1 (Ry, Rz on both qubits, then CX), 60 n blocks
+        n = int(name[8:])
+        return n, W.random_cx_blocks(n, 60 * n, W.SEED[4]), 0, "random CX blocks n=%d (%d blocks) from |0>" % (n, 60 * n)
     if name.startswith("qcrank"):
         # qcrank<a>x<d>: one QCrank image circuit (2^a addresses, d data qubits)
         a, d = (int(v) for v in name[6:].split("x"))
