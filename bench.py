@@ -58,8 +58,9 @@ UNIT = "amp_updates/s"
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
                    "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
-TRAFFIC = {"sha256": "bb21599293b90f469fcf304fe7c2c9a206f3ea793dcbb915c067ae8695d4594f",
-           "bytes_per_amp": 12.9808, "profile": "profiles/sv_jit_pass_qft26_c64_k5m13.md (n=26 capture, scaled to 2^n)"}
+TRAFFIC = {"sha256": "7b13a99f5b279e198b01ac12b5f67d77c6bf2bdf36f24179f5c2a4b16bf2a225",
+           "bytes_per_amp": 15.402,
+           "profile": "profiles/traffic_random26_c64_bench.md (the 85 tile passes of one step at n=26, scaled to 2^n)"}
 
 
 def sources_sha():

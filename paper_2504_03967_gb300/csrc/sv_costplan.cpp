@@ -97,7 +97,7 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const std::
             int m = dtype == SV_C64 ? ms_c64[mi] : ms_c128[mi];
             if (m > n) m = n;
             for (int tensor = -1; tensor <= 0; ++tensor)
-                for (int pk = 0; pk <= 1; ++pk) {
+                for (int pk = 0; pk <= 0; ++pk) {  // register-resident passes: the kernels the model is trained on
                     if (tensor == 0 && (dtype != SV_C64 || k < kMinTcK)) continue;
                     PlanOptions po = base;
                     po.k_max = k;
