@@ -93,3 +93,34 @@ def test_jit_auto_compiles_on_repeat():
     U.assert_close(U.run_gpu(n, g2, S.C64, psi0=psi0), U.run_oracle(n, g2, psi0), S.C64, "other angles")
     s4 = S.sv_jit_stats()
     assert s4["compiled"] == s3["compiled"] and s4["launched"] > s3["launched"]
+
+
+@pytest.mark.parametrize("tile_m", [12, 13])
+def test_direct_copies_and_warp_remaps_vs_oracle(tile_m):
+    """Compiled passes that load their first register layout straight from
+    the state and store their last straight back (no shared-memory copy), and
+    plans whose remaps stay within warps (ordered by warp barriers only), give
+    the oracle's state: a random U3+CX circuit whose plan has both, from a
+    random state and from the deferred |0...0> (its first pass builds the tile
+    in registers)."""
+    n = 20
+    g = W.random_u3_cx(n, 10, 17 + tile_m)
+    info = S.sv_plan_circuit(n, S.C64, g, k_max=5, tile_m=tile_m, tensor=-1)
+    assert info["warp_remaps"] > 0 and info["warp_remaps"] < info["remaps"]
+    psi0 = W.random_state(n, 44)
+    before = S.sv_jit_stats()
+    got = U.run_gpu(n, g, S.C64, psi0=psi0, jit=1, k_max=5, tile_m=tile_m, tensor=-1)
+    after = S.sv_jit_stats()
+    assert after["failed"] == before["failed"]
+    assert after["direct_load"] > before["direct_load"] and after["direct_store"] > before["direct_store"]
+    U.assert_close(got, U.run_oracle(n, g, psi0), S.C64, "direct copies m=%d" % tile_m)
+    h = S.sv_alloc(n, S.C64)
+    try:
+        S.sv_init_basis(h, 0)
+        f0 = S.sv_jit_stats()["filled"]
+        S.sv_apply_circuit(h, g, jit=1, k_max=5, tile_m=tile_m, tensor=-1)
+        got0 = S.sv_store_state(h).astype(np.complex128)
+        assert S.sv_jit_stats()["filled"] > f0
+    finally:
+        S.sv_free(h)
+    U.assert_close(got0, U.run_oracle(n, g), S.C64, "direct copies from |0> m=%d" % tile_m)
