@@ -98,7 +98,9 @@ typedef enum {
  * cost-model planner may choose either).
  * pass_kernel: 0 = default (passes run register-resident where they can:
  * every thread keeps 2^5 (c64) / 2^4 (c128) amplitudes of the tile in
- * registers; tiles move by 16-byte cp.async copies), 1 = always the
+ * registers; tiles move by 16-byte cp.async copies, or, in compiled passes
+ * whose first / last register layout has coalesced warp accesses, straight
+ * between the state and registers), 1 = always the
  * shared-memory pass kernel, 2 = register-resident passes whose tiles move by
  * TMA tensor copies through a ring of tile slots (one CTA per SM).  Results
  * agree within rounding whichever kernel runs.  relabel: 1 = SWAP gates

@@ -915,6 +915,12 @@ struct InterpOps {
     }
 };
 
+// One register-resident pass: each CTA walks tiles t = blockIdx.x, +gridDim.x,
+// ...  Per tile: the tile arrives (16-byte cp.async copies into shared memory,
+// double-buffered when the layout allows; or, for Ops::kDirectLoad, straight
+// into registers in the first layout), the op list runs on the registers with
+// remaps through shared memory, and the tile leaves (through shared memory,
+// or for Ops::kDirectStore straight from registers in the last layout).
 // MAXT/MINB: launch bounds of the instance (up to 128 threads: registers are
 // not capped below 255, so the 2^RB amplitudes and the op state never spill;
 // 256 and 512 threads: 128 registers).
