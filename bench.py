@@ -50,26 +50,35 @@ UNIT = "amp_updates/s"
 
 
 # DRAM traffic of the tile pass per amplitude per launch, from the ncu capture
-# summarised in profiles/ (QFT n=26 complex64, k_max 5, tile 13, the 3 passes
-# of one step on the run-time compiled kernel; dram__bytes_read.sum +
-# dram__bytes_write.sum), valid only for the kernel, compiler and planner
-# sources it was taken with (SHA-256 over the files below); a changed kernel
-# reports traffic null until it is captured again.
+# summarised in profiles/ (the bench's random U3+CX family at n=26 complex64,
+# the 85 passes of one step on the run-time compiled kernels;
+# dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel,
+# compiler and planner sources it was taken with (SHA-256 over the files
+# below); a changed kernel reports traffic null until it is captured again.
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
                    "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
-TRAFFIC = {"sha256": "7b13a99f5b279e198b01ac12b5f67d77c6bf2bdf36f24179f5c2a4b16bf2a225",
+TRAFFIC = {"sha256": "b0933a6d476206caec58eb875d54d7998ac7a0b49a398b75d3d7e688eea45e8e",
            "bytes_per_amp": 15.402,
            "profile": "profiles/traffic_random26_c64_bench.md (the 85 tile passes of one step at n=26, scaled to 2^n)"}
 
 
-def sources_sha():
+def sources_sha(read=None):
+    """SHA-256 over TRAFFIC_SOURCES without their whole-line comments and
+    blank lines (a comment edit does not void a capture)."""
     import hashlib
 
     hsh = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            hsh.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        for line in text.splitlines():
+            t = line.strip()
+            if t and not t.startswith(b"//"):
+                hsh.update(line + b"\n")
     return hsh.hexdigest()
 
 
