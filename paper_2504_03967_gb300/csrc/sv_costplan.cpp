@@ -96,20 +96,18 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const std::
         for (int mi = 0; mi < 3; ++mi) {
             int m = dtype == SV_C64 ? ms_c64[mi] : ms_c128[mi];
             if (m > n) m = n;
-            for (int tensor = -1; tensor <= 0; ++tensor)
-                for (int pk = 0; pk <= 0; ++pk) {  // register-resident passes: the kernels the model is trained on
-                    if (tensor == 0 && (dtype != SV_C64 || k < kMinTcK)) continue;
-                    PlanOptions po = base;
-                    po.k_max = k;
-                    po.tile_m = m;
-                    po.tensor = tensor;
-                    po.pass_kernel = pk;
-                    bool dup = false;
-                    for (const PlanOptions& c : cands)
-                        dup |= c.k_max == po.k_max && c.tile_m == po.tile_m && c.tensor == po.tensor &&
-                               c.pass_kernel == po.pass_kernel;
-                    if (!dup) cands.push_back(po);
-                }
+            for (int tensor = -1; tensor <= 0; ++tensor) {
+                if (tensor == 0 && (dtype != SV_C64 || k < kMinTcK)) continue;
+                PlanOptions po = base;
+                po.k_max = k;
+                po.tile_m = m;
+                po.tensor = tensor;
+                po.pass_kernel = 0;  // register-resident passes: the kernels the model is trained on
+                bool dup = false;
+                for (const PlanOptions& c : cands)
+                    dup |= c.k_max == po.k_max && c.tile_m == po.tile_m && c.tensor == po.tensor;
+                if (!dup) cands.push_back(po);
+            }
         }
     std::vector<float> feat;
     std::vector<int> owner;
