@@ -236,3 +236,18 @@ def test_tensor_core_plans_reproduce_the_circuit(case, tile_m):
     psi0 /= np.linalg.norm(psi0)
     got = _apply_ops(n, ops, psi0)
     assert np.abs(got - oracle.apply_circuit(n, g, psi0)).max() < 1e-12
+
+
+def test_register_layouts_keep_some_remaps_within_warps():
+    """Host plan summary of the register passes' layouts (no GPU): on random
+    U3+CX circuits some remaps keep every warp's amplitudes within the warp
+    (ordered by warp barriers), never all of them (a pass's first layout and
+    blocks whose qubits sit at warp bits need the block), and the CUDA-core
+    default plans every pass register-resident."""
+    for n, m in ((20, 12), (22, 13), (24, 13)):
+        g = W.random_u3_cx(n, 12, 60 + n)
+        info = S.sv_plan_circuit(n, S.C64, g, k_max=5, tile_m=m)
+        assert info["reg_passes"] == info["passes"]
+        assert info["tc_ops"] == 0  # CUDA cores by default
+        assert info["remaps"] >= info["passes"]  # every register pass starts with one
+        assert 0 < info["warp_remaps"] <= info["remaps"] - info["passes"]
