@@ -1410,6 +1410,23 @@ bool reg_region(const Plan& p, const HostPass& hp, PassDev* P, const int* loc, s
             else
                 local = false;
         }
+        // Shared-memory accesses are served a quarter warp (16-byte: lanes
+        // 0..7) or a half warp (8-byte: lanes 0..15) at a time: the first
+        // three / four lane bits take positions whose bank vectors are
+        // independent where the lanes hold such a set (lane bits may be
+        // permuted freely: the remap stays within warps either way)
+        {
+            const int nl = std::min(5, tb), q = c64 && !wide ? 4 : 3;
+            std::vector<int> lanes(fresh.begin(), fresh.begin() + nl), first, later;
+            std::sort(lanes.begin(), lanes.end());
+            int basis[4] = {0, 0, 0, 0};
+            for (int pos : lanes) {
+                if ((int)first.size() < q && reduce(basis, bank_vec(pos, wide))) first.push_back(pos);
+                else later.push_back(pos);
+            }
+            first.insert(first.end(), later.begin(), later.end());
+            std::copy(first.begin(), first.end(), fresh.begin());
+        }
         rpos = slots;
         tpos = fresh;
         OpDev O;
