@@ -58,8 +58,8 @@ UNIT = "amp_updates/s"
 TRAFFIC_SOURCES = ["paper_2504_03967_gb300/csrc/sv_apply.cu", "paper_2504_03967_gb300/csrc/sv_plan.cpp",
                    "paper_2504_03967_gb300/csrc/sv_internal.h", "paper_2504_03967_gb300/csrc/sv_dev.h",
                    "paper_2504_03967_gb300/csrc/sv_rpass.cuh", "paper_2504_03967_gb300/csrc/sv_jit.cpp"]
-TRAFFIC = {"sha256": "b0933a6d476206caec58eb875d54d7998ac7a0b49a398b75d3d7e688eea45e8e",
-           "bytes_per_amp": 15.402,
+TRAFFIC = {"sha256": "4bd6035baccc91a93d8298223b5a143c53015278da0dbc1a6127ae6bba04ed82",
+           "bytes_per_amp": 15.398,
            "profile": "profiles/traffic_random26_c64_bench.md (the 85 tile passes of one step at n=26, scaled to 2^n)"}
 
 
