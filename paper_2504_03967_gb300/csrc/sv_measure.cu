@@ -499,35 +499,40 @@ __global__ void __launch_bounds__(256) k_sample(const V* __restrict__ psi, int n
         // running CDF, and the first lane whose CDF exceeds t (and whose
         // probability is not zero) is the outcome.  complex64: |a|^2 as an
         // exact float pair and the scan in double-float (about 48 bits; no
-        // FP64 instruction in the loop); complex128: FP64.
+        // FP64 instruction in the loop) when the state's total lies well
+        // inside FP32's range; complex128, or a far from normalised state:
+        // FP64.
         uint64_t pick = UINT64_MAX, last_nz = b0;
         if constexpr (sizeof(V) == 8) {
-            const FF tf = ff_of(t);
-            FF base = ff_of(before);
-            for (uint64_t c = 0; c < len; c += 32) {
-                const bool valid = c + lane < len;
-                FF p = {0.f, 0.f};
-                if (valid) p = ff_prob(amp(b0 + c + lane));
-                FF inc = p;
+            if (S > 1e-20 && S < 1e20) {
+                const FF tf = ff_of(t);
+                FF base = ff_of(before);
+                for (uint64_t c = 0; c < len; c += 32) {
+                    const bool valid = c + lane < len;
+                    FF p = {0.f, 0.f};
+                    if (valid) p = ff_prob(amp(b0 + c + lane));
+                    FF inc = p;
 #pragma unroll
-                for (int sh = 1; sh < 32; sh <<= 1) {
-                    const float h = __shfl_up_sync(0xffffffffu, inc.hi, sh), l = __shfl_up_sync(0xffffffffu, inc.lo, sh);
-                    if (lane >= sh) ff_add(inc, h, l);
+                    for (int sh = 1; sh < 32; sh <<= 1) {
+                        const float h = __shfl_up_sync(0xffffffffu, inc.hi, sh);
+                        const float l = __shfl_up_sync(0xffffffffu, inc.lo, sh);
+                        if (lane >= sh) ff_add(inc, h, l);
+                    }
+                    FF cum = base;
+                    ff_add(cum, inc.hi, inc.lo);
+                    const float above = (cum.hi - tf.hi) + (cum.lo - tf.lo);  // sign of cum - t
+                    const unsigned hit = __ballot_sync(0xffffffffu, valid && p.hi > 0.f && above > 0.f);
+                    if (hit) {
+                        pick = b0 + c + (uint64_t)(__ffs(hit) - 1);
+                        break;
+                    }
+                    const unsigned nz = __ballot_sync(0xffffffffu, p.hi > 0.f);
+                    if (nz) last_nz = b0 + c + (uint64_t)(31 - __clz(nz));
+                    ff_add(base, __shfl_sync(0xffffffffu, inc.hi, 31), __shfl_sync(0xffffffffu, inc.lo, 31));
                 }
-                FF cum = base;
-                ff_add(cum, inc.hi, inc.lo);
-                const float above = (cum.hi - tf.hi) + (cum.lo - tf.lo);  // sign of cum - t
-                const unsigned hit = __ballot_sync(0xffffffffu, valid && p.hi > 0.f && above > 0.f);
-                if (hit) {
-                    pick = b0 + c + (uint64_t)(__ffs(hit) - 1);
-                    break;
-                }
-                const unsigned nz = __ballot_sync(0xffffffffu, p.hi > 0.f);
-                if (nz) last_nz = b0 + c + (uint64_t)(31 - __clz(nz));
-                ff_add(base, __shfl_sync(0xffffffffu, inc.hi, 31), __shfl_sync(0xffffffffu, inc.lo, 31));
+                if (lane == 0) out[s] = pick == UINT64_MAX ? last_nz : pick;
+                continue;
             }
-            if (lane == 0) out[s] = pick == UINT64_MAX ? last_nz : pick;
-            continue;
         }
         double base = before;
         for (uint64_t c = 0; c < len; c += 32) {
