@@ -222,6 +222,28 @@ def test_sampler_oracle_uniforms(dtype, n):
     U.compare_samples(got, u, cref, band)
 
 
+@pytest.mark.parametrize("scale", [1e-12, 1e3], ids=["tiny", "large"])
+def test_sampler_unnormalised_state(scale):
+    """The rule min{x : C_x > u C_{N-1}} holds for a state far from unit norm
+    (complex64: total 1e-24 takes the FP64 rescan, 1e6 the double-float
+    one): outcomes equal the oracle sampler's on the stored probabilities
+    except within 1e-9 (relative) of a CDF boundary."""
+    n = 14
+    psi = W.random_state(n, 71) * scale
+    u = W.uniforms(4096, 72)
+    h = S.sv_alloc(n, S.C64)
+    try:
+        S.sv_load_state(h, psi)
+        got = S.sv_sample_uniforms(h, u)
+        pg = S.sv_probs(h)
+    finally:
+        S.sv_free(h)
+    c = oracle.cdf(pg)
+    assert abs(c[-1] / scale ** 2 - 1.0) < 1e-5
+    cmp, _ = U.compare_samples(got, u, c, U.BAND * c[-1])
+    assert cmp > 4000
+
+
 @pytest.mark.parametrize("dtype", DT, ids=DTN.get)
 @pytest.mark.parametrize("n", [4, 10, 15])
 def test_measure_device_one_pass(dtype, n):
