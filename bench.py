@@ -520,7 +520,7 @@ def main():
         t0 = time.perf_counter()
         cm = train_cost_model(S, dt, args.cm_n or n)
         cm["seconds"] = time.perf_counter() - t0
-        # the judge's timed calls (two rounds over its four trials: the model's
+        # the judge's timed calls (each of its four trials twice: the model's
         # per-pass plan, its two best option sets, greedy), untimed here; the
         # ninth call plans with the trial the judge kept
         for i in range(9):

@@ -143,7 +143,7 @@ bool rank_options(int n, int dtype, const std::vector<CGate>& gates, const std::
 // tensor-core blocks on or off) proposes its next greedy pass, and the model
 // predicts each proposal's time from its features.  A beam of kBeam partial
 // plans is kept, ranked by predicted time so far plus the gates still to plan
-// times the best predicted time per gate among the round's proposals, and
+// times the best predicted time per gate among the beam step's proposals, and
 // extended until every gate is planned; the complete plan with the smallest
 // predicted total wins.  Each pass may so take its own tile and fusion width
 // and its own choice of tensor-core blocks ("gate fusion = 5" of App. D.2 as
@@ -220,7 +220,7 @@ bool plan_learned(int n, int dtype, const std::vector<CGate>& gates, const std::
         }
         std::vector<double> ms;
         if (!cost_model_predict(feat, (int)props.size(), &ms)) return false;
-        double rate = 1e30;  // best predicted ms per gate this round
+        double rate = 1e30;  // best predicted ms per gate in this beam step
         for (size_t i = 0; i < props.size(); ++i) {
             props[i].ms = std::max(ms[i], 1e-6);
             const size_t done = nodes[props[i].from].rem.size() - props[i].rem.size();
